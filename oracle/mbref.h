@@ -1,0 +1,92 @@
+/*
+ * mbref — plain FP64 CPU oracle of the multiblob inertial-coupling (ICM) time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or calls
+ * this code; only the tests, the package smoke check and the benchmark's CPU-baseline
+ * leg do.  It shares no source with the CUDA path.
+ *
+ * Every routine is written for clarity, not speed: fixed loop order, IEEE double,
+ * no fast-math, no contraction (built with -ffp-contract=off).
+ *
+ * Paper: Vazquez-Quesada, Balboa Usabiaga, Delgado-Buscalioni, "A multiblob approach to
+ * colloidal hydrodynamics with inherent lubrication" (arXiv:1407.5600).
+ *
+ * Conventions (shared with the C ABI only by specification, not by code):
+ *   - Periodic box of nx*ny*nz cubic cells of side h; L_b = n_b*h.
+ *   - Staggered (MAC) velocity: component a lives on the faces normal to a.
+ *     v_x[k][j][i] sits at (i*h, (j+1/2)h, (k+1/2)h); v_y at ((i+1/2)h, j*h, (k+1/2)h);
+ *     v_z at ((i+1/2)h, (j+1/2)h, k*h).
+ *   - Grids are 3 component arrays stored one after another, each [nz][ny][nx], x fastest.
+ *   - Blob arrays are [n][3] (x, y, z), row-major.
+ */
+#ifndef MBREF_H
+#define MBREF_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int nx, ny, nz;
+    double h;        /* mesh size */
+    double rho;      /* fluid density rho_f */
+    double eta;      /* shear viscosity */
+    double dt;       /* time step */
+    int mean_mode;   /* 0: the k=0 (mean) mode evolves with the net force; 1: it is held at 0 */
+} mbref_grid;
+
+/* Three-point kernel Phi of Eq. (delta): the Roma-Peskin-Berger function. */
+double mbref_phi(double r);
+
+/* f = S F : spreading of blob forces onto the MAC grid (f_i = delta_h(r - q_i) F_i, Sec. 2). */
+int mbref_spread(const mbref_grid* g, int64_t n, const double* q, const double* F, double* f);
+
+/* u = J v : interpolation of the MAC velocity at the blobs (Eq. ju). */
+int mbref_interp(const mbref_grid* g, int64_t n, const double* q, const double* v, double* u);
+
+/* Unnormalised 3-D DFT  X(k) = sum_j x_j exp(-/+ 2 pi i k.j/n), in place on (re, im),
+ * arrays [nz][ny][nx]; inverse != 0 selects the + sign (no 1/N factor). */
+int mbref_dft3(int nx, int ny, int nz, double* re, double* im, int inverse);
+
+/* One Crank-Nicolson + projection update of the fluid (Eq. vf with sigma = -eta E, m_e = 0):
+ *   (rho/dt - eta/2 L) v_out = P [ (rho/dt + eta/2 L) v + f + f_body ].
+ * body = {f0, axis, wave_dir, j} (force density f0 sin(2 pi j x_wave / L_wave) along axis)
+ * or NULL. */
+int mbref_fluid_update(const mbref_grid* g, const double* v, const double* f,
+                       const double* body, double* v_out);
+
+/* Steady Stokes solution v = P (-eta L)^-1 f with the mean mode set to zero. */
+int mbref_stokes_solve(const mbref_grid* g, const double* f, double* v);
+
+/* F += harmonic bond forces, F_i = -k (|r_ij| - r0) r_ij/|r_ij| (minimum image). */
+int mbref_bond_forces(const mbref_grid* g, int64_t n, const double* q, int64_t nbonds,
+                      const int32_t* bonds, const double* rest, double k, double* F);
+
+/* F += soft blob-blob repulsion k_rep (r_cut - r) r_hat for r < r_cut, between blobs of
+ * different particles, by brute force over all pairs. */
+int mbref_pair_forces(const mbref_grid* g, int64_t n, const double* q, const int32_t* pid,
+                      double k_rep, double r_cut, double* F);
+
+/* Same repulsion, evaluated only for the m blobs listed in idx (F is [m][3], overwritten). */
+int mbref_pair_forces_subset(const mbref_grid* g, int64_t n, const double* q,
+                             const int32_t* pid, double k_rep, double r_cut, int64_t m,
+                             const int64_t* idx, double* F);
+
+/* nsteps of the neutrally buoyant ICM step (midpoint blob update, CN fluid update),
+ * updating q (wrapped into [0, L)) and v in place.  ext ([n][3]) and body may be NULL. */
+int mbref_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
+               const int32_t* pid, int64_t nbonds, const int32_t* bonds, const double* rest,
+               double k_spring, double k_rep, double r_cut, const double* ext,
+               const double* body);
+
+/* Particle translational velocity U0 = mean of u_i (Sec. 2) and angular velocity
+ * Omega = I0^-1 sum_i s_i x (u_i - U0) (Eqs. torque, miner0), for np particles whose
+ * blobs carry particle ids 0..np-1. */
+int mbref_particle_velocities(const mbref_grid* g, int64_t n, const double* q, const double* u,
+                              const int32_t* pid, int64_t np, double* U, double* Omega);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
