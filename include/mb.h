@@ -1,0 +1,169 @@
+/*
+ * mb.h — C ABI of the GB300 multiblob inertial-coupling library (libmb.so).
+ *
+ * The library advances neutrally buoyant multiblob colloids coupled to an incompressible
+ * fluid on a periodic staggered (MAC) grid, following Vazquez-Quesada, Balboa Usabiaga and
+ * Delgado-Buscalioni, "A multiblob approach to colloidal hydrodynamics with inherent
+ * lubrication" (arXiv:1407.5600).  Section and equation labels below are that paper's.
+ *
+ * Common rules for every entry point
+ * ----------------------------------
+ *  - Status: every call returns an mb_status and never aborts the process.  On any error
+ *    the context is left as it was before the call and mb_last_error() describes the error.
+ *  - Streams: all device work is enqueued on the CUDA stream given to mb_create_grid and is
+ *    ordered with respect to other work on that stream.  A call that writes into HOST memory
+ *    synchronises that stream before it returns.
+ *  - Pointers: array arguments may be device pointers (on the context's device) or host
+ *    pointers (pageable or pinned); the library finds out which with
+ *    cudaPointerGetAttributes and stages host arrays through its own device buffers.  The
+ *    caller owns every array it passes; the library never keeps a caller pointer after the
+ *    call returns.
+ *  - Layouts: blob arrays are [n][3] row-major FP64 (x, y, z).  A velocity or force grid of
+ *    one box is 3 component arrays stored one after another, each [nz][ny][nx] with x
+ *    fastest, in the context's grid precision (float for precision 0, double for 1); a
+ *    batched grid is [batch] such boxes.  Component a lives on the faces normal to a:
+ *    v_x[k][j][i] at (i h, (j+1/2) h, (k+1/2) h), v_y at ((i+1/2) h, j h, (k+1/2) h),
+ *    v_z at ((i+1/2) h, (j+1/2) h, k h).  Blob positions are taken modulo the box.
+ *  - Kernel: every blob-grid coupling uses delta_h(r) = h^-3 prod_a Phi(r_a / h), Eq. (delta),
+ *    with Phi the three-point Peskin function of Roma, Peskin and Berger.
+ */
+#ifndef MB_H
+#define MB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mb_ctx mb_ctx;
+
+typedef enum {
+    MB_OK = 0,
+    MB_EINVAL = 1,   /* an argument is out of range or inconsistent */
+    MB_ENOMEM = 2,   /* a device or host allocation failed */
+    MB_ECUDA = 3,    /* a CUDA call or kernel launch failed */
+    MB_ESTATE = 4,   /* the call is not valid in the context's current state */
+    MB_ETIMEOUT = 5  /* a bounded device-side wait gave up */
+} mb_status;
+
+/* Grid and fluid description.
+ *   nx, ny, nz   cells per box side: powers of two in [4, 128].
+ *   batch        number of independent periodic boxes B >= 1 sharing the same geometry.
+ *   h            mesh size (> 0); box side L_a = n_a h.
+ *   rho, eta     fluid density and shear viscosity (> 0).
+ *   dt           time step (> 0).
+ *   precision    0: grid, spreading, interpolation and FFT in FP32 (blob positions, forces and
+ *                the mean fluid momentum stay FP64); 1: everything FP64.
+ *   deterministic  reserved for a bitwise-reproducible mode; must be 0 or 1 (1 currently
+ *                gives the same kernels as 0).
+ *   advection    must be 0: the convective term rho v v of Eq. (vf) is not provided (every
+ *                measurement in the paper is at vanishing Reynolds number).
+ *   mean_mode    0: the k = 0 fluid mode carries the net momentum, rho L^3 d(mean v)/dt =
+ *                sum of blob forces (+ mean body force); 1: the k = 0 mode is held at zero
+ *                (the frame of Hasimoto's periodic drag, Eq. rhinf).
+ *   kT           must be 0 (no fluctuating stress).
+ *   seed         reserved for the fluctuating stress. */
+typedef struct {
+    int nx, ny, nz;
+    int batch;
+    double h, rho, eta, dt;
+    int precision;
+    int deterministic;
+    int advection;
+    int mean_mode;
+    double kT;
+    uint64_t seed;
+} mb_grid_desc;
+
+/* Creates a context: validates *desc, allocates every grid buffer on the current CUDA
+ * device and zeroes the fluid velocity of all boxes.  cuda_stream is a cudaStream_t (NULL =
+ * the legacy default stream).  *out receives the context, or NULL on error.  Problem
+ * statement: Sec. 3, Eq. (vf) on a periodic box. */
+mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** out);
+
+/* Releases every buffer of ctx after synchronising its stream.  ctx may be NULL. */
+mb_status mb_destroy(mb_ctx* ctx);
+
+/* Sets the blobs of box `box` (0 <= box < batch), replacing any previous ones.
+ *   pos          [n_blobs][3] blob positions q_i.
+ *   particle_id  [n_blobs] particle index of each blob, in [0, n_particles); a particle is
+ *                the set of blobs sharing an id (Sec. 2: 12 icosahedron vertices + centre).
+ *   bonds        [n_bonds][2] box-local blob index pairs tied by harmonic springs of rest
+ *                length rest_len[e] and stiffness k_spring (Fig. ico: hard springs).
+ *   k_rep, r_cut soft repulsion k_rep (r_cut - r) r_hat between blobs of different particles
+ *                closer than r_cut (0 disables it); r_cut <= min(nx, ny, nz) h / 2.
+ * n_blobs may be 0 (an empty box).  The blob forces of a step are the spring, repulsion and
+ * external forces evaluated at the midpoint positions. */
+mb_status mb_set_particles(mb_ctx* ctx, int box, int64_t n_blobs, const double* pos,
+                           const int32_t* particle_id, int64_t n_bonds, const int32_t* bonds,
+                           const double* rest_len, double k_spring, double k_rep, double r_cut);
+
+/* Advances all boxes by n_steps time steps of the neutrally buoyant inertial coupling method
+ * (m_e = 0, so the blob-fluid force is minus the blob force, Eqs. blob1 and vf):
+ *   u^n       = J(q^n) v^n                                   (no-slip, Eq. ju)
+ *   q^{n+1/2} = q^n + dt/2 u^n
+ *   F         = springs + repulsion + ext at q^{n+1/2}
+ *   (rho/dt - eta/2 L) v^{n+1} = P[(rho/dt + eta/2 L) v^n + S(q^{n+1/2}) F + f_body]
+ *   q^{n+1}   = q^n + dt J(q^{n+1/2}) (v^n + v^{n+1})/2
+ * with L the 7-point Laplacian of each MAC component and P the exact discrete projection
+ * onto divergence-free fields, solved by FFT.
+ *   ext_blob_force  [total blobs][3] external blob forces, boxes in order (NULL = none); the
+ *                   same forces are applied in every one of the n_steps.
+ *   body_force      HOST array of 4 doubles {f0, axis, wave_dir, j} giving the force density
+ *                   f0 sin(2 pi j x_w / L_w) along `axis`, x_w the node coordinate along
+ *                   wave_dir (the viscosity protocol of Sec. 10), or NULL.
+ * Every box must have had mb_set_particles called (possibly with 0 blobs). */
+mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
+                  const double* body_force);
+
+/* Reads the current state.  Each output may be NULL.
+ *   blob_vel    [total blobs][3] u_i = J_i v at the current positions (Eq. ju).
+ *   blob_pos    [total blobs][3] current positions, wrapped into [0, L).
+ *   particle_U  [total particles][3] U0 = (1/N) sum_i u_i (Sec. 2), particles of box 0
+ *               first, then box 1, and so on.
+ *   grid_v      [batch] grids of the fluid velocity, in the context's precision. */
+mb_status mb_get_velocities(mb_ctx* ctx, double* blob_vel, double* blob_pos,
+                            double* particle_U, void* grid_v);
+
+/* Particle translational and angular velocities: U0 = (1/N) sum u_i and Omega solving
+ * I0 Omega = sum_i s_i x (u_i - U0), I0 = sum_i (s_i^2 1 - s_i s_i), s_i = q_i - q_0
+ * (Sec. 3.2, Eqs. torque and miner0).  Both [total particles][3]; either may be NULL. */
+mb_status mb_get_particle_velocities(mb_ctx* ctx, double* particle_U, double* particle_Omega);
+
+/* Replaces the fluid velocity of all boxes ([batch] grids in the context's precision), for
+ * example to resume from a checkpoint.  The field should be divergence-free. */
+mb_status mb_set_velocity_field(mb_ctx* ctx, const void* grid_v);
+
+/* Standalone spreading S (Sec. 2): grid_out = sum_i delta_h(r - q_i) F_i on one box of the
+ * context's geometry.  pos, F are [n][3]; grid_out is one box grid (3 components). */
+mb_status mb_spread(mb_ctx* ctx, int64_t n, const double* pos, const double* F, void* grid_out);
+
+/* Standalone interpolation J (Eq. ju): u_out_i = sum over nodes of prod Phi * v, on one box
+ * grid grid_v.  pos, u_out are [n][3]. */
+mb_status mb_interp(mb_ctx* ctx, int64_t n, const double* pos, const void* grid_v,
+                    double* u_out);
+
+/* Standalone fluid update of one box (Eq. vf with the viscous stress, Crank-Nicolson):
+ *   (rho/dt - eta/2 L) v_out = P[(rho/dt + eta/2 L) v_in + f + f_body].
+ * The k = 0 mode follows the grid (mean_mode 0) or is zeroed (mean_mode 1).  v_in, f and
+ * v_out are one box grid each; body_force as in mb_step (HOST, or NULL). */
+mb_status mb_fluid_update(mb_ctx* ctx, const void* v_in, const void* f,
+                          const double* body_force, void* v_out);
+
+/* The midpoint positions q^{n+1/2} and blob forces F (springs + repulsion + external) of the
+ * last step taken, each [total blobs][3]; either may be NULL.  Before the first step both
+ * are undefined (MB_ESTATE). */
+mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos);
+
+/* Number of blobs and particles of all boxes together. */
+mb_status mb_get_counts(const mb_ctx* ctx, int64_t* total_blobs, int64_t* total_particles);
+
+/* Message of the last error on ctx (or of the last failed mb_create_grid when ctx is NULL).
+ * The string stays valid until the next call on ctx. */
+const char* mb_last_error(const mb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MB_H */

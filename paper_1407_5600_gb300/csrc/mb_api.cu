@@ -1,0 +1,1004 @@
+// C ABI of libmb.so: context management, argument validation, host/device staging and the
+// orchestration of one inertial-coupling step (see include/mb.h for the contract).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mb_internal.cuh"
+#include "peskin.cuh"
+
+using namespace mbk;
+
+namespace {
+
+constexpr int SYM_LEN = 256;   // per-dimension symbol table length (n <= 128 today)
+
+thread_local std::string g_create_error;
+
+// Host-side fault injection: MB_FAULT_ALLOC=k makes the k-th device allocation of the
+// process fail as if the device were out of memory (tests of the MB_ENOMEM path).
+long g_alloc_counter = 0;
+bool injected_alloc_failure()
+{
+    static long k = [] {
+        const char* s = std::getenv("MB_FAULT_ALLOC");
+        return s ? std::atol(s) : 0L;
+    }();
+    ++g_alloc_counter;
+    return k > 0 && g_alloc_counter == k;
+}
+
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+cudaError_t dfree(DBuf& b)
+{
+    cudaError_t e = cudaSuccess;
+    if (b.p) e = cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    return e;
+}
+
+// Ensures b holds at least `bytes`; contents are not preserved.  Returns MB_ENOMEM/MB_ECUDA.
+mb_status ensure(DBuf& b, size_t bytes, std::string& err, const char* what)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return MB_OK;
+    dfree(b);
+    if (injected_alloc_failure()) {
+        err = std::string("injected allocation failure for ") + what;
+        return MB_ENOMEM;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        err = std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) +
+              " bytes): " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? MB_ENOMEM : MB_ECUDA;
+    }
+    b.bytes = bytes;
+    return MB_OK;
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct BoxData {
+    bool set = false;
+    std::vector<double> pos;
+    std::vector<int32_t> pid;
+    std::vector<int32_t> bonds;
+    std::vector<double> rest;
+    int64_t np = 0;
+    double k_spring = 0.0, k_rep = 0.0, r_cut = 0.0;
+};
+
+}  // namespace
+
+struct mb_ctx {
+    mb_grid_desc d{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    GridGeo g{};
+    BinGeo bg{};
+    int B = 1;
+    size_t rsz = 4;           // bytes per grid real
+    int nxh = 0;
+    int tile[3] = {8, 8, 8};
+
+    DBuf v[2], f, spec, vbar, fsum, tw[3], sym, body_prof, prof_scratch;
+    int cur = 0;
+    int64_t steps_taken = 0;
+    double body_cached[4] = {0, 0, 0, 0};
+    bool body_valid = false;
+
+    std::vector<BoxData> boxes;
+    bool dirty = true;
+    int64_t nb = 0, np = 0, max_box_blobs = 0;
+    int nchunk = 0;
+    std::vector<int64_t> box_off_h, part_off_h;
+    DBuf q, qh, u, F, rec, ext, pid, box_of, adj_start, adj_j, adj_rest, part_start,
+        part_blobs, box_off, box_par, cell_count, cell_start, blob_cell, blob_rank, sorted,
+        scan_tmp, partial, staging_in, staging_out, mean_scratch;
+    // standalone-operator scratch
+    DBuf s_q, s_F, s_rec, s_cell_count, s_cell_start, s_blob_cell, s_blob_rank, s_sorted,
+        s_scan, s_u, s_g0, s_g1, s_g2, s_out;
+
+    std::string err;
+};
+
+namespace {
+
+#define MB_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            cudaGetLastError();                                                           \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+            return MB_ECUDA;                                                              \
+        }                                                                                 \
+    } while (0)
+
+#define MB_TRY(expr)                                                                      \
+    do {                                                                                  \
+        mb_status s_ = (expr);                                                            \
+        if (s_ != MB_OK) return s_;                                                       \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) { cudaGetLastError(); ok = false; }
+    }
+    ~DeviceGuard()
+    {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+mb_status invalid(mb_ctx* ctx, const std::string& msg)
+{
+    ctx->err = msg;
+    return MB_EINVAL;
+}
+
+size_t grid_bytes(const mb_ctx* ctx, int boxes) { return (size_t)boxes * 3 * ctx->g.N * ctx->rsz; }
+
+// Copies an input array to the device if it lives in host memory.
+mb_status stage_in(mb_ctx* ctx, const void* p, size_t bytes, DBuf& buf, const void** out,
+                   const char* what)
+{
+    if (is_device_ptr(p)) {
+        *out = p;
+        return MB_OK;
+    }
+    MB_TRY(ensure(buf, bytes, ctx->err, what));
+    MB_CUDA(cudaMemcpyAsync(buf.p, p, bytes, cudaMemcpyHostToDevice, ctx->st));
+    *out = buf.p;
+    return MB_OK;
+}
+
+// Device destination for an output: the caller's pointer, or a staging buffer.
+mb_status out_target(mb_ctx* ctx, void* p, size_t bytes, DBuf& buf, void** dev, bool* host,
+                     const char* what)
+{
+    if (is_device_ptr(p)) {
+        *dev = p;
+        *host = false;
+        return MB_OK;
+    }
+    MB_TRY(ensure(buf, bytes, ctx->err, what));
+    *dev = buf.p;
+    *host = true;
+    return MB_OK;
+}
+
+mb_status finish_out(mb_ctx* ctx, void* p, const void* dev, size_t bytes, bool host)
+{
+    if (!host) return MB_OK;
+    MB_CUDA(cudaMemcpyAsync(p, dev, bytes, cudaMemcpyDeviceToHost, ctx->st));
+    MB_CUDA(cudaStreamSynchronize(ctx->st));
+    return MB_OK;
+}
+
+mb_status copy_to_host(mb_ctx* ctx, const void* p, size_t bytes, void* hostbuf)
+{
+    if (bytes == 0) return MB_OK;
+    if (is_device_ptr(p)) {
+        MB_CUDA(cudaMemcpyAsync(hostbuf, p, bytes, cudaMemcpyDeviceToHost, ctx->st));
+        MB_CUDA(cudaStreamSynchronize(ctx->st));
+    } else {
+        std::memcpy(hostbuf, p, bytes);
+    }
+    return MB_OK;
+}
+
+double wrap_host(double x, double L)
+{
+    double y = std::fmod(x, L);
+    if (y < 0.0) y += L;
+    if (y >= L) y -= L;
+    return y;
+}
+
+__global__ void k_wrap(int64_t n, double* q, double L0, double L1, double L2)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const int d = (int)(i % 3);
+    const double L = d == 0 ? L0 : (d == 1 ? L1 : L2);
+    double y = fmod(q[i], L);
+    if (y < 0.0) y += L;
+    if (y >= L) y -= L;
+    q[i] = y;
+}
+
+// Choose the bin cell side: a power of two of mesh cells, at least 2 and at least r_cut.
+void choose_bins(mb_ctx* ctx, double r_cut)
+{
+    int bs = 2;
+    while (bs * ctx->d.h < r_cut) bs *= 2;
+    const int nmin = std::min(ctx->g.n[0], std::min(ctx->g.n[1], ctx->g.n[2]));
+    if (bs > nmin) bs = nmin;
+    ctx->bg.bs = bs;
+    for (int a = 0; a < 3; ++a) ctx->bg.nc[a] = ctx->g.n[a] / bs;
+    ctx->bg.ncell = (int64_t)ctx->bg.nc[0] * ctx->bg.nc[1] * ctx->bg.nc[2];
+    ctx->bg.inv_w = 1.0 / (bs * ctx->d.h);
+}
+
+// Concatenates the boxes' blobs into the device arrays used by the step.
+mb_status rebuild(mb_ctx* ctx)
+{
+    const int B = ctx->B;
+    ctx->box_off_h.assign(B + 1, 0);
+    ctx->part_off_h.assign(B + 1, 0);
+    double rmax = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const BoxData& bx = ctx->boxes[b];
+        ctx->box_off_h[b + 1] = ctx->box_off_h[b] + (int64_t)bx.pid.size();
+        ctx->part_off_h[b + 1] = ctx->part_off_h[b] + bx.np;
+        if (bx.k_rep != 0.0) rmax = std::max(rmax, bx.r_cut);
+    }
+    const int64_t nb = ctx->box_off_h[B], np = ctx->part_off_h[B];
+    ctx->nb = nb;
+    ctx->np = np;
+    ctx->max_box_blobs = 0;
+    for (int b = 0; b < B; ++b)
+        ctx->max_box_blobs = std::max(ctx->max_box_blobs, ctx->box_off_h[b + 1] - ctx->box_off_h[b]);
+    ctx->nchunk = (int)((ctx->max_box_blobs + 255) / 256);
+    choose_bins(ctx, rmax);
+
+    std::vector<double> q(3 * nb), par(3 * B);
+    std::vector<int32_t> pid(nb), box_of(nb), adj_start(nb + 1, 0), part_start(np + 1, 0),
+        part_blobs(nb);
+    std::vector<int64_t> off(ctx->box_off_h);
+    int64_t nadj = 0;
+    for (int b = 0; b < B; ++b) nadj += 2 * (int64_t)(ctx->boxes[b].rest.size());
+    std::vector<int32_t> adj_j(nadj);
+    std::vector<double> adj_rest(nadj);
+    for (int b = 0; b < B; ++b) {
+        const BoxData& bx = ctx->boxes[b];
+        const int64_t o = ctx->box_off_h[b];
+        const int64_t n = (int64_t)bx.pid.size();
+        for (int64_t i = 0; i < n; ++i) {
+            for (int a = 0; a < 3; ++a) q[3 * (o + i) + a] = wrap_host(bx.pos[3 * i + a], ctx->g.L[a]);
+            pid[o + i] = (int32_t)(ctx->part_off_h[b] + bx.pid[i]);
+            box_of[o + i] = b;
+        }
+        for (size_t e = 0; e < bx.rest.size(); ++e) {
+            adj_start[o + bx.bonds[2 * e] + 1]++;
+            adj_start[o + bx.bonds[2 * e + 1] + 1]++;
+        }
+        par[3 * b] = bx.k_spring;
+        par[3 * b + 1] = bx.k_rep;
+        par[3 * b + 2] = bx.r_cut;
+    }
+    for (int64_t i = 0; i < nb; ++i) adj_start[i + 1] += adj_start[i];
+    {
+        std::vector<int32_t> fill(adj_start.begin(), adj_start.end() - 1);
+        for (int b = 0; b < B; ++b) {
+            const BoxData& bx = ctx->boxes[b];
+            const int64_t o = ctx->box_off_h[b];
+            for (size_t e = 0; e < bx.rest.size(); ++e) {
+                const int64_t i = o + bx.bonds[2 * e], j = o + bx.bonds[2 * e + 1];
+                adj_j[fill[i]] = (int32_t)j;
+                adj_rest[fill[i]++] = bx.rest[e];
+                adj_j[fill[j]] = (int32_t)i;
+                adj_rest[fill[j]++] = bx.rest[e];
+            }
+        }
+    }
+    for (int64_t i = 0; i < nb; ++i) part_start[pid[i] + 1]++;
+    for (int64_t p = 0; p < np; ++p) part_start[p + 1] += part_start[p];
+    {
+        std::vector<int32_t> fill(part_start.begin(), part_start.end() - 1);
+        for (int64_t i = 0; i < nb; ++i) part_blobs[fill[pid[i]]++] = (int32_t)i;
+    }
+
+    const int64_t ncells = (int64_t)B * ctx->bg.ncell;
+    std::string& E = ctx->err;
+    MB_TRY(ensure(ctx->q, sizeof(double) * 3 * nb, E, "q"));
+    MB_TRY(ensure(ctx->qh, sizeof(double) * 3 * nb, E, "q_half"));
+    MB_TRY(ensure(ctx->u, sizeof(double) * 3 * nb, E, "u"));
+    MB_TRY(ensure(ctx->F, sizeof(double) * 3 * nb, E, "F"));
+    MB_TRY(ensure(ctx->rec, sizeof(double) * 6 * nb, E, "rec"));
+    MB_TRY(ensure(ctx->ext, sizeof(double) * 3 * nb, E, "ext"));
+    MB_TRY(ensure(ctx->pid, sizeof(int32_t) * nb, E, "pid"));
+    MB_TRY(ensure(ctx->box_of, sizeof(int32_t) * nb, E, "box_of"));
+    MB_TRY(ensure(ctx->adj_start, sizeof(int32_t) * (nb + 1), E, "adj_start"));
+    MB_TRY(ensure(ctx->adj_j, sizeof(int32_t) * nadj, E, "adj_j"));
+    MB_TRY(ensure(ctx->adj_rest, sizeof(double) * nadj, E, "adj_rest"));
+    MB_TRY(ensure(ctx->part_start, sizeof(int32_t) * (np + 1), E, "part_start"));
+    MB_TRY(ensure(ctx->part_blobs, sizeof(int32_t) * nb, E, "part_blobs"));
+    MB_TRY(ensure(ctx->box_off, sizeof(int64_t) * (B + 1), E, "box_off"));
+    MB_TRY(ensure(ctx->box_par, sizeof(double) * 3 * B, E, "box_par"));
+    MB_TRY(ensure(ctx->cell_count, sizeof(int32_t) * ncells, E, "cell_count"));
+    MB_TRY(ensure(ctx->cell_start, sizeof(int32_t) * (ncells + 1), E, "cell_start"));
+    MB_TRY(ensure(ctx->blob_cell, sizeof(int32_t) * nb, E, "blob_cell"));
+    MB_TRY(ensure(ctx->blob_rank, sizeof(int32_t) * nb, E, "blob_rank"));
+    MB_TRY(ensure(ctx->sorted, sizeof(int32_t) * nb, E, "sorted"));
+    MB_TRY(ensure(ctx->scan_tmp, sizeof(int32_t) * (ncells / 4096 + 2), E, "scan_tmp"));
+    MB_TRY(ensure(ctx->partial, sizeof(double) * 3 * B * std::max(ctx->nchunk, 1), E, "partial"));
+
+    cudaStream_t st = ctx->st;
+    auto up = [&](DBuf& d, const void* h, size_t bytes) -> mb_status {
+        if (bytes) MB_CUDA(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, st));
+        return MB_OK;
+    };
+    MB_TRY(up(ctx->q, q.data(), sizeof(double) * 3 * nb));
+    MB_TRY(up(ctx->pid, pid.data(), sizeof(int32_t) * nb));
+    MB_TRY(up(ctx->box_of, box_of.data(), sizeof(int32_t) * nb));
+    MB_TRY(up(ctx->adj_start, adj_start.data(), sizeof(int32_t) * (nb + 1)));
+    MB_TRY(up(ctx->adj_j, adj_j.data(), sizeof(int32_t) * nadj));
+    MB_TRY(up(ctx->adj_rest, adj_rest.data(), sizeof(double) * nadj));
+    MB_TRY(up(ctx->part_start, part_start.data(), sizeof(int32_t) * (np + 1)));
+    MB_TRY(up(ctx->part_blobs, part_blobs.data(), sizeof(int32_t) * nb));
+    MB_TRY(up(ctx->box_off, off.data(), sizeof(int64_t) * (B + 1)));
+    MB_TRY(up(ctx->box_par, par.data(), sizeof(double) * 3 * B));
+    // the host vectors die at return: make the copies complete first
+    MB_CUDA(cudaStreamSynchronize(st));
+    ctx->dirty = false;
+    return MB_OK;
+}
+
+mb_status ensure_ready(mb_ctx* ctx)
+{
+    for (int b = 0; b < ctx->B; ++b)
+        if (!ctx->boxes[b].set) {
+            ctx->err = "box " + std::to_string(b) + " has no particles set (call mb_set_particles)";
+            return MB_ESTATE;
+        }
+    if (ctx->dirty) return rebuild(ctx);
+    return MB_OK;
+}
+
+// Body-force profile along wave_dir on the component `axis`'s nodes (host sin, FP64).
+mb_status set_body(mb_ctx* ctx, const double* body, DBuf& target, bool use_cache)
+{
+    const double f0 = body[0], axis = body[1], dir = body[2], j = body[3];
+    if (!std::isfinite(f0) || !std::isfinite(j) || (axis != 0 && axis != 1 && axis != 2) ||
+        (dir != 0 && dir != 1 && dir != 2))
+        return invalid(ctx, "body_force must be {f0, axis in 0..2, wave_dir in 0..2, j} with finite f0, j");
+    if (use_cache && ctx->body_valid && std::memcmp(ctx->body_cached, body, sizeof(double) * 4) == 0)
+        return MB_OK;
+    const int ax = (int)axis, wd = (int)dir;
+    const int n = ctx->g.n[wd];
+    const double L = ctx->g.L[wd];
+    const double shift = ax == wd ? 0.0 : 0.5;
+    std::vector<double> pd(n);
+    std::vector<float> pf(n);
+    for (int i = 0; i < n; ++i) {
+        pd[i] = f0 * std::sin(2.0 * M_PI * j * ((double)i + shift) * ctx->d.h / L);
+        pf[i] = (float)pd[i];
+    }
+    MB_TRY(ensure(target, sizeof(double) * n, ctx->err, "body profile"));
+    const void* src = ctx->rsz == 8 ? (const void*)pd.data() : (const void*)pf.data();
+    MB_CUDA(cudaMemcpyAsync(target.p, src, ctx->rsz * n, cudaMemcpyHostToDevice, ctx->st));
+    MB_CUDA(cudaStreamSynchronize(ctx->st));
+    if (use_cache) {
+        std::memcpy(ctx->body_cached, body, sizeof(double) * 4);
+        ctx->body_valid = true;
+    }
+    return MB_OK;
+}
+
+template <typename R>
+FluidArgs<R> fluid_args(mb_ctx* ctx, const void* v, const void* f, void* v_out,
+                        const void* prof, const double* body, const double* mean_override)
+{
+    FluidArgs<R> a{};
+    a.v = static_cast<const R*>(v);
+    a.f = static_cast<const R*>(f);
+    a.spec = static_cast<typename C2<R>::T*>(ctx->spec.p);
+    a.v_out = static_cast<R*>(v_out);
+    for (int d = 0; d < 3; ++d) a.tw[d] = static_cast<const R*>(ctx->tw[d].p);
+    a.sym = static_cast<const double*>(ctx->sym.p);
+    a.body_prof = body ? static_cast<const R*>(prof) : nullptr;
+    a.body_axis = body ? (int)body[1] : -1;
+    a.body_dir = body ? (int)body[2] : 0;
+    a.mean_override = mean_override;
+    a.mean_mode = ctx->d.mean_mode;
+    a.rho_dt = ctx->d.rho / ctx->d.dt;
+    a.half_eta = 0.5 * ctx->d.eta;
+    return a;
+}
+
+// One time step of every box (see mb_step in include/mb.h).
+template <typename R>
+mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
+{
+    cudaStream_t st = ctx->st;
+    const GridGeo& g = ctx->g;
+    const int B = ctx->B;
+    R* vcur = static_cast<R*>(ctx->v[ctx->cur].p);
+    R* vnext = static_cast<R*>(ctx->v[ctx->cur ^ 1].p);
+    double* q = static_cast<double*>(ctx->q.p);
+    double* qh = static_cast<double*>(ctx->qh.p);
+    const int32_t* box_of = static_cast<const int32_t*>(ctx->box_of.p);
+    const bool blobs = ctx->nb > 0;
+    if (blobs) {
+        // u^n = J(q^n) v^n ; q^{n+1/2} = q^n + dt/2 u^n
+        MB_CUDA(launch_interp<R>(st, 1, ctx->nb, q, nullptr, vcur, nullptr, box_of, g,
+                                 ctx->d.dt, nullptr, qh));
+        MB_CUDA(launch_bin(st, ctx->nb, qh, box_of, B, ctx->bg,
+                           static_cast<int32_t*>(ctx->cell_count.p),
+                           static_cast<int32_t*>(ctx->cell_start.p),
+                           static_cast<int32_t*>(ctx->blob_cell.p),
+                           static_cast<int32_t*>(ctx->blob_rank.p),
+                           static_cast<int32_t*>(ctx->sorted.p),
+                           static_cast<int32_t*>(ctx->scan_tmp.p), ctx->d.deterministic != 0));
+        ForceArgs fa{};
+        fa.box_off = static_cast<const int64_t*>(ctx->box_off.p);
+        fa.sorted = static_cast<const int32_t*>(ctx->sorted.p);
+        fa.q = qh;
+        fa.pid = static_cast<const int32_t*>(ctx->pid.p);
+        fa.adj_start = static_cast<const int32_t*>(ctx->adj_start.p);
+        fa.adj_j = static_cast<const int32_t*>(ctx->adj_j.p);
+        fa.adj_rest = static_cast<const double*>(ctx->adj_rest.p);
+        fa.box_par = static_cast<const double*>(ctx->box_par.p);
+        fa.cell_start = static_cast<const int32_t*>(ctx->cell_start.p);
+        fa.blob_cell = static_cast<const int32_t*>(ctx->blob_cell.p);
+        fa.ext = ext;
+        fa.F = static_cast<double*>(ctx->F.p);
+        fa.rec = static_cast<double*>(ctx->rec.p);
+        fa.partial = static_cast<double*>(ctx->partial.p);
+        fa.nchunk = ctx->nchunk;
+        MB_CUDA(launch_forces(st, B, ctx->max_box_blobs, fa, g, ctx->bg));
+        const double L3 = g.L[0] * g.L[1] * g.L[2];
+        MB_CUDA(launch_force_sum(st, B, ctx->nchunk, static_cast<const double*>(ctx->partial.p),
+                                 static_cast<double*>(ctx->vbar.p),
+                                 ctx->d.dt / (ctx->d.rho * L3), ctx->d.mean_mode,
+                                 static_cast<double*>(ctx->fsum.p)));
+        MB_CUDA(launch_spread<R>(st, B, static_cast<const double*>(ctx->rec.p),
+                                 static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
+                                 ctx->tile, static_cast<R*>(ctx->f.p)));
+    }
+    const double* mean = ctx->d.mean_mode == 0 ? static_cast<const double*>(ctx->vbar.p) : nullptr;
+    FluidArgs<R> fa = fluid_args<R>(ctx, vcur, blobs ? ctx->f.p : nullptr, vnext,
+                                    ctx->body_prof.p, body, mean);
+    MB_CUDA(launch_fluid<R>(st, B, g, fa));
+    if (blobs) {
+        // q^{n+1} = q^n + dt J(q^{n+1/2}) (v^n + v^{n+1})/2
+        MB_CUDA(launch_interp<R>(st, 2, ctx->nb, qh, q, vcur, vnext, box_of, g, ctx->d.dt,
+                                 nullptr, q));
+    }
+    ctx->cur ^= 1;
+    ctx->steps_taken++;
+    return MB_OK;
+}
+
+void pick_tile(mb_ctx* ctx)
+{
+    const int want[3] = {32, 8, 8};
+    for (int d = 0; d < 3; ++d) ctx->tile[d] = std::min(want[d], ctx->g.n[d]);
+}
+
+mb_status upload_tables(mb_ctx* ctx)
+{
+    std::vector<double> sym(9 * SYM_LEN, 0.0);
+    for (int d = 0; d < 3; ++d) {
+        const int n = ctx->g.n[d];
+        std::vector<double> twd(n);         // n/2 complex
+        std::vector<float> twf(n);
+        for (int m = 0; m < n / 2; ++m) {
+            const double ang = -2.0 * M_PI * (double)m / (double)n;
+            twd[2 * m] = std::cos(ang);
+            twd[2 * m + 1] = std::sin(ang);
+            twf[2 * m] = (float)twd[2 * m];
+            twf[2 * m + 1] = (float)twd[2 * m + 1];
+        }
+        MB_TRY(ensure(ctx->tw[d], sizeof(double) * n, ctx->err, "twiddles"));
+        const void* src = ctx->rsz == 8 ? (const void*)twd.data() : (const void*)twf.data();
+        MB_CUDA(cudaMemcpyAsync(ctx->tw[d].p, src, ctx->rsz * n, cudaMemcpyHostToDevice, ctx->st));
+        for (int k = 0; k < n; ++k) {
+            const double th = 2.0 * M_PI * (double)k / (double)n;
+            const double s = std::sin(0.5 * th);
+            sym[(3 * d + 0) * SYM_LEN + k] = std::cos(th);
+            sym[(3 * d + 1) * SYM_LEN + k] = std::sin(th);
+            sym[(3 * d + 2) * SYM_LEN + k] = 4.0 / (ctx->d.h * ctx->d.h) * s * s;
+        }
+        MB_CUDA(cudaStreamSynchronize(ctx->st));
+    }
+    MB_TRY(ensure(ctx->sym, sizeof(double) * sym.size(), ctx->err, "symbols"));
+    MB_CUDA(cudaMemcpyAsync(ctx->sym.p, sym.data(), sizeof(double) * sym.size(),
+                            cudaMemcpyHostToDevice, ctx->st));
+    MB_CUDA(cudaStreamSynchronize(ctx->st));
+    return MB_OK;
+}
+
+void release(mb_ctx* ctx)
+{
+    DBuf* all[] = {&ctx->v[0], &ctx->v[1], &ctx->f, &ctx->spec, &ctx->vbar, &ctx->fsum,
+                   &ctx->tw[0], &ctx->tw[1], &ctx->tw[2], &ctx->sym, &ctx->body_prof,
+                   &ctx->prof_scratch, &ctx->q, &ctx->qh, &ctx->u, &ctx->F, &ctx->rec,
+                   &ctx->ext, &ctx->pid, &ctx->box_of, &ctx->adj_start, &ctx->adj_j,
+                   &ctx->adj_rest, &ctx->part_start, &ctx->part_blobs, &ctx->box_off,
+                   &ctx->box_par, &ctx->cell_count, &ctx->cell_start, &ctx->blob_cell,
+                   &ctx->blob_rank, &ctx->sorted, &ctx->scan_tmp, &ctx->partial,
+                   &ctx->staging_in, &ctx->staging_out, &ctx->mean_scratch, &ctx->s_q,
+                   &ctx->s_F, &ctx->s_rec, &ctx->s_cell_count, &ctx->s_cell_start,
+                   &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
+                   &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out};
+    for (DBuf* b : all) dfree(*b);
+}
+
+// Standalone spreading of n blobs into one box grid `out_dev` (device pointer).
+template <typename R>
+mb_status standalone_spread(mb_ctx* ctx, int64_t n, const double* qd, const double* Fd,
+                            R* out_dev)
+{
+    cudaStream_t st = ctx->st;
+    std::string& E = ctx->err;
+    BinGeo bg = ctx->bg;
+    // standalone operators bin with the default cell size
+    {
+        int bs = 2;
+        const int nmin = std::min(ctx->g.n[0], std::min(ctx->g.n[1], ctx->g.n[2]));
+        if (bs > nmin) bs = nmin;
+        bg.bs = bs;
+        for (int a = 0; a < 3; ++a) bg.nc[a] = ctx->g.n[a] / bs;
+        bg.ncell = (int64_t)bg.nc[0] * bg.nc[1] * bg.nc[2];
+        bg.inv_w = 1.0 / (bs * ctx->d.h);
+    }
+    MB_TRY(ensure(ctx->s_q, sizeof(double) * 3 * n, E, "spread q"));
+    MB_TRY(ensure(ctx->s_rec, sizeof(double) * 6 * n, E, "spread rec"));
+    MB_TRY(ensure(ctx->s_cell_count, sizeof(int32_t) * bg.ncell, E, "spread cells"));
+    MB_TRY(ensure(ctx->s_cell_start, sizeof(int32_t) * (bg.ncell + 1), E, "spread cells"));
+    MB_TRY(ensure(ctx->s_blob_cell, sizeof(int32_t) * n, E, "spread cells"));
+    MB_TRY(ensure(ctx->s_blob_rank, sizeof(int32_t) * n, E, "spread cells"));
+    MB_TRY(ensure(ctx->s_sorted, sizeof(int32_t) * n, E, "spread cells"));
+    MB_TRY(ensure(ctx->s_scan, sizeof(int32_t) * (bg.ncell / 4096 + 2), E, "spread scan"));
+    double* q = static_cast<double*>(ctx->s_q.p);
+    if (n > 0) {
+        MB_CUDA(cudaMemcpyAsync(q, qd, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+        k_wrap<<<(unsigned)((3 * n + 255) / 256), 256, 0, st>>>(n, q, ctx->g.L[0], ctx->g.L[1],
+                                                                ctx->g.L[2]);
+        MB_CUDA(cudaGetLastError());
+    }
+    MB_CUDA(launch_bin(st, n, q, nullptr, 1, bg, static_cast<int32_t*>(ctx->s_cell_count.p),
+                       static_cast<int32_t*>(ctx->s_cell_start.p),
+                       static_cast<int32_t*>(ctx->s_blob_cell.p),
+                       static_cast<int32_t*>(ctx->s_blob_rank.p),
+                       static_cast<int32_t*>(ctx->s_sorted.p),
+                       static_cast<int32_t*>(ctx->s_scan.p), ctx->d.deterministic != 0));
+    MB_CUDA(launch_make_rec(st, n, static_cast<const int32_t*>(ctx->s_sorted.p), q, Fd,
+                            static_cast<double*>(ctx->s_rec.p)));
+    MB_CUDA(launch_spread<R>(st, 1, static_cast<const double*>(ctx->s_rec.p),
+                             static_cast<const int32_t*>(ctx->s_cell_start.p), ctx->g, bg,
+                             ctx->tile, out_dev));
+    return MB_OK;
+}
+
+}  // namespace
+
+// ==========================================================================================
+extern "C" {
+
+mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** out)
+{
+    if (out) *out = nullptr;
+    if (!desc || !out) {
+        g_create_error = "mb_create_grid: desc and out must be non-null";
+        return MB_EINVAL;
+    }
+    const mb_grid_desc& d = *desc;
+    const int ns[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; ++a)
+        if (!is_pow2(ns[a]) || ns[a] < 4 || ns[a] > 128) {
+            g_create_error = "nx, ny, nz must be powers of two in [4, 128]";
+            return MB_EINVAL;
+        }
+    if (d.batch < 1 || d.batch > 65535) {
+        g_create_error = "batch must be in [1, 65535]";
+        return MB_EINVAL;
+    }
+    if (!(d.h > 0 && std::isfinite(d.h)) || !(d.rho > 0 && std::isfinite(d.rho)) ||
+        !(d.eta > 0 && std::isfinite(d.eta)) || !(d.dt > 0 && std::isfinite(d.dt))) {
+        g_create_error = "h, rho, eta and dt must be finite and positive";
+        return MB_EINVAL;
+    }
+    if (d.precision != 0 && d.precision != 1) {
+        g_create_error = "precision must be 0 (FP32 grid) or 1 (FP64)";
+        return MB_EINVAL;
+    }
+    if (d.deterministic != 0 && d.deterministic != 1) {
+        g_create_error = "deterministic must be 0 or 1";
+        return MB_EINVAL;
+    }
+    if (d.advection != 0) {
+        g_create_error = "advection (the rho v v term) is not provided; set advection = 0";
+        return MB_EINVAL;
+    }
+    if (d.mean_mode != 0 && d.mean_mode != 1) {
+        g_create_error = "mean_mode must be 0 (conserve) or 1 (zero)";
+        return MB_EINVAL;
+    }
+    if (d.kT != 0.0) {
+        g_create_error = "fluctuating hydrodynamics (kT != 0) is not provided; set kT = 0";
+        return MB_EINVAL;
+    }
+    mb_ctx* ctx = new (std::nothrow) mb_ctx();
+    if (!ctx) {
+        g_create_error = "out of host memory";
+        return MB_ENOMEM;
+    }
+    ctx->d = d;
+    ctx->st = static_cast<cudaStream_t>(cuda_stream);
+    ctx->B = d.batch;
+    ctx->rsz = d.precision == 1 ? 8 : 4;
+    for (int a = 0; a < 3; ++a) {
+        ctx->g.n[a] = ns[a];
+        ctx->g.L[a] = ns[a] * d.h;
+    }
+    ctx->g.N = (int64_t)ns[0] * ns[1] * ns[2];
+    ctx->g.h = d.h;
+    ctx->g.inv_h = 1.0 / d.h;
+    ctx->nxh = ns[0] / 2 + 1;
+    ctx->boxes.resize(ctx->B);
+    pick_tile(ctx);
+    choose_bins(ctx, 0.0);
+
+    auto fail = [&](mb_status s) {
+        g_create_error = ctx->err;
+        release(ctx);
+        delete ctx;
+        return s;
+    };
+    const size_t gb = grid_bytes(ctx, ctx->B);
+    const size_t sb = (size_t)ctx->B * 3 * ns[2] * ns[1] * ctx->nxh * 2 * ctx->rsz;
+    mb_status s;
+    if ((s = ensure(ctx->v[0], gb, ctx->err, "v")) != MB_OK) return fail(s);
+    if ((s = ensure(ctx->v[1], gb, ctx->err, "v")) != MB_OK) return fail(s);
+    if ((s = ensure(ctx->f, gb, ctx->err, "f")) != MB_OK) return fail(s);
+    if ((s = ensure(ctx->spec, sb, ctx->err, "spectrum")) != MB_OK) return fail(s);
+    if ((s = ensure(ctx->vbar, sizeof(double) * 3 * ctx->B, ctx->err, "vbar")) != MB_OK) return fail(s);
+    if ((s = ensure(ctx->fsum, sizeof(double) * 3 * ctx->B, ctx->err, "fsum")) != MB_OK) return fail(s);
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "no CUDA device";
+        return fail(MB_ECUDA);
+    }
+    if (cudaMemsetAsync(ctx->v[0].p, 0, gb, ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->v[1].p, 0, gb, ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->vbar.p, 0, sizeof(double) * 3 * ctx->B, ctx->st) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "cudaMemsetAsync failed";
+        return fail(MB_ECUDA);
+    }
+    if ((s = upload_tables(ctx)) != MB_OK) return fail(s);
+    *out = ctx;
+    return MB_OK;
+}
+
+mb_status mb_destroy(mb_ctx* ctx)
+{
+    if (!ctx) return MB_OK;
+    DeviceGuard dg(ctx->device);
+    cudaStreamSynchronize(ctx->st);
+    cudaGetLastError();
+    release(ctx);
+    delete ctx;
+    return MB_OK;
+}
+
+const char* mb_last_error(const mb_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+mb_status mb_set_particles(mb_ctx* ctx, int box, int64_t n_blobs, const double* pos,
+                           const int32_t* particle_id, int64_t n_bonds, const int32_t* bonds,
+                           const double* rest_len, double k_spring, double k_rep, double r_cut)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (box < 0 || box >= ctx->B) return invalid(ctx, "box out of range");
+    if (n_blobs < 0 || n_bonds < 0) return invalid(ctx, "negative count");
+    if (n_blobs > 0 && (!pos || !particle_id)) return invalid(ctx, "pos and particle_id required");
+    if (n_bonds > 0 && (!bonds || !rest_len)) return invalid(ctx, "bonds and rest_len required");
+    if (!std::isfinite(k_spring) || !std::isfinite(k_rep) || !std::isfinite(r_cut) ||
+        k_rep < 0 || r_cut < 0)
+        return invalid(ctx, "k_spring must be finite, k_rep and r_cut finite and >= 0");
+    const double half_min = 0.5 * ctx->d.h * std::min(ctx->g.n[0], std::min(ctx->g.n[1], ctx->g.n[2]));
+    if (k_rep > 0 && r_cut > half_min) return invalid(ctx, "r_cut exceeds half the box");
+    if (n_blobs > (int64_t)1 << 30) return invalid(ctx, "too many blobs");
+    BoxData bx;
+    bx.pos.resize(3 * n_blobs);
+    bx.pid.resize(n_blobs);
+    bx.bonds.resize(2 * n_bonds);
+    bx.rest.resize(n_bonds);
+    MB_TRY(copy_to_host(ctx, pos, sizeof(double) * 3 * n_blobs, bx.pos.data()));
+    MB_TRY(copy_to_host(ctx, particle_id, sizeof(int32_t) * n_blobs, bx.pid.data()));
+    MB_TRY(copy_to_host(ctx, bonds, sizeof(int32_t) * 2 * n_bonds, bx.bonds.data()));
+    MB_TRY(copy_to_host(ctx, rest_len, sizeof(double) * n_bonds, bx.rest.data()));
+    int64_t maxp = -1;
+    for (int64_t i = 0; i < n_blobs; ++i) {
+        if (bx.pid[i] < 0) return invalid(ctx, "particle_id must be >= 0");
+        maxp = std::max<int64_t>(maxp, bx.pid[i]);
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(bx.pos[3 * i + a])) return invalid(ctx, "non-finite position");
+    }
+    for (int64_t e = 0; e < n_bonds; ++e) {
+        const int32_t i = bx.bonds[2 * e], j = bx.bonds[2 * e + 1];
+        if (i < 0 || j < 0 || i >= n_blobs || j >= n_blobs || i == j)
+            return invalid(ctx, "bond " + std::to_string(e) + " has an invalid blob index");
+        if (!(bx.rest[e] >= 0) || !std::isfinite(bx.rest[e]))
+            return invalid(ctx, "rest lengths must be finite and >= 0");
+    }
+    bx.np = maxp + 1;
+    bx.k_spring = k_spring;
+    bx.k_rep = k_rep;
+    bx.r_cut = r_cut;
+    bx.set = true;
+    ctx->boxes[box] = std::move(bx);
+    ctx->dirty = true;
+    ctx->steps_taken = 0;
+    return MB_OK;
+}
+
+mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
+                  const double* body_force)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (n_steps < 0) return invalid(ctx, "n_steps must be >= 0");
+    MB_TRY(ensure_ready(ctx));
+    if (body_force) MB_TRY(set_body(ctx, body_force, ctx->body_prof, true));
+    const double* ext = nullptr;
+    if (ext_blob_force && ctx->nb > 0) {
+        const void* src = nullptr;
+        MB_TRY(stage_in(ctx, ext_blob_force, sizeof(double) * 3 * ctx->nb, ctx->ext, &src, "ext"));
+        if (src != ctx->ext.p)
+            MB_CUDA(cudaMemcpyAsync(ctx->ext.p, src, sizeof(double) * 3 * ctx->nb,
+                                    cudaMemcpyDeviceToDevice, ctx->st));
+        ext = static_cast<const double*>(ctx->ext.p);
+    }
+    for (int s = 0; s < n_steps; ++s) {
+        if (ctx->rsz == 4) MB_TRY(do_step<float>(ctx, ext, body_force));
+        else MB_TRY(do_step<double>(ctx, ext, body_force));
+    }
+    return MB_OK;
+}
+
+mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (ctx->dirty || ctx->steps_taken == 0) {
+        ctx->err = "no step has been taken with the current particles";
+        return MB_ESTATE;
+    }
+    const size_t by = sizeof(double) * 3 * ctx->nb;
+    if (ctx->nb == 0) return MB_OK;
+    double* outs[2] = {blob_force, midpoint_pos};
+    DBuf* srcs[2] = {&ctx->F, &ctx->qh};
+    for (int i = 0; i < 2; ++i) {
+        if (!outs[i]) continue;
+        void* dst;
+        bool host;
+        MB_TRY(out_target(ctx, outs[i], by, ctx->staging_out, &dst, &host, "forces"));
+        MB_CUDA(cudaMemcpyAsync(dst, srcs[i]->p, by, cudaMemcpyDeviceToDevice, ctx->st));
+        MB_TRY(finish_out(ctx, outs[i], dst, by, host));
+    }
+    return MB_OK;
+}
+
+mb_status mb_get_counts(const mb_ctx* ctx, int64_t* total_blobs, int64_t* total_particles)
+{
+    if (!ctx) return MB_EINVAL;
+    int64_t nb = 0, np = 0;
+    for (const BoxData& b : ctx->boxes) {
+        nb += (int64_t)b.pid.size();
+        np += b.np;
+    }
+    if (total_blobs) *total_blobs = nb;
+    if (total_particles) *total_particles = np;
+    return MB_OK;
+}
+
+static mb_status blob_velocities(mb_ctx* ctx)
+{
+    if (ctx->nb == 0) return MB_OK;
+    if (ctx->rsz == 4)
+        MB_CUDA(launch_interp<float>(ctx->st, 0, ctx->nb, static_cast<const double*>(ctx->q.p),
+                                     nullptr, static_cast<const float*>(ctx->v[ctx->cur].p),
+                                     nullptr, static_cast<const int32_t*>(ctx->box_of.p), ctx->g,
+                                     ctx->d.dt, static_cast<double*>(ctx->u.p), nullptr));
+    else
+        MB_CUDA(launch_interp<double>(ctx->st, 0, ctx->nb, static_cast<const double*>(ctx->q.p),
+                                      nullptr, static_cast<const double*>(ctx->v[ctx->cur].p),
+                                      nullptr, static_cast<const int32_t*>(ctx->box_of.p),
+                                      ctx->g, ctx->d.dt, static_cast<double*>(ctx->u.p), nullptr));
+    return MB_OK;
+}
+
+mb_status mb_get_velocities(mb_ctx* ctx, double* blob_vel, double* blob_pos, double* particle_U,
+                            void* grid_v)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    MB_TRY(ensure_ready(ctx));
+    if (blob_vel || particle_U) MB_TRY(blob_velocities(ctx));
+    if (blob_vel && ctx->nb > 0) {
+        void* dst;
+        bool host;
+        const size_t by = sizeof(double) * 3 * ctx->nb;
+        MB_TRY(out_target(ctx, blob_vel, by, ctx->staging_out, &dst, &host, "blob_vel"));
+        MB_CUDA(cudaMemcpyAsync(dst, ctx->u.p, by, cudaMemcpyDeviceToDevice, ctx->st));
+        MB_TRY(finish_out(ctx, blob_vel, dst, by, host));
+    }
+    if (blob_pos && ctx->nb > 0) {
+        void* dst;
+        bool host;
+        const size_t by = sizeof(double) * 3 * ctx->nb;
+        MB_TRY(out_target(ctx, blob_pos, by, ctx->staging_out, &dst, &host, "blob_pos"));
+        MB_CUDA(cudaMemcpyAsync(dst, ctx->q.p, by, cudaMemcpyDeviceToDevice, ctx->st));
+        MB_TRY(finish_out(ctx, blob_pos, dst, by, host));
+    }
+    if (particle_U && ctx->np > 0) {
+        void* dst;
+        bool host;
+        const size_t by = sizeof(double) * 3 * ctx->np;
+        MB_TRY(out_target(ctx, particle_U, by, ctx->staging_out, &dst, &host, "particle_U"));
+        MB_CUDA(launch_particle_reduce(ctx->st, ctx->np,
+                                       static_cast<const int32_t*>(ctx->part_start.p),
+                                       static_cast<const int32_t*>(ctx->part_blobs.p), nullptr,
+                                       static_cast<const double*>(ctx->q.p),
+                                       static_cast<const double*>(ctx->u.p), ctx->g,
+                                       static_cast<double*>(dst), nullptr));
+        MB_TRY(finish_out(ctx, particle_U, dst, by, host));
+    }
+    if (grid_v) {
+        void* dst;
+        bool host;
+        const size_t by = grid_bytes(ctx, ctx->B);
+        MB_TRY(out_target(ctx, grid_v, by, ctx->staging_out, &dst, &host, "grid_v"));
+        MB_CUDA(cudaMemcpyAsync(dst, ctx->v[ctx->cur].p, by, cudaMemcpyDeviceToDevice, ctx->st));
+        MB_TRY(finish_out(ctx, grid_v, dst, by, host));
+    }
+    return MB_OK;
+}
+
+mb_status mb_get_particle_velocities(mb_ctx* ctx, double* particle_U, double* particle_Omega)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    MB_TRY(ensure_ready(ctx));
+    if (ctx->np == 0 || (!particle_U && !particle_Omega)) return MB_OK;
+    MB_TRY(blob_velocities(ctx));
+    const size_t by = sizeof(double) * 3 * ctx->np;
+    void *dU = nullptr, *dW = nullptr;
+    bool hU = false, hW = false;
+    if (particle_U) MB_TRY(out_target(ctx, particle_U, by, ctx->staging_out, &dU, &hU, "U"));
+    if (particle_Omega) MB_TRY(out_target(ctx, particle_Omega, by, ctx->s_out, &dW, &hW, "Omega"));
+    MB_CUDA(launch_particle_reduce(ctx->st, ctx->np, static_cast<const int32_t*>(ctx->part_start.p),
+                                   static_cast<const int32_t*>(ctx->part_blobs.p), nullptr,
+                                   static_cast<const double*>(ctx->q.p),
+                                   static_cast<const double*>(ctx->u.p), ctx->g,
+                                   static_cast<double*>(dU), static_cast<double*>(dW)));
+    if (particle_U) MB_TRY(finish_out(ctx, particle_U, dU, by, hU));
+    if (particle_Omega) MB_TRY(finish_out(ctx, particle_Omega, dW, by, hW));
+    return MB_OK;
+}
+
+mb_status mb_set_velocity_field(mb_ctx* ctx, const void* grid_v)
+{
+    if (!ctx) return MB_EINVAL;
+    if (!grid_v) return invalid(ctx, "grid_v must be non-null");
+    DeviceGuard dg(ctx->device);
+    const size_t by = grid_bytes(ctx, ctx->B);
+    const void* src;
+    MB_TRY(stage_in(ctx, grid_v, by, ctx->staging_in, &src, "grid_v"));
+    MB_CUDA(cudaMemcpyAsync(ctx->v[ctx->cur].p, src, by, cudaMemcpyDeviceToDevice, ctx->st));
+    if (ctx->rsz == 4)
+        MB_CUDA(launch_grid_mean<float>(ctx->st, ctx->B, ctx->g, static_cast<const float*>(ctx->v[ctx->cur].p),
+                                        static_cast<double*>(ctx->vbar.p), nullptr));
+    else
+        MB_CUDA(launch_grid_mean<double>(ctx->st, ctx->B, ctx->g, static_cast<const double*>(ctx->v[ctx->cur].p),
+                                         static_cast<double*>(ctx->vbar.p), nullptr));
+    if (ctx->d.mean_mode == 1)
+        MB_CUDA(cudaMemsetAsync(ctx->vbar.p, 0, sizeof(double) * 3 * ctx->B, ctx->st));
+    MB_CUDA(cudaStreamSynchronize(ctx->st));
+    return MB_OK;
+}
+
+mb_status mb_spread(mb_ctx* ctx, int64_t n, const double* pos, const double* F, void* grid_out)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (n < 0 || (n > 0 && (!pos || !F)) || !grid_out) return invalid(ctx, "bad spread arguments");
+    const void *qd = nullptr, *Fd = nullptr;
+    if (n > 0) {
+        MB_TRY(stage_in(ctx, pos, sizeof(double) * 3 * n, ctx->s_g0, &qd, "pos"));
+        MB_TRY(stage_in(ctx, F, sizeof(double) * 3 * n, ctx->s_F, &Fd, "F"));
+    }
+    const size_t by = grid_bytes(ctx, 1);
+    void* dst;
+    bool host;
+    MB_TRY(out_target(ctx, grid_out, by, ctx->s_out, &dst, &host, "grid_out"));
+    if (ctx->rsz == 4)
+        MB_TRY(standalone_spread<float>(ctx, n, static_cast<const double*>(qd),
+                                        static_cast<const double*>(Fd), static_cast<float*>(dst)));
+    else
+        MB_TRY(standalone_spread<double>(ctx, n, static_cast<const double*>(qd),
+                                         static_cast<const double*>(Fd), static_cast<double*>(dst)));
+    return finish_out(ctx, grid_out, dst, by, host);
+}
+
+mb_status mb_interp(mb_ctx* ctx, int64_t n, const double* pos, const void* grid_v, double* u_out)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (n < 0 || (n > 0 && (!pos || !u_out)) || !grid_v) return invalid(ctx, "bad interp arguments");
+    if (n == 0) return MB_OK;
+    const void *qd = nullptr, *vd = nullptr;
+    MB_TRY(stage_in(ctx, pos, sizeof(double) * 3 * n, ctx->s_g0, &qd, "pos"));
+    MB_TRY(ensure(ctx->s_q, sizeof(double) * 3 * n, ctx->err, "interp q"));
+    double* q = static_cast<double*>(ctx->s_q.p);
+    MB_CUDA(cudaMemcpyAsync(q, qd, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, ctx->st));
+    k_wrap<<<(unsigned)((3 * n + 255) / 256), 256, 0, ctx->st>>>(n, q, ctx->g.L[0], ctx->g.L[1],
+                                                                  ctx->g.L[2]);
+    MB_CUDA(cudaGetLastError());
+    MB_TRY(stage_in(ctx, grid_v, grid_bytes(ctx, 1), ctx->s_g1, &vd, "grid_v"));
+    const size_t by = sizeof(double) * 3 * n;
+    void* dst;
+    bool host;
+    MB_TRY(out_target(ctx, u_out, by, ctx->s_out, &dst, &host, "u_out"));
+    if (ctx->rsz == 4)
+        MB_CUDA(launch_interp<float>(ctx->st, 0, n, q, nullptr, static_cast<const float*>(vd),
+                                     nullptr, nullptr, ctx->g, ctx->d.dt,
+                                     static_cast<double*>(dst), nullptr));
+    else
+        MB_CUDA(launch_interp<double>(ctx->st, 0, n, q, nullptr, static_cast<const double*>(vd),
+                                      nullptr, nullptr, ctx->g, ctx->d.dt,
+                                      static_cast<double*>(dst), nullptr));
+    return finish_out(ctx, u_out, dst, by, host);
+}
+
+mb_status mb_fluid_update(mb_ctx* ctx, const void* v_in, const void* f, const double* body_force,
+                          void* v_out)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (!v_in || !v_out) return invalid(ctx, "v_in and v_out must be non-null");
+    const size_t by = grid_bytes(ctx, 1);
+    const void *vd = nullptr, *fd = nullptr;
+    MB_TRY(stage_in(ctx, v_in, by, ctx->s_g1, &vd, "v_in"));
+    if (f) MB_TRY(stage_in(ctx, f, by, ctx->s_g2, &fd, "f"));
+    if (body_force) MB_TRY(set_body(ctx, body_force, ctx->prof_scratch, false));
+    void* dst;
+    bool host;
+    MB_TRY(out_target(ctx, v_out, by, ctx->s_out, &dst, &host, "v_out"));
+    if (ctx->rsz == 4) {
+        FluidArgs<float> a = fluid_args<float>(ctx, vd, fd, dst, ctx->prof_scratch.p, body_force, nullptr);
+        MB_CUDA(launch_fluid<float>(ctx->st, 1, ctx->g, a));
+    } else {
+        FluidArgs<double> a = fluid_args<double>(ctx, vd, fd, dst, ctx->prof_scratch.p, body_force, nullptr);
+        MB_CUDA(launch_fluid<double>(ctx->st, 1, ctx->g, a));
+    }
+    return finish_out(ctx, v_out, dst, by, host);
+}
+
+}  // extern "C"

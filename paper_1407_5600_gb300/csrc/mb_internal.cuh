@@ -1,0 +1,120 @@
+// Internal declarations shared by the translation units of libmb.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mb.h"
+
+namespace mbk {
+
+// ------------------------------------------------------------------------------------------
+// Geometry passed by value to kernels.
+struct GridGeo {
+    int n[3];          // cells per side (powers of two)
+    int64_t N;         // cells per box
+    double h, inv_h;
+    double L[3];
+};
+
+struct BinGeo {
+    int nc[3];         // bin cells per side
+    int64_t ncell;     // bin cells per box
+    int bs;            // bin cell side in mesh cells
+    double inv_w;      // 1 / (bs h)
+};
+
+// Complex helpers on float2 / double2.
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+// ------------------------------------------------------------------------------------------
+// Launchers (each returns cudaGetLastError() after enqueuing).
+
+// Interpolation J of one or two grids at blob positions q.
+//   mode 0: u_out = J(q) v0
+//   mode 1: u_out = J(q) v0, q_out = wrap(q + 0.5 dt u)            (predictor)
+//   mode 2: u = J(q) (v0 + v1)/2, q_out = wrap(q_base + dt u), u_out = u if non-null (corrector)
+template <typename R>
+cudaError_t launch_interp(cudaStream_t st, int mode, int64_t nb, const double* q,
+                          const double* q_base, const R* v0, const R* v1,
+                          const int32_t* box_of, const GridGeo& g, double dt, double* u_out,
+                          double* q_out);
+
+// Cell binning: count, scan, scatter (and per-cell ordering when deterministic).
+cudaError_t launch_bin(cudaStream_t st, int64_t nb, const double* q, const int32_t* box_of,
+                       int B, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
+                       int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
+                       int32_t* scan_tmp, bool deterministic);
+
+// Blob forces at q (springs, repulsion, external) in sorted-slot order; writes F (blob order),
+// rec (sorted order: q, F) and per-(box, block) partial force sums.
+struct ForceArgs {
+    const int64_t* box_off;    // [B+1]
+    const int32_t* sorted;
+    const double* q;
+    const int32_t* pid;        // global particle ids
+    const int32_t* adj_start;  // [nb+1]
+    const int32_t* adj_j;
+    const double* adj_rest;
+    const double* box_par;     // [B][3]: k_spring, k_rep, r_cut
+    const int32_t* cell_start;
+    const int32_t* blob_cell;
+    const double* ext;         // may be null
+    double* F;
+    double* rec;
+    double* partial;           // [B][nchunk][3]
+    int nchunk;
+};
+cudaError_t launch_forces(cudaStream_t st, int B, int64_t max_box_blobs, const ForceArgs& a,
+                          const GridGeo& g, const BinGeo& bg);
+
+// Sum partial forces per box (fixed order) and update the FP64 mean velocity:
+// vbar += dt * sumF / (rho L^3) when mean_mode == 0, vbar = 0 otherwise; optionally copies
+// the force sum to fsum_out [B][3].
+cudaError_t launch_force_sum(cudaStream_t st, int B, int nchunk, const double* partial,
+                             double* vbar, double scale, int mean_mode, double* fsum_out);
+
+// Sorted records from arbitrary q, F (standalone spreading).
+cudaError_t launch_make_rec(cudaStream_t st, int64_t nb, const int32_t* sorted, const double* q,
+                            const double* F, double* rec);
+
+// Tile-owner spreading from sorted records.
+template <typename R>
+cudaError_t launch_spread(cudaStream_t st, int B, const double* rec, const int32_t* cell_start,
+                          const GridGeo& g, const BinGeo& bg, const int tile[3], R* f);
+
+// Particle velocities U0, Omega from blob velocities (particle CSR).
+cudaError_t launch_particle_reduce(cudaStream_t st, int64_t np, const int32_t* part_start,
+                                   const int32_t* part_blobs, const int32_t* box_of_part,
+                                   const double* q, const double* u, const GridGeo& g,
+                                   double* U, double* Omega);
+
+// Fluid update pipeline on B boxes.
+template <typename R>
+struct FluidArgs {
+    const R* v;            // [B][3][N]
+    const R* f;            // [B][3][N] or null
+    typename C2<R>::T* spec;   // [B][3][nz][ny][nx/2+1]
+    R* v_out;
+    const R* tw[3];        // twiddles per dimension, n/2 complex each (interleaved re, im)
+    const double* sym;     // [3 dims][3][128]: cos, sin, lambda of 2 pi k / n
+    const R* body_prof;    // body-force profile along wave_dir (null = none)
+    int body_axis, body_dir;
+    const double* mean_override;   // [B][3] mean velocity to impose at k = 0, or null
+    int mean_mode;
+    double rho_dt, half_eta;
+};
+template <typename R>
+cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a);
+
+// Reductions / utilities.
+template <typename R>
+cudaError_t launch_grid_mean(cudaStream_t st, int B, const GridGeo& g, const R* v,
+                             double* mean_out /*[B][3]*/, double* scratch);
+
+}  // namespace mbk

@@ -1,0 +1,323 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances are relative L2 errors: 1e-10 for the FP64 grid path and 1e-5 for the FP32 grid
+(FP64 blobs) path.  Sizes span several spreading tiles and ragged blob counts; the full 128^3
+dense workload is checked operator by operator and through properties of one step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import TOL, min_image, rel_l2, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_1407_5600_gb300 as mb  # noqa: E402
+from paper_1407_5600_gb300 import workloads as wl  # noqa: E402
+
+
+def _desc(shape, prec, **kw):
+    nz, ny, nx = shape
+    return mb.GridDesc(nx, ny, nz, precision=prec, **kw)
+
+
+def _oracle_grid(d: mb.GridDesc):
+    return oracle.Grid(d.nx, d.ny, d.nz, h=d.h, rho=d.rho, eta=d.eta, dt=d.dt,
+                       mean_mode=d.mean_mode)
+
+
+# ------------------------------------------------------------------------------------------
+# Operators
+
+SHAPES = [((8, 8, 8), 1.0, 300), ((16, 16, 16), 0.7, 5003), ((16, 32, 64), 1.0, 20011),
+          ((4, 4, 4), 2.0, 37), ((8, 16, 128), 1.0, 7777)]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("shape,h,n", SHAPES)
+def test_spread_parity(prec, shape, h, n):
+    d = _desc(shape, prec, h=h)
+    q, F, _ = wl.random_blobs(n, shape, seed=n, h=h)
+    q[0] = 0.0
+    q[1] = [0.5 * h, h, 1.5 * h]
+    q[2] = np.array([shape[2], shape[1], shape[0]]) * h - 1e-12   # just inside the box
+    q[3] = [-0.3 * h, 1e3 * h, -2.5 * h]                              # outside: wrapped
+    with mb.Multiblob(d) as sim:
+        f_gpu = to_np(sim.spread(q, F))[0]
+    f_ref = oracle.spread(_oracle_grid(d), np.mod(q, _oracle_grid(d).L), F)
+    assert rel_l2(f_gpu, f_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("shape,h,n", SHAPES)
+def test_interp_parity(prec, shape, h, n):
+    d = _desc(shape, prec, h=h)
+    q, _, _ = wl.random_blobs(n, shape, seed=n + 1, h=h)
+    v = wl.random_field(shape, seed=n + 2)
+    with mb.Multiblob(d) as sim:
+        u_gpu = to_np(sim.interp(q, v[None].astype(d.grid_dtype)))
+    u_ref = oracle.interp(_oracle_grid(d), q, v.astype(d.grid_dtype).astype(np.float64))
+    assert rel_l2(u_gpu, u_ref) < TOL[prec]
+
+
+def test_spread_interp_adjoint_on_gpu():
+    shape = (16, 16, 32)
+    d = _desc(shape, 1, h=0.9)
+    q, F, _ = wl.random_blobs(3001, shape, seed=3, h=d.h)
+    v = wl.random_field(shape, seed=4)
+    with mb.Multiblob(d) as sim:
+        f = to_np(sim.spread(q, F))[0]
+        u = to_np(sim.interp(q, v[None]))
+    lhs = d.h ** 3 * np.sum(f * v)
+    rhs = np.sum(F * u)
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+
+
+def _projected_field(shape, seed, scale=1.0):
+    nz, ny, nx = shape
+    g = oracle.Grid(nx, ny, nz, rho=1.0, eta=0.0, dt=1.0)
+    return oracle.fluid_update(g, g.zeros(), wl.random_field(shape, seed, scale))
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("shape,h,mean_mode,body", [
+    ((16, 16, 16), 1.0, 0, None), ((8, 16, 32), 0.5, 1, None),
+    ((32, 32, 32), 1.0, 0, (1e-2, 0, 2, 1)), ((16, 8, 64), 1.3, 1, (0.3, 1, 0, 3)),
+    ((4, 8, 4), 2.0, 0, (1.0, 2, 1, 1)),
+])
+def test_fluid_update_parity(prec, shape, h, mean_mode, body):
+    d = _desc(shape, prec, h=h, rho=1.3, eta=0.7, dt=0.05, mean_mode=mean_mode)
+    v = _projected_field(shape, 11).astype(d.grid_dtype).astype(np.float64)
+    f = wl.random_field(shape, 12, scale=0.5).astype(d.grid_dtype).astype(np.float64)
+    with mb.Multiblob(d) as sim:
+        vn = to_np(sim.fluid_update(v[None].astype(d.grid_dtype), f[None].astype(d.grid_dtype),
+                                    body_force=body))[0]
+    ref = oracle.fluid_update(_oracle_grid(d), v, f, body=body)
+    assert rel_l2(vn, ref) < TOL[prec]
+
+
+# ------------------------------------------------------------------------------------------
+# Full step
+
+def _run_gpu(d, susp_list, nsteps, ext_list=None, body=None, v0=None):
+    with mb.Multiblob(d) as sim:
+        for b, s in enumerate(susp_list):
+            sim.set_particles(b, s.pos, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut)
+        if v0 is not None:
+            sim.set_velocity_field(v0.astype(d.grid_dtype))
+        ext = None
+        if ext_list is not None:
+            ext = np.concatenate(ext_list, axis=0)
+        sim.step(nsteps, ext_blob_force=ext, body_force=body)
+        q = to_np(sim.blob_positions())
+        v = to_np(sim.velocity_field()).astype(np.float64)
+        u = to_np(sim.blob_velocities())
+        U, W = sim.particle_velocities()
+        return q, v, u, to_np(U), to_np(W)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_step_parity_single_particle(prec):
+    spec, s = wl.single_particle(n=32, a=1.0, seed=1)
+    d = mb.GridDesc(32, 32, 32, h=spec.h, rho=spec.rho, eta=spec.eta, dt=spec.dt,
+                    precision=prec, mean_mode=spec.mean_mode)
+    nsteps = 20
+    q, v, u, U, W = _run_gpu(d, [s], nsteps, ext_list=[s.ext])
+    g = _oracle_grid(d)
+    q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
+                               ext=s.ext)
+    disp_ref = min_image(q_ref - s.pos, g.L)
+    assert rel_l2(min_image(q - s.pos, g.L), disp_ref) < TOL[prec]
+    assert rel_l2(v[0], v_ref) < TOL[prec]
+    u_ref = oracle.interp(g, q_ref, v_ref)
+    assert rel_l2(u, u_ref) < TOL[prec]
+    U_ref, W_ref = oracle.particle_velocities(g, q_ref, u_ref, s.pid, 1)
+    assert rel_l2(U, U_ref) < TOL[prec]
+    assert np.max(np.abs(W - W_ref)) < TOL[prec] * max(np.max(np.abs(W_ref)), np.max(np.abs(U_ref)))
+
+
+def _dense_small(seed=5, n=32, a=2.2, phi=0.40):
+    spec, s = wl.dense_suspension(n=n, a=a, phi=phi, seed=seed, mc_sweeps=3)
+    return spec, s
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_step_parity_dense_with_repulsion(prec):
+    spec, s = _dense_small()
+    d = mb.GridDesc(spec.nx, spec.ny, spec.nz, h=spec.h, rho=spec.rho, eta=spec.eta,
+                    dt=spec.dt, precision=prec, mean_mode=spec.mean_mode)
+    rng = np.random.default_rng(9)
+    ext = rng.normal(scale=1e-3, size=s.pos.shape)
+    # start slightly off the rest shape so springs and repulsion both act
+    s.pos = np.mod(s.pos + rng.normal(scale=0.05, size=s.pos.shape), s.L)
+    nsteps = 3
+    v0 = _projected_field((spec.nz, spec.ny, spec.nx), 21, scale=1e-3)
+    q, v, u, U, W = _run_gpu(d, [s], nsteps, ext_list=[ext], body=s.body, v0=v0[None])
+    g = _oracle_grid(d)
+    v0r = v0.astype(d.grid_dtype).astype(np.float64)
+    q_ref, v_ref = oracle.step(g, nsteps, s.pos, v0r, s.pid, s.bonds, s.rest, s.k_spring,
+                               s.k_rep, s.r_cut, ext=ext, body=s.body)
+    assert rel_l2(min_image(q - s.pos, g.L), min_image(q_ref - s.pos, g.L)) < TOL[prec]
+    assert rel_l2(v[0], v_ref) < TOL[prec]
+
+
+def test_forces_parity_after_step():
+    spec, s = _dense_small(seed=6)
+    d = mb.GridDesc(spec.nx, spec.ny, spec.nz, precision=1, dt=spec.dt)
+    rng = np.random.default_rng(2)
+    s.pos = np.mod(s.pos + rng.normal(scale=0.1, size=s.pos.shape), s.L)
+    ext = rng.normal(size=s.pos.shape)
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut)
+        sim.step(1, ext_blob_force=ext)
+        F, qh = (to_np(x) for x in sim.last_forces())
+    g = _oracle_grid(d)
+    F_ref = ext + oracle.bond_forces(g, qh, s.bonds, s.rest, s.k_spring) \
+        + oracle.pair_forces(g, qh, s.pid, s.k_rep, s.r_cut)
+    assert np.max(np.abs(F - F_ref)) < 1e-10 * np.max(np.abs(F_ref))
+    # repulsion was active
+    assert np.max(np.abs(oracle.pair_forces(g, qh, s.pid, s.k_rep, s.r_cut))) > 0
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_batched_boxes_match_independent_runs(prec):
+    B = 4
+    boxes = []
+    for b in range(B):
+        spec, s = wl.gap_sweep_box(b, n_boxes=B, n=16, a=1.6)
+        boxes.append(s)
+    d = mb.GridDesc(16, 16, 16, batch=B, precision=prec, dt=0.05, mean_mode=0)
+    nsteps = 8
+    q, v, u, U, W = _run_gpu(d, boxes, nsteps, ext_list=[s.ext for s in boxes])
+    g = _oracle_grid(d)
+    off = 0
+    for b, s in enumerate(boxes):
+        q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest,
+                                   s.k_spring, ext=s.ext)
+        qb = q[off:off + s.n_blobs]
+        assert rel_l2(min_image(qb - s.pos, g.L), min_image(q_ref - s.pos, g.L)) < TOL[prec]
+        assert rel_l2(v[b], v_ref) < TOL[prec]
+        off += s.n_blobs
+
+
+# ------------------------------------------------------------------------------------------
+# Edge cases
+
+def test_empty_box_and_single_blob():
+    d = mb.GridDesc(8, 8, 8, batch=2, precision=1)
+    single = wl.Suspension(pos=np.array([[7.999999999, 0.0, 3.5]]),
+                           pid=np.zeros(1, dtype=np.int32),
+                           bonds=np.zeros((0, 2), dtype=np.int32), rest=np.zeros(0),
+                           n_particles=1, a=0.0, L=np.array([8.0, 8, 8]))
+    empty = wl.Suspension(pos=np.zeros((0, 3)), pid=np.zeros(0, dtype=np.int32),
+                          bonds=np.zeros((0, 2), dtype=np.int32), rest=np.zeros(0),
+                          n_particles=0, a=0.0, L=np.array([8.0, 8, 8]))
+    ext = np.array([[0.1, -0.2, 0.05]])
+    q, v, u, U, W = _run_gpu(d, [single, empty], 4, ext_list=[ext, np.zeros((0, 3))])
+    g = _oracle_grid(d)
+    q_ref, v_ref = oracle.step(g, 4, single.pos, g.zeros(), single.pid, single.bonds,
+                               single.rest, 0.0, ext=ext)
+    assert rel_l2(min_image(q - single.pos, g.L), min_image(q_ref - single.pos, g.L)) < 1e-10
+    assert rel_l2(v[0], v_ref) < 1e-10
+    assert np.all(v[1] == 0.0)
+
+
+def test_invalid_calls_leave_state_and_report():
+    d = mb.GridDesc(8, 8, 8, precision=1)
+    with mb.Multiblob(d) as sim:
+        with pytest.raises(mb.MBError) as ei:
+            sim.step(1)
+        assert ei.value.status == 4
+        with pytest.raises(mb.MBError) as ei:
+            sim.set_particles(0, np.zeros((2, 3)), np.zeros(2, dtype=np.int32),
+                              np.array([[0, 5]], dtype=np.int32), np.ones(1), 1.0)
+        assert ei.value.status == 1
+        with pytest.raises(mb.MBError) as ei:
+            sim.set_particles(1, np.zeros((2, 3)), np.zeros(2, dtype=np.int32),
+                              np.zeros((0, 2), dtype=np.int32), np.zeros(0), 1.0)
+        assert ei.value.status == 1
+        with pytest.raises(mb.MBError):
+            sim.step(1, body_force=(1.0, 3, 0, 1))
+
+
+def test_host_buffers_through_the_abi():
+    """The same call with host (numpy) arrays stages through device buffers."""
+    shape = (16, 16, 16)
+    d = _desc(shape, 1)
+    q, F, _ = wl.random_blobs(999, shape, seed=77)
+    ctx = mb.create_grid(d)
+    try:
+        out = np.zeros((1, 3) + shape)
+        mb.spread(ctx, q, F, out)
+        u = np.zeros((999, 3))
+        mb.interp(ctx, q, out, u)
+    finally:
+        mb.destroy(ctx)
+    g = _oracle_grid(d)
+    f_ref = oracle.spread(g, q, F)
+    assert rel_l2(out[0], f_ref) < 1e-12
+    assert rel_l2(u, oracle.interp(g, q, f_ref)) < 1e-12
+
+
+# ------------------------------------------------------------------------------------------
+# Full-size dense workload (128^3, 18,808 particles, 244,504 blobs): operators against the
+# oracle element by element, and one step in the benchmark's configuration through properties.
+
+@pytest.fixture(scope="module")
+def dense128():
+    return wl.dense_suspension()
+
+
+def test_full_size_spread_and_interp(dense128):
+    spec, s = dense128
+    d = mb.GridDesc(128, 128, 128, precision=0)
+    rng = np.random.default_rng(1)
+    F = rng.normal(size=s.pos.shape)
+    with mb.Multiblob(d) as sim:
+        f = to_np(sim.spread(s.pos, F))[0]
+        v = _projected_field((128, 128, 128), 3)
+        u = to_np(sim.interp(s.pos, v[None].astype(np.float32)))
+    g = _oracle_grid(d)
+    assert rel_l2(f, oracle.spread(g, s.pos, F)) < 1e-5
+    assert rel_l2(u, oracle.interp(g, s.pos, v.astype(np.float32).astype(np.float64))) < 1e-5
+
+
+def test_full_size_fluid_update():
+    d = mb.GridDesc(128, 128, 128, precision=0, mean_mode=0)
+    v = _projected_field((128, 128, 128), 5).astype(np.float32)
+    f = wl.random_field((128, 128, 128), 6, scale=0.1).astype(np.float32)
+    body = (1e-4, 0, 2, 1)
+    with mb.Multiblob(d) as sim:
+        vn = to_np(sim.fluid_update(v[None], f[None], body_force=body))[0]
+    ref = oracle.fluid_update(_oracle_grid(d), v.astype(np.float64), f.astype(np.float64), body)
+    assert rel_l2(vn, ref) < 1e-5
+
+
+def test_full_size_step_properties(dense128):
+    spec, s = dense128
+    d = mb.GridDesc(128, 128, 128, precision=0, mean_mode=0, dt=spec.dt)
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut)
+        sim.step(2, body_force=s.body)
+        F, qh = (to_np(x) for x in sim.last_forces())
+        v = to_np(sim.velocity_field())[0].astype(np.float64)
+        q = to_np(sim.blob_positions())
+    g = _oracle_grid(d)
+    # divergence-free fluid (FP32 grid)
+    div = ((np.roll(v[0], -1, 2) - v[0]) + (np.roll(v[1], -1, 1) - v[1])
+           + (np.roll(v[2], -1, 0) - v[2]))
+    assert np.max(np.abs(div)) < 1e-5 * np.max(np.abs(v))
+    # mean momentum: internal forces cancel and the body force has zero mean
+    assert np.max(np.abs(v.mean((1, 2, 3)))) < 1e-5 * np.max(np.abs(v))
+    # forces at the midpoint positions, on a sample of blobs, against the brute-force oracle
+    idx = np.random.default_rng(0).choice(len(qh), 200, replace=False)
+    Fb = oracle.bond_forces(g, qh, s.bonds, s.rest, s.k_spring)[idx]
+    Fp = oracle.pair_forces_subset(g, qh, s.pid, s.k_rep, s.r_cut, idx)
+    assert np.max(np.abs(F[idx] - Fb - Fp)) < 1e-10 * max(1e-12, np.max(np.abs(F[idx])))
+    # the stiff particles stay rigid and every blob moved by a finite amount
+    r = np.linalg.norm(min_image(q[s.bonds[:, 0]] - q[s.bonds[:, 1]], g.L), axis=1)
+    assert np.all(np.isfinite(q)) and np.max(np.abs(r - s.rest) / s.rest) < 1e-3
