@@ -100,6 +100,7 @@ __device__ __forceinline__ int bin_coord(double x, double inv_w, int nc)
     int c = (int)floor(x * inv_w);
     if (c >= nc) c -= nc;
     if (c < 0) c += nc;
+    if (c < 0 || c >= nc) c = 0;   // non-finite position: keep every index in bounds
     return c;
 }
 
@@ -572,15 +573,15 @@ cudaError_t launch_spread(cudaStream_t st, int B, const double* rec, const int32
                           const GridGeo& g, const BinGeo& bg, const int tile[3], R* f)
 {
     const int TX = tile[0], TY = tile[1], TZ = tile[2];
-    int cnt[3], lo;
     int max_rows = 1;
     for (int d = 1; d < 3; ++d) {
-        // the count does not depend on the tile position except through clamping
-        halo_cells(0, tile[d], bg.bs, bg.nc[d], lo, cnt[d]);
-        int c2;
-        halo_cells(tile[d], tile[d], bg.bs, bg.nc[d], lo, c2);
-        if (c2 > cnt[d]) cnt[d] = c2;
-        max_rows *= cnt[d] + 1;
+        int most = 0;
+        for (int T0 = 0; T0 < g.n[d]; T0 += tile[d]) {
+            int lo, cnt;
+            halo_cells(T0, tile[d], bg.bs, bg.nc[d], lo, cnt);
+            most = cnt > most ? cnt : most;
+        }
+        max_rows *= most;
     }
     const int max_ranges = 2 * max_rows;
     const size_t smem = 3 * (size_t)TX * TY * TZ * sizeof(R) + sizeof(int32_t) * (2 * max_ranges + 1);
