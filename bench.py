@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput of the multiblob inertial-coupling step on the dense 128^3 suspension.
+
+Workload: periodic 128^3 MAC grid (h = rho = eta = 1, dt = 0.05), 18,808 filled icosahedra of
+vertex radius 2.2h at volume fraction 0.40 (244,504 blobs), seeded FCC start randomised by
+hard-sphere Monte Carlo, springs k = 100, blob repulsion k_rep = 100 within r_cut = 1h, body
+force 1e-4 sin(2 pi z / L) x_hat.  One step = one full ICM step of every blob and the fluid.
+
+Metric: fluid cell-steps/s (value) and blob-steps/s, FP32 grid path, with the FP64 grid path
+reported beside it.  Device time from CUDA events around each step on the library's stream; the
+L2 cache is flushed (a 256 MiB write) between timed steps, outside the events.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank runs an independent replica (no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID_N = 128
+METRIC = "fluid cell-steps/s at 128^3 (FP32 grid); blob-steps/s and FP64 beside it"
+WORKLOAD = "dense suspension 128^3, a=2.2h, phi=0.40, 18808 particles x 13 blobs"
+
+# Algorithmic bytes moved by each stage per step, per unit (documented in the design doc):
+#   grid real = 4 B (FP32) / 8 B (FP64); half-spectrum complex = 2 reals; blob FP64 vec = 24 B.
+def stage_model(n, nb, rsz, ncell):
+    N = n ** 3
+    grid = 3 * N * rsz                                  # one 3-component grid
+    spec = 3 * n * n * (n // 2 + 1) * 2 * rsz           # one 3-component half spectrum
+    vec = 24 * nb
+    return {
+        "interp_predict": ("hbm", grid + 2 * vec),       # read v, q; write q_half
+        "bin": ("hbm", vec + 3 * 4 * nb + 4 * 4 * ncell), # q_half; cell, rank, slot; counts/scan
+        # q_half, slot, pid, 42/13 bonds x 2 ends x (index + rest); write F and (q, F) record
+        "forces": ("hbm", nb * (24 + 4 + 4 + 2 * 42 / 13 * 12 + 24 + 48)),
+        "force_sum": ("hbm", 0),
+        "spread": ("hbm", 48 * nb + grid),               # sorted (q, F) records; write f
+        "fluid_x_fwd": ("hbm", 2 * grid + spec),         # read v, f; write spectrum
+        "fluid_y_fwd": ("hbm", 2 * spec),
+        "fluid_z_solve": ("hbm", 2 * spec),
+        "fluid_y_inv": ("hbm", 2 * spec),
+        "fluid_x_inv": ("hbm", spec + grid),             # read spectrum; write v
+        "interp_correct": ("hbm", 2 * grid + 3 * vec),   # read v^n, v^{n+1}, q_half, q; write q
+    }
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed steps of the FP64 grid variant (default: min(steps, 10))")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--stage-json", default=None, help="also write per-stage times here")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        smax = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------------------------
+def oracle_sample(max_seconds=20.0, min_steps=2):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload: the same
+    suspension recipe (a, phi, springs, repulsion, body force) in a 64^3 box, stepped until
+    about max_seconds of CPU time.  Returns (cell-steps/s, blob-steps/s, steps, seconds, blobs)."""
+    import oracle
+    from paper_1407_5600_gb300 import workloads as wl
+
+    spec, s = wl.dense_suspension(n=64, seed=3)
+    g = oracle.Grid(spec.nx, spec.ny, spec.nz, h=spec.h, rho=spec.rho, eta=spec.eta,
+                    dt=spec.dt, mean_mode=spec.mean_mode)
+    q, v = s.pos, g.zeros()
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        q, v = oracle.step(g, 1, q, v, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut,
+                           body=s.body)
+        steps += 1
+        el = time.perf_counter() - t0
+        if steps >= min_steps and el >= max_seconds * 0.5 or el >= max_seconds:
+            break
+    cells = spec.nx * spec.ny * spec.nz
+    return cells * steps / el, s.n_blobs * steps / el, steps, el, s.n_blobs
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    if args.warmup:
+        oracle_sample(max_seconds=1.0, min_steps=1)
+    cps, bps, steps, el, nblobs = oracle_sample(max_seconds=max(10.0, 3.0 * args.steps),
+                                                min_steps=max(1, args.steps // 10))
+    sample = (f"{steps} oracle steps of the same suspension recipe in a 64^3 box "
+              f"({nblobs} blobs), {el:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": cps, "unit": "cell-steps/s",
+            "n_gpus": 0, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "64^3 box of the same recipe"},
+            "blob_steps_per_s": bps,
+            "cpu_baseline": {"value": cps, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": cps, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    import paper_1407_5600_gb300 as mb
+    from paper_1407_5600_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    spec, s = wl.dense_suspension(n=GRID_N, seed=3 + rank)
+    n, nb = GRID_N, s.n_blobs
+    cells = n ** 3
+
+    def make(prec):
+        sim = mb.Multiblob(mb.GridDesc(n, n, n, precision=prec, dt=spec.dt, rho=spec.rho,
+                                       eta=spec.eta, h=spec.h, mean_mode=spec.mean_mode),
+                           stream=stream, device=dev)
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut)
+        return sim
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+
+    def timed_steps(sim, K, stage_timing):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+        if stage_timing:
+            mb.set_stage_timing(sim.ctx, True)
+        l0 = mb.get_launch_count(sim.ctx)
+        barrier()
+        for i in range(K):
+            flush.fill_(i & 0xFF)                     # evict L2 between timed steps
+            evs[i][0].record(stream)
+            mb.step(sim.ctx, 1, None, s.body)
+            evs[i][1].record(stream)
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        launches = mb.get_launch_count(sim.ctx) - l0
+        stages = mb.get_stage_times(sim.ctx) if stage_timing else None
+        if stage_timing:
+            mb.set_stage_timing(sim.ctx, False)
+        return ms, launches, stages
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- FP32 grid (the headline) -------------------------------------------------------
+    sim = make(0)
+    for _ in range(args.warmup):
+        mb.step(sim.ctx, 1, None, s.body)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches, stages = timed_steps(sim, args.steps, True)
+    clocks.stop()
+    ms = max_over_ranks(ms)
+    ms_step = ms / args.steps
+    value = world * cells * args.steps / (ms * 1e-3)
+    blob_value = world * nb * args.steps / (ms * 1e-3)
+
+    # ---- roofline of the dominant kernel -----------------------------------------------
+    ncell = (n // 2) ** 3
+    model = stage_model(n, nb, 4, ncell)
+    per_stage = {k: {"ms_per_step": v[0] / max(v[1], 1)} for k, v in stages.items()}
+    single_kernel = [k for k in per_stage if k not in ("bin", "force_sum")]
+    dom = max(single_kernel, key=lambda k: per_stage[k]["ms_per_step"])
+    peak, peak_kind = peaks()
+    for k, d in per_stage.items():
+        bound, byts = model[k]
+        d["algorithmic_MB"] = byts / 1e6
+        d["GBps"] = byts / (d["ms_per_step"] * 1e-3) / 1e9 if d["ms_per_step"] > 0 else None
+        d["frac_hbm"] = d["GBps"] / peak if d["GBps"] else None
+    achieved = per_stage[dom]["GBps"]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None,
+                "algorithmic_bytes": model[dom][1]}
+    step_bytes = sum(model[k][1] for k in model)
+    step_frac = step_bytes / (ms_step * 1e-3) / 1e9 / peak
+
+    # ---- end to end through the C ABI with pinned host buffers ---------------------------
+    ext_h = torch.zeros((nb, 3), dtype=torch.float64).pin_memory().numpy()
+    u_h = torch.empty((nb, 3), dtype=torch.float64).pin_memory().numpy()
+    K_e2e = max(3, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K_e2e):
+        mb.step(sim.ctx, 1, ext_h, s.body)           # H2D of the step's blob forces
+        mb.get_velocities(sim.ctx, blob_vel=u_h)      # D2H of the step's blob velocities
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * cells * K_e2e / e2e_s, "unit": "cell-steps/s",
+           "h2d_bytes_per_step": int(ext_h.nbytes), "d2h_bytes_per_step": int(u_h.nbytes),
+           "blob_steps_per_s": world * nb * K_e2e / e2e_s,
+           "note": "mb_step with external blob forces in pinned host memory + mb_get_velocities "
+                   "into pinned host memory every step (zero external force in this workload)"}
+    sim.close()
+
+    # ---- FP64 grid variant --------------------------------------------------------------
+    K64 = args.fp64_steps if args.fp64_steps is not None else min(args.steps, 10)
+    fp64 = None
+    if K64 > 0:
+        sim64 = make(1)
+        for _ in range(max(1, min(args.warmup, 3))):
+            mb.step(sim64.ctx, 1, None, s.body)
+        ms64, _, stages64 = timed_steps(sim64, K64, True)
+        ms64 = max_over_ranks(ms64)
+        sim64.close()
+        fp64 = {"value": world * cells * K64 / (ms64 * 1e-3), "unit": "cell-steps/s",
+                "blob_steps_per_s": world * nb * K64 / (ms64 * 1e-3),
+                "ms_per_step": ms64 / K64, "steps": K64,
+                "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stages64.items()}}
+
+    # ---- CPU baseline (oracle, rank 0, N = 1 only) ---------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        cps, bps, st, el, nbl = oracle_sample()
+        cpu = {"value": cps, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+               "blob_steps_per_s": bps,
+               "sample": f"{st} FP64 oracle steps (single thread) of the same suspension recipe "
+                         f"in a 64^3 box ({nbl} blobs), {el:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "128^3 MAC, h=rho=eta=1, dt=0.05",
+                       "blobs": nb, "particles": s.n_particles, "precision":
+                       "FP32 grid/spread/interp/FFT; FP64 positions, forces, mean mode",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MiB write outside the events)"},
+            "blob_steps_per_s": blob_value,
+            "step_hbm_frac": step_frac,
+            "roofline": roofline,
+            "stages": per_stage,
+            "fp64": fp64,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+        if args.stage_json:
+            with open(args.stage_json, "w") as f:
+                json.dump(line, f, indent=1)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

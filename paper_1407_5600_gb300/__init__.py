@@ -19,7 +19,8 @@ import numpy as np
 __all__ = [
     "GridDesc", "MBError", "load_library", "create_grid", "destroy", "set_particles", "step",
     "get_velocities", "get_particle_velocities", "set_velocity_field", "spread", "interp",
-    "fluid_update", "get_counts", "get_forces", "last_error", "Multiblob",
+    "fluid_update", "get_counts", "get_forces", "set_stage_timing", "get_stage_times",
+    "get_launch_count", "last_error", "Multiblob",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -99,11 +100,16 @@ def load_library(path: str | None = None):
         "mb_fluid_update": [P, P, P, P, P],
         "mb_get_counts": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "mb_get_forces": [P, P, P],
+        "mb_set_stage_timing": [P, I],
+        "mb_get_stage_times": [P, I, P, P, ctypes.POINTER(I)],
+        "mb_get_launch_count": [P, ctypes.POINTER(I64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.mb_stage_name.argtypes = [I]
+    lib.mb_stage_name.restype = ctypes.c_char_p
     lib.mb_last_error.argtypes = [P]
     lib.mb_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -212,6 +218,26 @@ def fluid_update(ctx, v_in, f, v_out, body_force=None):
 def get_forces(ctx, blob_force=None, midpoint_pos=None):
     _check(ctx, load_library().mb_get_forces(ctx, _ptr(blob_force, np.float64),
                                              _ptr(midpoint_pos, np.float64)))
+
+
+def set_stage_timing(ctx, enable=True):
+    _check(ctx, load_library().mb_set_stage_timing(ctx, int(bool(enable))))
+
+
+def get_stage_times(ctx):
+    """{stage name: (total ms, calls)} accumulated since timing was enabled."""
+    lib = load_library()
+    n = ctypes.c_int()
+    ms = (ctypes.c_double * 64)()
+    calls = (ctypes.c_int64 * 64)()
+    _check(ctx, lib.mb_get_stage_times(ctx, 64, ms, calls, ctypes.byref(n)))
+    return {lib.mb_stage_name(i).decode(): (ms[i], calls[i]) for i in range(n.value)}
+
+
+def get_launch_count(ctx):
+    n = ctypes.c_int64()
+    _check(ctx, load_library().mb_get_launch_count(ctx, ctypes.byref(n)))
+    return n.value
 
 
 def get_counts(ctx):

@@ -263,7 +263,8 @@ k_fft_x_c2r(FluidArgs<R> a, GridGeo g, int RP)
 }
 
 template <typename R>
-cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a)
+cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a,
+                         cudaEvent_t* marks)
 {
     using T = typename C2<R>::T;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
@@ -283,16 +284,23 @@ cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidAr
     const size_t smem_y = (size_t)ny * C * sizeof(T);
     const size_t smem_z = (size_t)3 * nz * C * sizeof(T);
     const unsigned nchunk = (unsigned)((nxh + C - 1) / C);
+    auto mark = [&](int i) { if (marks) cudaEventRecord(marks[i], st); };
+    mark(0);
     k_rhs_fft_x<R><<<dim3(ny / 2 / RP, nz, 3 * B), 256, smem_x, st>>>(a, g, RP);
+    mark(1);
     k_fft_y<R><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.tw[1], g, C, false);
+    mark(2);
     k_fft_z_solve<R><<<dim3(nchunk, ny, B), 256, smem_z, st>>>(a, g, C);
+    mark(3);
     k_fft_y<R><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.tw[1], g, C, true);
+    mark(4);
     k_fft_x_c2r<R><<<dim3(ny / 2 / RP, nz, 3 * B), 256, smem_x, st>>>(a, g, RP);
+    mark(5);
     return cudaGetLastError();
 }
 template cudaError_t launch_fluid<float>(cudaStream_t, int, const GridGeo&,
-                                         const FluidArgs<float>&);
+                                         const FluidArgs<float>&, cudaEvent_t*);
 template cudaError_t launch_fluid<double>(cudaStream_t, int, const GridGeo&,
-                                          const FluidArgs<double>&);
+                                          const FluidArgs<double>&, cudaEvent_t*);
 
 }  // namespace mbk

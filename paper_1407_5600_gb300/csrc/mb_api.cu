@@ -17,6 +17,16 @@ namespace {
 
 constexpr int SYM_LEN = 256;   // per-dimension symbol table length (n <= 128 today)
 
+// Stages of one step, in launch order (names returned by mb_stage_name).
+enum Stage {
+    ST_INTERP_PREDICT, ST_BIN, ST_FORCES, ST_FORCE_SUM, ST_SPREAD, ST_FLUID_X_FWD,
+    ST_FLUID_Y_FWD, ST_FLUID_Z_SOLVE, ST_FLUID_Y_INV, ST_FLUID_X_INV, ST_INTERP_CORRECT,
+    NUM_STAGES
+};
+const char* const STAGE_NAMES[NUM_STAGES] = {
+    "interp_predict", "bin", "forces", "force_sum", "spread", "fluid_x_fwd", "fluid_y_fwd",
+    "fluid_z_solve", "fluid_y_inv", "fluid_x_inv", "interp_correct"};
+
 thread_local std::string g_create_error;
 
 // Host-side fault injection: MB_FAULT_ALLOC=k makes the k-th device allocation of the
@@ -121,6 +131,13 @@ struct mb_ctx {
     // standalone-operator scratch
     DBuf s_q, s_F, s_rec, s_cell_count, s_cell_start, s_blob_cell, s_blob_rank, s_sorted,
         s_scan, s_u, s_g0, s_g1, s_g2, s_out;
+
+    // stage timing (CUDA events on the context stream) and kernel launch count
+    bool timing = false;
+    cudaEvent_t ev[NUM_STAGES + 1] = {};
+    double stage_ms[NUM_STAGES] = {};
+    int64_t stage_calls[NUM_STAGES] = {};
+    int64_t launches = 0;
 
     std::string err;
 };
@@ -438,10 +455,16 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
     double* qh = static_cast<double*>(ctx->qh.p);
     const int32_t* box_of = static_cast<const int32_t*>(ctx->box_of.p);
     const bool blobs = ctx->nb > 0;
+    auto mark = [&](int i) { if (ctx->timing) cudaEventRecord(ctx->ev[i], st); };
+    mark(ST_INTERP_PREDICT);
     if (blobs) {
         // u^n = J(q^n) v^n ; q^{n+1/2} = q^n + dt/2 u^n
         MB_CUDA(launch_interp<R>(st, 1, ctx->nb, q, nullptr, vcur, nullptr, box_of, g,
                                  ctx->d.dt, nullptr, qh));
+        ctx->launches += 1;
+    }
+    mark(ST_BIN);
+    if (blobs) {
         MB_CUDA(launch_bin(st, ctx->nb, qh, box_of, B, ctx->bg,
                            static_cast<int32_t*>(ctx->cell_count.p),
                            static_cast<int32_t*>(ctx->cell_start.p),
@@ -449,6 +472,10 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
                            static_cast<int32_t*>(ctx->blob_rank.p),
                            static_cast<int32_t*>(ctx->sorted.p),
                            static_cast<int32_t*>(ctx->scan_tmp.p), ctx->d.deterministic != 0));
+        ctx->launches += 5 + (ctx->d.deterministic != 0);
+    }
+    mark(ST_FORCES);
+    if (blobs) {
         ForceArgs fa{};
         fa.box_off = static_cast<const int64_t*>(ctx->box_off.p);
         fa.sorted = static_cast<const int32_t*>(ctx->sorted.p);
@@ -466,23 +493,44 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
         fa.partial = static_cast<double*>(ctx->partial.p);
         fa.nchunk = ctx->nchunk;
         MB_CUDA(launch_forces(st, B, ctx->max_box_blobs, fa, g, ctx->bg));
+        ctx->launches += 1;
+    }
+    mark(ST_FORCE_SUM);
+    if (blobs) {
         const double L3 = g.L[0] * g.L[1] * g.L[2];
         MB_CUDA(launch_force_sum(st, B, ctx->nchunk, static_cast<const double*>(ctx->partial.p),
                                  static_cast<double*>(ctx->vbar.p),
                                  ctx->d.dt / (ctx->d.rho * L3), ctx->d.mean_mode,
                                  static_cast<double*>(ctx->fsum.p)));
+        ctx->launches += 1;
+    }
+    mark(ST_SPREAD);
+    if (blobs) {
         MB_CUDA(launch_spread<R>(st, B, static_cast<const double*>(ctx->rec.p),
                                  static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
                                  ctx->tile, static_cast<R*>(ctx->f.p)));
+        ctx->launches += 1;
     }
     const double* mean = ctx->d.mean_mode == 0 ? static_cast<const double*>(ctx->vbar.p) : nullptr;
     FluidArgs<R> fa = fluid_args<R>(ctx, vcur, blobs ? ctx->f.p : nullptr, vnext,
                                     ctx->body_prof.p, body, mean);
-    MB_CUDA(launch_fluid<R>(st, B, g, fa));
+    MB_CUDA(launch_fluid<R>(st, B, g, fa, ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr));
+    ctx->launches += FLUID_KERNELS;
     if (blobs) {
         // q^{n+1} = q^n + dt J(q^{n+1/2}) (v^n + v^{n+1})/2
         MB_CUDA(launch_interp<R>(st, 2, ctx->nb, qh, q, vcur, vnext, box_of, g, ctx->d.dt,
                                  nullptr, q));
+        ctx->launches += 1;
+    }
+    mark(NUM_STAGES);
+    if (ctx->timing) {
+        MB_CUDA(cudaEventSynchronize(ctx->ev[NUM_STAGES]));
+        for (int i = 0; i < NUM_STAGES; ++i) {
+            float ms = 0.f;
+            MB_CUDA(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+            ctx->stage_ms[i] += ms;
+            ctx->stage_calls[i] += 1;
+        }
     }
     ctx->cur ^= 1;
     ctx->steps_taken++;
@@ -542,6 +590,11 @@ void release(mb_ctx* ctx)
                    &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
                    &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out};
     for (DBuf* b : all) dfree(*b);
+    for (cudaEvent_t& e : ctx->ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
 }
 
 // Standalone spreading of n blobs into one box grid `out_dev` (device pointer).
@@ -802,6 +855,44 @@ mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos)
         MB_CUDA(cudaMemcpyAsync(dst, srcs[i]->p, by, cudaMemcpyDeviceToDevice, ctx->st));
         MB_TRY(finish_out(ctx, outs[i], dst, by, host));
     }
+    return MB_OK;
+}
+
+mb_status mb_set_stage_timing(mb_ctx* ctx, int enable)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (enable && !ctx->ev[0])
+        for (cudaEvent_t& e : ctx->ev) MB_CUDA(cudaEventCreate(&e));
+    ctx->timing = enable != 0;
+    for (int i = 0; i < NUM_STAGES; ++i) {
+        ctx->stage_ms[i] = 0.0;
+        ctx->stage_calls[i] = 0;
+    }
+    return MB_OK;
+}
+
+mb_status mb_get_stage_times(const mb_ctx* ctx, int max_stages, double* ms_total,
+                             int64_t* calls, int* n_stages)
+{
+    if (!ctx || max_stages < 0) return MB_EINVAL;
+    if (n_stages) *n_stages = NUM_STAGES;
+    for (int i = 0; i < NUM_STAGES && i < max_stages; ++i) {
+        if (ms_total) ms_total[i] = ctx->stage_ms[i];
+        if (calls) calls[i] = ctx->stage_calls[i];
+    }
+    return MB_OK;
+}
+
+const char* mb_stage_name(int stage)
+{
+    return stage >= 0 && stage < NUM_STAGES ? STAGE_NAMES[stage] : "";
+}
+
+mb_status mb_get_launch_count(const mb_ctx* ctx, int64_t* launches)
+{
+    if (!ctx || !launches) return MB_EINVAL;
+    *launches = ctx->launches;
     return MB_OK;
 }
 

@@ -109,8 +109,11 @@ struct FluidArgs {
     int mean_mode;
     double rho_dt, half_eta;
 };
+// marks: null, or 6 events recorded before pass 1 and after each of the 5 passes.
 template <typename R>
-cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a);
+cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a,
+                         cudaEvent_t* marks = nullptr);
+constexpr int FLUID_KERNELS = 5;
 
 // Reductions / utilities.
 template <typename R>

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import TOL, min_image, rel_l2, to_np
+from helpers import TOL, min_image, position_error, rel_l2, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -130,8 +130,7 @@ def test_step_parity_single_particle(prec):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
                                ext=s.ext)
-    disp_ref = min_image(q_ref - s.pos, g.L)
-    assert rel_l2(min_image(q - s.pos, g.L), disp_ref) < TOL[prec]
+    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
     assert rel_l2(v[0], v_ref) < TOL[prec]
     u_ref = oracle.interp(g, q_ref, v_ref)
     assert rel_l2(u, u_ref) < TOL[prec]
@@ -161,7 +160,7 @@ def test_step_parity_dense_with_repulsion(prec):
     v0r = v0.astype(d.grid_dtype).astype(np.float64)
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, v0r, s.pid, s.bonds, s.rest, s.k_spring,
                                s.k_rep, s.r_cut, ext=ext, body=s.body)
-    assert rel_l2(min_image(q - s.pos, g.L), min_image(q_ref - s.pos, g.L)) < TOL[prec]
+    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
     assert rel_l2(v[0], v_ref) < TOL[prec]
 
 
@@ -199,7 +198,7 @@ def test_batched_boxes_match_independent_runs(prec):
         q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest,
                                    s.k_spring, ext=s.ext)
         qb = q[off:off + s.n_blobs]
-        assert rel_l2(min_image(qb - s.pos, g.L), min_image(q_ref - s.pos, g.L)) < TOL[prec]
+        assert position_error(qb, q_ref, s.pos, g.L, nsteps) < TOL[prec]
         assert rel_l2(v[b], v_ref) < TOL[prec]
         off += s.n_blobs
 
@@ -221,7 +220,7 @@ def test_empty_box_and_single_blob():
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.step(g, 4, single.pos, g.zeros(), single.pid, single.bonds,
                                single.rest, 0.0, ext=ext)
-    assert rel_l2(min_image(q - single.pos, g.L), min_image(q_ref - single.pos, g.L)) < 1e-10
+    assert position_error(q, q_ref, single.pos, g.L, 4) < 1e-10
     assert rel_l2(v[0], v_ref) < 1e-10
     assert np.all(v[1] == 0.0)
 
