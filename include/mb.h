@@ -174,8 +174,28 @@ mb_status mb_get_launch_count(const mb_ctx* ctx, int64_t* launches);
 /* Number of blobs and particles of all boxes together. */
 mb_status mb_get_counts(const mb_ctx* ctx, int64_t* total_blobs, int64_t* total_particles);
 
-/* Message of the last error on ctx (or of the last failed mb_create_grid when ctx is NULL).
- * The string stays valid until the next call on ctx. */
+/* Spreading that allocates nothing.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory (a plugin running inside another framework's
+ * memory budget, or code that must not trigger an allocation mid-run).  It needs no context:
+ * it computes the same grid_out = sum_i delta_h(r - q_i) F_i as mb_spread, for one box of the
+ * geometry in *desc (only nx, ny, nz, h and precision are read), using a fixed scratch array
+ * compiled into the library instead of buffers it would otherwise have to allocate.
+ *   pos, F       [n][3] FP64 DEVICE arrays (positions are taken modulo the box).
+ *   grid_out     one box grid (3 components, desc->precision) in DEVICE memory, overwritten.
+ *   cuda_stream  stream the work is enqueued on (NULL = legacy default stream).
+ * Limits: 0 <= n <= 262144 blobs, grids up to 128^3; larger sizes and host pointers are
+ * rejected with MB_EINVAL.  The scratch array (about 5 MiB) is held by every GPU that loads
+ * the library until the process exits.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  Every call reuses the same array, so calls that overlap on the GPU (on different
+ * streams, or from different threads) race and corrupt each other's results.  Errors are
+ * reported through mb_last_error(NULL). */
+mb_status mb_spread_static(const mb_grid_desc* desc, int64_t n, const double* pos,
+                           const double* F, void* grid_out, void* cuda_stream);
+
+/* Message of the last error on ctx (or, when ctx is NULL, of the last failed context-free
+ * call: mb_create_grid or mb_spread_static).  The string stays valid until the next call on
+ * ctx. */
 const char* mb_last_error(const mb_ctx* ctx);
 
 #ifdef __cplusplus

@@ -18,7 +18,8 @@ import numpy as np
 
 __all__ = [
     "GridDesc", "MBError", "load_library", "create_grid", "destroy", "set_particles", "step",
-    "get_velocities", "get_particle_velocities", "set_velocity_field", "spread", "interp",
+    "get_velocities", "get_particle_velocities", "set_velocity_field", "spread", "spread_static",
+    "interp",
     "fluid_update", "get_counts", "get_forces", "set_stage_timing", "get_stage_times",
     "get_launch_count", "last_error", "Multiblob",
 ]
@@ -100,6 +101,7 @@ def load_library(path: str | None = None):
         "mb_fluid_update": [P, P, P, P, P],
         "mb_get_counts": [P, ctypes.POINTER(I64), ctypes.POINTER(I64)],
         "mb_get_forces": [P, P, P],
+        "mb_spread_static": [ctypes.POINTER(_Desc), I64, P, P, P, P],
         "mb_set_stage_timing": [P, I],
         "mb_get_stage_times": [P, I, P, P, ctypes.POINTER(I)],
         "mb_get_launch_count": [P, ctypes.POINTER(I64)],
@@ -200,6 +202,14 @@ def set_velocity_field(ctx, grid_v):
 def spread(ctx, pos, F, grid_out):
     _check(ctx, load_library().mb_spread(ctx, int(pos.shape[0]), _ptr(pos, np.float64),
                                          _ptr(F, np.float64), _ptr(grid_out)))
+
+
+def spread_static(desc: GridDesc, pos, F, grid_out, stream=None):
+    """mb_spread_static: spreading without any allocation (device arrays only, no context)."""
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(None, load_library().mb_spread_static(ctypes.byref(desc._c()), int(pos.shape[0]),
+                                                 _ptr(pos, np.float64), _ptr(F, np.float64),
+                                                 _ptr(grid_out), s))
 
 
 def interp(ctx, pos, grid_v, u_out):

@@ -646,6 +646,11 @@ mb_status standalone_spread(mb_ctx* ctx, int64_t n, const double* qd, const doub
 
 }  // namespace
 
+namespace mbk {
+// Error of the last failed context-free call, reported by mb_last_error(NULL).
+void set_context_free_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace mbk
+
 // ==========================================================================================
 extern "C" {
 
