@@ -157,14 +157,15 @@ mb_status mb_fluid_update(mb_ctx* ctx, const void* v_in, const void* f,
 mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos);
 
 /* Per-stage device timing for profiling.  With timing enabled, mb_step records a CUDA event
- * on the context stream between consecutive stages of every step and synchronises the stream
- * after each step to accumulate the elapsed times.  Enabling (or disabling) resets the totals.
- * mb_get_stage_times copies up to max_stages totals (milliseconds) and call counts, and sets
- * *n_stages to the number of stages; mb_stage_name gives a stage's name ("" if out of range).
+ * on the context stream between consecutive stages of every step (no synchronisation; every
+ * 64th step waits for the previous 64 to finish and accumulates their times).  Enabling (or
+ * disabling) resets the totals.  mb_get_stage_times waits for the recorded steps, then copies
+ * up to max_stages totals (milliseconds) and call counts, and sets *n_stages to the number of
+ * stages; mb_stage_name gives a stage's name ("" if out of range).
  * Stages, in launch order: interp_predict, bin, forces, force_sum, spread, fluid_x_fwd,
  * fluid_y_fwd, fluid_z_solve, fluid_y_inv, fluid_x_inv, interp_correct. */
 mb_status mb_set_stage_timing(mb_ctx* ctx, int enable);
-mb_status mb_get_stage_times(const mb_ctx* ctx, int max_stages, double* ms_total,
+mb_status mb_get_stage_times(mb_ctx* ctx, int max_stages, double* ms_total,
                              int64_t* calls, int* n_stages);
 const char* mb_stage_name(int stage);
 

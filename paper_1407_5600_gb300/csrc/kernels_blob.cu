@@ -50,18 +50,19 @@ k_interp(int64_t nb, const double* __restrict__ q, const double* __restrict__ q_
         }
         u[a] = MODE == 2 ? 0.5 * (double)acc : (double)acc;
     }
+    // position updates round like the plain expression q + (c dt) u (no contraction)
     if (MODE == 0) {
         for (int a = 0; a < 3; ++a) u_out[3 * b + a] = u[a];
     } else if (MODE == 1) {
         for (int a = 0; a < 3; ++a) {
             if (u_out) u_out[3 * b + a] = u[a];
-            q_out[3 * b + a] = wrap_position(p[a] + 0.5 * dt * u[a], g.L[a]);
+            q_out[3 * b + a] = wrap_position(__dadd_rn(p[a], __dmul_rn(0.5 * dt, u[a])), g.L[a]);
         }
     } else {
         for (int a = 0; a < 3; ++a) {
             const double qb = q_base[3 * b + a];
             if (u_out) u_out[3 * b + a] = u[a];
-            q_out[3 * b + a] = wrap_position(qb + dt * u[a], g.L[a]);
+            q_out[3 * b + a] = wrap_position(__dadd_rn(qb, __dmul_rn(dt, u[a])), g.L[a]);
         }
     }
 }
@@ -208,13 +209,29 @@ __global__ void k_scan_add(int32_t* __restrict__ out, int64_t n,
     if (i < n) out[i] += tile_offsets[i / SCAN_TILE];
 }
 
+// Scatter into sorted order; optionally record each blob's position relative to the lower
+// corner of its bin cell (FP32, |x| < cell side) and its particle id, for the FP32 prefilter of
+// the pair search.
 __global__ void k_bin_scatter(int64_t nb, const int32_t* __restrict__ blob_cell,
                               const int32_t* __restrict__ blob_rank,
-                              const int32_t* __restrict__ cell_start, int32_t* __restrict__ sorted)
+                              const int32_t* __restrict__ cell_start, int32_t* __restrict__ sorted,
+                              const double* __restrict__ q, const int32_t* __restrict__ pid,
+                              BinGeo bg, float4* __restrict__ loc)
 {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nb) return;
-    sorted[cell_start[blob_cell[b]] + blob_rank[b]] = (int32_t)b;
+    const int cell = blob_cell[b];
+    const int slot = cell_start[cell] + blob_rank[b];
+    sorted[slot] = (int32_t)b;
+    if (loc) {
+        const int local = (int)(cell % bg.ncell);
+        const int c[3] = {local % bg.nc[0], (local / bg.nc[0]) % bg.nc[1],
+                          local / (bg.nc[0] * bg.nc[1])};
+        const double w = 1.0 / bg.inv_w;   // cell side
+        float r[3];
+        for (int d = 0; d < 3; ++d) r[d] = (float)(q[3 * b + d] - c[d] * w);
+        loc[slot] = make_float4(r[0], r[1], r[2], __int_as_float(pid ? pid[b] : 0));
+    }
 }
 
 // Deterministic order inside each cell: ascending blob index (cells hold a handful of blobs).
@@ -235,10 +252,27 @@ __global__ void k_cell_order(int64_t ncells, const int32_t* __restrict__ cell_st
     }
 }
 
+// Cell-local coordinates in the final (reordered) slot order.
+__global__ void k_fill_loc(int64_t nb, const int32_t* __restrict__ sorted,
+                           const int32_t* __restrict__ blob_cell, const double* __restrict__ q,
+                           const int32_t* __restrict__ pid, BinGeo bg, float4* __restrict__ loc)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    const int b = sorted[t];
+    const int local = (int)(blob_cell[b] % bg.ncell);
+    const int c[3] = {local % bg.nc[0], (local / bg.nc[0]) % bg.nc[1],
+                      local / (bg.nc[0] * bg.nc[1])};
+    const double w = 1.0 / bg.inv_w;
+    float r[3];
+    for (int d = 0; d < 3; ++d) r[d] = (float)(q[3 * b + d] - c[d] * w);
+    loc[t] = make_float4(r[0], r[1], r[2], __int_as_float(pid ? pid[b] : 0));
+}
+
 cudaError_t launch_bin(cudaStream_t st, int64_t nb, const double* q, const int32_t* box_of,
                        int B, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
                        int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
-                       int32_t* scan_tmp, bool deterministic)
+                       int32_t* scan_tmp, bool deterministic, const int32_t* pid, float4* loc)
 {
     const int64_t ncells = (int64_t)B * bg.ncell;
     cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, st);
@@ -253,9 +287,14 @@ cudaError_t launch_bin(cudaStream_t st, int64_t nb, const double* q, const int32
     k_scan_add<<<(unsigned)((ncells + T - 1) / T), T, 0, st>>>(cell_start, ncells, scan_tmp);
     if (nb > 0)
         k_bin_scatter<<<(unsigned)((nb + T - 1) / T), T, 0, st>>>(nb, blob_cell, blob_rank,
-                                                                  cell_start, sorted);
-    if (deterministic)
+                                                                  cell_start, sorted, q, pid, bg,
+                                                                  deterministic ? nullptr : loc);
+    if (deterministic) {
         k_cell_order<<<(unsigned)((ncells + T - 1) / T), T, 0, st>>>(ncells, cell_start, sorted);
+        if (loc && nb > 0)
+            k_fill_loc<<<(unsigned)((nb + T - 1) / T), T, 0, st>>>(nb, sorted, blob_cell, q, pid,
+                                                                   bg, loc);
+    }
     return cudaGetLastError();
 }
 
@@ -287,6 +326,63 @@ __device__ __forceinline__ void block_sum3(double v[3], double* sh /*[3][32]*/)
     }
 }
 
+// Spring force on blob b from bond (b, j): -k (|r| - r0) r/|r|, r = q_b - q_j (minimum image).
+// PRECISE: FP64 with the operations in the plain order and no contraction, so that a blob's
+// spring force is the same bits however the work is scheduled.  Otherwise: r, |r|^2 and
+// |r|^2 - r0^2 in FP64 (the only cancellation), the rest in FP32, accumulated in FP64.
+template <bool PRECISE>
+__device__ __forceinline__ void spring_term(const double qb[3], const double* __restrict__ qj,
+                                            double r0, double k, const double L[3],
+                                            const double halfL[3], double F[3])
+{
+    double r[3];
+    for (int d = 0; d < 3; ++d) {
+        double x = __dsub_rn(qb[d], qj[d]);
+        if (x > halfL[d]) x = __dsub_rn(x, L[d]);
+        else if (x < -halfL[d]) x = __dadd_rn(x, L[d]);
+        r[d] = x;
+    }
+    if (PRECISE) {
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])),
+                                    __dmul_rn(r[2], r[2]));
+        const double len = __dsqrt_rn(r2);
+        const double mag = __ddiv_rn(__dmul_rn(-k, __dsub_rn(len, r0)), len);
+        for (int d = 0; d < 3; ++d) F[d] = __dadd_rn(F[d], __dmul_rn(mag, r[d]));
+    } else {
+        const double r2 = fma(r[0], r[0], fma(r[1], r[1], r[2] * r[2]));
+        const float d2 = (float)(r2 - r0 * r0);               // |r|^2 - r0^2
+        const float len = sqrtf((float)r2);
+        const float mag = -(float)k * d2 / ((len + (float)r0) * len);
+        for (int d = 0; d < 3; ++d) F[d] += (double)(mag * (float)r[d]);
+    }
+}
+
+// Repulsion k_rep (r_cut - |r|) r/|r| for |r| < r_cut, r = q_b - q_j.
+template <bool PRECISE>
+__device__ __forceinline__ void pair_term(const double qb[3], const double* __restrict__ qj,
+                                          const float rf[3], double k_rep, double r_cut,
+                                          const double L[3], double Fp[3])
+{
+    if (PRECISE) {
+        double r[3];
+        for (int d = 0; d < 3; ++d) r[d] = min_image(__dsub_rn(qb[d], qj[d]), L[d]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])),
+                                    __dmul_rn(r[2], r[2]));
+        if (r2 >= r_cut * r_cut || r2 == 0.0) return;
+        const double len = __dsqrt_rn(r2);
+        const double mag = __ddiv_rn(__dmul_rn(k_rep, __dsub_rn(r_cut, len)), len);
+        for (int d = 0; d < 3; ++d) Fp[d] = __dadd_rn(Fp[d], __dmul_rn(mag, r[d]));
+    } else {
+        const float r2 = rf[0] * rf[0] + rf[1] * rf[1] + rf[2] * rf[2];
+        const float rc = (float)r_cut;
+        if (r2 >= rc * rc || r2 == 0.0f) return;
+        const float len = sqrtf(r2);
+        const float mag = (float)k_rep * (rc - len) / len;
+        for (int d = 0; d < 3; ++d) Fp[d] += (double)(mag * rf[d]);
+    }
+}
+
+template <bool PRECISE>
 __global__ void __launch_bounds__(256)
 k_forces(ForceArgs a, GridGeo g, BinGeo bg)
 {
@@ -299,6 +395,7 @@ k_forces(ForceArgs a, GridGeo g, BinGeo bg)
         const int64_t slot = s0 + local;
         const int b = a.sorted[slot];
         const double qb[3] = {a.q[3 * b], a.q[3 * b + 1], a.q[3 * b + 2]};
+        const double halfL[3] = {0.5 * g.L[0], 0.5 * g.L[1], 0.5 * g.L[2]};
         if (a.ext) {
             F[0] = a.ext[3 * b];
             F[1] = a.ext[3 * b + 1];
@@ -307,27 +404,24 @@ k_forces(ForceArgs a, GridGeo g, BinGeo bg)
         const double k_spring = a.box_par[3 * box];
         const double k_rep = a.box_par[3 * box + 1];
         const double r_cut = a.box_par[3 * box + 2];
-        // springs: F_b += -k (|r| - r0) r/|r|, r = q_b - q_j (minimum image)
-        for (int e = a.adj_start[b]; e < a.adj_start[b + 1]; ++e) {
-            const int j = a.adj_j[e];
-            double r[3];
-            for (int d = 0; d < 3; ++d) r[d] = min_image(qb[d] - a.q[3 * j + d], g.L[d]);
-            const double len = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-            const double mag = -k_spring * (len - a.adj_rest[e]) / len;
-            for (int d = 0; d < 3; ++d) F[d] += mag * r[d];
-        }
-        // repulsion: F_b += k_rep (r_cut - |r|) r/|r| for |r| < r_cut, other particles only
+        for (int e = a.adj_start[b]; e < a.adj_start[b + 1]; ++e)
+            spring_term<PRECISE>(qb, a.q + 3 * a.adj_j[e], a.adj_rest[e], k_spring, g.L, halfL, F);
         if (k_rep != 0.0 && r_cut > 0.0) {
-            const int pb = a.pid[b];
+            double Fp[3] = {0.0, 0.0, 0.0};
+            const float4 lb = a.loc[slot];
+            const int pb = __float_as_int(lb.w);
             const int cell = a.blob_cell[b] - (int)(box * bg.ncell);
             const int c[3] = {cell % bg.nc[0], (cell / bg.nc[0]) % bg.nc[1],
                               cell / (bg.nc[0] * bg.nc[1])};
+            const float w = (float)(1.0 / bg.inv_w);
+            const float rcf = (float)r_cut;
+            const float pre = rcf * rcf * 1.0001f + 1e-6f;     // conservative FP32 prefilter
+            const bool wide = bg.nc[0] >= 3 && bg.nc[1] >= 3 && bg.nc[2] >= 3;
             int lo[3], hi[3];
             for (int d = 0; d < 3; ++d) {
                 if (bg.nc[d] >= 3) { lo[d] = -1; hi[d] = 1; }
                 else { lo[d] = 0; hi[d] = bg.nc[d] - 1; }
             }
-            const double rc2 = r_cut * r_cut;
             for (int dz = lo[2]; dz <= hi[2]; ++dz) {
                 const int cz = bg.nc[2] >= 3 ? (c[2] + dz + bg.nc[2]) % bg.nc[2] : dz;
                 for (int dy = lo[1]; dy <= hi[1]; ++dy) {
@@ -335,21 +429,24 @@ k_forces(ForceArgs a, GridGeo g, BinGeo bg)
                     for (int dx = lo[0]; dx <= hi[0]; ++dx) {
                         const int cx = bg.nc[0] >= 3 ? (c[0] + dx + bg.nc[0]) % bg.nc[0] : dx;
                         const int64_t cc = box * bg.ncell + ((int64_t)cz * bg.nc[1] + cy) * bg.nc[0] + cx;
+                        const float ox = dx * w, oy = dy * w, oz = dz * w;
                         for (int t = a.cell_start[cc]; t < a.cell_start[cc + 1]; ++t) {
+                            if (t == slot) continue;
+                            const float4 lj = a.loc[t];
+                            if (__float_as_int(lj.w) == pb) continue;
+                            float rf[3] = {lb.x - lj.x - ox, lb.y - lj.y - oy, lb.z - lj.z - oz};
+                            if (wide && rf[0] * rf[0] + rf[1] * rf[1] + rf[2] * rf[2] > pre) continue;
                             const int j = a.sorted[t];
-                            if (j == b || a.pid[j] == pb) continue;
-                            double r[3];
-                            for (int d = 0; d < 3; ++d)
-                                r[d] = min_image(qb[d] - a.q[3 * j + d], g.L[d]);
-                            const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-                            if (r2 >= rc2 || r2 == 0.0) continue;
-                            const double len = sqrt(r2);
-                            const double mag = k_rep * (r_cut - len) / len;
-                            for (int d = 0; d < 3; ++d) F[d] += mag * r[d];
+                            if (!PRECISE && !wide) {
+                                for (int d = 0; d < 3; ++d)
+                                    rf[d] = (float)min_image(qb[d] - a.q[3 * j + d], g.L[d]);
+                            }
+                            pair_term<PRECISE>(qb, a.q + 3 * j, rf, k_rep, r_cut, g.L, Fp);
                         }
                     }
                 }
             }
+            for (int d = 0; d < 3; ++d) F[d] = __dadd_rn(F[d], Fp[d]);
         }
         for (int d = 0; d < 3; ++d) {
             a.F[3 * b + d] = F[d];
@@ -364,12 +461,13 @@ k_forces(ForceArgs a, GridGeo g, BinGeo bg)
 }
 
 cudaError_t launch_forces(cudaStream_t st, int B, int64_t max_box_blobs, const ForceArgs& a,
-                          const GridGeo& g, const BinGeo& bg)
+                          const GridGeo& g, const BinGeo& bg, bool precise)
 {
     if (a.nchunk <= 0) return cudaSuccess;
     dim3 grid((unsigned)a.nchunk, (unsigned)B);
     (void)max_box_blobs;
-    k_forces<<<grid, 256, 0, st>>>(a, g, bg);
+    if (precise) k_forces<true><<<grid, 256, 0, st>>>(a, g, bg);
+    else k_forces<false><<<grid, 256, 0, st>>>(a, g, bg);
     return cudaGetLastError();
 }
 

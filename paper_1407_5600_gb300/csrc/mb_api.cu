@@ -127,14 +127,17 @@ struct mb_ctx {
     std::vector<int64_t> box_off_h, part_off_h;
     DBuf q, qh, u, F, rec, ext, pid, box_of, adj_start, adj_j, adj_rest, part_start,
         part_blobs, box_off, box_par, cell_count, cell_start, blob_cell, blob_rank, sorted,
-        scan_tmp, partial, staging_in, staging_out, mean_scratch;
+        loc, scan_tmp, partial, staging_in, staging_out, mean_scratch;
     // standalone-operator scratch
     DBuf s_q, s_F, s_rec, s_cell_count, s_cell_start, s_blob_cell, s_blob_rank, s_sorted,
         s_scan, s_u, s_g0, s_g1, s_g2, s_out;
 
     // stage timing (CUDA events on the context stream) and kernel launch count
     bool timing = false;
-    cudaEvent_t ev[NUM_STAGES + 1] = {};
+    static constexpr int EV_RING = 64;             // steps recorded before a forced readback
+    std::vector<cudaEvent_t> ev_ring;              // EV_RING sets of NUM_STAGES + 1 events
+    int ev_pending = 0;
+    cudaEvent_t* ev = nullptr;                     // the set used by the current step
     double stage_ms[NUM_STAGES] = {};
     int64_t stage_calls[NUM_STAGES] = {};
     int64_t launches = 0;
@@ -356,6 +359,7 @@ mb_status rebuild(mb_ctx* ctx)
     MB_TRY(ensure(ctx->blob_cell, sizeof(int32_t) * nb, E, "blob_cell"));
     MB_TRY(ensure(ctx->blob_rank, sizeof(int32_t) * nb, E, "blob_rank"));
     MB_TRY(ensure(ctx->sorted, sizeof(int32_t) * nb, E, "sorted"));
+    MB_TRY(ensure(ctx->loc, sizeof(float4) * nb, E, "loc"));
     MB_TRY(ensure(ctx->scan_tmp, sizeof(int32_t) * (ncells / 4096 + 2), E, "scan_tmp"));
     MB_TRY(ensure(ctx->partial, sizeof(double) * 3 * B * std::max(ctx->nchunk, 1), E, "partial"));
 
@@ -442,6 +446,25 @@ FluidArgs<R> fluid_args(mb_ctx* ctx, const void* v, const void* f, void* v_out,
     return a;
 }
 
+// Accumulates the stage times of every recorded step (waits for the last one).
+mb_status drain_stage_events(mb_ctx* ctx)
+{
+    if (ctx->ev_pending == 0) return MB_OK;
+    cudaEvent_t* last = ctx->ev_ring.data() + (size_t)(ctx->ev_pending - 1) * (NUM_STAGES + 1);
+    MB_CUDA(cudaEventSynchronize(last[NUM_STAGES]));
+    for (int s = 0; s < ctx->ev_pending; ++s) {
+        cudaEvent_t* e = ctx->ev_ring.data() + (size_t)s * (NUM_STAGES + 1);
+        for (int i = 0; i < NUM_STAGES; ++i) {
+            float ms = 0.f;
+            MB_CUDA(cudaEventElapsedTime(&ms, e[i], e[i + 1]));
+            ctx->stage_ms[i] += ms;
+            ctx->stage_calls[i] += 1;
+        }
+    }
+    ctx->ev_pending = 0;
+    return MB_OK;
+}
+
 // One time step of every box (see mb_step in include/mb.h).
 template <typename R>
 mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
@@ -455,6 +478,10 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
     double* qh = static_cast<double*>(ctx->qh.p);
     const int32_t* box_of = static_cast<const int32_t*>(ctx->box_of.p);
     const bool blobs = ctx->nb > 0;
+    if (ctx->timing) {
+        if (ctx->ev_pending == mb_ctx::EV_RING) MB_TRY(drain_stage_events(ctx));
+        ctx->ev = ctx->ev_ring.data() + (size_t)ctx->ev_pending * (NUM_STAGES + 1);
+    }
     auto mark = [&](int i) { if (ctx->timing) cudaEventRecord(ctx->ev[i], st); };
     mark(ST_INTERP_PREDICT);
     if (blobs) {
@@ -471,8 +498,10 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
                            static_cast<int32_t*>(ctx->blob_cell.p),
                            static_cast<int32_t*>(ctx->blob_rank.p),
                            static_cast<int32_t*>(ctx->sorted.p),
-                           static_cast<int32_t*>(ctx->scan_tmp.p), ctx->d.deterministic != 0));
-        ctx->launches += 5 + (ctx->d.deterministic != 0);
+                           static_cast<int32_t*>(ctx->scan_tmp.p), ctx->d.deterministic != 0,
+                           static_cast<const int32_t*>(ctx->pid.p),
+                           static_cast<float4*>(ctx->loc.p)));
+        ctx->launches += 5 + 2 * (ctx->d.deterministic != 0);
     }
     mark(ST_FORCES);
     if (blobs) {
@@ -488,11 +517,12 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
         fa.cell_start = static_cast<const int32_t*>(ctx->cell_start.p);
         fa.blob_cell = static_cast<const int32_t*>(ctx->blob_cell.p);
         fa.ext = ext;
+        fa.loc = static_cast<const float4*>(ctx->loc.p);
         fa.F = static_cast<double*>(ctx->F.p);
         fa.rec = static_cast<double*>(ctx->rec.p);
         fa.partial = static_cast<double*>(ctx->partial.p);
         fa.nchunk = ctx->nchunk;
-        MB_CUDA(launch_forces(st, B, ctx->max_box_blobs, fa, g, ctx->bg));
+        MB_CUDA(launch_forces(st, B, ctx->max_box_blobs, fa, g, ctx->bg, ctx->rsz == 8));
         ctx->launches += 1;
     }
     mark(ST_FORCE_SUM);
@@ -523,15 +553,7 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
         ctx->launches += 1;
     }
     mark(NUM_STAGES);
-    if (ctx->timing) {
-        MB_CUDA(cudaEventSynchronize(ctx->ev[NUM_STAGES]));
-        for (int i = 0; i < NUM_STAGES; ++i) {
-            float ms = 0.f;
-            MB_CUDA(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
-            ctx->stage_ms[i] += ms;
-            ctx->stage_calls[i] += 1;
-        }
-    }
+    if (ctx->timing) ctx->ev_pending++;
     ctx->cur ^= 1;
     ctx->steps_taken++;
     return MB_OK;
@@ -584,17 +606,15 @@ void release(mb_ctx* ctx)
                    &ctx->ext, &ctx->pid, &ctx->box_of, &ctx->adj_start, &ctx->adj_j,
                    &ctx->adj_rest, &ctx->part_start, &ctx->part_blobs, &ctx->box_off,
                    &ctx->box_par, &ctx->cell_count, &ctx->cell_start, &ctx->blob_cell,
-                   &ctx->blob_rank, &ctx->sorted, &ctx->scan_tmp, &ctx->partial,
+                   &ctx->blob_rank, &ctx->sorted, &ctx->loc, &ctx->scan_tmp, &ctx->partial,
                    &ctx->staging_in, &ctx->staging_out, &ctx->mean_scratch, &ctx->s_q,
                    &ctx->s_F, &ctx->s_rec, &ctx->s_cell_count, &ctx->s_cell_start,
                    &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
                    &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out};
     for (DBuf* b : all) dfree(*b);
-    for (cudaEvent_t& e : ctx->ev)
-        if (e) {
-            cudaEventDestroy(e);
-            e = nullptr;
-        }
+    for (cudaEvent_t& e : ctx->ev_ring)
+        if (e) cudaEventDestroy(e);
+    ctx->ev_ring.clear();
 }
 
 // Standalone spreading of n blobs into one box grid `out_dev` (device pointer).
@@ -867,8 +887,11 @@ mb_status mb_set_stage_timing(mb_ctx* ctx, int enable)
 {
     if (!ctx) return MB_EINVAL;
     DeviceGuard dg(ctx->device);
-    if (enable && !ctx->ev[0])
-        for (cudaEvent_t& e : ctx->ev) MB_CUDA(cudaEventCreate(&e));
+    if (enable && ctx->ev_ring.empty()) {
+        ctx->ev_ring.assign((size_t)mb_ctx::EV_RING * (NUM_STAGES + 1), nullptr);
+        for (cudaEvent_t& e : ctx->ev_ring) MB_CUDA(cudaEventCreate(&e));
+    }
+    MB_TRY(drain_stage_events(ctx));
     ctx->timing = enable != 0;
     for (int i = 0; i < NUM_STAGES; ++i) {
         ctx->stage_ms[i] = 0.0;
@@ -877,10 +900,12 @@ mb_status mb_set_stage_timing(mb_ctx* ctx, int enable)
     return MB_OK;
 }
 
-mb_status mb_get_stage_times(const mb_ctx* ctx, int max_stages, double* ms_total,
+mb_status mb_get_stage_times(mb_ctx* ctx, int max_stages, double* ms_total,
                              int64_t* calls, int* n_stages)
 {
     if (!ctx || max_stages < 0) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    MB_TRY(drain_stage_events(ctx));
     if (n_stages) *n_stages = NUM_STAGES;
     for (int i = 0; i < NUM_STAGES && i < max_stages; ++i) {
         if (ms_total) ms_total[i] = ctx->stage_ms[i];

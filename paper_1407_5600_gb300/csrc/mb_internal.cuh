@@ -49,7 +49,8 @@ cudaError_t launch_interp(cudaStream_t st, int mode, int64_t nb, const double* q
 cudaError_t launch_bin(cudaStream_t st, int64_t nb, const double* q, const int32_t* box_of,
                        int B, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
                        int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
-                       int32_t* scan_tmp, bool deterministic);
+                       int32_t* scan_tmp, bool deterministic, const int32_t* pid = nullptr,
+                       float4* loc = nullptr);
 
 // Blob forces at q (springs, repulsion, external) in sorted-slot order; writes F (blob order),
 // rec (sorted order: q, F) and per-(box, block) partial force sums.
@@ -65,13 +66,15 @@ struct ForceArgs {
     const int32_t* cell_start;
     const int32_t* blob_cell;
     const double* ext;         // may be null
+    const float4* loc;         // [nb] sorted-order cell-local coordinates and particle id
     double* F;
     double* rec;
     double* partial;           // [B][nchunk][3]
     int nchunk;
 };
+// precise: FP64 in the plain operation order without contraction (FP64 grid mode).
 cudaError_t launch_forces(cudaStream_t st, int B, int64_t max_box_blobs, const ForceArgs& a,
-                          const GridGeo& g, const BinGeo& bg);
+                          const GridGeo& g, const BinGeo& bg, bool precise);
 
 // Sum partial forces per box (fixed order) and update the FP64 mean velocity:
 // vbar += dt * sumF / (rho L^3) when mean_mode == 0, vbar = 0 otherwise; optionally copies
