@@ -114,7 +114,8 @@ struct mb_ctx {
     int nxh = 0;
     int tile[3] = {8, 8, 8};
 
-    DBuf v[2], f, spec, vbar, fsum, tw[3], sym, body_prof, prof_scratch;
+    DBuf v[2], f, spec, vbar, fsum, tw[3], twf[3], sym, body_prof, prof_scratch;
+    int fft_passes = 3;     // 3: plane/z/plane pipeline; 5: one pass per axis (reference layout)
     int cur = 0;
     int64_t steps_taken = 0;
     double body_cached[4] = {0, 0, 0, 0};
@@ -434,7 +435,10 @@ FluidArgs<R> fluid_args(mb_ctx* ctx, const void* v, const void* f, void* v_out,
     a.f = static_cast<const R*>(f);
     a.spec = static_cast<typename C2<R>::T*>(ctx->spec.p);
     a.v_out = static_cast<R*>(v_out);
-    for (int d = 0; d < 3; ++d) a.tw[d] = static_cast<const R*>(ctx->tw[d].p);
+    for (int d = 0; d < 3; ++d) {
+        a.tw[d] = static_cast<const R*>(ctx->tw[d].p);
+        a.twf[d] = static_cast<const R*>(ctx->twf[d].p);
+    }
     a.sym = static_cast<const double*>(ctx->sym.p);
     a.body_prof = body ? static_cast<const R*>(prof) : nullptr;
     a.body_axis = body ? (int)body[1] : -1;
@@ -544,8 +548,14 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
     const double* mean = ctx->d.mean_mode == 0 ? static_cast<const double*>(ctx->vbar.p) : nullptr;
     FluidArgs<R> fa = fluid_args<R>(ctx, vcur, blobs ? ctx->f.p : nullptr, vnext,
                                     ctx->body_prof.p, body, mean);
-    MB_CUDA(launch_fluid<R>(st, B, g, fa, ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr));
-    ctx->launches += FLUID_KERNELS;
+    cudaEvent_t* fm = ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr;
+    if (ctx->fft_passes == 5) {
+        MB_CUDA(launch_fluid<R>(st, B, g, fa, fm));
+        ctx->launches += FLUID_KERNELS;
+    } else {
+        MB_CUDA(launch_fluid3<R>(st, B, g, fa, fm));
+        ctx->launches += FLUID3_KERNELS;
+    }
     if (blobs) {
         // q^{n+1} = q^n + dt J(q^{n+1/2}) (v^n + v^{n+1})/2
         MB_CUDA(launch_interp<R>(st, 2, ctx->nb, qh, q, vcur, vnext, box_of, g, ctx->d.dt,
@@ -582,6 +592,18 @@ mb_status upload_tables(mb_ctx* ctx)
         MB_TRY(ensure(ctx->tw[d], sizeof(double) * n, ctx->err, "twiddles"));
         const void* src = ctx->rsz == 8 ? (const void*)twd.data() : (const void*)twf.data();
         MB_CUDA(cudaMemcpyAsync(ctx->tw[d].p, src, ctx->rsz * n, cudaMemcpyHostToDevice, ctx->st));
+        std::vector<double> fd(2 * n);
+        std::vector<float> ff(2 * n);
+        for (int m = 0; m < n; ++m) {
+            const double ang = -2.0 * M_PI * (double)m / (double)n;
+            fd[2 * m] = std::cos(ang);
+            fd[2 * m + 1] = std::sin(ang);
+            ff[2 * m] = (float)fd[2 * m];
+            ff[2 * m + 1] = (float)fd[2 * m + 1];
+        }
+        MB_TRY(ensure(ctx->twf[d], sizeof(double) * 2 * n, ctx->err, "twiddles"));
+        const void* srcf = ctx->rsz == 8 ? (const void*)fd.data() : (const void*)ff.data();
+        MB_CUDA(cudaMemcpyAsync(ctx->twf[d].p, srcf, ctx->rsz * 2 * n, cudaMemcpyHostToDevice, ctx->st));
         for (int k = 0; k < n; ++k) {
             const double th = 2.0 * M_PI * (double)k / (double)n;
             const double s = std::sin(0.5 * th);
@@ -601,7 +623,8 @@ mb_status upload_tables(mb_ctx* ctx)
 void release(mb_ctx* ctx)
 {
     DBuf* all[] = {&ctx->v[0], &ctx->v[1], &ctx->f, &ctx->spec, &ctx->vbar, &ctx->fsum,
-                   &ctx->tw[0], &ctx->tw[1], &ctx->tw[2], &ctx->sym, &ctx->body_prof,
+                   &ctx->tw[0], &ctx->tw[1], &ctx->tw[2], &ctx->twf[0], &ctx->twf[1],
+                   &ctx->twf[2], &ctx->sym, &ctx->body_prof,
                    &ctx->prof_scratch, &ctx->q, &ctx->qh, &ctx->u, &ctx->F, &ctx->rec,
                    &ctx->ext, &ctx->pid, &ctx->box_of, &ctx->adj_start, &ctx->adj_j,
                    &ctx->adj_rest, &ctx->part_start, &ctx->part_blobs, &ctx->box_off,
@@ -735,6 +758,7 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     ctx->g.inv_h = 1.0 / d.h;
     ctx->nxh = ns[0] / 2 + 1;
     ctx->boxes.resize(ctx->B);
+    if (const char* e = std::getenv("MB_FFT_PASSES")) ctx->fft_passes = std::atoi(e) == 5 ? 5 : 3;
     pick_tile(ctx);
     choose_bins(ctx, 0.0);
 
@@ -1114,10 +1138,12 @@ mb_status mb_fluid_update(mb_ctx* ctx, const void* v_in, const void* f, const do
     MB_TRY(out_target(ctx, v_out, by, ctx->s_out, &dst, &host, "v_out"));
     if (ctx->rsz == 4) {
         FluidArgs<float> a = fluid_args<float>(ctx, vd, fd, dst, ctx->prof_scratch.p, body_force, nullptr);
-        MB_CUDA(launch_fluid<float>(ctx->st, 1, ctx->g, a));
+        if (ctx->fft_passes == 5) MB_CUDA(launch_fluid<float>(ctx->st, 1, ctx->g, a));
+        else MB_CUDA(launch_fluid3<float>(ctx->st, 1, ctx->g, a));
     } else {
         FluidArgs<double> a = fluid_args<double>(ctx, vd, fd, dst, ctx->prof_scratch.p, body_force, nullptr);
-        MB_CUDA(launch_fluid<double>(ctx->st, 1, ctx->g, a));
+        if (ctx->fft_passes == 5) MB_CUDA(launch_fluid<double>(ctx->st, 1, ctx->g, a));
+        else MB_CUDA(launch_fluid3<double>(ctx->st, 1, ctx->g, a));
     }
     return finish_out(ctx, v_out, dst, by, host);
 }

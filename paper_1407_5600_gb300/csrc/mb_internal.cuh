@@ -105,6 +105,7 @@ struct FluidArgs {
     typename C2<R>::T* spec;   // [B][3][nz][ny][nx/2+1]
     R* v_out;
     const R* tw[3];        // twiddles per dimension, n/2 complex each (interleaved re, im)
+    const R* twf[3];       // full tables W_n^j, j < n, per dimension (interleaved re, im)
     const double* sym;     // [3 dims][3][128]: cos, sin, lambda of 2 pi k / n
     const R* body_prof;    // body-force profile along wave_dir (null = none)
     int body_axis, body_dir;
@@ -117,6 +118,12 @@ template <typename R>
 cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a,
                          cudaEvent_t* marks = nullptr);
 constexpr int FLUID_KERNELS = 5;
+// Three-pass variant (plane R2C, z solve, plane C2R); marks as for launch_fluid, with the
+// y-pass marks recorded back to back.
+template <typename R>
+cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a,
+                          cudaEvent_t* marks = nullptr);
+constexpr int FLUID3_KERNELS = 3;
 
 // Reductions / utilities.
 template <typename R>
