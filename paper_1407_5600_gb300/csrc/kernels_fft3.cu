@@ -87,7 +87,9 @@ __device__ __forceinline__ void lines_fft(T* buf, int lines, Idx idx, const T* _
     constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, M = N1 / N2;
     constexpr int LPW = 32 / N2;                 // lines per warp per round
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int t = lane % N2, sub = lane / N2;
+    // consecutive lanes take consecutive lines: with the callers' padded layouts the lanes of
+    // a half-warp then fall on distinct shared-memory banks
+    const int sub = lane % LPW, t = lane / LPW;
     for (int l0 = warp * LPW; l0 < lines; l0 += nw * LPW) {
         const int l = l0 + sub;
         const bool on = l < lines;
@@ -139,6 +141,14 @@ __device__ void lines_fft_n(int n, T* buf, int lines, Idx idx, const T* tw, bool
     }
 }
 
+// Padded position of element j of a line of n points: one spare slot every N2 elements (N2 of
+// the line FFT), which spreads the strided accesses of the second stage over the banks.
+__host__ __device__ __forceinline__ int pad_shift(int n)
+{
+    return n >= 64 ? 3 : (n >= 16 ? 2 : 1);
+}
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> pad_shift(n)); }
+
 template <typename T> __device__ __forceinline__ void load_table(T* dst, const T* src, int n)
 {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
@@ -146,20 +156,49 @@ template <typename T> __device__ __forceinline__ void load_table(T* dst, const T
 
 }  // namespace
 
-// Row stride (in complex) of the plane buffer: room for the nx + 2 unpacked values.
-__host__ __device__ inline int plane_ld(int nx) { return nx + 2; }
+// Row stride (in complex) of the plane buffer: room for the padded nx + 2 separated values,
+// rounded to 8 (mod 16) so that two consecutive rows fall on different halves of the banks.
+__host__ __device__ inline int plane_ld(int nx)
+{
+    int s = nx + 2 + ((nx + 1) >> pad_shift(nx)) + 1;
+    while ((s & 15) != 8) ++s;
+    return s;
+}
+
+// Four consecutive grid values (x0 .. x0+3, x0 a multiple of 4) as one vector load.
+__device__ __forceinline__ void load4(const float* p, float v[4])
+{
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double v[4])
+{
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void store4(float* p, const float v[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double v[4])
+{
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
 
 // ------------------------------------------------------------------------------------------
-// Pass A.  Plane buffer P[p][j], p < ny/2: first rows 2p, 2p+1 packed as re + i im; after the
-// row FFT and the in-place separation, P[p][2k + e] = X_{2p+e}[k] for k <= nx/2.
+// Pass A.  Plane buffer P[p][pad(j)], p < ny/2: first rows 2p, 2p+1 packed as re + i im; after
+// the row FFT and the in-place separation, logical slot 2k + e of row p holds X_{2p+e}[k],
+// k <= nx/2.  pad(j) = j + (j >> pad_shift(nx)).
 template <typename R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_plane_fwd(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
-    const int S = plane_ld(nx);
+    const int S = plane_ld(nx), sx = pad_shift(nx);
     T* P = reinterpret_cast<T*>(smem_raw);
     T* twx = P + (ny / 2) * S;
     T* twy = twx + nx;
@@ -170,24 +209,67 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     const R* fc = a.f ? a.f + (size_t)bc * g.N : nullptr;
     const R ih2 = R(g.inv_h * g.inv_h), rho_dt = R(a.rho_dt), half_eta = R(a.half_eta);
     const bool body = a.body_prof && comp == a.body_axis;
-    const size_t z0 = (size_t)z * ny, zp = (size_t)((z + 1) & (nz - 1)) * ny,
-                 zm = (size_t)((z - 1) & (nz - 1)) * ny;
-    for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
-        const int x = i & (nx - 1), y = i / nx;
-        const int yp = (y + 1) & (ny - 1), ym = (y - 1) & (ny - 1);
-        const size_t row = (z0 + y) * nx;
-        const R c = vc[row + x];
-        const R lap = ((vc[row + ((x + 1) & (nx - 1))] + vc[row + ((x - 1) & (nx - 1))]) +
-                       (vc[(z0 + yp) * nx + x] + vc[(z0 + ym) * nx + x]) +
-                       (vc[(zp + y) * nx + x] + vc[(zm + y) * nx + x]) - R(6) * c) * ih2;
-        R val = rho_dt * c + half_eta * lap;
-        if (fc) val += fc[row + x];
-        if (body) val += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y : z)];
-        T* s = P + (y >> 1) * S + x;
-        if (y & 1) s->y = val; else s->x = val;
+    const R* pz = vc + (size_t)z * ny * nx;
+    const R* pzp = vc + (size_t)((z + 1) & (nz - 1)) * ny * nx;
+    const R* pzm = vc + (size_t)((z - 1) & (nz - 1)) * ny * nx;
+    const R* pf = fc ? fc + (size_t)z * ny * nx : nullptr;
+    // each work unit: 4 consecutive x of the two rows 2p, 2p+1
+    const int qx = nx / 4;
+    for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
+        const int x0 = 4 * (u % qx), p = u / qx;
+        const int y0 = 2 * p, y1 = y0 + 1;
+        const int ym = (y0 - 1) & (ny - 1), yp = (y1 + 1) & (ny - 1);
+        R c0[4], c1[4], am[4], ap[4], t[4];
+        load4(pz + (size_t)y0 * nx + x0, c0);
+        load4(pz + (size_t)y1 * nx + x0, c1);
+        load4(pz + (size_t)ym * nx + x0, am);
+        load4(pz + (size_t)yp * nx + x0, ap);
+        R l0[4], l1[4];
+        for (int i = 0; i < 4; ++i) {
+            l0[i] = am[i] + c1[i] - R(6) * c0[i];
+            l1[i] = c0[i] + ap[i] - R(6) * c1[i];
+        }
+        load4(pzp + (size_t)y0 * nx + x0, t);
+        for (int i = 0; i < 4; ++i) l0[i] += t[i];
+        load4(pzm + (size_t)y0 * nx + x0, t);
+        for (int i = 0; i < 4; ++i) l0[i] += t[i];
+        load4(pzp + (size_t)y1 * nx + x0, t);
+        for (int i = 0; i < 4; ++i) l1[i] += t[i];
+        load4(pzm + (size_t)y1 * nx + x0, t);
+        for (int i = 0; i < 4; ++i) l1[i] += t[i];
+        const int xm = (x0 - 1) & (nx - 1), xp = (x0 + 4) & (nx - 1);
+        const R e0m = pz[(size_t)y0 * nx + xm], e0p = pz[(size_t)y0 * nx + xp];
+        const R e1m = pz[(size_t)y1 * nx + xm], e1p = pz[(size_t)y1 * nx + xp];
+        for (int i = 0; i < 4; ++i) {
+            l0[i] += (i == 0 ? e0m : c0[i - 1]) + (i == 3 ? e0p : c0[i + 1]);
+            l1[i] += (i == 0 ? e1m : c1[i - 1]) + (i == 3 ? e1p : c1[i + 1]);
+        }
+        R r0[4], r1[4];
+        for (int i = 0; i < 4; ++i) {
+            r0[i] = rho_dt * c0[i] + half_eta * (l0[i] * ih2);
+            r1[i] = rho_dt * c1[i] + half_eta * (l1[i] * ih2);
+        }
+        if (pf) {
+            load4(pf + (size_t)y0 * nx + x0, t);
+            for (int i = 0; i < 4; ++i) r0[i] += t[i];
+            load4(pf + (size_t)y1 * nx + x0, t);
+            for (int i = 0; i < 4; ++i) r1[i] += t[i];
+        }
+        if (body) {
+            for (int i = 0; i < 4; ++i) {
+                const int x = x0 + i;
+                r0[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y0 : z)];
+                r1[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)];
+            }
+        }
+        T* row = P + p * S;
+        for (int i = 0; i < 4; ++i) {
+            const int j = x0 + i;
+            row[j + (j >> sx)] = T{r0[i], r1[i]};
+        }
     }
     __syncthreads();
-    lines_fft_n(nx, P, ny / 2, [S](int l, int j) { return l * S + j; }, twx, false);
+    lines_fft_n(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx, false);
     __syncthreads();
     // separate the two real rows of each packed row (one warp per packed row, in place)
     {
@@ -199,7 +281,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
             for (int r = 0; r < 3; ++r) {
                 const int k = lane + 32 * r;
                 if (k < nxh) {
-                    const T Z = rowp[k], Zr = rowp[(nx - k) & (nx - 1)];
+                    const int kr = (nx - k) & (nx - 1);
+                    const T Z = rowp[k + (k >> sx)], Zr = rowp[kr + (kr >> sx)];
                     ev[r] = T{(Z.x + Zr.x) * R(0.5), (Z.y - Zr.y) * R(0.5)};
                     od[r] = T{(Z.y + Zr.y) * R(0.5), (Zr.x - Z.x) * R(0.5)};
                 }
@@ -209,62 +292,66 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
             for (int r = 0; r < 3; ++r) {
                 const int k = lane + 32 * r;
                 if (k < nxh) {
-                    rowp[2 * k] = ev[r];
-                    rowp[2 * k + 1] = od[r];
+                    const int j0 = 2 * k, j1 = 2 * k + 1;
+                    rowp[j0 + (j0 >> sx)] = ev[r];
+                    rowp[j1 + (j1 >> sx)] = od[r];
                 }
             }
             __syncwarp();
         }
     }
     __syncthreads();
-    lines_fft_n(ny, P, nxh, [S](int k, int y) { return (y >> 1) * S + 2 * k + (y & 1); }, twy,
-                false);
+    auto col = [S, sx](int k, int y) {
+        const int j = 2 * k + (y & 1);
+        return (y >> 1) * S + j + (j >> sx);
+    };
+    lines_fft_n(ny, P, nxh, col, twy, false);
     __syncthreads();
     T* out = a.spec + ((size_t)bc * nz + z) * (size_t)nxh * ny;
-    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) {
-        const int y = i % ny, k = i / ny;
-        out[i] = P[(y >> 1) * S + 2 * k + (y & 1)];
-    }
+    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) out[i] = P[col(i / ny, i % ny)];
 }
 
 // ------------------------------------------------------------------------------------------
-// Pass B.  CTA = (ky block of width C, kx, box); shared buffer [3][nz][C].
+// Pass B.  CTA = (ky block of width C, kx, box); shared buffer [3][pad(nz)][Cp].
 template <typename R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2)
 k_zsolve(FluidArgs<R> a, GridGeo g, int C)
 {
     using T = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
-    const int Cp = C + 2;                        // padded row: 8 z-rows hit distinct banks
-    T* Bf = reinterpret_cast<T*>(smem_raw);
-    T* twz = Bf + 3 * nz * Cp;
+    const int sz = pad_shift(nz), nzp = padded_len(nz);
+    const int Cp = C + 4;                        // rows of C + 4 complex: (4 z-rows x 4 lines)
+    T* Bf = reinterpret_cast<T*>(smem_raw);      //  per half-warp hit distinct banks
+    T* twz = Bf + 3 * nzp * Cp;
     load_table(twz, reinterpret_cast<const T*>(a.twf[2]), nz);
     const int ky0 = blockIdx.x * C, kx = blockIdx.y, box = blockIdx.z;
     const size_t zstride = (size_t)nxh * ny;
-    const T* base[3];
+    T* base[3];
     for (int c = 0; c < 3; ++c)
         base[c] = a.spec + (size_t)(box * 3 + c) * nz * zstride + (size_t)kx * ny + ky0;
+    auto at = [=](int c, int z, int k) { return (c * nzp + z + (z >> sz)) * Cp + k; };
     for (int i = threadIdx.x; i < 3 * nz * C; i += blockDim.x) {
         const int k = i % C, z = (i / C) % nz, c = i / (C * nz);
-        Bf[(c * nz + z) * Cp + k] = base[c][(size_t)z * zstride + k];
+        Bf[at(c, z, k)] = base[c][(size_t)z * zstride + k];
     }
     __syncthreads();
-    auto idx = [C, Cp, nz](int l, int z) { return ((l / C) * nz + z) * Cp + (l % C); };
+    auto idx = [=](int l, int z) { return at(l / C, z, l % C); };
     lines_fft_n(nz, Bf, 3 * C, idx, twz, false);
     __syncthreads();
-    const double* sym = a.sym;
+    const R* sym = reinterpret_cast<const R*>(a.symr);     // [9][256] cos, sin, lambda
     const R ih = R(g.inv_h);
-    const R csx = R(sym[0 * 256 + kx]), snx = R(sym[1 * 256 + kx]), lx = R(sym[2 * 256 + kx]);
+    const R csx = sym[0 * 256 + kx], snx = sym[1 * 256 + kx], lx = sym[2 * 256 + kx];
+    const R rho_dt = R(a.rho_dt), half_eta = R(a.half_eta);
     for (int i = threadIdx.x; i < nz * C; i += blockDim.x) {
         const int k = i % C, kz = i / C, ky = ky0 + k;
-        const R cs[3] = {csx, R(sym[3 * 256 + ky]), R(sym[6 * 256 + kz])};
-        const R sn[3] = {snx, R(sym[4 * 256 + ky]), R(sym[7 * 256 + kz])};
-        const R lam = lx + R(sym[5 * 256 + ky]) + R(sym[8 * 256 + kz]);
-        const R cinv = R(1) / (R(a.rho_dt) + R(a.half_eta) * lam);
+        const R cs[3] = {csx, sym[3 * 256 + ky], sym[6 * 256 + kz]};
+        const R sn[3] = {snx, sym[4 * 256 + ky], sym[7 * 256 + kz]};
+        const R lam = lx + sym[5 * 256 + ky] + sym[8 * 256 + kz];
+        const R cinv = R(1) / (rho_dt + half_eta * lam);
         T W[3];
         for (int c = 0; c < 3; ++c) {
-            const T v = Bf[(c * nz + kz) * Cp + k];
+            const T v = Bf[at(c, kz, k)];
             W[c] = T{v.x * cinv, v.y * cinv};
         }
         if (kx == 0 && ky == 0 && kz == 0) {
@@ -290,14 +377,14 @@ k_zsolve(FluidArgs<R> a, GridGeo g, int C)
                 W[c].y += Gr * di + Gi * dr;
             }
         }
-        for (int c = 0; c < 3; ++c) Bf[(c * nz + kz) * Cp + k] = W[c];
+        for (int c = 0; c < 3; ++c) Bf[at(c, kz, k)] = W[c];
     }
     __syncthreads();
     lines_fft_n(nz, Bf, 3 * C, idx, twz, true);
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * nz * C; i += blockDim.x) {
         const int k = i % C, z = (i / C) % nz, c = i / (C * nz);
-        const_cast<T*>(base[c])[(size_t)z * zstride + k] = Bf[(c * nz + z) * Cp + k];
+        base[c][(size_t)z * zstride + k] = Bf[at(c, z, k)];
     }
 }
 
@@ -305,13 +392,13 @@ k_zsolve(FluidArgs<R> a, GridGeo g, int C)
 // Pass C.  Inverse of pass A: columns, then the packed rows Z = X_{2p} + i X_{2p+1} (with the
 // Hermitian extension X[nx - k] = conj X[k]), then the real rows, scaled by 1/N.
 template <typename R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_plane_inv(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
-    const int S = plane_ld(nx);
+    const int S = plane_ld(nx), sx = pad_shift(nx);
     T* P = reinterpret_cast<T*>(smem_raw);
     T* twx = P + (ny / 2) * S;
     T* twy = twx + nx;
@@ -319,13 +406,13 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     load_table(twy, reinterpret_cast<const T*>(a.twf[1]), ny);
     const int z = blockIdx.x, bc = blockIdx.y;
     const T* in = a.spec + ((size_t)bc * nz + z) * (size_t)nxh * ny;
-    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) {
-        const int y = i % ny, k = i / ny;
-        P[(y >> 1) * S + 2 * k + (y & 1)] = in[i];
-    }
+    auto col = [S, sx](int k, int y) {
+        const int j = 2 * k + (y & 1);
+        return (y >> 1) * S + j + (j >> sx);
+    };
+    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) P[col(i / ny, i % ny)] = in[i];
     __syncthreads();
-    lines_fft_n(ny, P, nxh, [S](int k, int y) { return (y >> 1) * S + 2 * k + (y & 1); }, twy,
-                true);
+    lines_fft_n(ny, P, nxh, col, twy, true);
     __syncthreads();
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -337,7 +424,8 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
                 const int k = lane + 32 * r;
                 if (k < nx) {
                     const int kk = k <= nx / 2 ? k : nx - k;
-                    T e = rowp[2 * kk], o = rowp[2 * kk + 1];
+                    const int j0 = 2 * kk, j1 = 2 * kk + 1;
+                    T e = rowp[j0 + (j0 >> sx)], o = rowp[j1 + (j1 >> sx)];
                     if (k == 0 || k == nx / 2) { e.y = R(0); o.y = R(0); }
                     if (k > nx / 2) { e.y = -e.y; o.y = -o.y; }
                     zv[r] = T{e.x - o.y, e.y + o.x};
@@ -347,20 +435,28 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int k = lane + 32 * r;
-                if (k < nx) rowp[k] = zv[r];
+                if (k < nx) rowp[k + (k >> sx)] = zv[r];
             }
             __syncwarp();
         }
     }
     __syncthreads();
-    lines_fft_n(nx, P, ny / 2, [S](int l, int j) { return l * S + j; }, twx, true);
+    lines_fft_n(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx, true);
     __syncthreads();
     const R scale = R(1.0 / (double)g.N);
     R* out = a.v_out + (size_t)bc * g.N + (size_t)z * ny * nx;
-    for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
-        const int x = i & (nx - 1), y = i / nx;
-        const T zv = P[(y >> 1) * S + x];
-        out[i] = ((y & 1) ? zv.y : zv.x) * scale;
+    const int qx = nx / 4;
+    for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
+        const int x0 = 4 * (u % qx), p = u / qx;
+        R r0[4], r1[4];
+        for (int i = 0; i < 4; ++i) {
+            const int j = x0 + i;
+            const T zv = P[p * S + j + (j >> sx)];
+            r0[i] = zv.x * scale;
+            r1[i] = zv.y * scale;
+        }
+        store4(out + (size_t)(2 * p) * nx + x0, r0);
+        store4(out + (size_t)(2 * p + 1) * nx + x0, r1);
     }
 }
 
@@ -382,7 +478,7 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
     const size_t smem_plane = ((size_t)(ny / 2) * plane_ld(nx) + nx + ny) * sizeof(T);
     int C = sizeof(R) == 4 ? 16 : 8;
     if (C > ny) C = ny;
-    const size_t smem_z = ((size_t)3 * nz * (C + 2) + nz) * sizeof(T);
+    const size_t smem_z = ((size_t)3 * padded_len(nz) * (C + 4) + nz) * sizeof(T);
     auto mark = [&](int i) { if (marks) cudaEventRecord(marks[i], st); };
     mark(0);
     k_plane_fwd<R><<<dim3(nz, 3 * B), 256, smem_plane, st>>>(a, g);

@@ -114,7 +114,7 @@ struct mb_ctx {
     int nxh = 0;
     int tile[3] = {8, 8, 8};
 
-    DBuf v[2], f, spec, vbar, fsum, tw[3], twf[3], sym, body_prof, prof_scratch;
+    DBuf v[2], f, spec, vbar, fsum, tw[3], twf[3], sym, symr, body_prof, prof_scratch;
     int fft_passes = 3;     // 3: plane/z/plane pipeline; 5: one pass per axis (reference layout)
     int cur = 0;
     int64_t steps_taken = 0;
@@ -440,6 +440,7 @@ FluidArgs<R> fluid_args(mb_ctx* ctx, const void* v, const void* f, void* v_out,
         a.twf[d] = static_cast<const R*>(ctx->twf[d].p);
     }
     a.sym = static_cast<const double*>(ctx->sym.p);
+    a.symr = ctx->symr.p;
     a.body_prof = body ? static_cast<const R*>(prof) : nullptr;
     a.body_axis = body ? (int)body[1] : -1;
     a.body_dir = body ? (int)body[2] : 0;
@@ -616,6 +617,14 @@ mb_status upload_tables(mb_ctx* ctx)
     MB_TRY(ensure(ctx->sym, sizeof(double) * sym.size(), ctx->err, "symbols"));
     MB_CUDA(cudaMemcpyAsync(ctx->sym.p, sym.data(), sizeof(double) * sym.size(),
                             cudaMemcpyHostToDevice, ctx->st));
+    std::vector<float> symf(sym.begin(), sym.end());
+    MB_TRY(ensure(ctx->symr, sizeof(double) * sym.size(), ctx->err, "symbols"));
+    if (ctx->rsz == 8)
+        MB_CUDA(cudaMemcpyAsync(ctx->symr.p, sym.data(), sizeof(double) * sym.size(),
+                                cudaMemcpyHostToDevice, ctx->st));
+    else
+        MB_CUDA(cudaMemcpyAsync(ctx->symr.p, symf.data(), sizeof(float) * symf.size(),
+                                cudaMemcpyHostToDevice, ctx->st));
     MB_CUDA(cudaStreamSynchronize(ctx->st));
     return MB_OK;
 }
@@ -624,7 +633,7 @@ void release(mb_ctx* ctx)
 {
     DBuf* all[] = {&ctx->v[0], &ctx->v[1], &ctx->f, &ctx->spec, &ctx->vbar, &ctx->fsum,
                    &ctx->tw[0], &ctx->tw[1], &ctx->tw[2], &ctx->twf[0], &ctx->twf[1],
-                   &ctx->twf[2], &ctx->sym, &ctx->body_prof,
+                   &ctx->twf[2], &ctx->sym, &ctx->symr, &ctx->body_prof,
                    &ctx->prof_scratch, &ctx->q, &ctx->qh, &ctx->u, &ctx->F, &ctx->rec,
                    &ctx->ext, &ctx->pid, &ctx->box_of, &ctx->adj_start, &ctx->adj_j,
                    &ctx->adj_rest, &ctx->part_start, &ctx->part_blobs, &ctx->box_off,

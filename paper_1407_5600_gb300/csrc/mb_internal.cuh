@@ -106,7 +106,8 @@ struct FluidArgs {
     R* v_out;
     const R* tw[3];        // twiddles per dimension, n/2 complex each (interleaved re, im)
     const R* twf[3];       // full tables W_n^j, j < n, per dimension (interleaved re, im)
-    const double* sym;     // [3 dims][3][128]: cos, sin, lambda of 2 pi k / n
+    const double* sym;     // [3 dims][3][256]: cos, sin, lambda of 2 pi k / n (FP64)
+    const void* symr;      // the same tables in the grid precision R
     const R* body_prof;    // body-force profile along wave_dir (null = none)
     int body_axis, body_dir;
     const double* mean_override;   // [B][3] mean velocity to impose at k = 0, or null
