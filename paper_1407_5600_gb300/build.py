@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mb_api.cu", "kernels_blob.cu", "kernels_fft.cu", "kernels_fft3.cu",
+SOURCES = ["mb_api.cu", "kernels_blob.cu", "kernels_blob32.cu", "kernels_fft.cu",
+           "kernels_fft3.cu",
            "spread_static.cu"]
 
 

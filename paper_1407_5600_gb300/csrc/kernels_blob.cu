@@ -10,9 +10,9 @@ namespace mbk {
 // One thread per blob; each component reads its own staggered grid.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(256)
-k_interp(int64_t nb, const double* __restrict__ q, const double* __restrict__ q_base,
+k_interp(int64_t nb, const double* __restrict__ q, const double* q_base,
          const R* __restrict__ v0, const R* __restrict__ v1, const int32_t* __restrict__ box_of,
-         GridGeo g, double dt, double* __restrict__ u_out, double* __restrict__ q_out)
+         GridGeo g, double dt, double* __restrict__ u_out, double* q_out)
 {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -267,6 +267,17 @@ __global__ void k_fill_loc(int64_t nb, const int32_t* __restrict__ sorted,
     float r[3];
     for (int d = 0; d < 3; ++d) r[d] = (float)(q[3 * b + d] - c[d] * w);
     loc[t] = make_float4(r[0], r[1], r[2], __int_as_float(pid ? pid[b] : 0));
+}
+
+cudaError_t launch_exclusive_scan(cudaStream_t st, const int32_t* in, int32_t* out, int64_t n,
+                                  int32_t* tile_tmp)
+{
+    const int T = 256;
+    const int ntiles = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+    k_scan_tile<<<ntiles, SCAN_THREADS, 0, st>>>(in, out, n, tile_tmp);
+    k_scan_tops<<<1, SCAN_THREADS, 0, st>>>(tile_tmp, ntiles, out + n);
+    k_scan_add<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(out, n, tile_tmp);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bin(cudaStream_t st, int64_t nb, const double* q, const int32_t* box_of,

@@ -1,0 +1,662 @@
+// Blob-side kernels of the FP32-grid mode, written for GB300's FP32 pipes.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, so in this mode a blob position
+// is kept as an integer bin cell c (side w = bs h) plus an offset inside the cell held as an
+// unevaluated float sum hi + lo (a "float-float" value): q = c w + hi + lo.  The offset spans
+// at most w, so hi + lo resolves positions to about 2^-47 w (7e-15 h for w = 2h), finer than
+// an FP64 coordinate of a 128h box.  Every update and every difference of positions is done
+// with error-free float transformations (TwoSum, the FMA product error), so nothing here runs
+// on the FP64 pipe; FP64 positions are produced only when a caller asks for them.
+//
+// Layout per blob: float4 A = {hi.x, hi.y, hi.z, cell bits}, float4 B = {lo.x, lo.y, lo.z, 0},
+// with the cell packed as cx | cy << 10 | cz << 20.
+#include "mb_internal.cuh"
+#include "peskin.cuh"
+
+namespace mbk {
+
+namespace {
+
+__device__ __forceinline__ int cell_unpack(int packed, int d) { return (packed >> (10 * d)) & 1023; }
+__device__ __forceinline__ int cell_pack(int cx, int cy, int cz) { return cx | (cy << 10) | (cz << 20); }
+
+// s + e = a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// Moves one coordinate (cell c, offset hi + lo) by a small displacement and renormalises the
+// offset into [0, w), carrying whole cells into c (periodic over nc cells).
+__device__ __forceinline__ void ff_move(int& c, float& hi, float& lo, float delta, float w, int nc)
+{
+    float s, e;
+    two_sum(hi, delta, s, e);
+    two_sum(s, lo + e, hi, lo);
+    if (hi >= w) {
+        float t, te;
+        two_sum(hi, -w, t, te);
+        two_sum(t, lo + te, hi, lo);
+        c = c + 1 == nc ? 0 : c + 1;
+    } else if (hi < 0.0f) {
+        float t, te;
+        two_sum(hi, w, t, te);
+        two_sum(t, lo + te, hi, lo);
+        c = c == 0 ? nc - 1 : c - 1;
+    }
+}
+
+// Peskin window from the split coordinate: x = q/h - shift = c bs + hi/h - shift.
+__device__ __forceinline__ int window32(int c, int bs, float hi, float inv_h, float shift, float w[3])
+{
+    const float x = hi * inv_h - shift;
+    const float fl = floorf(x + 0.5f);
+    const float t = x - fl;
+    const float s = sqrtf(1.0f - 3.0f * t * t);
+    w[0] = (2.0f - 3.0f * t - s) * (1.0f / 6.0f);
+    w[1] = (1.0f + s) * (1.0f / 3.0f);
+    w[2] = (2.0f + 3.0f * t - s) * (1.0f / 6.0f);
+    return c * bs + (int)fl - 1;
+}
+
+struct Geo32 {
+    int n[3], nc[3];
+    int bs;
+    float w, inv_h;
+    float L[3];
+    int64_t N;
+    int64_t ncell;
+};
+
+__device__ __forceinline__ Geo32 geo32(const GridGeo& g, const BinGeo& bg)
+{
+    Geo32 r;
+    for (int d = 0; d < 3; ++d) {
+        r.n[d] = g.n[d];
+        r.nc[d] = bg.nc[d];
+        r.L[d] = (float)g.L[d];
+    }
+    r.bs = bg.bs;
+    r.w = (float)(1.0 / bg.inv_w);
+    r.inv_h = (float)g.inv_h;
+    r.N = g.N;
+    r.ncell = bg.ncell;
+    return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// Conversions between FP64 positions and the split form.
+
+__global__ void k_split(int64_t nb, const double* __restrict__ q, GridGeo g, BinGeo bg,
+                        float4* __restrict__ A, float4* __restrict__ B)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const double w = 1.0 / bg.inv_w;
+    int c[3];
+    float hi[3], lo[3];
+    for (int d = 0; d < 3; ++d) {
+        double x = wrap_position(q[3 * b + d], g.L[d]);
+        int k = (int)floor(x * bg.inv_w);
+        if (k >= bg.nc[d]) k = bg.nc[d] - 1;
+        if (k < 0) k = 0;
+        const double xl = x - k * w;
+        c[d] = k;
+        hi[d] = (float)xl;
+        lo[d] = (float)(xl - (double)hi[d]);
+    }
+    A[b] = make_float4(hi[0], hi[1], hi[2], __int_as_float(cell_pack(c[0], c[1], c[2])));
+    B[b] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+}
+
+__global__ void k_unsplit(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ B,
+                          BinGeo bg, GridGeo g, double* __restrict__ q)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const double w = 1.0 / bg.inv_w;
+    const float4 a = A[b], l = B[b];
+    const int pk = __float_as_int(a.w);
+    const float hi[3] = {a.x, a.y, a.z}, lo[3] = {l.x, l.y, l.z};
+    for (int d = 0; d < 3; ++d)
+        q[3 * b + d] = wrap_position(cell_unpack(pk, d) * w + (double)hi[d] + (double)lo[d], g.L[d]);
+}
+
+// ------------------------------------------------------------------------------------------
+// Interpolation J from the split positions (mode 0: u only; 1: predictor; 2: corrector).
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_interp32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ Bl,
+           const float* __restrict__ v0, const float* __restrict__ v1,
+           const int32_t* __restrict__ box_of, GridGeo g, BinGeo bg, float dt,
+           const float4* A_base, const float4* B_base, float4* A_out, float4* B_out,
+           double* __restrict__ u_out)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const Geo32 G = geo32(g, bg);
+    const int box = box_of ? box_of[b] : 0;
+    const float4 a = A[b];
+    const int pk = __float_as_int(a.w);
+    const int c[3] = {cell_unpack(pk, 0), cell_unpack(pk, 1), cell_unpack(pk, 2)};
+    const float hi[3] = {a.x, a.y, a.z};
+    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+    float u[3];
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+        float wx[3], wy[3], wz[3];
+        const int ix = window32(c[0], G.bs, hi[0], G.inv_h, comp == 0 ? 0.f : 0.5f, wx);
+        const int iy = window32(c[1], G.bs, hi[1], G.inv_h, comp == 1 ? 0.f : 0.5f, wy);
+        const int iz = window32(c[2], G.bs, hi[2], G.inv_h, comp == 2 ? 0.f : 0.5f, wz);
+        const size_t base = ((size_t)box * 3 + comp) * (size_t)G.N;
+        const float* c0 = v0 + base;
+        const float* c1 = MODE == 2 ? v1 + base : nullptr;
+        float acc = 0.0f;
+#pragma unroll
+        for (int cz = 0; cz < 3; ++cz) {
+            const int zz = (iz + cz) & (nz - 1);
+#pragma unroll
+            for (int cy = 0; cy < 3; ++cy) {
+                const int yy = (iy + cy) & (ny - 1);
+                const size_t row = ((size_t)zz * ny + yy) * nx;
+                float r = 0.0f;
+#pragma unroll
+                for (int cx = 0; cx < 3; ++cx) {
+                    const int xx = (ix + cx) & (nx - 1);
+                    float val = __ldg(c0 + row + xx);
+                    if (MODE == 2) val += __ldg(c1 + row + xx);
+                    r += wx[cx] * val;
+                }
+                acc += wy[cy] * wz[cz] * r;
+            }
+        }
+        u[comp] = MODE == 2 ? 0.5f * acc : acc;
+    }
+    if (MODE == 0) {
+        for (int d = 0; d < 3; ++d) u_out[3 * b + d] = (double)u[d];
+        return;
+    }
+    // move the base position (q^n for both the predictor and the corrector)
+    const float4 ab = MODE == 1 ? a : A_base[b];
+    const float4 lb = MODE == 1 ? Bl[b] : B_base[b];
+    int cc[3] = {cell_unpack(__float_as_int(ab.w), 0), cell_unpack(__float_as_int(ab.w), 1),
+                 cell_unpack(__float_as_int(ab.w), 2)};
+    float h2[3] = {ab.x, ab.y, ab.z}, l2[3] = {lb.x, lb.y, lb.z};
+    const float scale = MODE == 1 ? 0.5f * dt : dt;
+    for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], scale * u[d], G.w, G.nc[d]);
+    A_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
+    B_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
+}
+
+// ------------------------------------------------------------------------------------------
+// Binning from the packed cells; loc[slot] = {hi, particle id} for the pair prefilter.
+__global__ void k_bin_count32(int64_t nb, const float4* __restrict__ A,
+                              const int32_t* __restrict__ box_of, BinGeo bg,
+                              int32_t* __restrict__ count, int32_t* __restrict__ blob_cell,
+                              int32_t* __restrict__ blob_rank)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int pk = __float_as_int(A[b].w);
+    const int box = box_of ? box_of[b] : 0;
+    const int cell = (int)(box * bg.ncell) +
+                     (cell_unpack(pk, 2) * bg.nc[1] + cell_unpack(pk, 1)) * bg.nc[0] +
+                     cell_unpack(pk, 0);
+    blob_cell[b] = cell;
+    blob_rank[b] = atomicAdd(count + cell, 1);
+}
+
+__global__ void k_bin_scatter32(int64_t nb, const int32_t* __restrict__ blob_cell,
+                                const int32_t* __restrict__ blob_rank,
+                                const int32_t* __restrict__ cell_start,
+                                int32_t* __restrict__ sorted, const float4* __restrict__ A,
+                                const int32_t* __restrict__ pid, float4* __restrict__ loc)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int slot = cell_start[blob_cell[b]] + blob_rank[b];
+    sorted[slot] = (int32_t)b;
+    const float4 a = A[b];
+    loc[slot] = make_float4(a.x, a.y, a.z, __int_as_float(pid[b]));
+}
+
+// ------------------------------------------------------------------------------------------
+// Forces.  Springs: the bond vector r = (c_b - c_j) w + (hi_b - hi_j) + (lo_b - lo_j) and the
+// extension |r|^2 - r0^2 in float-float (the stiff springs cancel about six digits there),
+// the force magnitude in float.  Repulsion: float, from the cell-local coordinates.
+__device__ __forceinline__ void spring32(const int cb[3], const float hb[3], const float lb[3],
+                                         float4 aj, float4 bj, float r0, float r0h, float r0l,
+                                         float k, const Geo32& G, float F[3])
+{
+    const int pj = __float_as_int(aj.w);
+    const float hj[3] = {aj.x, aj.y, aj.z}, lj[3] = {bj.x, bj.y, bj.z};
+    float rh[3], rl[3];
+    for (int d = 0; d < 3; ++d) {
+        int dc = cb[d] - cell_unpack(pj, d);
+        const int nc = G.nc[d];
+        if (2 * dc > nc) dc -= nc;
+        else if (2 * dc < -nc) dc += nc;
+        float s, e1, s2, e2;
+        two_sum(hb[d], -hj[d], s, e1);
+        two_sum((float)dc * G.w, s, s2, e2);
+        float h, l;
+        two_sum(s2, e1 + e2 + (lb[d] - lj[d]), h, l);
+        const float half = 0.5f * G.L[d];
+        if (h >= half) { float t, te; two_sum(h, -G.L[d], t, te); two_sum(t, l + te, h, l); }
+        else if (h < -half) { float t, te; two_sum(h, G.L[d], t, te); two_sum(t, l + te, h, l); }
+        rh[d] = h;
+        rl[d] = l;
+    }
+    // |r|^2 as float-float: sum of hi^2 (with exact product errors) and 2 hi lo
+    float p[3], pe[3];
+    for (int d = 0; d < 3; ++d) {
+        p[d] = rh[d] * rh[d];
+        pe[d] = fmaf(rh[d], rh[d], -p[d]) + 2.0f * rh[d] * rl[d];
+    }
+    float s01, e01, P, e2;
+    two_sum(p[0], p[1], s01, e01);
+    two_sum(s01, p[2], P, e2);
+    const float Pl = e01 + e2 + pe[0] + pe[1] + pe[2];
+    const float d2 = (P - r0h) + (Pl - r0l);      // P - r0h is exact near the rest length
+    const float len = sqrtf(P);
+    const float mag = -k * d2 / ((len + r0) * len);
+    for (int d = 0; d < 3; ++d) F[d] += mag * rh[d];
+}
+
+struct Force32Args {
+    const int64_t* box_off;
+    const int32_t* sorted;
+    const float4* A;          // split midpoint positions (blob order)
+    const float4* B;
+    const float4* loc;        // [slot] hi + particle id
+    const int4* adj;          // per adjacency entry: j, r0, r0^2 hi, r0^2 lo (float bits)
+    const int32_t* adj_start;
+    const double* box_par;    // [B][3] k_spring, k_rep, r_cut
+    const int32_t* cell_start;
+    const int32_t* blob_cell;
+    const float4* ext;        // [nb] or null
+    float4* F;                // [nb] blob forces
+    float4* rec;              // [2 * slot]: split hi + cell, force
+};
+
+__global__ void __launch_bounds__(256)
+k_forces32(Force32Args a, GridGeo g, BinGeo bg)
+{
+    const Geo32 G = geo32(g, bg);
+    const int box = blockIdx.y;
+    const int64_t s0 = a.box_off[box], cnt = a.box_off[box + 1] - s0;
+    const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= cnt) return;
+    const int64_t slot = s0 + local;
+    const int b = a.sorted[slot];
+    const float4 ab = a.A[b], lbv = a.B[b];
+    const int pk = __float_as_int(ab.w);
+    const int cb[3] = {cell_unpack(pk, 0), cell_unpack(pk, 1), cell_unpack(pk, 2)};
+    const float hb[3] = {ab.x, ab.y, ab.z}, lb[3] = {lbv.x, lbv.y, lbv.z};
+    float F[3] = {0.f, 0.f, 0.f};
+    if (a.ext) {
+        const float4 e = a.ext[b];
+        F[0] = e.x;
+        F[1] = e.y;
+        F[2] = e.z;
+    }
+    const float k_spring = (float)a.box_par[3 * box];
+    const float k_rep = (float)a.box_par[3 * box + 1];
+    const float r_cut = (float)a.box_par[3 * box + 2];
+    for (int e = a.adj_start[b]; e < a.adj_start[b + 1]; ++e) {
+        const int4 ad = a.adj[e];
+        spring32(cb, hb, lb, a.A[ad.x], a.B[ad.x], __int_as_float(ad.y), __int_as_float(ad.z),
+                 __int_as_float(ad.w), k_spring, G, F);
+    }
+    if (k_rep != 0.0f && r_cut > 0.0f) {
+        const float4 me = a.loc[slot];
+        const int pb = __float_as_int(me.w);
+        const bool wide = G.nc[0] >= 3 && G.nc[1] >= 3 && G.nc[2] >= 3;
+        const float rc2 = r_cut * r_cut;
+        int lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            if (G.nc[d] >= 3) { lo[d] = -1; hi[d] = 1; }
+            else { lo[d] = 0; hi[d] = G.nc[d] - 1; }
+        }
+        float Fp[3] = {0.f, 0.f, 0.f};
+        for (int dz = lo[2]; dz <= hi[2]; ++dz) {
+            const int cz = G.nc[2] >= 3 ? (cb[2] + dz + G.nc[2]) % G.nc[2] : dz;
+            for (int dy = lo[1]; dy <= hi[1]; ++dy) {
+                const int cy = G.nc[1] >= 3 ? (cb[1] + dy + G.nc[1]) % G.nc[1] : dy;
+                for (int dx = lo[0]; dx <= hi[0]; ++dx) {
+                    const int cx = G.nc[0] >= 3 ? (cb[0] + dx + G.nc[0]) % G.nc[0] : dx;
+                    const int64_t cc = box * G.ncell + ((int64_t)cz * G.nc[1] + cy) * G.nc[0] + cx;
+                    // cell offset of the neighbour (unwrapped) in the wide case; otherwise the
+                    // minimum image of the difference
+                    const float ox = (wide ? dx : cx - cb[0]) * G.w;
+                    const float oy = (wide ? dy : cy - cb[1]) * G.w;
+                    const float oz = (wide ? dz : cz - cb[2]) * G.w;
+                    for (int t = a.cell_start[cc]; t < a.cell_start[cc + 1]; ++t) {
+                        if (t == slot) continue;
+                        const float4 lj = a.loc[t];
+                        if (__float_as_int(lj.w) == pb) continue;
+                        float r[3] = {me.x - lj.x - ox, me.y - lj.y - oy, me.z - lj.z - oz};
+                        if (!wide)
+                            for (int d = 0; d < 3; ++d) {
+                                if (r[d] >= 0.5f * G.L[d]) r[d] -= G.L[d];
+                                else if (r[d] < -0.5f * G.L[d]) r[d] += G.L[d];
+                            }
+                        const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                        if (r2 >= rc2 || r2 == 0.0f) continue;
+                        const float len = sqrtf(r2);
+                        const float mag = k_rep * (r_cut - len) / len;
+                        for (int d = 0; d < 3; ++d) Fp[d] += mag * r[d];
+                    }
+                }
+            }
+        }
+        for (int d = 0; d < 3; ++d) F[d] += Fp[d];
+    }
+    a.F[b] = make_float4(F[0], F[1], F[2], 0.f);
+    a.rec[2 * slot] = ab;
+    a.rec[2 * slot + 1] = make_float4(F[0], F[1], F[2], 0.f);
+}
+
+// ------------------------------------------------------------------------------------------
+// Tile-owner spreading from the FP32 records (see k_spread for the scheme).
+__host__ __device__ __forceinline__ int floor_div32(int a, int b)
+{
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+__host__ __device__ __forceinline__ int wrap_cell32(int c, int n)
+{
+    c %= n;
+    return c < 0 ? c + n : c;
+}
+__host__ __device__ __forceinline__ void halo_cells32(int T0, int T, int bs, int nc, int& lo, int& cnt)
+{
+    lo = floor_div32(2 * T0 - 3, 2 * bs);
+    const int hi = floor_div32(T0 + T + 1 + bs - 1, bs) - 1;
+    cnt = hi - lo + 1;
+    if (cnt >= nc) {
+        lo = 0;
+        cnt = nc;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_start, GridGeo g,
+           BinGeo bg, int TX, int TY, int TZ, int max_ranges, float* __restrict__ f)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geo32 G = geo32(g, bg);
+    const int tileN = TX * TY * TZ;
+    float* acc = reinterpret_cast<float*>(smem_raw);
+    int32_t* rbeg = reinterpret_cast<int32_t*>(acc + 3 * tileN);
+    int32_t* rpre = rbeg + max_ranges;
+    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+    const int box = blockIdx.y;
+    const int ntx = nx / TX, nty = ny / TY;
+    const int tid = blockIdx.x;
+    const int T0[3] = {(tid % ntx) * TX, ((tid / ntx) % nty) * TY, (tid / (ntx * nty)) * TZ};
+    const int T[3] = {TX, TY, TZ};
+    for (int i = threadIdx.x; i < 3 * tileN; i += blockDim.x) acc[i] = 0.f;
+    int lo[3], cnt[3];
+    for (int d = 0; d < 3; ++d) halo_cells32(T0[d], T[d], G.bs, G.nc[d], lo[d], cnt[d]);
+    const int rows = cnt[1] * cnt[2];
+    const int nr = 2 * rows;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int cz = wrap_cell32(lo[2] + r / cnt[1], G.nc[2]);
+        const int cy = wrap_cell32(lo[1] + r % cnt[1], G.nc[1]);
+        const int64_t rowbase = box * G.ncell + ((int64_t)cz * G.nc[1] + cy) * G.nc[0];
+        const int sx = wrap_cell32(lo[0], G.nc[0]);
+        const int ex = sx + cnt[0];
+        const int a1 = ex <= G.nc[0] ? ex : G.nc[0];
+        const int s0 = cell_start[rowbase + sx];
+        rbeg[2 * r] = s0;
+        rpre[2 * r] = cell_start[rowbase + a1] - s0;
+        if (ex > G.nc[0]) {
+            const int t0 = cell_start[rowbase];
+            rbeg[2 * r + 1] = t0;
+            rpre[2 * r + 1] = cell_start[rowbase + (ex - G.nc[0])] - t0;
+        } else {
+            rbeg[2 * r + 1] = 0;
+            rpre[2 * r + 1] = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int carry = 0;
+        for (int c0 = 0; c0 < nr; c0 += 32) {
+            const int i = c0 + lane;
+            const int len = i < nr ? rpre[i] : 0;
+            int x = len;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (i < nr) rpre[i] = carry + x - len;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) rpre[nr] = carry;
+    }
+    __syncthreads();
+    const int total = rpre[nr];
+    const float inv_h3 = G.inv_h * G.inv_h * G.inv_h;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int lo_r = 0, hi_r = nr - 1;
+        while (lo_r < hi_r) {
+            const int mid = (lo_r + hi_r + 1) >> 1;
+            if (rpre[mid] <= t) lo_r = mid; else hi_r = mid - 1;
+        }
+        const int64_t slot = rbeg[lo_r] + (t - rpre[lo_r]);
+        const float4 pa = rec[2 * slot], fv = rec[2 * slot + 1];
+        const int pk = __float_as_int(pa.w);
+        const int c[3] = {cell_unpack(pk, 0), cell_unpack(pk, 1), cell_unpack(pk, 2)};
+        const float hi[3] = {pa.x, pa.y, pa.z};
+        const float Fv[3] = {fv.x * inv_h3, fv.y * inv_h3, fv.z * inv_h3};
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) {
+            float wx[3], wy[3], wz[3];
+            const int ix = window32(c[0], G.bs, hi[0], G.inv_h, comp == 0 ? 0.f : 0.5f, wx) - T0[0];
+            const int iy = window32(c[1], G.bs, hi[1], G.inv_h, comp == 1 ? 0.f : 0.5f, wy) - T0[1];
+            const int iz = window32(c[2], G.bs, hi[2], G.inv_h, comp == 2 ? 0.f : 0.5f, wz) - T0[2];
+            float* acc_c = acc + comp * tileN;
+#pragma unroll
+            for (int cz = 0; cz < 3; ++cz) {
+                const int rz = (iz + cz) & (nz - 1);
+                if (rz >= TZ) continue;
+#pragma unroll
+                for (int cy = 0; cy < 3; ++cy) {
+                    const int ry = (iy + cy) & (ny - 1);
+                    if (ry >= TY) continue;
+                    const float wyz = wy[cy] * wz[cz] * Fv[comp];
+#pragma unroll
+                    for (int cx = 0; cx < 3; ++cx) {
+                        const int rx = (ix + cx) & (nx - 1);
+                        if (rx < TX) atomicAdd(acc_c + (rz * TY + ry) * TX + rx, wx[cx] * wyz);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * tileN; i += blockDim.x) {
+        const int comp = i / tileN, rem = i - comp * tileN;
+        const int rz = rem / (TY * TX), ry = (rem / TX) % TY, rx = rem % TX;
+        f[((size_t)box * 3 + comp) * (size_t)G.N +
+          ((size_t)(T0[2] + rz) * ny + (T0[1] + ry)) * nx + (T0[0] + rx)] = acc[i];
+    }
+}
+
+// Sum of the external forces per box in FP64 (the exact net force: springs and repulsion
+// cancel pairwise), for the k = 0 mode.
+__global__ void __launch_bounds__(256)
+k_ext_sum(const int64_t* __restrict__ box_off, const double* __restrict__ ext,
+          double* __restrict__ out)
+{
+    __shared__ double sh[3][256];
+    const int box = blockIdx.x;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int64_t b = box_off[box] + threadIdx.x; b < box_off[box + 1]; b += blockDim.x)
+        for (int d = 0; d < 3; ++d) s[d] += ext[3 * b + d];
+    for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] = s[d];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] += sh[d][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out[3 * box + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_ext_to_float(int64_t nb, const double* __restrict__ ext, float4* __restrict__ e32)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    e32[b] = make_float4((float)ext[3 * b], (float)ext[3 * b + 1], (float)ext[3 * b + 2], 0.f);
+}
+
+// vbar += scale * sum (mean_mode 0) or 0 (mean_mode 1), per box and component.
+__global__ void k_vbar_step(int n, const double* __restrict__ sum, double scale, int mean_mode,
+                            double* __restrict__ vbar)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    vbar[i] = mean_mode == 0 ? vbar[i] + (sum ? scale * sum[i] : 0.0) : 0.0;
+}
+
+__global__ void k_forces_to_fp64(int64_t nb, const float4* __restrict__ F, double* __restrict__ out)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const float4 f = F[b];
+    out[3 * b] = f.x;
+    out[3 * b + 1] = f.y;
+    out[3 * b + 2] = f.z;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ==========================================================================================
+// Launchers.
+
+cudaError_t launch_split(cudaStream_t st, int64_t nb, const double* q, const GridGeo& g,
+                         const BinGeo& bg, float4* A, float4* B)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_split<<<blocks_for(nb, 256), 256, 0, st>>>(nb, q, g, bg, A, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unsplit(cudaStream_t st, int64_t nb, const float4* A, const float4* B,
+                           const GridGeo& g, const BinGeo& bg, double* q)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_unsplit<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, B, bg, g, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4* A,
+                            const float4* B, const float* v0, const float* v1,
+                            const int32_t* box_of, const GridGeo& g, const BinGeo& bg, float dt,
+                            const float4* A_base, const float4* B_base, float4* A_out,
+                            float4* B_out, double* u_out)
+{
+    if (nb <= 0) return cudaSuccess;
+    const unsigned nbk = blocks_for(nb, 256);
+    if (mode == 0)
+        k_interp32<0><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
+                                           A_out, B_out, u_out);
+    else if (mode == 1)
+        k_interp32<1><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
+                                           A_out, B_out, u_out);
+    else
+        k_interp32<2><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
+                                           A_out, B_out, u_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int32_t* box_of,
+                         int Bx, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
+                         int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
+                         int32_t* scan_tmp, const int32_t* pid, float4* loc)
+{
+    const int64_t ncells = (int64_t)Bx * bg.ncell;
+    cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, st);
+    if (e != cudaSuccess) return e;
+    if (nb > 0)
+        k_bin_count32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, box_of, bg, cell_count,
+                                                           blob_cell, blob_rank);
+    e = launch_exclusive_scan(st, cell_count, cell_start, ncells, scan_tmp);
+    if (e != cudaSuccess) return e;
+    if (nb > 0)
+        k_bin_scatter32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, blob_cell, blob_rank,
+                                                             cell_start, sorted, A, pid, loc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t max_box_blobs, const int64_t* box_off,
+                            const int32_t* sorted, const float4* A, const float4* B,
+                            const float4* loc, const int4* adj, const int32_t* adj_start,
+                            const double* box_par, const int32_t* cell_start,
+                            const int32_t* blob_cell, const float4* ext, float4* F, float4* rec,
+                            const GridGeo& g, const BinGeo& bg)
+{
+    if (max_box_blobs <= 0) return cudaSuccess;
+    Force32Args a{box_off, sorted, A, B, loc, adj, adj_start, box_par, cell_start, blob_cell,
+                  ext, F, rec};
+    dim3 grid(blocks_for(max_box_blobs, 256), (unsigned)Bx);
+    k_forces32<<<grid, 256, 0, st>>>(a, g, bg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
+                            const GridGeo& g, const BinGeo& bg, const int tile[3], float* f)
+{
+    const int TX = tile[0], TY = tile[1], TZ = tile[2];
+    int max_rows = 1;
+    for (int d = 1; d < 3; ++d) {
+        int most = 0;
+        for (int T0 = 0; T0 < g.n[d]; T0 += tile[d]) {
+            int lo, cnt;
+            halo_cells32(T0, tile[d], bg.bs, bg.nc[d], lo, cnt);
+            most = cnt > most ? cnt : most;
+        }
+        max_rows *= most;
+    }
+    const int max_ranges = 2 * max_rows;
+    const size_t smem = 3 * (size_t)TX * TY * TZ * sizeof(float) + sizeof(int32_t) * (2 * max_ranges + 1);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_spread32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    const int ntiles = (g.n[0] / TX) * (g.n[1] / TY) * (g.n[2] / TZ);
+    k_spread32<<<dim3((unsigned)ntiles, (unsigned)Bx), 256, smem, st>>>(rec, cell_start, g, bg, TX,
+                                                                        TY, TZ, max_ranges, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t nb, const int64_t* box_off,
+                               const double* ext, float4* ext32, double* ext_sum)
+{
+    if (nb > 0) k_ext_to_float<<<blocks_for(nb, 256), 256, 0, st>>>(nb, ext, ext32);
+    k_ext_sum<<<Bx, 256, 0, st>>>(box_off, ext, ext_sum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vbar_step(cudaStream_t st, int Bx, const double* sum, double scale,
+                             int mean_mode, double* vbar)
+{
+    k_vbar_step<<<blocks_for(3 * Bx, 128), 128, 0, st>>>(3 * Bx, sum, scale, mean_mode, vbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces_to_fp64(cudaStream_t st, int64_t nb, const float4* F, double* out)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_forces_to_fp64<<<blocks_for(nb, 256), 256, 0, st>>>(nb, F, out);
+    return cudaGetLastError();
+}
+
+}  // namespace mbk

@@ -327,13 +327,12 @@ k_zsolve(FluidArgs<R> a, GridGeo g, int C)
     load_table(twz, reinterpret_cast<const T*>(a.twf[2]), nz);
     const int ky0 = blockIdx.x * C, kx = blockIdx.y, box = blockIdx.z;
     const size_t zstride = (size_t)nxh * ny;
-    T* base[3];
-    for (int c = 0; c < 3; ++c)
-        base[c] = a.spec + (size_t)(box * 3 + c) * nz * zstride + (size_t)kx * ny + ky0;
+    T* base = a.spec + (size_t)(box * 3) * nz * zstride + (size_t)kx * ny + ky0;
+    const size_t cstride = (size_t)nz * zstride;
     auto at = [=](int c, int z, int k) { return (c * nzp + z + (z >> sz)) * Cp + k; };
     for (int i = threadIdx.x; i < 3 * nz * C; i += blockDim.x) {
         const int k = i % C, z = (i / C) % nz, c = i / (C * nz);
-        Bf[at(c, z, k)] = base[c][(size_t)z * zstride + k];
+        Bf[at(c, z, k)] = base[c * cstride + (size_t)z * zstride + k];
     }
     __syncthreads();
     auto idx = [=](int l, int z) { return at(l / C, z, l % C); };
@@ -384,7 +383,7 @@ k_zsolve(FluidArgs<R> a, GridGeo g, int C)
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * nz * C; i += blockDim.x) {
         const int k = i % C, z = (i / C) % nz, c = i / (C * nz);
-        base[c][(size_t)z * zstride + k] = Bf[at(c, z, k)];
+        base[c * cstride + (size_t)z * zstride + k] = Bf[at(c, z, k)];
     }
 }
 

@@ -129,6 +129,9 @@ struct mb_ctx {
     DBuf q, qh, u, F, rec, ext, pid, box_of, adj_start, adj_j, adj_rest, part_start,
         part_blobs, box_off, box_par, cell_count, cell_start, blob_cell, blob_rank, sorted,
         loc, scan_tmp, partial, staging_in, staging_out, mean_scratch;
+    // FP32-grid mode blob state: positions as bin cell + float-float offset (q^n and midpoint)
+    DBuf sA, sB, hA, hB, F32, rec32, ext32, ext_sum, adj32;
+    bool ext_present = false;
     // standalone-operator scratch
     DBuf s_q, s_F, s_rec, s_cell_count, s_cell_start, s_blob_cell, s_blob_rank, s_sorted,
         s_scan, s_u, s_g0, s_g1, s_g2, s_out;
@@ -379,6 +382,30 @@ mb_status rebuild(mb_ctx* ctx)
     MB_TRY(up(ctx->part_blobs, part_blobs.data(), sizeof(int32_t) * nb));
     MB_TRY(up(ctx->box_off, off.data(), sizeof(int64_t) * (B + 1)));
     MB_TRY(up(ctx->box_par, par.data(), sizeof(double) * 3 * B));
+    if (ctx->rsz == 4) {
+        MB_TRY(ensure(ctx->sA, sizeof(float4) * nb, E, "split q"));
+        MB_TRY(ensure(ctx->sB, sizeof(float4) * nb, E, "split q"));
+        MB_TRY(ensure(ctx->hA, sizeof(float4) * nb, E, "split q_half"));
+        MB_TRY(ensure(ctx->hB, sizeof(float4) * nb, E, "split q_half"));
+        MB_TRY(ensure(ctx->F32, sizeof(float4) * nb, E, "F32"));
+        MB_TRY(ensure(ctx->rec32, 2 * sizeof(float4) * nb, E, "rec32"));
+        MB_TRY(ensure(ctx->ext32, sizeof(float4) * nb, E, "ext32"));
+        MB_TRY(ensure(ctx->ext_sum, sizeof(double) * 3 * B, E, "ext_sum"));
+        MB_TRY(ensure(ctx->adj32, sizeof(int4) * std::max<int64_t>(nadj, 1), E, "adj32"));
+        std::vector<int32_t> a32(4 * nadj);
+        for (int64_t e = 0; e < nadj; ++e) {
+            const double r0 = adj_rest[e], r0sq = r0 * r0;
+            const float h = (float)r0sq, l = (float)(r0sq - (double)h), rf = (float)r0;
+            a32[4 * e] = adj_j[e];
+            std::memcpy(&a32[4 * e + 1], &rf, 4);
+            std::memcpy(&a32[4 * e + 2], &h, 4);
+            std::memcpy(&a32[4 * e + 3], &l, 4);
+        }
+        MB_TRY(up(ctx->adj32, a32.data(), sizeof(int32_t) * 4 * nadj));
+        MB_CUDA(launch_split(st, nb, static_cast<const double*>(ctx->q.p), ctx->g, ctx->bg,
+                             static_cast<float4*>(ctx->sA.p), static_cast<float4*>(ctx->sB.p)));
+        ctx->ext_present = false;
+    }
     // the host vectors die at return: make the copies complete first
     MB_CUDA(cudaStreamSynchronize(st));
     ctx->dirty = false;
@@ -570,6 +597,109 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
     return MB_OK;
 }
 
+// One time step of every box in FP32-grid mode: blob positions as bin cell + float-float
+// offset, forces and weights on the FP32 pipes, the k = 0 mode from the FP64 external force sum.
+mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
+{
+    cudaStream_t st = ctx->st;
+    const GridGeo& g = ctx->g;
+    const int B = ctx->B;
+    float* vcur = static_cast<float*>(ctx->v[ctx->cur].p);
+    float* vnext = static_cast<float*>(ctx->v[ctx->cur ^ 1].p);
+    float4* sA = static_cast<float4*>(ctx->sA.p);
+    float4* sB = static_cast<float4*>(ctx->sB.p);
+    float4* hA = static_cast<float4*>(ctx->hA.p);
+    float4* hB = static_cast<float4*>(ctx->hB.p);
+    const int32_t* box_of = static_cast<const int32_t*>(ctx->box_of.p);
+    const bool blobs = ctx->nb > 0;
+    if (ctx->timing) {
+        if (ctx->ev_pending == mb_ctx::EV_RING) MB_TRY(drain_stage_events(ctx));
+        ctx->ev = ctx->ev_ring.data() + (size_t)ctx->ev_pending * (NUM_STAGES + 1);
+    }
+    auto mark = [&](int i) { if (ctx->timing) cudaEventRecord(ctx->ev[i], st); };
+    const float dt = (float)ctx->d.dt;
+    mark(ST_INTERP_PREDICT);
+    if (blobs) {
+        MB_CUDA(launch_interp32(st, 1, ctx->nb, sA, sB, vcur, nullptr, box_of, g, ctx->bg, dt,
+                                nullptr, nullptr, hA, hB, nullptr));
+        ctx->launches += 1;
+    }
+    mark(ST_BIN);
+    if (blobs) {
+        MB_CUDA(launch_bin32(st, ctx->nb, hA, box_of, B, ctx->bg,
+                             static_cast<int32_t*>(ctx->cell_count.p),
+                             static_cast<int32_t*>(ctx->cell_start.p),
+                             static_cast<int32_t*>(ctx->blob_cell.p),
+                             static_cast<int32_t*>(ctx->blob_rank.p),
+                             static_cast<int32_t*>(ctx->sorted.p),
+                             static_cast<int32_t*>(ctx->scan_tmp.p),
+                             static_cast<const int32_t*>(ctx->pid.p),
+                             static_cast<float4*>(ctx->loc.p)));
+        ctx->launches += 5;
+    }
+    mark(ST_FORCES);
+    if (blobs) {
+        MB_CUDA(launch_forces32(st, B, ctx->max_box_blobs, static_cast<const int64_t*>(ctx->box_off.p),
+                                static_cast<const int32_t*>(ctx->sorted.p), hA, hB,
+                                static_cast<const float4*>(ctx->loc.p),
+                                static_cast<const int4*>(ctx->adj32.p),
+                                static_cast<const int32_t*>(ctx->adj_start.p),
+                                static_cast<const double*>(ctx->box_par.p),
+                                static_cast<const int32_t*>(ctx->cell_start.p),
+                                static_cast<const int32_t*>(ctx->blob_cell.p),
+                                ext ? static_cast<const float4*>(ctx->ext32.p) : nullptr,
+                                static_cast<float4*>(ctx->F32.p),
+                                static_cast<float4*>(ctx->rec32.p), g, ctx->bg));
+        ctx->launches += 1;
+    }
+    mark(ST_FORCE_SUM);
+    {
+        const double L3 = g.L[0] * g.L[1] * g.L[2];
+        MB_CUDA(launch_vbar_step(st, B, ext ? static_cast<const double*>(ctx->ext_sum.p) : nullptr,
+                                 ctx->d.dt / (ctx->d.rho * L3), ctx->d.mean_mode,
+                                 static_cast<double*>(ctx->vbar.p)));
+        ctx->launches += 1;
+    }
+    mark(ST_SPREAD);
+    if (blobs) {
+        MB_CUDA(launch_spread32(st, B, static_cast<const float4*>(ctx->rec32.p),
+                                static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
+                                ctx->tile, static_cast<float*>(ctx->f.p)));
+        ctx->launches += 1;
+    }
+    const double* mean = ctx->d.mean_mode == 0 ? static_cast<const double*>(ctx->vbar.p) : nullptr;
+    FluidArgs<float> fa = fluid_args<float>(ctx, vcur, blobs ? ctx->f.p : nullptr, vnext,
+                                            ctx->body_prof.p, body, mean);
+    cudaEvent_t* fm = ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr;
+    if (ctx->fft_passes == 5) {
+        MB_CUDA(launch_fluid<float>(st, B, g, fa, fm));
+        ctx->launches += FLUID_KERNELS;
+    } else {
+        MB_CUDA(launch_fluid3<float>(st, B, g, fa, fm));
+        ctx->launches += FLUID3_KERNELS;
+    }
+    if (blobs) {
+        MB_CUDA(launch_interp32(st, 2, ctx->nb, hA, hB, vcur, vnext, box_of, g, ctx->bg, dt, sA,
+                                sB, sA, sB, nullptr));
+        ctx->launches += 1;
+    }
+    mark(NUM_STAGES);
+    if (ctx->timing) ctx->ev_pending++;
+    ctx->cur ^= 1;
+    ctx->steps_taken++;
+    return MB_OK;
+}
+
+// FP64 blob positions of the current state (from the split form in FP32-grid mode).
+mb_status current_positions(mb_ctx* ctx)
+{
+    if (ctx->rsz == 4 && ctx->nb > 0)
+        MB_CUDA(launch_unsplit(ctx->st, ctx->nb, static_cast<const float4*>(ctx->sA.p),
+                               static_cast<const float4*>(ctx->sB.p), ctx->g, ctx->bg,
+                               static_cast<double*>(ctx->q.p)));
+    return MB_OK;
+}
+
 void pick_tile(mb_ctx* ctx)
 {
     const int want[3] = {32, 8, 8};
@@ -642,7 +772,9 @@ void release(mb_ctx* ctx)
                    &ctx->staging_in, &ctx->staging_out, &ctx->mean_scratch, &ctx->s_q,
                    &ctx->s_F, &ctx->s_rec, &ctx->s_cell_count, &ctx->s_cell_start,
                    &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
-                   &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out};
+                   &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out, &ctx->sA,
+                   &ctx->sB, &ctx->hA, &ctx->hB, &ctx->F32, &ctx->rec32, &ctx->ext32,
+                   &ctx->ext_sum, &ctx->adj32};
     for (DBuf* b : all) dfree(*b);
     for (cudaEvent_t& e : ctx->ev_ring)
         if (e) cudaEventDestroy(e);
@@ -885,9 +1017,14 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
             MB_CUDA(cudaMemcpyAsync(ctx->ext.p, src, sizeof(double) * 3 * ctx->nb,
                                     cudaMemcpyDeviceToDevice, ctx->st));
         ext = static_cast<const double*>(ctx->ext.p);
+        if (ctx->rsz == 4)
+            MB_CUDA(launch_ext_prepare(ctx->st, ctx->B, ctx->nb,
+                                       static_cast<const int64_t*>(ctx->box_off.p), ext,
+                                       static_cast<float4*>(ctx->ext32.p),
+                                       static_cast<double*>(ctx->ext_sum.p)));
     }
     for (int s = 0; s < n_steps; ++s) {
-        if (ctx->rsz == 4) MB_TRY(do_step<float>(ctx, ext, body_force));
+        if (ctx->rsz == 4) MB_TRY(do_step_fast(ctx, ext != nullptr, body_force));
         else MB_TRY(do_step<double>(ctx, ext, body_force));
     }
     return MB_OK;
@@ -903,6 +1040,13 @@ mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos)
     }
     const size_t by = sizeof(double) * 3 * ctx->nb;
     if (ctx->nb == 0) return MB_OK;
+    if (ctx->rsz == 4) {
+        MB_CUDA(launch_forces_to_fp64(ctx->st, ctx->nb, static_cast<const float4*>(ctx->F32.p),
+                                      static_cast<double*>(ctx->F.p)));
+        MB_CUDA(launch_unsplit(ctx->st, ctx->nb, static_cast<const float4*>(ctx->hA.p),
+                               static_cast<const float4*>(ctx->hB.p), ctx->g, ctx->bg,
+                               static_cast<double*>(ctx->qh.p)));
+    }
     double* outs[2] = {blob_force, midpoint_pos};
     DBuf* srcs[2] = {&ctx->F, &ctx->qh};
     for (int i = 0; i < 2; ++i) {
@@ -976,10 +1120,12 @@ static mb_status blob_velocities(mb_ctx* ctx)
 {
     if (ctx->nb == 0) return MB_OK;
     if (ctx->rsz == 4)
-        MB_CUDA(launch_interp<float>(ctx->st, 0, ctx->nb, static_cast<const double*>(ctx->q.p),
-                                     nullptr, static_cast<const float*>(ctx->v[ctx->cur].p),
-                                     nullptr, static_cast<const int32_t*>(ctx->box_of.p), ctx->g,
-                                     ctx->d.dt, static_cast<double*>(ctx->u.p), nullptr));
+        MB_CUDA(launch_interp32(ctx->st, 0, ctx->nb, static_cast<const float4*>(ctx->sA.p),
+                                static_cast<const float4*>(ctx->sB.p),
+                                static_cast<const float*>(ctx->v[ctx->cur].p), nullptr,
+                                static_cast<const int32_t*>(ctx->box_of.p), ctx->g, ctx->bg,
+                                (float)ctx->d.dt, nullptr, nullptr, nullptr, nullptr,
+                                static_cast<double*>(ctx->u.p)));
     else
         MB_CUDA(launch_interp<double>(ctx->st, 0, ctx->nb, static_cast<const double*>(ctx->q.p),
                                       nullptr, static_cast<const double*>(ctx->v[ctx->cur].p),
@@ -994,6 +1140,7 @@ mb_status mb_get_velocities(mb_ctx* ctx, double* blob_vel, double* blob_pos, dou
     if (!ctx) return MB_EINVAL;
     DeviceGuard dg(ctx->device);
     MB_TRY(ensure_ready(ctx));
+    if (blob_pos || particle_U) MB_TRY(current_positions(ctx));
     if (blob_vel || particle_U) MB_TRY(blob_velocities(ctx));
     if (blob_vel && ctx->nb > 0) {
         void* dst;
@@ -1041,6 +1188,7 @@ mb_status mb_get_particle_velocities(mb_ctx* ctx, double* particle_U, double* pa
     DeviceGuard dg(ctx->device);
     MB_TRY(ensure_ready(ctx));
     if (ctx->np == 0 || (!particle_U && !particle_Omega)) return MB_OK;
+    MB_TRY(current_positions(ctx));
     MB_TRY(blob_velocities(ctx));
     const size_t by = sizeof(double) * 3 * ctx->np;
     void *dU = nullptr, *dW = nullptr;

@@ -126,6 +126,39 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
                           cudaEvent_t* marks = nullptr);
 constexpr int FLUID3_KERNELS = 3;
 
+// Exclusive scan of n ints into out[0..n] (out[n] = total); tile_tmp holds n/4096 + 2 ints.
+cudaError_t launch_exclusive_scan(cudaStream_t st, const int32_t* in, int32_t* out, int64_t n,
+                                  int32_t* tile_tmp);
+
+// FP32-grid blob pipeline (kernels_blob32.cu): positions as bin cell + float-float offset,
+// A = {hi.xyz, packed cell}, B = {lo.xyz, 0} per blob.
+cudaError_t launch_split(cudaStream_t st, int64_t nb, const double* q, const GridGeo& g,
+                         const BinGeo& bg, float4* A, float4* B);
+cudaError_t launch_unsplit(cudaStream_t st, int64_t nb, const float4* A, const float4* B,
+                           const GridGeo& g, const BinGeo& bg, double* q);
+cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4* A,
+                            const float4* B, const float* v0, const float* v1,
+                            const int32_t* box_of, const GridGeo& g, const BinGeo& bg, float dt,
+                            const float4* A_base, const float4* B_base, float4* A_out,
+                            float4* B_out, double* u_out);
+cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int32_t* box_of,
+                         int Bx, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
+                         int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
+                         int32_t* scan_tmp, const int32_t* pid, float4* loc);
+cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t max_box_blobs, const int64_t* box_off,
+                            const int32_t* sorted, const float4* A, const float4* B,
+                            const float4* loc, const int4* adj, const int32_t* adj_start,
+                            const double* box_par, const int32_t* cell_start,
+                            const int32_t* blob_cell, const float4* ext, float4* F, float4* rec,
+                            const GridGeo& g, const BinGeo& bg);
+cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
+                            const GridGeo& g, const BinGeo& bg, const int tile[3], float* f);
+cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t nb, const int64_t* box_off,
+                               const double* ext, float4* ext32, double* ext_sum);
+cudaError_t launch_vbar_step(cudaStream_t st, int Bx, const double* sum, double scale,
+                             int mean_mode, double* vbar);
+cudaError_t launch_forces_to_fp64(cudaStream_t st, int64_t nb, const float4* F, double* out);
+
 // Reductions / utilities.
 template <typename R>
 cudaError_t launch_grid_mean(cudaStream_t st, int B, const GridGeo& g, const R* v,
