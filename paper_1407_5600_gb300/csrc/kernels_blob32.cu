@@ -131,10 +131,12 @@ k_interp32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ 
            const float* __restrict__ v0, const float* __restrict__ v1,
            const int32_t* __restrict__ box_of, GridGeo g, BinGeo bg, float dt,
            const float4* A_base, const float4* B_base, float4* A_out, float4* B_out,
-           double* __restrict__ u_out)
+           double* __restrict__ u_out, const int32_t* __restrict__ order)
 {
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= nb) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    // blobs in cell order (when known) so that neighbouring threads gather neighbouring nodes
+    const int64_t b = order ? order[t] : t;
     const Geo32 G = geo32(g, bg);
     const int box = box_of ? box_of[b] : 0;
     const float4 a = A[b];
@@ -560,19 +562,19 @@ cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4*
                             const float4* B, const float* v0, const float* v1,
                             const int32_t* box_of, const GridGeo& g, const BinGeo& bg, float dt,
                             const float4* A_base, const float4* B_base, float4* A_out,
-                            float4* B_out, double* u_out)
+                            float4* B_out, double* u_out, const int32_t* order)
 {
     if (nb <= 0) return cudaSuccess;
     const unsigned nbk = blocks_for(nb, 256);
     if (mode == 0)
         k_interp32<0><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
-                                           A_out, B_out, u_out);
+                                           A_out, B_out, u_out, order);
     else if (mode == 1)
         k_interp32<1><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
-                                           A_out, B_out, u_out);
+                                           A_out, B_out, u_out, order);
     else
         k_interp32<2><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
-                                           A_out, B_out, u_out);
+                                           A_out, B_out, u_out, order);
     return cudaGetLastError();
 }
 

@@ -312,26 +312,29 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
 }
 
 // ------------------------------------------------------------------------------------------
-// Pass B.  CTA = (ky block of width C, kx, box); shared buffer [3][pad(nz)][Cp].
-template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2)
-k_zsolve(FluidArgs<R> a, GridGeo g, int C)
+// Pass B.  CTA = (ky block of width C, kx, box); shared buffer [3][pad(nz)][C + 4].  C is a
+// compile-time width (16 FP32, 8 FP64) and the block has 3 C N2 threads, one round of lines.
+template <typename R, int C>
+__global__ void __launch_bounds__(3 * C * 8)
+k_zsolve(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<R>::T;
+    constexpr int Cp = C + 4;                    // 4 z-rows x 4 lines per half-warp: distinct banks
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
+    const int lz = 31 - __clz(nz);
     const int sz = pad_shift(nz), nzp = padded_len(nz);
-    const int Cp = C + 4;                        // rows of C + 4 complex: (4 z-rows x 4 lines)
-    T* Bf = reinterpret_cast<T*>(smem_raw);      //  per half-warp hit distinct banks
+    T* Bf = reinterpret_cast<T*>(smem_raw);
     T* twz = Bf + 3 * nzp * Cp;
     load_table(twz, reinterpret_cast<const T*>(a.twf[2]), nz);
     const int ky0 = blockIdx.x * C, kx = blockIdx.y, box = blockIdx.z;
     const size_t zstride = (size_t)nxh * ny;
-    T* base = a.spec + (size_t)(box * 3) * nz * zstride + (size_t)kx * ny + ky0;
     const size_t cstride = (size_t)nz * zstride;
+    T* base = a.spec + (size_t)(box * 3) * cstride + (size_t)kx * ny + ky0;
     auto at = [=](int c, int z, int k) { return (c * nzp + z + (z >> sz)) * Cp + k; };
-    for (int i = threadIdx.x; i < 3 * nz * C; i += blockDim.x) {
-        const int k = i % C, z = (i / C) % nz, c = i / (C * nz);
+    const int total = 3 * nz * C;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
         Bf[at(c, z, k)] = base[c * cstride + (size_t)z * zstride + k];
     }
     __syncthreads();
@@ -381,8 +384,8 @@ k_zsolve(FluidArgs<R> a, GridGeo g, int C)
     __syncthreads();
     lines_fft_n(nz, Bf, 3 * C, idx, twz, true);
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * nz * C; i += blockDim.x) {
-        const int k = i % C, z = (i / C) % nz, c = i / (C * nz);
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
         base[c * cstride + (size_t)z * zstride + k] = Bf[at(c, z, k)];
     }
 }
@@ -465,25 +468,27 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
 {
     using T = typename C2<R>::T;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
+    constexpr int CZ = sizeof(R) == 4 ? 16 : 8;      // ky columns per z-pass block
     static bool attr[2] = {false, false};
     const int w = sizeof(R) == 8;
     if (!attr[w]) {
         const int lim = 200 * 1024;
         cudaFuncSetAttribute(k_plane_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_zsolve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_zsolve<R, CZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_zsolve<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_plane_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         attr[w] = true;
     }
     const size_t smem_plane = ((size_t)(ny / 2) * plane_ld(nx) + nx + ny) * sizeof(T);
-    int C = sizeof(R) == 4 ? 16 : 8;
-    if (C > ny) C = ny;
+    const int C = ny >= CZ ? CZ : 4;
     const size_t smem_z = ((size_t)3 * padded_len(nz) * (C + 4) + nz) * sizeof(T);
     auto mark = [&](int i) { if (marks) cudaEventRecord(marks[i], st); };
     mark(0);
     k_plane_fwd<R><<<dim3(nz, 3 * B), 256, smem_plane, st>>>(a, g);
     mark(1);
     mark(2);
-    k_zsolve<R><<<dim3(ny / C, nxh, B), 256, smem_z, st>>>(a, g, C);
+    if (C == CZ) k_zsolve<R, CZ><<<dim3(ny / C, nxh, B), 3 * CZ * 8, smem_z, st>>>(a, g);
+    else k_zsolve<R, 4><<<dim3(ny / 4, nxh, B), 3 * 4 * 8, smem_z, st>>>(a, g);
     mark(3);
     mark(4);
     k_plane_inv<R><<<dim3(nz, 3 * B), 256, smem_plane, st>>>(a, g);

@@ -132,6 +132,7 @@ struct mb_ctx {
     // FP32-grid mode blob state: positions as bin cell + float-float offset (q^n and midpoint)
     DBuf sA, sB, hA, hB, F32, rec32, ext32, ext_sum, adj32;
     bool ext_present = false;
+    bool sorted_valid = false;     // `sorted` holds a permutation of the current blobs
     // standalone-operator scratch
     DBuf s_q, s_F, s_rec, s_cell_count, s_cell_start, s_blob_cell, s_blob_rank, s_sorted,
         s_scan, s_u, s_g0, s_g1, s_g2, s_out;
@@ -405,6 +406,7 @@ mb_status rebuild(mb_ctx* ctx)
         MB_CUDA(launch_split(st, nb, static_cast<const double*>(ctx->q.p), ctx->g, ctx->bg,
                              static_cast<float4*>(ctx->sA.p), static_cast<float4*>(ctx->sB.p)));
         ctx->ext_present = false;
+        ctx->sorted_valid = false;
     }
     // the host vectors die at return: make the copies complete first
     MB_CUDA(cudaStreamSynchronize(st));
@@ -620,8 +622,11 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     const float dt = (float)ctx->d.dt;
     mark(ST_INTERP_PREDICT);
     if (blobs) {
+        // the previous step's cell order still groups neighbouring blobs
         MB_CUDA(launch_interp32(st, 1, ctx->nb, sA, sB, vcur, nullptr, box_of, g, ctx->bg, dt,
-                                nullptr, nullptr, hA, hB, nullptr));
+                                nullptr, nullptr, hA, hB, nullptr,
+                                ctx->sorted_valid ? static_cast<const int32_t*>(ctx->sorted.p)
+                                                  : nullptr));
         ctx->launches += 1;
     }
     mark(ST_BIN);
@@ -636,6 +641,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                              static_cast<const int32_t*>(ctx->pid.p),
                              static_cast<float4*>(ctx->loc.p)));
         ctx->launches += 5;
+        ctx->sorted_valid = true;
     }
     mark(ST_FORCES);
     if (blobs) {
@@ -680,7 +686,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     }
     if (blobs) {
         MB_CUDA(launch_interp32(st, 2, ctx->nb, hA, hB, vcur, vnext, box_of, g, ctx->bg, dt, sA,
-                                sB, sA, sB, nullptr));
+                                sB, sA, sB, nullptr, static_cast<const int32_t*>(ctx->sorted.p)));
         ctx->launches += 1;
     }
     mark(NUM_STAGES);

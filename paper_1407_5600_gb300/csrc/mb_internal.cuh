@@ -140,7 +140,7 @@ cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4*
                             const float4* B, const float* v0, const float* v1,
                             const int32_t* box_of, const GridGeo& g, const BinGeo& bg, float dt,
                             const float4* A_base, const float4* B_base, float4* A_out,
-                            float4* B_out, double* u_out);
+                            float4* B_out, double* u_out, const int32_t* order = nullptr);
 cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int32_t* box_of,
                          int Bx, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
                          int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
