@@ -172,6 +172,35 @@ const char* mb_stage_name(int stage);
 /* Number of CUDA kernels the context's steps have launched so far. */
 mb_status mb_get_launch_count(const mb_ctx* ctx, int64_t* launches);
 
+/* Replaces the blob positions of all boxes ([total blobs][3], the same blobs and order as set
+ * by mb_set_particles), for example to resume from a checkpoint.  Positions are taken modulo
+ * the box.  mb_get_forces is undefined until the next step. */
+mb_status mb_set_positions(mb_ctx* ctx, const double* pos);
+
+/* Reverse-mode derivative of one mb_step (the adjoint of the step map).  Given the state the
+ * step started from (pos_n [total blobs][3], grid_v_n one box grid) and the gradients of a
+ * scalar loss with respect to the state after the step, it overwrites
+ *   grad_pos  (in: dL/dq^{n+1}; out: dL/dq^n)            [total blobs][3]
+ *   grad_v    (in: dL/dv^{n+1}; out: dL/dv^n)            one box grid
+ * and adds dL/dk_spring of this step to *grad_k_spring (may be NULL).  ext_blob_force and
+ * body_force must be those of the forward step (either may be NULL).  The step is recomputed
+ * from (pos_n, grid_v_n), then its stages are transposed in reverse order: the transpose of J
+ * is h^3 S and of S is h^-3 J; the position derivatives of J and S use the derivative of the
+ * kernel Phi (Eq. delta, Phi is C^1); the fluid update v^{n+1} = A v^n + T f has symmetric A
+ * and T (Eq. vf: the projection P, the Laplacian and the CN factors are symmetric and commute),
+ * so its transpose reuses the forward solver; the blob-force transpose is the force Hessian
+ * applied to the incoming gradient (forces derive from a potential).  Provided for FP64
+ * contexts (precision 1) with batch 1; MB_EINVAL otherwise.  Arrays may be host or device. */
+mb_status mb_adjoint_step(mb_ctx* ctx, const double* pos_n, const void* grid_v_n,
+                          const double* ext_blob_force, const double* body_force,
+                          double* grad_pos, void* grad_v, double* grad_k_spring);
+
+/* Adjoint of the blob velocities u = J(q) v (Eq. ju) at positions pos and field grid_v:
+ * grad_pos += (du/dq)^T grad_u and grad_v += J^T grad_u = h^3 S(q) grad_u.  FP64 contexts with
+ * batch 1.  Arrays may be host or device. */
+mb_status mb_velocity_adjoint(mb_ctx* ctx, const double* pos, const void* grid_v,
+                              const double* grad_u, double* grad_pos, void* grad_v);
+
 /* Number of blobs and particles of all boxes together. */
 mb_status mb_get_counts(const mb_ctx* ctx, int64_t* total_blobs, int64_t* total_particles);
 

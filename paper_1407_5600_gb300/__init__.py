@@ -21,7 +21,7 @@ __all__ = [
     "get_velocities", "get_particle_velocities", "set_velocity_field", "spread", "spread_static",
     "interp",
     "fluid_update", "get_counts", "get_forces", "set_stage_timing", "get_stage_times",
-    "get_launch_count", "last_error", "Multiblob",
+    "get_launch_count", "set_positions", "adjoint_step", "velocity_adjoint", "last_error", "Multiblob",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -103,6 +103,9 @@ def load_library(path: str | None = None):
         "mb_get_forces": [P, P, P],
         "mb_spread_static": [ctypes.POINTER(_Desc), I64, P, P, P, P],
         "mb_set_stage_timing": [P, I],
+        "mb_set_positions": [P, P],
+        "mb_adjoint_step": [P, P, P, P, P, P, P, P],
+        "mb_velocity_adjoint": [P, P, P, P, P, P],
         "mb_get_stage_times": [P, I, P, P, ctypes.POINTER(I)],
         "mb_get_launch_count": [P, ctypes.POINTER(I64)],
     }
@@ -250,6 +253,29 @@ def get_launch_count(ctx):
     return n.value
 
 
+def set_positions(ctx, pos):
+    _check(ctx, load_library().mb_set_positions(ctx, _ptr(pos, np.float64)))
+
+
+def adjoint_step(ctx, pos_n, grid_v_n, ext_blob_force, body_force, grad_pos, grad_v,
+                 grad_k_spring=None):
+    """mb_adjoint_step: overwrites grad_pos and grad_v in place, adds to grad_k_spring[0]."""
+    body = None
+    if body_force is not None:
+        body = np.ascontiguousarray(np.asarray(body_force, dtype=np.float64).reshape(4))
+    _check(ctx, load_library().mb_adjoint_step(
+        ctx, _ptr(pos_n, np.float64), _ptr(grid_v_n), _ptr(ext_blob_force, np.float64),
+        _ptr(body), _ptr(grad_pos, np.float64), _ptr(grad_v),
+        _ptr(grad_k_spring, np.float64) if grad_k_spring is not None else None))
+
+
+def velocity_adjoint(ctx, pos, grid_v, grad_u, grad_pos, grad_v):
+    """mb_velocity_adjoint: grad_pos += (du/dq)^T grad_u, grad_v += J^T grad_u."""
+    _check(ctx, load_library().mb_velocity_adjoint(
+        ctx, _ptr(pos, np.float64), _ptr(grid_v), _ptr(grad_u, np.float64),
+        _ptr(grad_pos, np.float64), _ptr(grad_v)))
+
+
 def get_counts(ctx):
     nb, np_ = ctypes.c_int64(), ctypes.c_int64()
     _check(ctx, load_library().mb_get_counts(ctx, ctypes.byref(nb), ctypes.byref(np_)))
@@ -350,6 +376,9 @@ class Multiblob:
         out = self.torch.empty(self.grid_shape(), dtype=self.grid_dtype, device=self.device)
         get_velocities(self.ctx, grid_v=out)
         return out
+
+    def set_positions(self, pos):
+        set_positions(self.ctx, self._dev(pos, self.torch.float64))
 
     def set_velocity_field(self, v):
         set_velocity_field(self.ctx, self._dev(v, self.grid_dtype))

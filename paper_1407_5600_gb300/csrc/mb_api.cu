@@ -133,6 +133,9 @@ struct mb_ctx {
     DBuf sA, sB, hA, hB, F32, rec32, ext32, ext_sum, adj32;
     bool ext_present = false;
     bool sorted_valid = false;     // `sorted` holds a permutation of the current blobs
+    // adjoint scratch: blob vectors and grids (FP64 contexts)
+    DBuf a_qn, a_u, a_qh, a_gq, a_guc, a_gqh, a_gF, a_gu, a_gk;
+    DBuf a_vn, a_vp, a_w, a_gw, a_gvp, a_gvn, a_gf, a_tmp, a_zero;
     // standalone-operator scratch
     DBuf s_q, s_F, s_rec, s_cell_count, s_cell_start, s_blob_cell, s_blob_rank, s_sorted,
         s_scan, s_u, s_g0, s_g1, s_g2, s_out;
@@ -780,7 +783,10 @@ void release(mb_ctx* ctx)
                    &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
                    &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out, &ctx->sA,
                    &ctx->sB, &ctx->hA, &ctx->hB, &ctx->F32, &ctx->rec32, &ctx->ext32,
-                   &ctx->ext_sum, &ctx->adj32};
+                   &ctx->ext_sum, &ctx->adj32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
+                   &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk,
+                   &ctx->a_vn, &ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvp, &ctx->a_gvn,
+                   &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero};
     for (DBuf* b : all) dfree(*b);
     for (cudaEvent_t& e : ctx->ev_ring)
         if (e) cudaEventDestroy(e);
@@ -1106,6 +1112,232 @@ mb_status mb_get_launch_count(const mb_ctx* ctx, int64_t* launches)
 {
     if (!ctx || !launches) return MB_EINVAL;
     *launches = ctx->launches;
+    return MB_OK;
+}
+
+mb_status mb_set_positions(mb_ctx* ctx, const double* pos)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (!pos) return invalid(ctx, "pos must be non-null");
+    MB_TRY(ensure_ready(ctx));
+    if (ctx->nb == 0) return MB_OK;
+    const size_t by = sizeof(double) * 3 * ctx->nb;
+    MB_CUDA(cudaMemcpyAsync(ctx->q.p, pos, by, cudaMemcpyDefault, ctx->st));
+    double* q = static_cast<double*>(ctx->q.p);
+    k_wrap<<<(unsigned)((3 * ctx->nb + 255) / 256), 256, 0, ctx->st>>>(ctx->nb, q, ctx->g.L[0],
+                                                                      ctx->g.L[1], ctx->g.L[2]);
+    MB_CUDA(cudaGetLastError());
+    if (ctx->rsz == 4)
+        MB_CUDA(launch_split(ctx->st, ctx->nb, q, ctx->g, ctx->bg, static_cast<float4*>(ctx->sA.p),
+                             static_cast<float4*>(ctx->sB.p)));
+    ctx->sorted_valid = false;
+    ctx->steps_taken = 0;
+    MB_CUDA(cudaStreamSynchronize(ctx->st));
+    return MB_OK;
+}
+
+namespace {
+
+// Copies a caller array (host or device) into a device scratch buffer.
+mb_status pull(mb_ctx* ctx, DBuf& dst, const void* src, size_t bytes, const char* what)
+{
+    MB_TRY(ensure(dst, bytes, ctx->err, what));
+    MB_CUDA(cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyDefault, ctx->st));
+    return MB_OK;
+}
+
+// Copies a device scratch buffer back to a caller array (host or device).
+mb_status push(mb_ctx* ctx, void* dst, const DBuf& src, size_t bytes)
+{
+    MB_CUDA(cudaMemcpyAsync(dst, src.p, bytes, cudaMemcpyDefault, ctx->st));
+    if (!is_device_ptr(dst)) MB_CUDA(cudaStreamSynchronize(ctx->st));
+    return MB_OK;
+}
+
+mb_status adjoint_preconditions(mb_ctx* ctx)
+{
+    if (ctx->rsz != 8) return invalid(ctx, "the adjoint is provided for FP64 contexts (precision 1)");
+    if (ctx->B != 1) return invalid(ctx, "the adjoint is provided for batch 1");
+    return ensure_ready(ctx);
+}
+
+// gq += G(q; v, gu) and gv += h^3 S(q) gu (the transpose of u = J(q) v), all on device buffers.
+mb_status velocity_adjoint_dev(mb_ctx* ctx, const double* q, const double* v, const double* gu,
+                               double* gq, double* gv)
+{
+    const int64_t n3N = 3 * ctx->g.N;
+    const double h3 = ctx->d.h * ctx->d.h * ctx->d.h;
+    MB_CUDA(launch_grad_interp(ctx->st, ctx->nb, q, v, gu, ctx->g, 1.0, gq));
+    MB_TRY(ensure(ctx->a_tmp, sizeof(double) * n3N, ctx->err, "adjoint grid"));
+    double* tmp = static_cast<double*>(ctx->a_tmp.p);
+    MB_TRY(standalone_spread<double>(ctx, ctx->nb, q, gu, tmp));
+    MB_CUDA(launch_axpby(ctx->st, n3N, 1.0, gv, h3, tmp, gv));
+    return MB_OK;
+}
+
+}  // namespace
+
+mb_status mb_velocity_adjoint(mb_ctx* ctx, const double* pos, const void* grid_v,
+                              const double* grad_u, double* grad_pos, void* grad_v)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (!pos || !grid_v || !grad_u || !grad_pos || !grad_v) return invalid(ctx, "null argument");
+    MB_TRY(adjoint_preconditions(ctx));
+    const int64_t nb = ctx->nb;
+    const size_t bv = sizeof(double) * 3 * nb, bg = sizeof(double) * 3 * ctx->g.N;
+    MB_TRY(pull(ctx, ctx->a_qn, pos, bv, "adjoint q"));
+    MB_TRY(pull(ctx, ctx->a_vn, grid_v, bg, "adjoint v"));
+    MB_TRY(pull(ctx, ctx->a_gu, grad_u, bv, "adjoint gu"));
+    MB_TRY(pull(ctx, ctx->a_gq, grad_pos, bv, "adjoint gq"));
+    MB_TRY(pull(ctx, ctx->a_gvn, grad_v, bg, "adjoint gv"));
+    double* q = static_cast<double*>(ctx->a_qn.p);
+    k_wrap<<<(unsigned)((3 * nb + 255) / 256), 256, 0, ctx->st>>>(nb, q, ctx->g.L[0], ctx->g.L[1],
+                                                                 ctx->g.L[2]);
+    MB_CUDA(cudaGetLastError());
+    MB_TRY(velocity_adjoint_dev(ctx, q, static_cast<const double*>(ctx->a_vn.p),
+                                static_cast<const double*>(ctx->a_gu.p),
+                                static_cast<double*>(ctx->a_gq.p),
+                                static_cast<double*>(ctx->a_gvn.p)));
+    MB_TRY(push(ctx, grad_pos, ctx->a_gq, bv));
+    return push(ctx, grad_v, ctx->a_gvn, bg);
+}
+
+mb_status mb_adjoint_step(mb_ctx* ctx, const double* pos_n, const void* grid_v_n,
+                          const double* ext_blob_force, const double* body_force,
+                          double* grad_pos, void* grad_v, double* grad_k_spring)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (!pos_n || !grid_v_n || !grad_pos || !grad_v) return invalid(ctx, "null argument");
+    MB_TRY(adjoint_preconditions(ctx));
+    if (body_force) MB_TRY(set_body(ctx, body_force, ctx->prof_scratch, false));
+    cudaStream_t st = ctx->st;
+    const GridGeo& g = ctx->g;
+    const int64_t nb = ctx->nb, n3N = 3 * g.N;
+    const size_t bv = sizeof(double) * 3 * nb, bg = sizeof(double) * n3N;
+    const double h = ctx->d.h, h3 = h * h * h, dt = ctx->d.dt;
+    std::string& E = ctx->err;
+    // ---- inputs
+    MB_TRY(pull(ctx, ctx->a_qn, pos_n, bv, "adjoint q"));
+    MB_TRY(pull(ctx, ctx->a_vn, grid_v_n, bg, "adjoint v"));
+    MB_TRY(pull(ctx, ctx->a_gq, grad_pos, bv, "adjoint gq"));
+    MB_TRY(pull(ctx, ctx->a_gvp, grad_v, bg, "adjoint gv"));   // becomes dL/dv^{n+1} + gw/2
+    const double* ext = nullptr;
+    if (ext_blob_force && nb > 0) {
+        MB_TRY(pull(ctx, ctx->ext, ext_blob_force, bv, "adjoint ext"));
+        ext = static_cast<const double*>(ctx->ext.p);
+    }
+    for (DBuf* b : {&ctx->a_u, &ctx->a_qh, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu})
+        MB_TRY(ensure(*b, bv, E, "adjoint blobs"));
+    for (DBuf* b : {&ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvn, &ctx->a_gf, &ctx->a_tmp,
+                    &ctx->a_zero})
+        MB_TRY(ensure(*b, bg, E, "adjoint grids"));
+    MB_TRY(ensure(ctx->a_gk, sizeof(double), E, "adjoint gk"));
+    MB_CUDA(cudaMemsetAsync(ctx->a_zero.p, 0, bg, st));
+    MB_CUDA(cudaMemsetAsync(ctx->a_gk.p, 0, sizeof(double), st));
+    MB_CUDA(cudaMemsetAsync(ctx->a_gqh.p, 0, bv, st));
+    double* qn = static_cast<double*>(ctx->a_qn.p);
+    double* qh = static_cast<double*>(ctx->a_qh.p);
+    double* vn = static_cast<double*>(ctx->a_vn.p);
+    double* vp = static_cast<double*>(ctx->a_vp.p);
+    double* w = static_cast<double*>(ctx->a_w.p);
+    double* f = static_cast<double*>(ctx->f.p);
+    double* gq = static_cast<double*>(ctx->a_gq.p);
+    double* gqh = static_cast<double*>(ctx->a_gqh.p);
+    double* guc = static_cast<double*>(ctx->a_guc.p);
+    double* gF = static_cast<double*>(ctx->a_gF.p);
+    double* gu = static_cast<double*>(ctx->a_gu.p);
+    double* gw = static_cast<double*>(ctx->a_gw.p);
+    double* gvp = static_cast<double*>(ctx->a_gvp.p);
+    double* gvn = static_cast<double*>(ctx->a_gvn.p);
+    double* gf = static_cast<double*>(ctx->a_gf.p);
+    double* tmp = static_cast<double*>(ctx->a_tmp.p);
+    double* F = static_cast<double*>(ctx->F.p);
+    k_wrap<<<(unsigned)((3 * nb + 255) / 256), 256, 0, st>>>(nb, qn, g.L[0], g.L[1], g.L[2]);
+    MB_CUDA(cudaGetLastError());
+    const BoxData& bx = ctx->boxes[0];
+    // ---- recompute the step: u^n, q^{n+1/2}, F, f, v^{n+1}, w = (v^n + v^{n+1})/2
+    MB_CUDA(launch_interp<double>(st, 1, nb, qn, nullptr, vn, nullptr, nullptr, g, dt,
+                                  static_cast<double*>(ctx->a_u.p), qh));
+    MB_CUDA(launch_bin(st, nb, qh, nullptr, 1, ctx->bg, static_cast<int32_t*>(ctx->cell_count.p),
+                       static_cast<int32_t*>(ctx->cell_start.p),
+                       static_cast<int32_t*>(ctx->blob_cell.p),
+                       static_cast<int32_t*>(ctx->blob_rank.p), static_cast<int32_t*>(ctx->sorted.p),
+                       static_cast<int32_t*>(ctx->scan_tmp.p), false,
+                       static_cast<const int32_t*>(ctx->pid.p), static_cast<float4*>(ctx->loc.p)));
+    ForceArgs fa{};
+    fa.box_off = static_cast<const int64_t*>(ctx->box_off.p);
+    fa.sorted = static_cast<const int32_t*>(ctx->sorted.p);
+    fa.q = qh;
+    fa.pid = static_cast<const int32_t*>(ctx->pid.p);
+    fa.adj_start = static_cast<const int32_t*>(ctx->adj_start.p);
+    fa.adj_j = static_cast<const int32_t*>(ctx->adj_j.p);
+    fa.adj_rest = static_cast<const double*>(ctx->adj_rest.p);
+    fa.box_par = static_cast<const double*>(ctx->box_par.p);
+    fa.cell_start = static_cast<const int32_t*>(ctx->cell_start.p);
+    fa.blob_cell = static_cast<const int32_t*>(ctx->blob_cell.p);
+    fa.ext = ext;
+    fa.loc = static_cast<const float4*>(ctx->loc.p);
+    fa.F = F;
+    fa.rec = static_cast<double*>(ctx->rec.p);
+    fa.partial = static_cast<double*>(ctx->partial.p);
+    fa.nchunk = ctx->nchunk;
+    MB_CUDA(launch_forces(st, 1, ctx->max_box_blobs, fa, g, ctx->bg, true));
+    MB_CUDA(launch_spread<double>(st, 1, static_cast<const double*>(ctx->rec.p),
+                                  static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
+                                  ctx->tile, f));
+    FluidArgs<double> fl = fluid_args<double>(ctx, vn, f, vp, ctx->prof_scratch.p, body_force, nullptr);
+    MB_CUDA(launch_fluid3<double>(st, 1, g, fl));
+    MB_CUDA(launch_axpby(st, n3N, 0.5, vn, 0.5, vp, w));
+    // ---- backward
+    // corrector q^{n+1} = q^n + dt J(q^{n+1/2}) w
+    MB_CUDA(launch_axpby(st, 3 * nb, dt, gq, 0.0, nullptr, guc));
+    MB_CUDA(launch_make_rec(st, nb, static_cast<const int32_t*>(ctx->sorted.p), qh, guc,
+                            static_cast<double*>(ctx->rec.p)));
+    MB_CUDA(launch_spread<double>(st, 1, static_cast<const double*>(ctx->rec.p),
+                                  static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
+                                  ctx->tile, gw));
+    MB_CUDA(launch_axpby(st, n3N, h3, gw, 0.0, nullptr, gw));                 // gw = J^T guc
+    MB_CUDA(launch_grad_interp(st, nb, qh, w, guc, g, 1.0, gqh));
+    MB_CUDA(launch_axpby(st, n3N, 1.0, gvp, 0.5, gw, gvp));                  // dL/dv^{n+1}
+    // fluid update v^{n+1} = A v^n + T f (A, T symmetric)
+    FluidArgs<double> fa1 = fluid_args<double>(ctx, gvp, nullptr, tmp, nullptr, nullptr, nullptr);
+    MB_CUDA(launch_fluid3<double>(st, 1, g, fa1));                           // A gvp
+    MB_CUDA(launch_axpby(st, n3N, 1.0, tmp, 0.5, gw, gvn));                  // + gw/2
+    FluidArgs<double> fa2 = fluid_args<double>(ctx, ctx->a_zero.p, gvp, gf, nullptr, nullptr, nullptr);
+    MB_CUDA(launch_fluid3<double>(st, 1, g, fa2));                           // T gvp
+    // spreading f = S(q^{n+1/2}) F
+    MB_CUDA(launch_interp<double>(st, 0, nb, qh, nullptr, gf, nullptr, nullptr, g, dt, gF, nullptr));
+    MB_CUDA(launch_axpby(st, 3 * nb, 1.0 / h3, gF, 0.0, nullptr, gF));       // gF = S^T gf
+    MB_CUDA(launch_grad_interp(st, nb, qh, gf, F, g, 1.0 / h3, gqh));
+    // forces F(q^{n+1/2}; k)
+    double* gk_dev = static_cast<double*>(ctx->a_gk.p);
+    MB_CUDA(launch_force_jvp(st, nb, qh, gF, static_cast<const int32_t*>(ctx->pid.p),
+                             static_cast<const int32_t*>(ctx->adj_start.p),
+                             static_cast<const int32_t*>(ctx->adj_j.p),
+                             static_cast<const double*>(ctx->adj_rest.p), bx.k_spring, bx.k_rep,
+                             bx.r_cut, static_cast<const int32_t*>(ctx->cell_start.p),
+                             static_cast<const int32_t*>(ctx->sorted.p),
+                             static_cast<const int32_t*>(ctx->blob_cell.p), g, ctx->bg, gqh, gk_dev));
+    // predictor q^{n+1/2} = q^n + dt/2 J(q^n) v^n
+    MB_CUDA(launch_axpby(st, 3 * nb, 1.0, gq, 1.0, gqh, gq));
+    MB_CUDA(launch_axpby(st, 3 * nb, 0.5 * dt, gqh, 0.0, nullptr, gu));
+    MB_TRY(velocity_adjoint_dev(ctx, qn, vn, gu, gq, gvn));
+    // ---- outputs
+    MB_TRY(push(ctx, grad_pos, ctx->a_gq, bv));
+    MB_TRY(push(ctx, grad_v, ctx->a_gvn, bg));
+    if (grad_k_spring) {
+        double gk = 0.0;
+        MB_CUDA(cudaMemcpyAsync(&gk, gk_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MB_CUDA(cudaStreamSynchronize(st));
+        double prev = 0.0;
+        MB_CUDA(cudaMemcpy(&prev, grad_k_spring, sizeof(double), cudaMemcpyDefault));
+        prev += gk;
+        MB_CUDA(cudaMemcpy(grad_k_spring, &prev, sizeof(double), cudaMemcpyDefault));
+    }
+    ctx->steps_taken = 0;     // the recomputation overwrote the last step's forces
     return MB_OK;
 }
 

@@ -159,6 +159,18 @@ cudaError_t launch_vbar_step(cudaStream_t st, int Bx, const double* sum, double 
                              int mean_mode, double* vbar);
 cudaError_t launch_forces_to_fp64(cudaStream_t st, int64_t nb, const float4* F, double* out);
 
+// Adjoint kernels (adjoint.cu), FP64.
+cudaError_t launch_grad_interp(cudaStream_t st, int64_t nb, const double* q, const double* w,
+                               const double* c, const GridGeo& g, double scale, double* out);
+cudaError_t launch_force_jvp(cudaStream_t st, int64_t nb, const double* q, const double* gF,
+                             const int32_t* pid, const int32_t* adj_start, const int32_t* adj_j,
+                             const double* adj_rest, double k_spring, double k_rep, double r_cut,
+                             const int32_t* cell_start, const int32_t* sorted,
+                             const int32_t* blob_cell, const GridGeo& g, const BinGeo& bg,
+                             double* out, double* gk);
+cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b,
+                         const double* y, double* out);
+
 // Reductions / utilities.
 template <typename R>
 cudaError_t launch_grid_mean(cudaStream_t st, int B, const GridGeo& g, const R* v,
