@@ -3,7 +3,8 @@
 The gradient of a scalar loss with respect to every blob coordinate and the spring stiffness
 comes from the hand-written adjoint (mb_adjoint_step, mb_velocity_adjoint) through
 torch.autograd; it is checked along seeded random directions against central differences of
-the FP64 GPU forward (step 1e-6) and against central differences of the FP64 CPU oracle.
+the FP64 GPU forward (step 1e-6 for positions, 1e-3 relative for the stiffness) and against
+central differences of the FP64 CPU oracle.
 """
 import numpy as np
 import pytest
@@ -96,7 +97,7 @@ def test_rollout_gradient_against_gpu_finite_differences(K, chk):
         with torch.no_grad():
             dq = torch.tensor(rng.normal(size=s.pos.shape), device="cuda")
             fd_q = (float(L(q0 + EPS * dq, k0)) - float(L(q0 - EPS * dq, k0))) / (2 * EPS)
-            fd_k = (float(L(q0, k0 + EPS * 100.0)) - float(L(q0, k0 - EPS * 100.0))) / (2 * EPS * 100.0)
+            fd_k = (float(L(q0, k0 + 0.1)) - float(L(q0, k0 - 0.1))) / 0.2
         an_q = float((gq * dq).sum())
         assert abs(an_q - fd_q) < 1e-5 * abs(fd_q) + 1e-18, (an_q, fd_q)
         assert abs(gk - fd_k) < 1e-5 * abs(fd_k) + 1e-20, (gk, fd_k)
@@ -157,7 +158,9 @@ def test_differentiable_workload_64cube_k50():
         with torch.no_grad():
             dq = torch.tensor(rng.normal(size=s.pos.shape), device="cuda")
             fd = (float(L(q0 + EPS * dq, k0)) - float(L(q0 - EPS * dq, k0))) / (2 * EPS)
-            fdk = (float(L(q0, k0 + 1e-4)) - float(L(q0, k0 - 1e-4))) / 2e-4
+            # k enters through bond extensions ~1e-6 of the bond length: a relative step of
+            # 1e-3 keeps the loss difference far above the forward's rounding reproducibility
+            fdk = (float(L(q0, k0 + 0.1)) - float(L(q0, k0 - 0.1))) / 0.2
         an = float((q0.grad * dq).sum())
         assert abs(an - fd) < 1e-5 * abs(fd), (an, fd)
         assert abs(float(k0.grad) - fdk) < 1e-5 * abs(fdk), (float(k0.grad), fdk)
