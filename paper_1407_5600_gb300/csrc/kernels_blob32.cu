@@ -131,7 +131,9 @@ k_interp32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ 
            const float* __restrict__ v0, const float* __restrict__ v1,
            const int32_t* __restrict__ box_of, GridGeo g, BinGeo bg, float dt,
            const float4* A_base, const float4* B_base, float4* A_out, float4* B_out,
-           double* __restrict__ u_out, const int32_t* __restrict__ order)
+           double* __restrict__ u_out, const int32_t* __restrict__ order,
+           int32_t* __restrict__ count, int32_t* __restrict__ blob_cell,
+           int32_t* __restrict__ blob_rank)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nb) return;
@@ -189,6 +191,11 @@ k_interp32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ 
     for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], scale * u[d], G.w, G.nc[d]);
     A_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
     B_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
+    if (MODE == 1 && count) {        // bin the midpoint position (first step of the cell sort)
+        const int cell = (int)(box * G.ncell) + (cc[2] * G.nc[1] + cc[1]) * G.nc[0] + cc[0];
+        blob_cell[b] = cell;
+        blob_rank[b] = atomicAdd(count + cell, 1);
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -382,16 +389,30 @@ __host__ __device__ __forceinline__ void halo_cells32(int T0, int T, int bs, int
     }
 }
 
+// Per-dimension windows for both MAC shifts (0 along the component's own axis, 1/2 across).
+struct Win2 {
+    float w[2][3];
+    int i0[2];
+};
+__device__ __forceinline__ Win2 windows2(int c, int bs, float hi, float inv_h)
+{
+    Win2 r;
+    r.i0[0] = window32(c, bs, hi, inv_h, 0.0f, r.w[0]);
+    r.i0[1] = window32(c, bs, hi, inv_h, 0.5f, r.w[1]);
+    return r;
+}
+
 __global__ void __launch_bounds__(256)
 k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_start, GridGeo g,
-           BinGeo bg, int TX, int TY, int TZ, int max_ranges, float* __restrict__ f)
+           BinGeo bg, int TX, int TY, int TZ, int max_ranges, int max_cand, float* __restrict__ f)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo32 G = geo32(g, bg);
     const int tileN = TX * TY * TZ;
     float* acc = reinterpret_cast<float*>(smem_raw);
     int32_t* rbeg = reinterpret_cast<int32_t*>(acc + 3 * tileN);
-    int32_t* rpre = rbeg + max_ranges;
+    int32_t* rpre = rbeg + max_ranges;                    // max_ranges + 1
+    uint16_t* rmap = reinterpret_cast<uint16_t*>(rpre + max_ranges + 1);   // candidate -> range
     const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
     const int box = blockIdx.y;
     const int ntx = nx / TX, nty = ny / TY;
@@ -441,39 +462,50 @@ k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_star
     }
     __syncthreads();
     const int total = rpre[nr];
+    // candidate -> range map (ranges are short; each thread fills the spans of its ranges);
+    // candidates beyond the map's capacity (unusually dense tiles) find their range by search
+    for (int r = threadIdx.x; r < nr; r += blockDim.x)
+        for (int t = rpre[r]; t < rpre[r + 1] && t < max_cand; ++t) rmap[t] = (uint16_t)r;
+    __syncthreads();
     const float inv_h3 = G.inv_h * G.inv_h * G.inv_h;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        int lo_r = 0, hi_r = nr - 1;
-        while (lo_r < hi_r) {
-            const int mid = (lo_r + hi_r + 1) >> 1;
-            if (rpre[mid] <= t) lo_r = mid; else hi_r = mid - 1;
+        int r;
+        if (t < max_cand) {
+            r = rmap[t];
+        } else {
+            int a = 0, b = nr - 1;
+            while (a < b) {
+                const int m = (a + b + 1) >> 1;
+                if (rpre[m] <= t) a = m; else b = m - 1;
+            }
+            r = a;
         }
-        const int64_t slot = rbeg[lo_r] + (t - rpre[lo_r]);
+        const int64_t slot = rbeg[r] + (t - rpre[r]);
         const float4 pa = rec[2 * slot], fv = rec[2 * slot + 1];
         const int pk = __float_as_int(pa.w);
-        const int c[3] = {cell_unpack(pk, 0), cell_unpack(pk, 1), cell_unpack(pk, 2)};
-        const float hi[3] = {pa.x, pa.y, pa.z};
+        const Win2 wx = windows2(cell_unpack(pk, 0), G.bs, pa.x, G.inv_h);
+        const Win2 wy = windows2(cell_unpack(pk, 1), G.bs, pa.y, G.inv_h);
+        const Win2 wz = windows2(cell_unpack(pk, 2), G.bs, pa.z, G.inv_h);
         const float Fv[3] = {fv.x * inv_h3, fv.y * inv_h3, fv.z * inv_h3};
 #pragma unroll
         for (int comp = 0; comp < 3; ++comp) {
-            float wx[3], wy[3], wz[3];
-            const int ix = window32(c[0], G.bs, hi[0], G.inv_h, comp == 0 ? 0.f : 0.5f, wx) - T0[0];
-            const int iy = window32(c[1], G.bs, hi[1], G.inv_h, comp == 1 ? 0.f : 0.5f, wy) - T0[1];
-            const int iz = window32(c[2], G.bs, hi[2], G.inv_h, comp == 2 ? 0.f : 0.5f, wz) - T0[2];
+            const int sxs = comp == 0 ? 0 : 1, sys = comp == 1 ? 0 : 1, szs = comp == 2 ? 0 : 1;
+            const int ix = wx.i0[sxs] - T0[0], iy = wy.i0[sys] - T0[1], iz = wz.i0[szs] - T0[2];
             float* acc_c = acc + comp * tileN;
 #pragma unroll
             for (int cz = 0; cz < 3; ++cz) {
                 const int rz = (iz + cz) & (nz - 1);
-                if (rz >= TZ) continue;
+                const float wzc = wz.w[szs][cz] * Fv[comp];
 #pragma unroll
                 for (int cy = 0; cy < 3; ++cy) {
                     const int ry = (iy + cy) & (ny - 1);
-                    if (ry >= TY) continue;
-                    const float wyz = wy[cy] * wz[cz] * Fv[comp];
+                    const bool inyz = rz < TZ && ry < TY;
+                    const float wyz = wy.w[sys][cy] * wzc;
+                    const int rowoff = (rz * TY + ry) * TX;
 #pragma unroll
                     for (int cx = 0; cx < 3; ++cx) {
                         const int rx = (ix + cx) & (nx - 1);
-                        if (rx < TX) atomicAdd(acc_c + (rz * TY + ry) * TX + rx, wx[cx] * wyz);
+                        if (inyz && rx < TX) atomicAdd(acc_c + rowoff + rx, wx.w[sxs][cx] * wyz);
                     }
                 }
             }
@@ -562,33 +594,38 @@ cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4*
                             const float4* B, const float* v0, const float* v1,
                             const int32_t* box_of, const GridGeo& g, const BinGeo& bg, float dt,
                             const float4* A_base, const float4* B_base, float4* A_out,
-                            float4* B_out, double* u_out, const int32_t* order)
+                            float4* B_out, double* u_out, const int32_t* order,
+                            int32_t* count, int32_t* blob_cell, int32_t* blob_rank)
 {
     if (nb <= 0) return cudaSuccess;
     const unsigned nbk = blocks_for(nb, 256);
     if (mode == 0)
         k_interp32<0><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
-                                           A_out, B_out, u_out, order);
+                                           A_out, B_out, u_out, order, nullptr, nullptr, nullptr);
     else if (mode == 1)
         k_interp32<1><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
-                                           A_out, B_out, u_out, order);
+                                           A_out, B_out, u_out, order, count, blob_cell,
+                                           blob_rank);
     else
         k_interp32<2><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
-                                           A_out, B_out, u_out, order);
+                                           A_out, B_out, u_out, order, nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int32_t* box_of,
                          int Bx, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
                          int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
-                         int32_t* scan_tmp, const int32_t* pid, float4* loc)
+                         int32_t* scan_tmp, const int32_t* pid, float4* loc, bool counted)
 {
     const int64_t ncells = (int64_t)Bx * bg.ncell;
-    cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, st);
-    if (e != cudaSuccess) return e;
-    if (nb > 0)
-        k_bin_count32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, box_of, bg, cell_count,
-                                                           blob_cell, blob_rank);
+    cudaError_t e = cudaSuccess;
+    if (!counted) {
+        e = cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * ncells, st);
+        if (e != cudaSuccess) return e;
+        if (nb > 0)
+            k_bin_count32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, box_of, bg, cell_count,
+                                                               blob_cell, blob_rank);
+    }
     e = launch_exclusive_scan(st, cell_count, cell_start, ncells, scan_tmp);
     if (e != cudaSuccess) return e;
     if (nb > 0)
@@ -627,7 +664,11 @@ cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const in
         max_rows *= most;
     }
     const int max_ranges = 2 * max_rows;
-    const size_t smem = 3 * (size_t)TX * TY * TZ * sizeof(float) + sizeof(int32_t) * (2 * max_ranges + 1);
+    // map capacity: 8 blobs per halo bin cell (the dense workload averages about one); the
+    // kernel falls back to a search for candidates beyond it
+    const int max_cand = max_rows * (TX / bg.bs + 3) * 8;
+    const size_t smem = 3 * (size_t)TX * TY * TZ * sizeof(float) +
+                        sizeof(int32_t) * (2 * max_ranges + 1) + sizeof(uint16_t) * max_cand + 16;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_spread32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -635,7 +676,8 @@ cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const in
     }
     const int ntiles = (g.n[0] / TX) * (g.n[1] / TY) * (g.n[2] / TZ);
     k_spread32<<<dim3((unsigned)ntiles, (unsigned)Bx), 256, smem, st>>>(rec, cell_start, g, bg, TX,
-                                                                        TY, TZ, max_ranges, f);
+                                                                        TY, TZ, max_ranges,
+                                                                        max_cand, f);
     return cudaGetLastError();
 }
 

@@ -133,6 +133,12 @@ struct mb_ctx {
     DBuf sA, sB, hA, hB, F32, rec32, ext32, ext_sum, adj32;
     bool ext_present = false;
     bool sorted_valid = false;     // `sorted` holds a permutation of the current blobs
+    // CUDA graphs of one FP32-grid step, one per velocity-buffer parity
+    bool use_graph = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+    bool graph_ext[2] = {false, false}, graph_body[2] = {false, false};
+    int64_t graph_launches = 0;        // kernels per graph launch
     // adjoint scratch: blob vectors and grids (FP64 contexts)
     DBuf a_qn, a_u, a_qh, a_gq, a_guc, a_gqh, a_gF, a_gu, a_gk;
     DBuf a_vn, a_vp, a_w, a_gw, a_gvp, a_gvn, a_gf, a_tmp, a_zero;
@@ -276,9 +282,18 @@ void choose_bins(mb_ctx* ctx, double r_cut)
     ctx->bg.inv_w = 1.0 / (bs * ctx->d.h);
 }
 
+void drop_graph(mb_ctx* ctx)
+{
+    for (cudaGraphExec_t& g : ctx->graph_exec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
 // Concatenates the boxes' blobs into the device arrays used by the step.
 mb_status rebuild(mb_ctx* ctx)
 {
+    drop_graph(ctx);
     const int B = ctx->B;
     ctx->box_off_h.assign(B + 1, 0);
     ctx->part_off_h.assign(B + 1, 0);
@@ -625,11 +640,16 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     const float dt = (float)ctx->d.dt;
     mark(ST_INTERP_PREDICT);
     if (blobs) {
-        // the previous step's cell order still groups neighbouring blobs
+        // the predictor also bins the midpoint positions (counts per cell); the previous
+        // step's cell order still groups neighbouring blobs
+        MB_CUDA(cudaMemsetAsync(ctx->cell_count.p, 0, sizeof(int32_t) * B * ctx->bg.ncell, st));
         MB_CUDA(launch_interp32(st, 1, ctx->nb, sA, sB, vcur, nullptr, box_of, g, ctx->bg, dt,
                                 nullptr, nullptr, hA, hB, nullptr,
                                 ctx->sorted_valid ? static_cast<const int32_t*>(ctx->sorted.p)
-                                                  : nullptr));
+                                                  : nullptr,
+                                static_cast<int32_t*>(ctx->cell_count.p),
+                                static_cast<int32_t*>(ctx->blob_cell.p),
+                                static_cast<int32_t*>(ctx->blob_rank.p)));
         ctx->launches += 1;
     }
     mark(ST_BIN);
@@ -642,8 +662,8 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                              static_cast<int32_t*>(ctx->sorted.p),
                              static_cast<int32_t*>(ctx->scan_tmp.p),
                              static_cast<const int32_t*>(ctx->pid.p),
-                             static_cast<float4*>(ctx->loc.p)));
-        ctx->launches += 5;
+                             static_cast<float4*>(ctx->loc.p), true));
+        ctx->launches += 4;
         ctx->sorted_valid = true;
     }
     mark(ST_FORCES);
@@ -696,6 +716,72 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     if (ctx->timing) ctx->ev_pending++;
     ctx->cur ^= 1;
     ctx->steps_taken++;
+    return MB_OK;
+}
+
+// Captures one FP32-grid step from the current velocity buffer into a CUDA graph (on a private
+// stream; nothing executes during the capture).
+mb_status capture_graph(mb_ctx* ctx, bool ext, const double* body)
+{
+    const int cur0 = ctx->cur;
+    if (ctx->graph_exec[cur0]) cudaGraphExecDestroy(ctx->graph_exec[cur0]);
+    ctx->graph_exec[cur0] = nullptr;
+    if (!ctx->cap_stream)
+        MB_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = ctx->st;
+    const int64_t steps0 = ctx->steps_taken, l0 = ctx->launches;
+    ctx->st = ctx->cap_stream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal);
+    mb_status s = MB_OK;
+    if (e == cudaSuccess) {
+        s = do_step_fast(ctx, ext, body);
+        e = cudaStreamEndCapture(ctx->st, &graph);
+    }
+    ctx->st = user;
+    ctx->cur = cur0;
+    ctx->steps_taken = steps0;
+    ctx->graph_launches = ctx->launches - l0;
+    ctx->launches = l0;
+    if (s != MB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = std::string("graph capture: ") + cudaGetErrorString(e);
+        return MB_ECUDA;
+    }
+    e = cudaGraphInstantiate(&ctx->graph_exec[cur0], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->graph_exec[cur0] = nullptr;
+        ctx->err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+        return MB_ECUDA;
+    }
+    ctx->graph_ext[cur0] = ext;
+    ctx->graph_body[cur0] = body != nullptr;
+    return MB_OK;
+}
+
+// n_steps FP32-grid steps, each replaying the captured graph of its parity (stage timing off).
+mb_status run_fast_steps(mb_ctx* ctx, int n_steps, bool ext, const double* body)
+{
+    const bool graphs = ctx->use_graph && !ctx->timing && ctx->nb > 0;
+    for (int s = 0; s < n_steps; ++s) {
+        if (!graphs || !ctx->sorted_valid) {          // first step after a rebuild: direct
+            MB_TRY(do_step_fast(ctx, ext, body));
+            continue;
+        }
+        const int c = ctx->cur;
+        if (!ctx->graph_exec[c] || ctx->graph_ext[c] != ext || ctx->graph_body[c] != (body != nullptr))
+            MB_TRY(capture_graph(ctx, ext, body));
+        MB_CUDA(cudaGraphLaunch(ctx->graph_exec[c], ctx->st));
+        ctx->cur ^= 1;
+        ctx->steps_taken += 1;
+        ctx->launches += ctx->graph_launches;
+    }
     return MB_OK;
 }
 
@@ -770,6 +856,9 @@ mb_status upload_tables(mb_ctx* ctx)
 
 void release(mb_ctx* ctx)
 {
+    drop_graph(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    ctx->cap_stream = nullptr;
     DBuf* all[] = {&ctx->v[0], &ctx->v[1], &ctx->f, &ctx->spec, &ctx->vbar, &ctx->fsum,
                    &ctx->tw[0], &ctx->tw[1], &ctx->tw[2], &ctx->twf[0], &ctx->twf[1],
                    &ctx->twf[2], &ctx->sym, &ctx->symr, &ctx->body_prof,
@@ -912,6 +1001,7 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     ctx->nxh = ns[0] / 2 + 1;
     ctx->boxes.resize(ctx->B);
     if (const char* e = std::getenv("MB_FFT_PASSES")) ctx->fft_passes = std::atoi(e) == 5 ? 5 : 3;
+    if (const char* e = std::getenv("MB_NO_GRAPH")) ctx->use_graph = std::atoi(e) == 0;
     pick_tile(ctx);
     choose_bins(ctx, 0.0);
 
@@ -1020,7 +1110,11 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
     DeviceGuard dg(ctx->device);
     if (n_steps < 0) return invalid(ctx, "n_steps must be >= 0");
     MB_TRY(ensure_ready(ctx));
-    if (body_force) MB_TRY(set_body(ctx, body_force, ctx->body_prof, true));
+    if (body_force) {
+        const void* before = ctx->body_prof.p;
+        MB_TRY(set_body(ctx, body_force, ctx->body_prof, true));
+        if (ctx->body_prof.p != before) drop_graph(ctx);   // captured steps hold the old buffer
+    }
     const double* ext = nullptr;
     if (ext_blob_force && ctx->nb > 0) {
         const void* src = nullptr;
@@ -1035,10 +1129,8 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
                                        static_cast<float4*>(ctx->ext32.p),
                                        static_cast<double*>(ctx->ext_sum.p)));
     }
-    for (int s = 0; s < n_steps; ++s) {
-        if (ctx->rsz == 4) MB_TRY(do_step_fast(ctx, ext != nullptr, body_force));
-        else MB_TRY(do_step<double>(ctx, ext, body_force));
-    }
+    if (ctx->rsz == 4) return run_fast_steps(ctx, n_steps, ext != nullptr, body_force);
+    for (int s = 0; s < n_steps; ++s) MB_TRY(do_step<double>(ctx, ext, body_force));
     return MB_OK;
 }
 

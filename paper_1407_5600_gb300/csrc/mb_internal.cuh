@@ -140,11 +140,14 @@ cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4*
                             const float4* B, const float* v0, const float* v1,
                             const int32_t* box_of, const GridGeo& g, const BinGeo& bg, float dt,
                             const float4* A_base, const float4* B_base, float4* A_out,
-                            float4* B_out, double* u_out, const int32_t* order = nullptr);
+                            float4* B_out, double* u_out, const int32_t* order = nullptr,
+                            int32_t* count = nullptr, int32_t* blob_cell = nullptr,
+                            int32_t* blob_rank = nullptr);
 cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int32_t* box_of,
                          int Bx, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
                          int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
-                         int32_t* scan_tmp, const int32_t* pid, float4* loc);
+                         int32_t* scan_tmp, const int32_t* pid, float4* loc,
+                         bool counted = false);
 cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t max_box_blobs, const int64_t* box_off,
                             const int32_t* sorted, const float4* A, const float4* B,
                             const float4* loc, const int4* adj, const int32_t* adj_start,
