@@ -329,13 +329,23 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
             else { lo[d] = 0; hi[d] = G.nc[d] - 1; }
         }
         float Fp[3] = {0.f, 0.f, 0.f};
+        // neighbour cell coordinate with a conditional periodic wrap (no integer division)
+        auto nbr = [](int c, int d, int nc) {
+            if (nc < 3) return d;
+            int x = c + d;
+            x += x < 0 ? nc : 0;
+            x -= x >= nc ? nc : 0;
+            return x;
+        };
+        const int boxbase = (int)(box * G.ncell);
         for (int dz = lo[2]; dz <= hi[2]; ++dz) {
-            const int cz = G.nc[2] >= 3 ? (cb[2] + dz + G.nc[2]) % G.nc[2] : dz;
+            const int cz = nbr(cb[2], dz, G.nc[2]);
             for (int dy = lo[1]; dy <= hi[1]; ++dy) {
-                const int cy = G.nc[1] >= 3 ? (cb[1] + dy + G.nc[1]) % G.nc[1] : dy;
+                const int cy = nbr(cb[1], dy, G.nc[1]);
+                const int rowc = boxbase + (cz * G.nc[1] + cy) * G.nc[0];
                 for (int dx = lo[0]; dx <= hi[0]; ++dx) {
-                    const int cx = G.nc[0] >= 3 ? (cb[0] + dx + G.nc[0]) % G.nc[0] : dx;
-                    const int64_t cc = box * G.ncell + ((int64_t)cz * G.nc[1] + cy) * G.nc[0] + cx;
+                    const int cx = nbr(cb[0], dx, G.nc[0]);
+                    const int cc = rowc + cx;
                     // cell offset of the neighbour (unwrapped) in the wide case; otherwise the
                     // minimum image of the difference
                     const float ox = (wide ? dx : cx - cb[0]) * G.w;
@@ -512,40 +522,44 @@ k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_star
         }
     }
     __syncthreads();
+    const int lx = 31 - __clz(TX), lxy = lx + (31 - __clz(TY)), lt = lxy + (31 - __clz(TZ));
     for (int i = threadIdx.x; i < 3 * tileN; i += blockDim.x) {
-        const int comp = i / tileN, rem = i - comp * tileN;
-        const int rz = rem / (TY * TX), ry = (rem / TX) % TY, rx = rem % TX;
+        const int comp = i >> lt, rem = i & (tileN - 1);
+        const int rz = rem >> lxy, ry = (rem >> lx) & (TY - 1), rx = rem & (TX - 1);
         f[((size_t)box * 3 + comp) * (size_t)G.N +
           ((size_t)(T0[2] + rz) * ny + (T0[1] + ry)) * nx + (T0[0] + rx)] = acc[i];
     }
 }
 
-// Sum of the external forces per box in FP64 (the exact net force: springs and repulsion
-// cancel pairwise), for the k = 0 mode.
+// External forces to FP32 and their per-box FP64 sums (the exact net force: springs and
+// repulsion cancel pairwise).  Grid (chunk of 256 blobs, box); one partial sum per block,
+// reduced in a fixed order afterwards.
 __global__ void __launch_bounds__(256)
-k_ext_sum(const int64_t* __restrict__ box_off, const double* __restrict__ ext,
-          double* __restrict__ out)
+k_ext_prepare(const int64_t* __restrict__ box_off, const double* __restrict__ ext,
+              float4* __restrict__ e32, int nchunk, double* __restrict__ partial)
 {
-    __shared__ double sh[3][256];
-    const int box = blockIdx.x;
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int64_t b = box_off[box] + threadIdx.x; b < box_off[box + 1]; b += blockDim.x)
-        for (int d = 0; d < 3; ++d) s[d] += ext[3 * b + d];
-    for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] = s[d];
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] += sh[d][threadIdx.x + w];
-        __syncthreads();
+    __shared__ double sh[3][8];
+    const int box = blockIdx.y;
+    const int64_t s0 = box_off[box], cnt = box_off[box + 1] - s0;
+    const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (local < cnt) {
+        const int64_t b = s0 + local;
+        for (int d = 0; d < 3; ++d) v[d] = ext[3 * b + d];
+        e32[b] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
     }
-    if (threadIdx.x < 3) out[3 * box + threadIdx.x] = sh[threadIdx.x][0];
-}
-
-__global__ void k_ext_to_float(int64_t nb, const double* __restrict__ ext, float4* __restrict__ e32)
-{
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    e32[b] = make_float4((float)ext[3 * b], (float)ext[3 * b + 1], (float)ext[3 * b + 2], 0.f);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = 0; d < 3; ++d) {
+        double x = v[d];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[d][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+        partial[((int64_t)box * nchunk + blockIdx.x) * 3 + threadIdx.x] = t;
+    }
 }
 
 // vbar += scale * sum (mean_mode 0) or 0 (mean_mode 1), per box and component.
@@ -681,12 +695,17 @@ cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const in
     return cudaGetLastError();
 }
 
-cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t nb, const int64_t* box_off,
-                               const double* ext, float4* ext32, double* ext_sum)
+cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t max_box_blobs,
+                               const int64_t* box_off, const double* ext, float4* ext32,
+                               double* partial, double* ext_sum)
 {
-    if (nb > 0) k_ext_to_float<<<blocks_for(nb, 256), 256, 0, st>>>(nb, ext, ext32);
-    k_ext_sum<<<Bx, 256, 0, st>>>(box_off, ext, ext_sum);
-    return cudaGetLastError();
+    const int nchunk = (int)((max_box_blobs + 255) / 256);
+    if (nchunk <= 0) return cudaMemsetAsync(ext_sum, 0, sizeof(double) * 3 * Bx, st);
+    k_ext_prepare<<<dim3((unsigned)nchunk, (unsigned)Bx), 256, 0, st>>>(box_off, ext, ext32,
+                                                                        nchunk, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_force_sum(st, Bx, nchunk, partial, nullptr, 0.0, 0, ext_sum);
 }
 
 cudaError_t launch_vbar_step(cudaStream_t st, int Bx, const double* sum, double scale,

@@ -1124,9 +1124,10 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
                                     cudaMemcpyDeviceToDevice, ctx->st));
         ext = static_cast<const double*>(ctx->ext.p);
         if (ctx->rsz == 4)
-            MB_CUDA(launch_ext_prepare(ctx->st, ctx->B, ctx->nb,
+            MB_CUDA(launch_ext_prepare(ctx->st, ctx->B, ctx->max_box_blobs,
                                        static_cast<const int64_t*>(ctx->box_off.p), ext,
                                        static_cast<float4*>(ctx->ext32.p),
+                                       static_cast<double*>(ctx->partial.p),
                                        static_cast<double*>(ctx->ext_sum.p)));
     }
     if (ctx->rsz == 4) return run_fast_steps(ctx, n_steps, ext != nullptr, body_force);

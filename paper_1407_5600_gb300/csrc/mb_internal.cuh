@@ -156,8 +156,10 @@ cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t max_box_blobs, cons
                             const GridGeo& g, const BinGeo& bg);
 cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
                             const GridGeo& g, const BinGeo& bg, const int tile[3], float* f);
-cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t nb, const int64_t* box_off,
-                               const double* ext, float4* ext32, double* ext_sum);
+// External forces to FP32 plus their per-box FP64 sums (partial: [B][chunks][3] scratch).
+cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t max_box_blobs,
+                               const int64_t* box_off, const double* ext, float4* ext32,
+                               double* partial, double* ext_sum);
 cudaError_t launch_vbar_step(cudaStream_t st, int Bx, const double* sum, double scale,
                              int mean_mode, double* vbar);
 cudaError_t launch_forces_to_fp64(cudaStream_t st, int64_t nb, const float4* F, double* out);

@@ -160,7 +160,9 @@ def test_differentiable_workload_64cube_k50():
             fd = (float(L(q0 + EPS * dq, k0)) - float(L(q0 - EPS * dq, k0))) / (2 * EPS)
             # k enters through bond extensions ~1e-6 of the bond length: a relative step of
             # 1e-3 keeps the loss difference far above the forward's rounding reproducibility
-            fdk = (float(L(q0, k0 + 0.1)) - float(L(q0, k0 - 0.1))) / 0.2
+            hk = 0.5     # fourth-order central difference
+            fdk = (-float(L(q0, k0 + 2 * hk)) + 8 * float(L(q0, k0 + hk))
+                   - 8 * float(L(q0, k0 - hk)) + float(L(q0, k0 - 2 * hk))) / (12 * hk)
         an = float((q0.grad * dq).sum())
         assert abs(an - fd) < 1e-5 * abs(fd), (an, fd)
         assert abs(float(k0.grad) - fdk) < 1e-5 * abs(fdk), (float(k0.grad), fdk)

@@ -340,6 +340,8 @@ def test_graph_replay_matches_direct_launches(monkeypatch):
             sim.step(1, body_force=s.body)
             sim.step(4, body_force=s.body)
             out.append((to_np(sim.blob_positions()), to_np(sim.velocity_field())))
+    # FP32 shared-memory atomics add in a run-dependent order: the two runs agree to the
+    # FP32-grid tolerance, not bitwise
     L = np.array([spec.nx, spec.ny, spec.nz], dtype=float)
-    assert np.max(np.abs(min_image(out[0][0] - out[1][0], L))) < 1e-9
-    assert rel_l2(out[0][1], out[1][1]) < 1e-6
+    assert position_error(out[0][0], out[1][0], s.pos, L, 8) < TOL[0]
+    assert rel_l2(out[0][1], out[1][1]) < TOL[0]
