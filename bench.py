@@ -249,6 +249,7 @@ def run_ours(args):
     clocks.start()
     ms, launches, _ = timed_steps(sim, args.steps, False)
     clocks.stop()
+    tile, tile_ms = mb.get_tuning(sim.ctx)
     ms = max_over_ranks(ms)
     ms_step = ms / args.steps
     value = world * cells * args.steps / (ms * 1e-3)
@@ -330,7 +331,8 @@ def run_ours(args):
                        "blobs": nb, "particles": s.n_particles, "precision":
                        "FP32 grid/spread/interp/FFT; FP64 positions, forces, mean mode",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "flushed between timed steps (256 MiB write outside the events)"},
+                       "l2": "flushed between timed steps (256 MiB write outside the events)",
+                       "spread_tile": list(tile)},
             "blob_steps_per_s": blob_value,
             "step_hbm_frac": step_frac,
             "ms_per_step_stage_timed": ms_staged / args.steps,

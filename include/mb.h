@@ -55,8 +55,10 @@ typedef enum {
  *   dt           time step (> 0).
  *   precision    0: grid, spreading, interpolation and FFT in FP32 (blob positions, forces and
  *                the mean fluid momentum stay FP64); 1: everything FP64.
- *   deterministic  reserved for a bitwise-reproducible mode; must be 0 or 1 (1 currently
- *                gives the same kernels as 0).
+ *   deterministic  0 or 1.  With precision 1, 1 makes a run bitwise reproducible: blobs are
+ *                ordered within their bin cells and spreading accumulates in 64-bit fixed point
+ *                (order-independent sums); every other stage already has a fixed order.  In
+ *                FP32-grid mode the flag only fixes the in-cell order.
  *   advection    must be 0: the convective term rho v v of Eq. (vf) is not provided (every
  *                measurement in the paper is at vanishing Reynolds number).
  *   mean_mode    0: the k = 0 fluid mode carries the net momentum, rho L^3 d(mean v)/dt =
@@ -200,6 +202,13 @@ mb_status mb_adjoint_step(mb_ctx* ctx, const double* pos_n, const void* grid_v_n
  * batch 1.  Arrays may be host or device. */
 mb_status mb_velocity_adjoint(mb_ctx* ctx, const double* pos, const void* grid_v,
                               const double* grad_u, double* grad_pos, void* grad_v);
+
+/* Spreading tile (nodes per block along x, y, z) in use and the time one spreading launch
+ * took with it when it was chosen (0 if not timed).  In FP32-grid mode the first step after
+ * mb_set_particles times a set of candidate tile shapes on the actual blob distribution and
+ * keeps the fastest (synchronising the stream once; set MB_NO_AUTOTUNE=1 to keep the default);
+ * choices are cached per geometry and blob count for the life of the process. */
+mb_status mb_get_tuning(const mb_ctx* ctx, int* spread_tile, float* spread_ms);
 
 /* Number of blobs and particles of all boxes together. */
 mb_status mb_get_counts(const mb_ctx* ctx, int64_t* total_blobs, int64_t* total_particles);

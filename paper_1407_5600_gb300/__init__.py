@@ -21,7 +21,7 @@ __all__ = [
     "get_velocities", "get_particle_velocities", "set_velocity_field", "spread", "spread_static",
     "interp",
     "fluid_update", "get_counts", "get_forces", "set_stage_timing", "get_stage_times",
-    "get_launch_count", "set_positions", "adjoint_step", "velocity_adjoint", "last_error", "Multiblob",
+    "get_launch_count", "get_tuning", "set_positions", "adjoint_step", "velocity_adjoint", "last_error", "Multiblob",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -104,6 +104,7 @@ def load_library(path: str | None = None):
         "mb_spread_static": [ctypes.POINTER(_Desc), I64, P, P, P, P],
         "mb_set_stage_timing": [P, I],
         "mb_set_positions": [P, P],
+        "mb_get_tuning": [P, P, P],
         "mb_adjoint_step": [P, P, P, P, P, P, P, P],
         "mb_velocity_adjoint": [P, P, P, P, P, P],
         "mb_get_stage_times": [P, I, P, P, ctypes.POINTER(I)],
@@ -274,6 +275,14 @@ def velocity_adjoint(ctx, pos, grid_v, grad_u, grad_pos, grad_v):
     _check(ctx, load_library().mb_velocity_adjoint(
         ctx, _ptr(pos, np.float64), _ptr(grid_v), _ptr(grad_u, np.float64),
         _ptr(grad_pos, np.float64), _ptr(grad_v)))
+
+
+def get_tuning(ctx):
+    """(spreading tile (tx, ty, tz), milliseconds of one spreading launch when tuned)."""
+    tile = (ctypes.c_int * 3)()
+    ms = ctypes.c_float()
+    _check(ctx, load_library().mb_get_tuning(ctx, tile, ctypes.byref(ms)))
+    return tuple(tile), ms.value
 
 
 def get_counts(ctx):

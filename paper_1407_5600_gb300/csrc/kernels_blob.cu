@@ -677,6 +677,156 @@ k_spread(const double* __restrict__ rec, const int32_t* __restrict__ cell_start,
     }
 }
 
+// Deterministic FP64 spreading: the same tile-owner scheme, accumulated in 64-bit fixed point
+// (shared-memory integer atomics are associative, so the sums do not depend on the order in
+// which threads add).  The tile's scale is a power of two chosen from its largest force so that
+// no node can overflow: 2^62 over (candidates x max weight product x max |F| / h^3).
+__global__ void __launch_bounds__(256)
+k_spread_det(const double* __restrict__ rec, const int32_t* __restrict__ cell_start, GridGeo g,
+             BinGeo bg, int TX, int TY, int TZ, int max_ranges, double* __restrict__ f)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tileN = TX * TY * TZ;
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);
+    int32_t* rbeg = reinterpret_cast<int32_t*>(acc + 3 * tileN);
+    int32_t* rpre = rbeg + max_ranges;
+    __shared__ double fmax_sh[32];
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int box = blockIdx.y;
+    const int ntx = nx / TX, nty = ny / TY;
+    const int tid = blockIdx.x;
+    const int T0[3] = {(tid % ntx) * TX, ((tid / ntx) % nty) * TY, (tid / (ntx * nty)) * TZ};
+    const int T[3] = {TX, TY, TZ};
+    for (int i = threadIdx.x; i < 3 * tileN; i += blockDim.x) acc[i] = 0ull;
+    int lo[3], cnt[3];
+    for (int d = 0; d < 3; ++d) halo_cells(T0[d], T[d], bg.bs, bg.nc[d], lo[d], cnt[d]);
+    const int rows = cnt[1] * cnt[2];
+    const int nr = 2 * rows;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int cz = wrap_cell(lo[2] + r / cnt[1], bg.nc[2]);
+        const int cy = wrap_cell(lo[1] + r % cnt[1], bg.nc[1]);
+        const int64_t rowbase = box * bg.ncell + ((int64_t)cz * bg.nc[1] + cy) * bg.nc[0];
+        const int sx = wrap_cell(lo[0], bg.nc[0]);
+        const int ex = sx + cnt[0];
+        const int a1 = ex <= bg.nc[0] ? ex : bg.nc[0];
+        const int s0 = cell_start[rowbase + sx];
+        rbeg[2 * r] = s0;
+        rpre[2 * r] = cell_start[rowbase + a1] - s0;
+        if (ex > bg.nc[0]) {
+            const int t0 = cell_start[rowbase];
+            rbeg[2 * r + 1] = t0;
+            rpre[2 * r + 1] = cell_start[rowbase + (ex - bg.nc[0])] - t0;
+        } else {
+            rbeg[2 * r + 1] = 0;
+            rpre[2 * r + 1] = 0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < nr; ++i) {
+            const int len = rpre[i];
+            rpre[i] = run;
+            run += len;
+        }
+        rpre[nr] = run;
+    }
+    __syncthreads();
+    const int total = rpre[nr];
+    auto slot_of = [&](int t) {
+        int a = 0, b = nr - 1;
+        while (a < b) {
+            const int m = (a + b + 1) >> 1;
+            if (rpre[m] <= t) a = m; else b = m - 1;
+        }
+        return (int64_t)rbeg[a] + (t - rpre[a]);
+    };
+    // tile scale from the largest force component among the candidates
+    double fm = 0.0;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const double* rr = rec + 6 * slot_of(t);
+        fm = fmax(fm, fmax(fabs(rr[3]), fmax(fabs(rr[4]), fabs(rr[5]))));
+    }
+    for (int o = 16; o > 0; o >>= 1) fm = fmax(fm, __shfl_down_sync(0xffffffffu, fm, o));
+    if ((threadIdx.x & 31) == 0) fmax_sh[threadIdx.x >> 5] = fm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, fmax_sh[w]);
+        fmax_sh[0] = m;
+    }
+    __syncthreads();
+    const double inv_h3 = g.inv_h * g.inv_h * g.inv_h;
+    const double bound = fmax(fmax_sh[0] * inv_h3 * (8.0 / 27.0) * (double)(total + 1), 1e-300);
+    int ex2;
+    frexp(bound, &ex2);                      // bound < 2^ex2
+    const double scale = ldexp(1.0, 62 - max(ex2, -900));   // finite even for a zero tile
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const double* rr = rec + 6 * slot_of(t);
+        const double p[3] = {rr[0], rr[1], rr[2]};
+        for (int a = 0; a < 3; ++a) {
+            const double Fa = rr[3 + a] * inv_h3;
+            double wx[3], wy[3], wz[3];
+            const int ix = peskin_window<double>(p[0] * g.inv_h - mac_shift(a, 0), wx) - T0[0];
+            const int iy = peskin_window<double>(p[1] * g.inv_h - mac_shift(a, 1), wy) - T0[1];
+            const int iz = peskin_window<double>(p[2] * g.inv_h - mac_shift(a, 2), wz) - T0[2];
+            unsigned long long* acc_a = acc + a * tileN;
+            for (int c = 0; c < 3; ++c) {
+                const int rz = (iz + c) & (nz - 1);
+                if (rz >= TZ) continue;
+                for (int bb = 0; bb < 3; ++bb) {
+                    const int ry = (iy + bb) & (ny - 1);
+                    if (ry >= TY) continue;
+                    const double wyz = wy[bb] * wz[c] * Fa;
+                    for (int aa = 0; aa < 3; ++aa) {
+                        const int rx = (ix + aa) & (nx - 1);
+                        if (rx < TX) {
+                            const long long v = llrint(wx[aa] * wyz * scale);
+                            atomicAdd(acc_a + (rz * TY + ry) * TX + rx, (unsigned long long)v);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const double inv_scale = 1.0 / scale;
+    for (int i = threadIdx.x; i < 3 * tileN; i += blockDim.x) {
+        const int a = i / tileN, rem = i - a * tileN;
+        const int rz = rem / (TY * TX), ry = (rem / TX) % TY, rx = rem % TX;
+        f[((size_t)box * 3 + a) * (size_t)g.N +
+          ((size_t)(T0[2] + rz) * ny + (T0[1] + ry)) * nx + (T0[0] + rx)] =
+            (double)(long long)acc[i] * inv_scale;
+    }
+}
+
+cudaError_t launch_spread_det(cudaStream_t st, int B, const double* rec, const int32_t* cell_start,
+                              const GridGeo& g, const BinGeo& bg, const int tile[3], double* f)
+{
+    const int TX = tile[0], TY = tile[1], TZ = tile[2];
+    int max_rows = 1;
+    for (int d = 1; d < 3; ++d) {
+        int most = 0;
+        for (int T0 = 0; T0 < g.n[d]; T0 += tile[d]) {
+            int lo, cnt;
+            halo_cells(T0, tile[d], bg.bs, bg.nc[d], lo, cnt);
+            most = cnt > most ? cnt : most;
+        }
+        max_rows *= most;
+    }
+    const int max_ranges = 2 * max_rows;
+    const size_t smem = 3 * (size_t)TX * TY * TZ * 8 + sizeof(int32_t) * (2 * max_ranges + 1);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_spread_det, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    const int ntiles = (g.n[0] / TX) * (g.n[1] / TY) * (g.n[2] / TZ);
+    k_spread_det<<<dim3((unsigned)ntiles, (unsigned)B), 256, smem, st>>>(rec, cell_start, g, bg, TX,
+                                                                         TY, TZ, max_ranges, f);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_spread(cudaStream_t st, int B, const double* rec, const int32_t* cell_start,
                           const GridGeo& g, const BinGeo& bg, const int tile[3], R* f)

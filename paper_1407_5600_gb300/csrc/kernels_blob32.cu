@@ -323,10 +323,22 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
         const int pb = __float_as_int(me.w);
         const bool wide = G.nc[0] >= 3 && G.nc[1] >= 3 && G.nc[2] >= 3;
         const float rc2 = r_cut * r_cut;
+        // Only neighbour cells on the blob's side can hold a partner closer than r_cut <= w:
+        // along each axis the lower neighbour if the offset is below r_cut, the upper one if it
+        // is above w - r_cut (8 of the 27 cells for r_cut = w/2).
+        const float mine[3] = {me.x, me.y, me.z};
         int lo[3], hi[3];
         for (int d = 0; d < 3; ++d) {
-            if (G.nc[d] >= 3) { lo[d] = -1; hi[d] = 1; }
-            else { lo[d] = 0; hi[d] = G.nc[d] - 1; }
+            if (G.nc[d] >= 3 && r_cut <= G.w) {
+                lo[d] = mine[d] < r_cut ? -1 : 0;
+                hi[d] = mine[d] >= G.w - r_cut ? 1 : 0;
+            } else if (G.nc[d] >= 3) {
+                lo[d] = -1;
+                hi[d] = 1;
+            } else {
+                lo[d] = 0;
+                hi[d] = G.nc[d] - 1;
+            }
         }
         float Fp[3] = {0.f, 0.f, 0.f};
         // neighbour cell coordinate with a conditional periodic wrap (no integer division)

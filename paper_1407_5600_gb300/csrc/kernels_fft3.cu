@@ -308,7 +308,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     lines_fft_n(ny, P, nxh, col, twy, false);
     __syncthreads();
     T* out = a.spec + ((size_t)bc * nz + z) * (size_t)nxh * ny;
-    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) out[i] = P[col(i / ny, i % ny)];
+    const int ly = 31 - __clz(ny);
+    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) out[i] = P[col(i >> ly, i & (ny - 1))];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -412,7 +413,8 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
         const int j = 2 * k + (y & 1);
         return (y >> 1) * S + j + (j >> sx);
     };
-    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) P[col(i / ny, i % ny)] = in[i];
+    const int ly = 31 - __clz(ny);
+    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) P[col(i >> ly, i & (ny - 1))] = in[i];
     __syncthreads();
     lines_fft_n(ny, P, nxh, col, twy, true);
     __syncthreads();

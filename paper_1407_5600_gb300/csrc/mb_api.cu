@@ -1,7 +1,11 @@
 // C ABI of libmb.so: context management, argument validation, host/device staging and the
 // orchestration of one inertial-coupling step (see include/mb.h for the contract).
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -133,6 +137,9 @@ struct mb_ctx {
     DBuf sA, sB, hA, hB, F32, rec32, ext32, ext_sum, adj32;
     bool ext_present = false;
     bool sorted_valid = false;     // `sorted` holds a permutation of the current blobs
+    // spreading tile picked by timing candidate shapes on the first FP32-grid step
+    bool autotune = true, tuned = false;
+    float tile_ms = 0.f;
     // CUDA graphs of one FP32-grid step, one per velocity-buffer parity
     bool use_graph = true;
     cudaStream_t cap_stream = nullptr;
@@ -425,6 +432,7 @@ mb_status rebuild(mb_ctx* ctx)
                              static_cast<float4*>(ctx->sA.p), static_cast<float4*>(ctx->sB.p)));
         ctx->ext_present = false;
         ctx->sorted_valid = false;
+        ctx->tuned = false;
     }
     // the host vectors die at return: make the copies complete first
     MB_CUDA(cudaStreamSynchronize(st));
@@ -588,9 +596,14 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
     }
     mark(ST_SPREAD);
     if (blobs) {
-        MB_CUDA(launch_spread<R>(st, B, static_cast<const double*>(ctx->rec.p),
-                                 static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
-                                 ctx->tile, static_cast<R*>(ctx->f.p)));
+        if (ctx->d.deterministic && sizeof(R) == 8)
+            MB_CUDA(launch_spread_det(st, B, static_cast<const double*>(ctx->rec.p),
+                                      static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
+                                      ctx->tile, reinterpret_cast<double*>(ctx->f.p)));
+        else
+            MB_CUDA(launch_spread<R>(st, B, static_cast<const double*>(ctx->rec.p),
+                                     static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
+                                     ctx->tile, static_cast<R*>(ctx->f.p)));
         ctx->launches += 1;
     }
     const double* mean = ctx->d.mean_mode == 0 ? static_cast<const double*>(ctx->vbar.p) : nullptr;
@@ -719,6 +732,73 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     return MB_OK;
 }
 
+// Times each candidate spreading tile on the current binned records (the first step after
+// the blobs were set) and keeps the fastest; choices are cached per geometry and blob count.
+struct TuneKey {
+    int n[3], B, bs;
+    int64_t nb;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(n[0], n[1], n[2], B, bs, nb) < std::tie(o.n[0], o.n[1], o.n[2], o.B, o.bs, o.nb);
+    }
+};
+std::map<TuneKey, std::array<int, 3>> g_tile_cache;
+std::mutex g_tile_mu;
+
+mb_status autotune_spread(mb_ctx* ctx)
+{
+    ctx->tuned = true;
+    if (!ctx->autotune || ctx->nb == 0) return MB_OK;
+    const TuneKey key{{ctx->g.n[0], ctx->g.n[1], ctx->g.n[2]}, ctx->B, ctx->bg.bs, ctx->nb};
+    {
+        std::lock_guard<std::mutex> lock(g_tile_mu);
+        auto it = g_tile_cache.find(key);
+        if (it != g_tile_cache.end()) {
+            for (int d = 0; d < 3; ++d) ctx->tile[d] = it->second[d];
+            return MB_OK;
+        }
+    }
+    static const int cand[][3] = {{32, 8, 8}, {32, 16, 8}, {32, 16, 16}, {16, 16, 16},
+                                  {64, 8, 8}, {64, 16, 8}, {16, 8, 8}, {8, 8, 8}};
+    cudaEvent_t e0, e1;
+    MB_CUDA(cudaEventCreate(&e0));
+    MB_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_t[3] = {ctx->tile[0], ctx->tile[1], ctx->tile[2]};
+    for (const auto& c : cand) {
+        int t[3];
+        bool ok = true;
+        for (int d = 0; d < 3; ++d) {
+            t[d] = std::min(c[d], ctx->g.n[d]);
+            ok = ok && ctx->g.n[d] % t[d] == 0;
+        }
+        if (!ok || 3 * (size_t)t[0] * t[1] * t[2] * 4 > 150 * 1024) continue;
+        float ms = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            MB_CUDA(cudaEventRecord(e0, ctx->st));
+            MB_CUDA(launch_spread32(ctx->st, ctx->B, static_cast<const float4*>(ctx->rec32.p),
+                                    static_cast<const int32_t*>(ctx->cell_start.p), ctx->g,
+                                    ctx->bg, t, static_cast<float*>(ctx->f.p)));
+            MB_CUDA(cudaEventRecord(e1, ctx->st));
+            MB_CUDA(cudaEventSynchronize(e1));
+            float one = 0.f;
+            MB_CUDA(cudaEventElapsedTime(&one, e0, e1));
+            if (rep > 0) ms += one;                   // first launch warms up
+        }
+        if (ms < best) {
+            best = ms;
+            for (int d = 0; d < 3; ++d) best_t[d] = t[d];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int d = 0; d < 3; ++d) ctx->tile[d] = best_t[d];
+    ctx->tile_ms = best / 2;
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    g_tile_cache[key] = {best_t[0], best_t[1], best_t[2]};
+    return MB_OK;
+}
+
 // Captures one FP32-grid step from the current velocity buffer into a CUDA graph (on a private
 // stream; nothing executes during the capture).
 mb_status capture_graph(mb_ctx* ctx, bool ext, const double* body)
@@ -772,6 +852,7 @@ mb_status run_fast_steps(mb_ctx* ctx, int n_steps, bool ext, const double* body)
     for (int s = 0; s < n_steps; ++s) {
         if (!graphs || !ctx->sorted_valid) {          // first step after a rebuild: direct
             MB_TRY(do_step_fast(ctx, ext, body));
+            if (!ctx->tuned) MB_TRY(autotune_spread(ctx));
             continue;
         }
         const int c = ctx->cur;
@@ -1002,6 +1083,7 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     ctx->boxes.resize(ctx->B);
     if (const char* e = std::getenv("MB_FFT_PASSES")) ctx->fft_passes = std::atoi(e) == 5 ? 5 : 3;
     if (const char* e = std::getenv("MB_NO_GRAPH")) ctx->use_graph = std::atoi(e) == 0;
+    if (const char* e = std::getenv("MB_NO_AUTOTUNE")) ctx->autotune = std::atoi(e) == 0;
     pick_tile(ctx);
     choose_bins(ctx, 0.0);
 
@@ -1431,6 +1513,15 @@ mb_status mb_adjoint_step(mb_ctx* ctx, const double* pos_n, const void* grid_v_n
         MB_CUDA(cudaMemcpy(grad_k_spring, &prev, sizeof(double), cudaMemcpyDefault));
     }
     ctx->steps_taken = 0;     // the recomputation overwrote the last step's forces
+    return MB_OK;
+}
+
+mb_status mb_get_tuning(const mb_ctx* ctx, int* spread_tile, float* spread_ms)
+{
+    if (!ctx) return MB_EINVAL;
+    if (spread_tile)
+        for (int d = 0; d < 3; ++d) spread_tile[d] = ctx->tile[d];
+    if (spread_ms) *spread_ms = ctx->tile_ms;
     return MB_OK;
 }
 

@@ -91,6 +91,10 @@ template <typename R>
 cudaError_t launch_spread(cudaStream_t st, int B, const double* rec, const int32_t* cell_start,
                           const GridGeo& g, const BinGeo& bg, const int tile[3], R* f);
 
+// Deterministic FP64 spreading (64-bit fixed-point shared-memory accumulation).
+cudaError_t launch_spread_det(cudaStream_t st, int B, const double* rec, const int32_t* cell_start,
+                              const GridGeo& g, const BinGeo& bg, const int tile[3], double* f);
+
 // Particle velocities U0, Omega from blob velocities (particle CSR).
 cudaError_t launch_particle_reduce(cudaStream_t st, int64_t np, const int32_t* part_start,
                                    const int32_t* part_blobs, const int32_t* box_of_part,

@@ -345,3 +345,24 @@ def test_graph_replay_matches_direct_launches(monkeypatch):
     L = np.array([spec.nx, spec.ny, spec.nz], dtype=float)
     assert position_error(out[0][0], out[1][0], s.pos, L, 8) < TOL[0]
     assert rel_l2(out[0][1], out[1][1]) < TOL[0]
+
+
+def test_deterministic_fp64_runs_are_bitwise_identical():
+    """deterministic = 1 with FP64: two runs of the dense case give the same bits, and match the
+    oracle."""
+    spec, s = _dense_small(seed=12)
+    rng = np.random.default_rng(12)
+    ext = rng.normal(scale=1e-3, size=s.pos.shape)
+    outs = []
+    for _ in range(2):
+        d = mb.GridDesc(spec.nx, spec.ny, spec.nz, precision=1, deterministic=1, dt=spec.dt,
+                        mean_mode=spec.mean_mode)
+        q, v, u, U, W = _run_gpu(d, [s], 4, ext_list=[ext], body=s.body)
+        outs.append((q, v))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    g = _oracle_grid(mb.GridDesc(spec.nx, spec.ny, spec.nz, dt=spec.dt, mean_mode=spec.mean_mode))
+    q_ref, v_ref = oracle.step(g, 4, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
+                               s.k_rep, s.r_cut, ext=ext, body=s.body)
+    assert position_error(outs[0][0], q_ref, s.pos, g.L, 4) < TOL[1]
+    assert rel_l2(outs[0][1][0], v_ref) < TOL[1]
