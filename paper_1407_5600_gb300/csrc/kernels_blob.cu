@@ -816,11 +816,9 @@ cudaError_t launch_spread_det(cudaStream_t st, int B, const double* rec, const i
     }
     const int max_ranges = 2 * max_rows;
     const size_t smem = 3 * (size_t)TX * TY * TZ * 8 + sizeof(int32_t) * (2 * max_ranges + 1);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned> attr{0};
+    if (first_on_device(attr))
         cudaFuncSetAttribute(k_spread_det, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
     const int ntiles = (g.n[0] / TX) * (g.n[1] / TY) * (g.n[2] / TZ);
     k_spread_det<<<dim3((unsigned)ntiles, (unsigned)B), 256, smem, st>>>(rec, cell_start, g, bg, TX,
                                                                          TY, TZ, max_ranges, f);
@@ -844,12 +842,9 @@ cudaError_t launch_spread(cudaStream_t st, int B, const double* rec, const int32
     }
     const int max_ranges = 2 * max_rows;
     const size_t smem = 3 * (size_t)TX * TY * TZ * sizeof(R) + sizeof(int32_t) * (2 * max_ranges + 1);
-    static bool attr_set[2] = {false, false};
-    const int which = sizeof(R) == 8;
-    if (!attr_set[which]) {
+    static std::atomic<unsigned> attr{0};
+    if (first_on_device(attr))
         cudaFuncSetAttribute(k_spread<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set[which] = true;
-    }
     const int ntiles = (g.n[0] / TX) * (g.n[1] / TY) * (g.n[2] / TZ);
     dim3 grid((unsigned)ntiles, (unsigned)B);
     k_spread<R><<<grid, 256, smem, st>>>(rec, cell_start, g, bg, TX, TY, TZ, max_ranges, f);

@@ -27,19 +27,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
-// Moves one coordinate (cell c, offset hi + lo) by a small displacement and renormalises the
-// offset into [0, w), carrying whole cells into c (periodic over nc cells).
+// Moves one coordinate (cell c, offset hi + lo) by a displacement and renormalises the offset
+// into [0, w), carrying whole cells into c (periodic over nc cells).
 __device__ __forceinline__ void ff_move(int& c, float& hi, float& lo, float delta, float w, int nc)
 {
     float s, e;
     two_sum(hi, delta, s, e);
     two_sum(s, lo + e, hi, lo);
-    if (hi >= w) {
+    while (hi >= w) {
         float t, te;
         two_sum(hi, -w, t, te);
         two_sum(t, lo + te, hi, lo);
         c = c + 1 == nc ? 0 : c + 1;
-    } else if (hi < 0.0f) {
+    }
+    while (hi < 0.0f) {
         float t, te;
         two_sum(hi, w, t, te);
         two_sum(t, lo + te, hi, lo);
@@ -695,11 +696,9 @@ cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const in
     const int max_cand = max_rows * (TX / bg.bs + 3) * 8;
     const size_t smem = 3 * (size_t)TX * TY * TZ * sizeof(float) +
                         sizeof(int32_t) * (2 * max_ranges + 1) + sizeof(uint16_t) * max_cand + 16;
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned> attr{0};
+    if (first_on_device(attr))
         cudaFuncSetAttribute(k_spread32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
     const int ntiles = (g.n[0] / TX) * (g.n[1] / TY) * (g.n[2] / TZ);
     k_spread32<<<dim3((unsigned)ntiles, (unsigned)Bx), 256, smem, st>>>(rec, cell_start, g, bg, TX,
                                                                         TY, TZ, max_ranges,

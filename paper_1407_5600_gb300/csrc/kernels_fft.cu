@@ -270,15 +270,13 @@ cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidAr
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     const int RP = ny / 2 < 4 ? ny / 2 : 4;
     const int C = sizeof(R) == 4 ? 16 : 8;
-    static bool attr[2] = {false, false};
-    const int w = sizeof(R) == 8;
-    if (!attr[w]) {
+    static std::atomic<unsigned> attr{0};     // per instantiation
+    if (first_on_device(attr)) {
         const int lim = 200 * 1024;
         cudaFuncSetAttribute(k_rhs_fft_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_fft_y<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_fft_z_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_fft_x_c2r<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        attr[w] = true;
     }
     const size_t smem_x = (size_t)RP * (nx + 1) * sizeof(T);
     const size_t smem_y = (size_t)ny * C * sizeof(T);

@@ -156,13 +156,11 @@ template <typename T> __device__ __forceinline__ void load_table(T* dst, const T
 
 }  // namespace
 
-// Row stride (in complex) of the plane buffer: room for the padded nx + 2 separated values,
-// rounded to 8 (mod 16) so that two consecutive rows fall on different halves of the banks.
+// Row stride (in complex) of the plane buffer: just room for the padded nx + 2 separated values
+// (a 128 x 128 FP32 plane then takes 73 KiB, three blocks per SM).
 __host__ __device__ inline int plane_ld(int nx)
 {
-    int s = nx + 2 + ((nx + 1) >> pad_shift(nx)) + 1;
-    while ((s & 15) != 8) ++s;
-    return s;
+    return nx + 2 + ((nx + 1) >> pad_shift(nx));
 }
 
 // Four consecutive grid values (x0 .. x0+3, x0 a multiple of 4) as one vector load.
@@ -192,7 +190,7 @@ __device__ __forceinline__ void store4(double* p, const double v[4])
 // the row FFT and the in-place separation, logical slot 2k + e of row p holds X_{2p+e}[k],
 // k <= nx/2.  pad(j) = j + (j >> pad_shift(nx)).
 template <typename R>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
 k_plane_fwd(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<R>::T;
@@ -200,10 +198,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     const int S = plane_ld(nx), sx = pad_shift(nx);
     T* P = reinterpret_cast<T*>(smem_raw);
-    T* twx = P + (ny / 2) * S;
-    T* twy = twx + nx;
-    load_table(twx, reinterpret_cast<const T*>(a.twf[0]), nx);
-    load_table(twy, reinterpret_cast<const T*>(a.twf[1]), ny);
+    const T* twx = reinterpret_cast<const T*>(a.twf[0]);      // twiddles through L1
+    const T* twy = reinterpret_cast<const T*>(a.twf[1]);
     const int z = blockIdx.x, bc = blockIdx.y, comp = bc % 3;
     const R* vc = a.v + (size_t)bc * g.N;
     const R* fc = a.f ? a.f + (size_t)bc * g.N : nullptr;
@@ -395,7 +391,7 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
 // Pass C.  Inverse of pass A: columns, then the packed rows Z = X_{2p} + i X_{2p+1} (with the
 // Hermitian extension X[nx - k] = conj X[k]), then the real rows, scaled by 1/N.
 template <typename R>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
 k_plane_inv(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<R>::T;
@@ -403,10 +399,8 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     const int S = plane_ld(nx), sx = pad_shift(nx);
     T* P = reinterpret_cast<T*>(smem_raw);
-    T* twx = P + (ny / 2) * S;
-    T* twy = twx + nx;
-    load_table(twx, reinterpret_cast<const T*>(a.twf[0]), nx);
-    load_table(twy, reinterpret_cast<const T*>(a.twf[1]), ny);
+    const T* twx = reinterpret_cast<const T*>(a.twf[0]);      // twiddles through L1
+    const T* twy = reinterpret_cast<const T*>(a.twf[1]);
     const int z = blockIdx.x, bc = blockIdx.y;
     const T* in = a.spec + ((size_t)bc * nz + z) * (size_t)nxh * ny;
     auto col = [S, sx](int k, int y) {
@@ -471,17 +465,15 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
     using T = typename C2<R>::T;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     constexpr int CZ = sizeof(R) == 4 ? 16 : 8;      // ky columns per z-pass block
-    static bool attr[2] = {false, false};
-    const int w = sizeof(R) == 8;
-    if (!attr[w]) {
+    static std::atomic<unsigned> attr{0};     // per instantiation
+    if (first_on_device(attr)) {
         const int lim = 200 * 1024;
         cudaFuncSetAttribute(k_plane_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_zsolve<R, CZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_zsolve<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_plane_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        attr[w] = true;
     }
-    const size_t smem_plane = ((size_t)(ny / 2) * plane_ld(nx) + nx + ny) * sizeof(T);
+    const size_t smem_plane = (size_t)(ny / 2) * plane_ld(nx) * sizeof(T);
     const int C = ny >= CZ ? CZ : 4;
     const size_t smem_z = ((size_t)3 * padded_len(nz) * (C + 4) + nz) * sizeof(T);
     auto mark = [&](int i) { if (marks) cudaEventRecord(marks[i], st); };

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -26,6 +27,16 @@ struct BinGeo {
     int bs;            // bin cell side in mesh cells
     double inv_w;      // 1 / (bs h)
 };
+
+// True the first time it is called for the current device with this flag set (function
+// attributes such as the dynamic shared-memory limit are set once per device).
+inline bool first_on_device(std::atomic<unsigned>& done)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned bit = 1u << (dev & 31);
+    return (done.fetch_or(bit) & bit) == 0;
+}
 
 // Complex helpers on float2 / double2.
 template <typename R> struct C2;
