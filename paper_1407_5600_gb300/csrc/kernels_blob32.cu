@@ -34,13 +34,14 @@ __device__ __forceinline__ void ff_move(int& c, float& hi, float& lo, float delt
     float s, e;
     two_sum(hi, delta, s, e);
     two_sum(s, lo + e, hi, lo);
-    while (hi >= w) {
+    // at most 8 cells per move (a bound, so that a non-finite offset cannot loop)
+    for (int it = 0; it < 8 && hi >= w; ++it) {
         float t, te;
         two_sum(hi, -w, t, te);
         two_sum(t, lo + te, hi, lo);
         c = c + 1 == nc ? 0 : c + 1;
     }
-    while (hi < 0.0f) {
+    for (int it = 0; it < 8 && hi < 0.0f; ++it) {
         float t, te;
         two_sum(hi, w, t, te);
         two_sum(t, lo + te, hi, lo);
@@ -106,6 +107,8 @@ __global__ void k_split(int64_t nb, const double* __restrict__ q, GridGeo g, Bin
         c[d] = k;
         hi[d] = (float)xl;
         lo[d] = (float)(xl - (double)hi[d]);
+        // rounding of x / w or of the float offset can leave hi just outside [0, w): carry
+        ff_move(c[d], hi[d], lo[d], 0.0f, (float)w, bg.nc[d]);
     }
     A[b] = make_float4(hi[0], hi[1], hi[2], __int_as_float(cell_pack(c[0], c[1], c[2])));
     B[b] = make_float4(lo[0], lo[1], lo[2], 0.0f);
@@ -392,26 +395,6 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
 
 // ------------------------------------------------------------------------------------------
 // Tile-owner spreading from the FP32 records (see k_spread for the scheme).
-__host__ __device__ __forceinline__ int floor_div32(int a, int b)
-{
-    return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
-__host__ __device__ __forceinline__ int wrap_cell32(int c, int n)
-{
-    c %= n;
-    return c < 0 ? c + n : c;
-}
-__host__ __device__ __forceinline__ void halo_cells32(int T0, int T, int bs, int nc, int& lo, int& cnt)
-{
-    lo = floor_div32(2 * T0 - 3, 2 * bs);
-    const int hi = floor_div32(T0 + T + 1 + bs - 1, bs) - 1;
-    cnt = hi - lo + 1;
-    if (cnt >= nc) {
-        lo = 0;
-        cnt = nc;
-    }
-}
-
 // Per-dimension windows for both MAC shifts (0 along the component's own axis, 1/2 across).
 struct Win2 {
     float w[2][3];
@@ -425,122 +408,124 @@ __device__ __forceinline__ Win2 windows2(int c, int bs, float hi, float inv_h)
     return r;
 }
 
+// Spreading, one block per tile of TX x TY x TZ nodes (whole bin cells).  The block spreads the
+// blobs binned in its cells, each exactly once, into a shared-memory copy of the nodes their
+// windows can reach: x over [T0 - 4, T0 + TX + 4) in 16-byte chunks, y and z over
+// [T0 - 1, T0 + T + 1] (a blob in the tile has its window start in [T0 - 1, T0 + T - 1]).  The
+// copy holds 32-bit fixed-point sums (integer shared-memory atomics), scaled per tile by a power
+// of two from a bound on its largest node value (blob count x largest force component x the
+// kernel's largest weight (2/3)^3).  The block then adds the copy to f (zeroed beforehand) with
+// vector atomics, skipping all-zero chunks; nodes shared with neighbouring tiles receive every
+// tile's part.  TXc = 0 takes the tile from the arguments (small grids).
+template <int TXc, int TYc, int TZc>
 __global__ void __launch_bounds__(256)
 k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_start, GridGeo g,
-           BinGeo bg, int TX, int TY, int TZ, int max_ranges, int max_cand, float* __restrict__ f)
+           BinGeo bg, int TXr, int TYr, int TZr, float* __restrict__ f)
 {
+    const int TX = TXc ? TXc : TXr, TY = TYc ? TYc : TYr, TZ = TZc ? TZc : TZr;
+    const int SXC = TX / 4 + 2, SX = 4 * SXC, SY = TY + 3, SZ = TZ + 3;
+    const int SN = SX * SY * SZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    int* acc = reinterpret_cast<int*>(smem_raw);                 // [3][SZ][SY][SX]
+    __shared__ int rb[64], rp[65];
+    __shared__ float wmax[8];
     const Geo32 G = geo32(g, bg);
-    const int tileN = TX * TY * TZ;
-    float* acc = reinterpret_cast<float*>(smem_raw);
-    int32_t* rbeg = reinterpret_cast<int32_t*>(acc + 3 * tileN);
-    int32_t* rpre = rbeg + max_ranges;                    // max_ranges + 1
-    uint16_t* rmap = reinterpret_cast<uint16_t*>(rpre + max_ranges + 1);   // candidate -> range
     const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
     const int box = blockIdx.y;
     const int ntx = nx / TX, nty = ny / TY;
-    const int tid = blockIdx.x;
-    const int T0[3] = {(tid % ntx) * TX, ((tid / ntx) % nty) * TY, (tid / (ntx * nty)) * TZ};
-    const int T[3] = {TX, TY, TZ};
-    for (int i = threadIdx.x; i < 3 * tileN; i += blockDim.x) acc[i] = 0.f;
-    int lo[3], cnt[3];
-    for (int d = 0; d < 3; ++d) halo_cells32(T0[d], T[d], G.bs, G.nc[d], lo[d], cnt[d]);
-    const int rows = cnt[1] * cnt[2];
-    const int nr = 2 * rows;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-        const int cz = wrap_cell32(lo[2] + r / cnt[1], G.nc[2]);
-        const int cy = wrap_cell32(lo[1] + r % cnt[1], G.nc[1]);
-        const int64_t rowbase = box * G.ncell + ((int64_t)cz * G.nc[1] + cy) * G.nc[0];
-        const int sx = wrap_cell32(lo[0], G.nc[0]);
-        const int ex = sx + cnt[0];
-        const int a1 = ex <= G.nc[0] ? ex : G.nc[0];
-        const int s0 = cell_start[rowbase + sx];
-        rbeg[2 * r] = s0;
-        rpre[2 * r] = cell_start[rowbase + a1] - s0;
-        if (ex > G.nc[0]) {
-            const int t0 = cell_start[rowbase];
-            rbeg[2 * r + 1] = t0;
-            rpre[2 * r + 1] = cell_start[rowbase + (ex - G.nc[0])] - t0;
-        } else {
-            rbeg[2 * r + 1] = 0;
-            rpre[2 * r + 1] = 0;
-        }
+    const int T0[3] = {((int)blockIdx.x % ntx) * TX, (((int)blockIdx.x / ntx) % nty) * TY,
+                       ((int)blockIdx.x / (ntx * nty)) * TZ};
+    const int ncx = TX / G.bs, ncy = TY / G.bs, ncz = TZ / G.bs;
+    const int rows = ncy * ncz;
+    if (threadIdx.x < rows) {
+        const int r = threadIdx.x;
+        const int cz = T0[2] / G.bs + r / ncy, cy = T0[1] / G.bs + r % ncy;
+        const int64_t base = box * G.ncell + ((int64_t)cz * G.nc[1] + cy) * G.nc[0] + T0[0] / G.bs;
+        rb[r] = cell_start[base];
+        rp[r] = cell_start[base + ncx] - rb[r];
+    }
+    {
+        int4* a4 = reinterpret_cast<int4*>(acc);
+        for (int i = threadIdx.x; i < 3 * SN / 4; i += blockDim.x) a4[i] = make_int4(0, 0, 0, 0);
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        int carry = 0;
-        for (int c0 = 0; c0 < nr; c0 += 32) {
-            const int i = c0 + lane;
-            const int len = i < nr ? rpre[i] : 0;
-            int x = len;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (i < nr) rpre[i] = carry + x - len;
-            carry += __shfl_sync(0xffffffffu, x, 31);
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int r = 0; r < rows; ++r) {
+            const int len = rp[r];
+            rp[r] = run;
+            run += len;
         }
-        if (lane == 0) rpre[nr] = carry;
+        rp[rows] = run;
     }
     __syncthreads();
-    const int total = rpre[nr];
-    // candidate -> range map (ranges are short; each thread fills the spans of its ranges);
-    // candidates beyond the map's capacity (unusually dense tiles) find their range by search
-    for (int r = threadIdx.x; r < nr; r += blockDim.x)
-        for (int t = rpre[r]; t < rpre[r + 1] && t < max_cand; ++t) rmap[t] = (uint16_t)r;
-    __syncthreads();
+    const int total = rp[rows];
+    auto slot_of = [&](int t) {
+        int r = 0;
+        while (rp[r + 1] <= t) ++r;
+        return (int64_t)rb[r] + (t - rp[r]);
+    };
+    // the tile's fixed-point scale: 2^(30 - e) with 2^e >= n (2/3)^3 max|F| / h^3
     const float inv_h3 = G.inv_h * G.inv_h * G.inv_h;
+    float fm = 0.f;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        int r;
-        if (t < max_cand) {
-            r = rmap[t];
-        } else {
-            int a = 0, b = nr - 1;
-            while (a < b) {
-                const int m = (a + b + 1) >> 1;
-                if (rpre[m] <= t) a = m; else b = m - 1;
-            }
-            r = a;
-        }
-        const int64_t slot = rbeg[r] + (t - rpre[r]);
+        const float4 fv = rec[2 * slot_of(t) + 1];
+        fm = fmaxf(fm, fmaxf(fabsf(fv.x), fmaxf(fabsf(fv.y), fabsf(fv.z))));
+    }
+    for (int o = 16; o > 0; o >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = fm;
+    __syncthreads();
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) fm = fmaxf(fm, wmax[w]);
+    const float bound = (float)total * (8.0f / 27.0f) * fm * inv_h3;
+    int e = 0;
+    frexpf(bound, &e);                                           // bound < 2^e
+    const float scale = bound > 0.f ? ldexpf(1.0f, 30 - e) : 1.0f;
+    // origin of the shared copy in node coordinates
+    const int ox = T0[0] - 4, oy = T0[1] - 1, oz = T0[2] - 1;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int64_t slot = slot_of(t);
         const float4 pa = rec[2 * slot], fv = rec[2 * slot + 1];
         const int pk = __float_as_int(pa.w);
         const Win2 wx = windows2(cell_unpack(pk, 0), G.bs, pa.x, G.inv_h);
         const Win2 wy = windows2(cell_unpack(pk, 1), G.bs, pa.y, G.inv_h);
         const Win2 wz = windows2(cell_unpack(pk, 2), G.bs, pa.z, G.inv_h);
-        const float Fv[3] = {fv.x * inv_h3, fv.y * inv_h3, fv.z * inv_h3};
+        const float Fv[3] = {fv.x * inv_h3 * scale, fv.y * inv_h3 * scale, fv.z * inv_h3 * scale};
 #pragma unroll
         for (int comp = 0; comp < 3; ++comp) {
             const int sxs = comp == 0 ? 0 : 1, sys = comp == 1 ? 0 : 1, szs = comp == 2 ? 0 : 1;
-            const int ix = wx.i0[sxs] - T0[0], iy = wy.i0[sys] - T0[1], iz = wz.i0[szs] - T0[2];
-            float* acc_c = acc + comp * tileN;
+            // window starts in the copy: [3, TX + 3] and [0, T] for blobs of the tile (offsets
+            // in [0, w)); clamped so that no offset can address outside the copy
+            const int lx = min(max(wx.i0[sxs] - ox, 0), SX - 3);
+            const int ly = min(max(wy.i0[sys] - oy, 0), SY - 3);
+            const int lz = min(max(wz.i0[szs] - oz, 0), SZ - 3);
+            int* a0 = acc + comp * SN + (lz * SY + ly) * SX + lx;
 #pragma unroll
             for (int cz = 0; cz < 3; ++cz) {
-                const int rz = (iz + cz) & (nz - 1);
                 const float wzc = wz.w[szs][cz] * Fv[comp];
 #pragma unroll
                 for (int cy = 0; cy < 3; ++cy) {
-                    const int ry = (iy + cy) & (ny - 1);
-                    const bool inyz = rz < TZ && ry < TY;
                     const float wyz = wy.w[sys][cy] * wzc;
-                    const int rowoff = (rz * TY + ry) * TX;
+                    int* row = a0 + (cz * SY + cy) * SX;
 #pragma unroll
-                    for (int cx = 0; cx < 3; ++cx) {
-                        const int rx = (ix + cx) & (nx - 1);
-                        if (inyz && rx < TX) atomicAdd(acc_c + rowoff + rx, wx.w[sxs][cx] * wyz);
-                    }
+                    for (int cx = 0; cx < 3; ++cx) atomicAdd(row + cx, __float2int_rn(wx.w[sxs][cx] * wyz));
                 }
             }
         }
     }
     __syncthreads();
-    const int lx = 31 - __clz(TX), lxy = lx + (31 - __clz(TY)), lt = lxy + (31 - __clz(TZ));
-    for (int i = threadIdx.x; i < 3 * tileN; i += blockDim.x) {
-        const int comp = i >> lt, rem = i & (tileN - 1);
-        const int rz = rem >> lxy, ry = (rem >> lx) & (TY - 1), rx = rem & (TX - 1);
-        f[((size_t)box * 3 + comp) * (size_t)G.N +
-          ((size_t)(T0[2] + rz) * ny + (T0[1] + ry)) * nx + (T0[0] + rx)] = acc[i];
+    const int4* a4 = reinterpret_cast<const int4*>(acc);
+    const size_t comp_stride = (size_t)G.N;
+    const float unscale = 1.0f / scale;
+    for (int i = threadIdx.x; i < 3 * SY * SZ * SXC; i += blockDim.x) {
+        const int4 q = a4[i];
+        if ((q.x | q.y | q.z | q.w) == 0) continue;
+        const int row = i / SXC, cx = i - row * SXC;
+        const int comp = row / (SY * SZ), rr = row - comp * (SY * SZ);
+        const int sz = rr / SY, sy = rr - sz * SY;
+        const int gx = (ox + 4 * cx) & (nx - 1), gy = (oy + sy) & (ny - 1), gz = (oz + sz) & (nz - 1);
+        float* dst = f + ((size_t)box * 3 + comp) * comp_stride + ((size_t)gz * ny + gy) * nx + gx;
+        atomicAdd(reinterpret_cast<float4*>(dst),
+                  make_float4(q.x * unscale, q.y * unscale, q.z * unscale, q.w * unscale));
     }
 }
 
@@ -676,34 +661,47 @@ cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t max_box_blobs, cons
     return cudaGetLastError();
 }
 
+size_t spread32_smem(const int tile[3])
+{
+    return (size_t)3 * (tile[0] + 8) * (tile[1] + 3) * (tile[2] + 3) * sizeof(float);
+}
+
+bool spread32_tile_ok(const int tile[3], const GridGeo& g, const BinGeo& bg)
+{
+    bool ok = spread32_smem(tile) <= 200 * 1024;
+    for (int d = 0; d < 3; ++d)
+        ok = ok && tile[d] >= 4 && tile[d] <= g.n[d] && g.n[d] % tile[d] == 0 && tile[d] % bg.bs == 0;
+    return ok && (tile[1] / bg.bs) * (tile[2] / bg.bs) <= 64;
+}
+
+template <int TX, int TY, int TZ>
+cudaError_t launch_spread32_t(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
+                              const GridGeo& g, const BinGeo& bg, const int tile[3], float* f)
+{
+    const size_t smem = spread32_smem(tile);
+    static std::atomic<unsigned> attr{0};
+    if (first_on_device(attr))
+        cudaFuncSetAttribute(k_spread32<TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+    const int ntiles = (g.n[0] / tile[0]) * (g.n[1] / tile[1]) * (g.n[2] / tile[2]);
+    k_spread32<TX, TY, TZ><<<dim3((unsigned)ntiles, (unsigned)Bx), 256, smem, st>>>(
+        rec, cell_start, g, bg, tile[0], tile[1], tile[2], f);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
                             const GridGeo& g, const BinGeo& bg, const int tile[3], float* f)
 {
-    const int TX = tile[0], TY = tile[1], TZ = tile[2];
-    int max_rows = 1;
-    for (int d = 1; d < 3; ++d) {
-        int most = 0;
-        for (int T0 = 0; T0 < g.n[d]; T0 += tile[d]) {
-            int lo, cnt;
-            halo_cells32(T0, tile[d], bg.bs, bg.nc[d], lo, cnt);
-            most = cnt > most ? cnt : most;
-        }
-        max_rows *= most;
-    }
-    const int max_ranges = 2 * max_rows;
-    // map capacity: 8 blobs per halo bin cell (the dense workload averages about one); the
-    // kernel falls back to a search for candidates beyond it
-    const int max_cand = max_rows * (TX / bg.bs + 3) * 8;
-    const size_t smem = 3 * (size_t)TX * TY * TZ * sizeof(float) +
-                        sizeof(int32_t) * (2 * max_ranges + 1) + sizeof(uint16_t) * max_cand + 16;
-    static std::atomic<unsigned> attr{0};
-    if (first_on_device(attr))
-        cudaFuncSetAttribute(k_spread32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    const int ntiles = (g.n[0] / TX) * (g.n[1] / TY) * (g.n[2] / TZ);
-    k_spread32<<<dim3((unsigned)ntiles, (unsigned)Bx), 256, smem, st>>>(rec, cell_start, g, bg, TX,
-                                                                        TY, TZ, max_ranges,
-                                                                        max_cand, f);
-    return cudaGetLastError();
+    if (!spread32_tile_ok(tile, g, bg)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(f, 0, sizeof(float) * 3 * (size_t)Bx * g.N, st);
+    if (e != cudaSuccess) return e;
+    const int a = tile[0], b = tile[1], c = tile[2];
+    if (a == 32 && b == 8 && c == 8) return launch_spread32_t<32, 8, 8>(st, Bx, rec, cell_start, g, bg, tile, f);
+    if (a == 16 && b == 8 && c == 8) return launch_spread32_t<16, 8, 8>(st, Bx, rec, cell_start, g, bg, tile, f);
+    if (a == 32 && b == 16 && c == 8) return launch_spread32_t<32, 16, 8>(st, Bx, rec, cell_start, g, bg, tile, f);
+    if (a == 16 && b == 16 && c == 8) return launch_spread32_t<16, 16, 8>(st, Bx, rec, cell_start, g, bg, tile, f);
+    if (a == 64 && b == 8 && c == 8) return launch_spread32_t<64, 8, 8>(st, Bx, rec, cell_start, g, bg, tile, f);
+    return launch_spread32_t<0, 0, 0>(st, Bx, rec, cell_start, g, bg, tile, f);
 }
 
 cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t max_box_blobs,

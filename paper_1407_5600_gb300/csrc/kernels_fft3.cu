@@ -211,6 +211,7 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     const R* pf = fc ? fc + (size_t)z * ny * nx : nullptr;
     // each work unit: 4 consecutive x of the two rows 2p, 2p+1
     const int qx = nx / 4;
+#pragma unroll 2
     for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
         const int x0 = 4 * (u % qx), p = u / qx;
         const int y0 = 2 * p, y1 = y0 + 1;
@@ -301,7 +302,35 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         const int j = 2 * k + (y & 1);
         return (y >> 1) * S + j + (j >> sx);
     };
-    lines_fft_n(ny, P, nxh, col, twy, false);
+    // columns k = 0 and k = nx/2 are real: transform them as one complex column
+    // Z_y = X_y[0] + i X_y[nx/2], so that nx/2 column lines remain
+    for (int y = threadIdx.x; y < ny; y += blockDim.x)
+        P[col(0, y)] = T{P[col(0, y)].x, P[col(nx / 2, y)].x};
+    __syncthreads();
+    lines_fft_n(ny, P, nxh - 1, col, twy, false);
+    __syncthreads();
+    // A = FFT X[0] = (Z_k + conj Z_-k) / 2,  B = FFT X[nx/2] = (Z_k - conj Z_-k) / (2i)
+    if (threadIdx.x < 32) {
+        T av[4], bv[4];            // ny <= 128: at most 4 per lane
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int k = threadIdx.x + 32 * r;
+            if (k < ny) {
+                const T Zk = P[col(0, k)], Zr = P[col(0, (ny - k) & (ny - 1))];
+                av[r] = T{(Zk.x + Zr.x) * R(0.5), (Zk.y - Zr.y) * R(0.5)};
+                bv[r] = T{(Zk.y + Zr.y) * R(0.5), (Zr.x - Zk.x) * R(0.5)};
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int k = threadIdx.x + 32 * r;
+            if (k < ny) {
+                P[col(0, k)] = av[r];
+                P[col(nx / 2, k)] = bv[r];
+            }
+        }
+    }
     __syncthreads();
     T* out = a.spec + ((size_t)bc * nz + z) * (size_t)nxh * ny;
     const int ly = 31 - __clz(ny);
@@ -330,7 +359,8 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     T* base = a.spec + (size_t)(box * 3) * cstride + (size_t)kx * ny + ky0;
     auto at = [=](int c, int z, int k) { return (c * nzp + z + (z >> sz)) * Cp + k; };
     const int total = 3 * nz * C;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+#pragma unroll 8
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {      // 8 loads in flight per thread
         const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
         Bf[at(c, z, k)] = base[c * cstride + (size_t)z * zstride + k];
     }
@@ -408,9 +438,41 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
         return (y >> 1) * S + j + (j >> sx);
     };
     const int ly = 31 - __clz(ny);
+#pragma unroll 8
     for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) P[col(i >> ly, i & (ny - 1))] = in[i];
     __syncthreads();
-    lines_fft_n(ny, P, nxh, col, twy, true);
+    // columns k = 0 and k = nx/2 invert to real sequences: transform their Hermitian parts as
+    // one complex column Z = herm(A) + i herm(B), whose inverse is Re(IFFT A) + i Re(IFFT B)
+    if (threadIdx.x < 32) {
+        T zv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int k = threadIdx.x + 32 * r;
+            if (k < ny) {
+                const int kr = (ny - k) & (ny - 1);
+                const T A = P[col(0, k)], Ar = P[col(0, kr)];
+                const T Bv = P[col(nx / 2, k)], Br = P[col(nx / 2, kr)];
+                // herm(A) = (A_k + conj A_-k) / 2, herm(B) likewise; Z = herm(A) + i herm(B)
+                const T ha = T{(A.x + Ar.x) * R(0.5), (A.y - Ar.y) * R(0.5)};
+                const T hb = T{(Bv.x + Br.x) * R(0.5), (Bv.y - Br.y) * R(0.5)};
+                zv[r] = T{ha.x - hb.y, ha.y + hb.x};
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int k = threadIdx.x + 32 * r;
+            if (k < ny) P[col(0, k)] = zv[r];
+        }
+    }
+    __syncthreads();
+    lines_fft_n(ny, P, nxh - 1, col, twy, true);
+    __syncthreads();
+    for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+        const T zc = P[col(0, y)];
+        P[col(0, y)] = T{zc.x, R(0)};
+        P[col(nx / 2, y)] = T{zc.y, R(0)};
+    }
     __syncthreads();
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;

@@ -289,6 +289,14 @@ void choose_bins(mb_ctx* ctx, double r_cut)
     ctx->bg.inv_w = 1.0 / (bs * ctx->d.h);
 }
 
+// Default spreading tile: {32, 8, 8} nodes, clamped to the grid and raised to whole bin cells.
+void pick_tile(mb_ctx* ctx)
+{
+    const int want[3] = {32, 8, 8};
+    for (int d = 0; d < 3; ++d)
+        ctx->tile[d] = std::min(std::max(std::min(want[d], ctx->g.n[d]), ctx->bg.bs), ctx->g.n[d]);
+}
+
 void drop_graph(mb_ctx* ctx)
 {
     for (cudaGraphExec_t& g : ctx->graph_exec) {
@@ -319,6 +327,7 @@ mb_status rebuild(mb_ctx* ctx)
         ctx->max_box_blobs = std::max(ctx->max_box_blobs, ctx->box_off_h[b + 1] - ctx->box_off_h[b]);
     ctx->nchunk = (int)((ctx->max_box_blobs + 255) / 256);
     choose_bins(ctx, rmax);
+    pick_tile(ctx);
 
     std::vector<double> q(3 * nb), par(3 * B);
     std::vector<int32_t> pid(nb), box_of(nb), adj_start(nb + 1, 0), part_start(np + 1, 0),
@@ -758,21 +767,15 @@ mb_status autotune_spread(mb_ctx* ctx)
             return MB_OK;
         }
     }
-    static const int cand[][3] = {{32, 8, 8}, {32, 16, 8}, {32, 16, 16}, {16, 16, 16},
-                                  {64, 8, 8}, {64, 16, 8}, {16, 8, 8}, {8, 8, 8}};
+    static const int cand[][3] = {{32, 8, 8}, {16, 8, 8}, {32, 16, 8}, {16, 16, 8}, {64, 8, 8}};
     cudaEvent_t e0, e1;
     MB_CUDA(cudaEventCreate(&e0));
     MB_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_t[3] = {ctx->tile[0], ctx->tile[1], ctx->tile[2]};
     for (const auto& c : cand) {
-        int t[3];
-        bool ok = true;
-        for (int d = 0; d < 3; ++d) {
-            t[d] = std::min(c[d], ctx->g.n[d]);
-            ok = ok && ctx->g.n[d] % t[d] == 0;
-        }
-        if (!ok || 3 * (size_t)t[0] * t[1] * t[2] * 4 > 150 * 1024) continue;
+        const int t[3] = {c[0], c[1], c[2]};
+        if (!spread32_tile_ok(t, ctx->g, ctx->bg)) continue;
         float ms = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
             MB_CUDA(cudaEventRecord(e0, ctx->st));
@@ -876,11 +879,6 @@ mb_status current_positions(mb_ctx* ctx)
     return MB_OK;
 }
 
-void pick_tile(mb_ctx* ctx)
-{
-    const int want[3] = {32, 8, 8};
-    for (int d = 0; d < 3; ++d) ctx->tile[d] = std::min(want[d], ctx->g.n[d]);
-}
 
 mb_status upload_tables(mb_ctx* ctx)
 {
@@ -1084,8 +1082,8 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     if (const char* e = std::getenv("MB_FFT_PASSES")) ctx->fft_passes = std::atoi(e) == 5 ? 5 : 3;
     if (const char* e = std::getenv("MB_NO_GRAPH")) ctx->use_graph = std::atoi(e) == 0;
     if (const char* e = std::getenv("MB_NO_AUTOTUNE")) ctx->autotune = std::atoi(e) == 0;
-    pick_tile(ctx);
     choose_bins(ctx, 0.0);
+    pick_tile(ctx);
 
     auto fail = [&](mb_status s) {
         g_create_error = ctx->err;
