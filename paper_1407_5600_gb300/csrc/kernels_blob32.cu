@@ -272,8 +272,10 @@ __device__ __forceinline__ void spring32(const int cb[3], const float hb[3], con
     two_sum(s01, p[2], P, e2);
     const float Pl = e01 + e2 + pe[0] + pe[1] + pe[2];
     const float d2 = (P - r0h) + (Pl - r0l);      // P - r0h is exact near the rest length
-    const float len = sqrtf(P);
-    const float mag = -k * d2 / ((len + r0) * len);
+    // |r| - r0 = d2 / (|r| + r0); the reciprocal square root and the fast divide carry a few
+    // ulps of float, far below the float grid's own rounding
+    const float len = P * rsqrtf(P);
+    const float mag = -k * __fdividef(d2, (len + r0) * len);
     for (int d = 0; d < 3; ++d) F[d] += mag * rh[d];
 }
 
@@ -317,6 +319,7 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
     const float k_spring = (float)a.box_par[3 * box];
     const float k_rep = (float)a.box_par[3 * box + 1];
     const float r_cut = (float)a.box_par[3 * box + 2];
+#pragma unroll 2
     for (int e = a.adj_start[b]; e < a.adj_start[b + 1]; ++e) {
         const int4 ad = a.adj[e];
         spring32(cb, hb, lb, a.A[ad.x], a.B[ad.x], __int_as_float(ad.y), __int_as_float(ad.z),
@@ -354,34 +357,67 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
             return x;
         };
         const int boxbase = (int)(box * G.ncell);
-        for (int dz = lo[2]; dz <= hi[2]; ++dz) {
-            const int cz = nbr(cb[2], dz, G.nc[2]);
-            for (int dy = lo[1]; dy <= hi[1]; ++dy) {
-                const int cy = nbr(cb[1], dy, G.nc[1]);
-                const int rowc = boxbase + (cz * G.nc[1] + cy) * G.nc[0];
-                for (int dx = lo[0]; dx <= hi[0]; ++dx) {
-                    const int cx = nbr(cb[0], dx, G.nc[0]);
-                    const int cc = rowc + cx;
-                    // cell offset of the neighbour (unwrapped) in the wide case; otherwise the
-                    // minimum image of the difference
-                    const float ox = (wide ? dx : cx - cb[0]) * G.w;
-                    const float oy = (wide ? dy : cy - cb[1]) * G.w;
-                    const float oz = (wide ? dz : cz - cb[2]) * G.w;
-                    for (int t = a.cell_start[cc]; t < a.cell_start[cc + 1]; ++t) {
-                        if (t == slot) continue;
-                        const float4 lj = a.loc[t];
-                        if (__float_as_int(lj.w) == pb) continue;
-                        float r[3] = {me.x - lj.x - ox, me.y - lj.y - oy, me.z - lj.z - oz};
-                        if (!wide)
-                            for (int d = 0; d < 3; ++d) {
-                                if (r[d] >= 0.5f * G.L[d]) r[d] -= G.L[d];
-                                else if (r[d] < -0.5f * G.L[d]) r[d] += G.L[d];
-                            }
-                        const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-                        if (r2 >= rc2 || r2 == 0.0f) continue;
-                        const float len = sqrtf(r2);
-                        const float mag = k_rep * (r_cut - len) / len;
-                        for (int d = 0; d < 3; ++d) Fp[d] += mag * r[d];
+        auto pair = [&](const float4 lj, float ox, float oy, float oz) {
+            float r[3] = {me.x - lj.x - ox, me.y - lj.y - oy, me.z - lj.z - oz};
+            if (!wide)
+                for (int d = 0; d < 3; ++d) {
+                    if (r[d] >= 0.5f * G.L[d]) r[d] -= G.L[d];
+                    else if (r[d] < -0.5f * G.L[d]) r[d] += G.L[d];
+                }
+            const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            if (r2 >= rc2 || r2 == 0.0f) return;
+            // k_rep (r_cut - |r|) / |r| = k_rep (r_cut / |r| - 1)
+            const float mag = k_rep * (r_cut * rsqrtf(r2) - 1.0f);
+            for (int d = 0; d < 3; ++d) Fp[d] += mag * r[d];
+        };
+        if (wide && 2.0f * r_cut <= G.w) {
+            // at most two cells per axis: read all (up to 8) cell ranges first, so that their
+            // loads are in flight together, then visit the candidates
+            // cell k = (kx, ky, kz) of a 2 x 2 x 2 block starting at (lo[0], lo[1], lo[2]);
+            // absent when the axis has one cell only (hi == lo)
+            int cs0[8], cs1[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+                cs0[k] = cs1[k] = 0;
+                if (lo[0] + kx <= hi[0] && lo[1] + ky <= hi[1] && lo[2] + kz <= hi[2]) {
+                    const int cc = boxbase + (nbr(cb[2], lo[2] + kz, G.nc[2]) * G.nc[1] +
+                                              nbr(cb[1], lo[1] + ky, G.nc[1])) * G.nc[0] +
+                                   nbr(cb[0], lo[0] + kx, G.nc[0]);
+                    cs0[k] = a.cell_start[cc];
+                    cs1[k] = a.cell_start[cc + 1];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int kx = k & 1, ky = (k >> 1) & 1, kz = k >> 2;
+                const float ox = (lo[0] + kx) * G.w, oy = (lo[1] + ky) * G.w, oz = (lo[2] + kz) * G.w;
+                for (int t = cs0[k]; t < cs1[k]; ++t) {
+                    const float4 lj = a.loc[t];
+                    if (t == slot || __float_as_int(lj.w) == pb) continue;
+                    pair(lj, ox, oy, oz);
+                }
+            }
+        } else {
+            for (int dz = lo[2]; dz <= hi[2]; ++dz) {
+                const int cz = nbr(cb[2], dz, G.nc[2]);
+                for (int dy = lo[1]; dy <= hi[1]; ++dy) {
+                    const int cy = nbr(cb[1], dy, G.nc[1]);
+                    const int rowc = boxbase + (cz * G.nc[1] + cy) * G.nc[0];
+                    for (int dx = lo[0]; dx <= hi[0]; ++dx) {
+                        const int cx = nbr(cb[0], dx, G.nc[0]);
+                        const int cc = rowc + cx;
+                        // cell offset of the neighbour (unwrapped) in the wide case; otherwise
+                        // the minimum image of the difference
+                        const float ox = (wide ? dx : cx - cb[0]) * G.w;
+                        const float oy = (wide ? dy : cy - cb[1]) * G.w;
+                        const float oz = (wide ? dz : cz - cb[2]) * G.w;
+                        for (int t = a.cell_start[cc]; t < a.cell_start[cc + 1]; ++t) {
+                            if (t == slot) continue;
+                            const float4 lj = a.loc[t];
+                            if (__float_as_int(lj.w) == pb) continue;
+                            pair(lj, ox, oy, oz);
+                        }
                     }
                 }
             }
@@ -394,7 +430,7 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
 }
 
 // ------------------------------------------------------------------------------------------
-// Tile-owner spreading from the FP32 records (see k_spread for the scheme).
+// Spreading from the FP32 records.
 // Per-dimension windows for both MAC shifts (0 along the component's own axis, 1/2 across).
 struct Win2 {
     float w[2][3];

@@ -34,10 +34,59 @@ __host__ __device__ constexpr int bitrev(int i, int bits)
 }
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
-// In-register radix-2 DIT DFT of P points.  tw[j] = W_N^j, j < N; W_P^m = tw[m * stride].
-template <int P, typename T>
-__device__ __forceinline__ void reg_dft(T (&x)[P], const T* __restrict__ tw, int stride, bool inv)
+// cos and sin of 2 pi j / 16, j < 8 (the twiddles of the in-register DFTs of up to 16 points;
+// after unrolling every index is a constant and the values fold into the arithmetic).
+template <typename R> __device__ __forceinline__ R cos16(int j)
 {
+    switch (j) {
+    case 0: return R(1.0);
+    case 1: return R(0.92387953251128675613);
+    case 2: return R(0.70710678118654752440);
+    case 3: return R(0.38268343236508977173);
+    case 4: return R(0.0);
+    case 5: return R(-0.38268343236508977173);
+    case 6: return R(-0.70710678118654752440);
+    default: return R(-0.92387953251128675613);
+    }
+}
+// sin(2 pi j / 16) = cos(2 pi (j - 4) / 16), j < 8
+template <typename R> __device__ __forceinline__ R sin16(int j) { return cos16<R>(j < 4 ? 4 - j : j - 4); }
+
+// b W_16^j (forward) or b W_16^-j (inverse), with W_16 = exp(-2 pi i / 16); j < 8.
+template <bool INV, typename T> __device__ __forceinline__ T twiddle16(T b, int j)
+{
+    using R = decltype(b.x);
+    if (j == 0) return b;
+    if (j == 4) return INV ? T{-b.y, b.x} : T{b.y, -b.x};
+    const R c = cos16<R>(j), sn = INV ? sin16<R>(j) : -sin16<R>(j);
+    return T{b.x * c - b.y * sn, b.x * sn + b.y * c};
+}
+
+// One radix-2 stage (butterfly span LEN) of an in-register DIT DFT, then the next stage.  The
+// span is a template argument so that every loop has a constant trip count and unrolls fully,
+// which turns each twiddle index into a constant.
+template <int P, int LEN, bool INV, typename T>
+__device__ __forceinline__ void dft_stage(T (&x)[P])
+{
+    constexpr int HALF = LEN / 2;
+#pragma unroll
+    for (int s0 = 0; s0 < P; s0 += LEN) {
+#pragma unroll
+        for (int m = 0; m < HALF; ++m) {
+            const T b = twiddle16<INV>(x[s0 + m + HALF], m * (16 / LEN));
+            const T a = x[s0 + m];
+            x[s0 + m] = cadd(a, b);
+            x[s0 + m + HALF] = csub(a, b);
+        }
+    }
+    if constexpr (LEN < P) dft_stage<P, 2 * LEN, INV>(x);
+}
+
+// In-register radix-2 DIT DFT of P <= 16 points with constant twiddles W_P^m = W_16^(16 m / P).
+template <int P, bool INV, typename T>
+__device__ __forceinline__ void reg_dft(T (&x)[P])
+{
+    static_assert(P <= 16, "in-register DFTs of at most 16 points");
     constexpr int bits = ilog2c(P);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -48,25 +97,7 @@ __device__ __forceinline__ void reg_dft(T (&x)[P], const T* __restrict__ tw, int
             x[r] = tmp;
         }
     }
-#pragma unroll
-    for (int len = 2; len <= P; len <<= 1) {
-        const int half = len >> 1;
-#pragma unroll
-        for (int s0 = 0; s0 < P; s0 += len) {
-#pragma unroll
-            for (int m = 0; m < half; ++m) {
-                T b = x[s0 + m + half];
-                if (m != 0) {
-                    T w = tw[m * (P / len) * stride];
-                    if (inv) w.y = -w.y;
-                    b = cm(b, w);
-                }
-                const T a = x[s0 + m];
-                x[s0 + m] = cadd(a, b);
-                x[s0 + m + half] = csub(a, b);
-            }
-        }
-    }
+    if constexpr (P > 1) dft_stage<P, 2, INV>(x);
 }
 
 template <int N> struct Split;                  // N = N1 * N2 with N1 >= N2, N1 % N2 == 0
@@ -80,9 +111,8 @@ template <> struct Split<128> { static constexpr int N1 = 16, N2 = 8; };
 // FFTs of `lines` lines of N points held in shared memory; element j of line l is at
 // buf[idx(l, j)].  All threads of the block call this; lines are spread over warps with the
 // N2 threads of a line inside one warp, so only warp-level synchronisation is needed.
-template <int N, typename T, typename Idx>
-__device__ __forceinline__ void lines_fft(T* buf, int lines, Idx idx, const T* __restrict__ tw,
-                                          bool inv)
+template <int N, bool INV, typename T, typename Idx>
+__device__ __forceinline__ void lines_fft(T* buf, int lines, Idx idx, const T* __restrict__ tw)
 {
     constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, M = N1 / N2;
     constexpr int LPW = 32 / N2;                 // lines per warp per round
@@ -96,11 +126,11 @@ __device__ __forceinline__ void lines_fft(T* buf, int lines, Idx idx, const T* _
         T a[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) a[n1] = on ? buf[idx(l, N2 * n1 + t)] : T{0, 0};
-        reg_dft<N1>(a, tw, N2, inv);
+        reg_dft<N1, INV>(a);
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) {
             T w = tw[(t * k1) & (N - 1)];
-            if (inv) w.y = -w.y;
+            if (INV) w.y = -w.y;
             a[k1] = cm(a[k1], w);
         }
         __syncwarp();
@@ -116,7 +146,7 @@ __device__ __forceinline__ void lines_fft(T* buf, int lines, Idx idx, const T* _
             for (int n2 = 0; n2 < N2; ++n2)
                 b[m][n2] = on ? buf[idx(l, (t + N2 * m) * N2 + n2)] : T{0, 0};
 #pragma unroll
-        for (int m = 0; m < M; ++m) reg_dft<N2>(b[m], tw, N1, inv);
+        for (int m = 0; m < M; ++m) reg_dft<N2, INV>(b[m]);
         __syncwarp();
         if (on) {
 #pragma unroll
@@ -128,16 +158,16 @@ __device__ __forceinline__ void lines_fft(T* buf, int lines, Idx idx, const T* _
     }
 }
 
-template <typename T, typename Idx>
-__device__ void lines_fft_n(int n, T* buf, int lines, Idx idx, const T* tw, bool inv)
+template <bool INV, typename T, typename Idx>
+__device__ __forceinline__ void lines_fft_n(int n, T* buf, int lines, Idx idx, const T* tw)
 {
     switch (n) {
-    case 4: lines_fft<4>(buf, lines, idx, tw, inv); break;
-    case 8: lines_fft<8>(buf, lines, idx, tw, inv); break;
-    case 16: lines_fft<16>(buf, lines, idx, tw, inv); break;
-    case 32: lines_fft<32>(buf, lines, idx, tw, inv); break;
-    case 64: lines_fft<64>(buf, lines, idx, tw, inv); break;
-    default: lines_fft<128>(buf, lines, idx, tw, inv); break;
+    case 4: lines_fft<4, INV>(buf, lines, idx, tw); break;
+    case 8: lines_fft<8, INV>(buf, lines, idx, tw); break;
+    case 16: lines_fft<16, INV>(buf, lines, idx, tw); break;
+    case 32: lines_fft<32, INV>(buf, lines, idx, tw); break;
+    case 64: lines_fft<64, INV>(buf, lines, idx, tw); break;
+    default: lines_fft<128, INV>(buf, lines, idx, tw); break;
     }
 }
 
@@ -211,7 +241,6 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     const R* pf = fc ? fc + (size_t)z * ny * nx : nullptr;
     // each work unit: 4 consecutive x of the two rows 2p, 2p+1
     const int qx = nx / 4;
-#pragma unroll 2
     for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
         const int x0 = 4 * (u % qx), p = u / qx;
         const int y0 = 2 * p, y1 = y0 + 1;
@@ -266,7 +295,7 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         }
     }
     __syncthreads();
-    lines_fft_n(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx, false);
+    lines_fft_n<false>(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx);
     __syncthreads();
     // separate the two real rows of each packed row (one warp per packed row, in place)
     {
@@ -307,7 +336,7 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     for (int y = threadIdx.x; y < ny; y += blockDim.x)
         P[col(0, y)] = T{P[col(0, y)].x, P[col(nx / 2, y)].x};
     __syncthreads();
-    lines_fft_n(ny, P, nxh - 1, col, twy, false);
+    lines_fft_n<false>(ny, P, nxh - 1, col, twy);
     __syncthreads();
     // A = FFT X[0] = (Z_k + conj Z_-k) / 2,  B = FFT X[nx/2] = (Z_k - conj Z_-k) / (2i)
     if (threadIdx.x < 32) {
@@ -366,7 +395,7 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     }
     __syncthreads();
     auto idx = [=](int l, int z) { return at(l / C, z, l % C); };
-    lines_fft_n(nz, Bf, 3 * C, idx, twz, false);
+    lines_fft_n<false>(nz, Bf, 3 * C, idx, twz);
     __syncthreads();
     const R* sym = reinterpret_cast<const R*>(a.symr);     // [9][256] cos, sin, lambda
     const R ih = R(g.inv_h);
@@ -409,7 +438,7 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
         for (int c = 0; c < 3; ++c) Bf[at(c, kz, k)] = W[c];
     }
     __syncthreads();
-    lines_fft_n(nz, Bf, 3 * C, idx, twz, true);
+    lines_fft_n<true>(nz, Bf, 3 * C, idx, twz);
     __syncthreads();
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
         const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
@@ -466,7 +495,7 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
         }
     }
     __syncthreads();
-    lines_fft_n(ny, P, nxh - 1, col, twy, true);
+    lines_fft_n<true>(ny, P, nxh - 1, col, twy);
     __syncthreads();
     for (int y = threadIdx.x; y < ny; y += blockDim.x) {
         const T zc = P[col(0, y)];
@@ -501,7 +530,7 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
         }
     }
     __syncthreads();
-    lines_fft_n(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx, true);
+    lines_fft_n<true>(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx);
     __syncthreads();
     const R scale = R(1.0 / (double)g.N);
     R* out = a.v_out + (size_t)bc * g.N + (size_t)z * ny * nx;
