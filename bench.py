@@ -40,7 +40,8 @@ def stage_model(n, nb, rsz, ncell):
     spec = 3 * n * n * (n // 2 + 1) * 2 * rsz           # one 3-component half spectrum
     vec = 24 * nb
     return {
-        "interp_predict": ("hbm", grid + 2 * vec),       # read v, q; write q_half
+        # the predictor of step n+1 runs inside step n's corrector pass (same gathered nodes)
+        "interp_predict": ("hbm", 0),
         "bin": ("hbm", vec + 3 * 4 * nb + 4 * 4 * ncell), # q_half; cell, rank, slot; counts/scan
         # q_half, slot, pid, 42/13 bonds x 2 ends x (index + rest); write F and (q, F) record
         "forces": ("hbm", nb * (24 + 4 + 4 + 2 * 42 / 13 * 12 + 24 + 48)),
@@ -51,7 +52,8 @@ def stage_model(n, nb, rsz, ncell):
         "fluid_z_solve": ("hbm", 2 * spec),
         "fluid_y_inv": ("hbm", 0),                       # no kernel in the three-pass FFT
         "fluid_x_inv": ("hbm", spec + grid),             # read spectrum; write v
-        "interp_correct": ("hbm", 2 * grid + 3 * vec),   # read v^n, v^{n+1}, q_half, q; write q
+        # read v^n, v^{n+1}, q_half, q; write q^{n+1} and the next q_half
+        "interp_correct": ("hbm", 2 * grid + 4 * vec),
     }
 
 

@@ -202,6 +202,87 @@ k_interp32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ 
     }
 }
 
+// J v at a split position for all three components: sum over the 27-node windows of one grid
+// (v1 == nullptr) or of the sum v0 + v1.
+__device__ __forceinline__ void gather32(const int c[3], const float hi[3], const float* v0,
+                                         const float* v1, size_t box_base, const Geo32& G,
+                                         float u[3])
+{
+    const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+        float wx[3], wy[3], wz[3];
+        const int ix = window32(c[0], G.bs, hi[0], G.inv_h, comp == 0 ? 0.f : 0.5f, wx);
+        const int iy = window32(c[1], G.bs, hi[1], G.inv_h, comp == 1 ? 0.f : 0.5f, wy);
+        const int iz = window32(c[2], G.bs, hi[2], G.inv_h, comp == 2 ? 0.f : 0.5f, wz);
+        const size_t base = box_base + (size_t)comp * (size_t)G.N;
+        float acc = 0.0f;
+#pragma unroll
+        for (int cz = 0; cz < 3; ++cz) {
+            const int zz = (iz + cz) & (nz - 1);
+#pragma unroll
+            for (int cy = 0; cy < 3; ++cy) {
+                const int yy = (iy + cy) & (ny - 1);
+                const size_t row = base + ((size_t)zz * ny + yy) * nx;
+                float r = 0.0f;
+#pragma unroll
+                for (int cx = 0; cx < 3; ++cx) {
+                    const int xx = (ix + cx) & (nx - 1);
+                    float val = __ldg(v0 + row + xx);
+                    if (v1) val += __ldg(v1 + row + xx);
+                    r += wx[cx] * val;
+                }
+                acc += wy[cy] * wz[cz] * r;
+            }
+        }
+        u[comp] = acc;
+    }
+}
+
+// The corrector of step n followed by the predictor of step n + 1, one thread per blob:
+//   q^{n+1}   = q^n + dt J(q^{n+1/2}) (v^n + v^{n+1}) / 2       (A_base, B_base -> A_out, B_out)
+//   q^{n+3/2} = q^{n+1} + (dt/2) J(q^{n+1}) v^{n+1}             (-> Ah_out, Bh_out, binned)
+// The second gather reads the nodes the first has just brought into L1.  A/Bl (q^{n+1/2}) and
+// Ah_out/Bh_out may alias, as may A_base/B_base and A_out/B_out: each thread reads its blob's
+// entries before writing them.
+__global__ void __launch_bounds__(256)
+k_interp32_fused(int64_t nb, const float4* A, const float* __restrict__ v0,
+                 const float* __restrict__ v1, const int32_t* __restrict__ box_of, GridGeo g,
+                 BinGeo bg, float dt, const float4* A_base, const float4* B_base, float4* A_out,
+                 float4* B_out, float4* Ah_out, float4* Bh_out, const int32_t* __restrict__ order,
+                 int32_t* __restrict__ count, int32_t* __restrict__ blob_cell,
+                 int32_t* __restrict__ blob_rank)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    const int64_t b = order ? order[t] : t;
+    const Geo32 G = geo32(g, bg);
+    const int box = box_of ? box_of[b] : 0;
+    const size_t box_base = (size_t)box * 3 * (size_t)G.N;
+    float u[3];
+    {
+        const float4 a = A[b];
+        const int pk = __float_as_int(a.w);
+        const int c[3] = {cell_unpack(pk, 0), cell_unpack(pk, 1), cell_unpack(pk, 2)};
+        const float hi[3] = {a.x, a.y, a.z};
+        gather32(c, hi, v0, v1, box_base, G, u);
+    }
+    const float4 ab = A_base[b], lb = B_base[b];
+    int cc[3] = {cell_unpack(__float_as_int(ab.w), 0), cell_unpack(__float_as_int(ab.w), 1),
+                 cell_unpack(__float_as_int(ab.w), 2)};
+    float h2[3] = {ab.x, ab.y, ab.z}, l2[3] = {lb.x, lb.y, lb.z};
+    for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], dt * (0.5f * u[d]), G.w, G.nc[d]);
+    A_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
+    B_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
+    gather32(cc, h2, v1, nullptr, box_base, G, u);
+    for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], 0.5f * dt * u[d], G.w, G.nc[d]);
+    Ah_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
+    Bh_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
+    const int cell = (int)(box * G.ncell) + (cc[2] * G.nc[1] + cc[1]) * G.nc[0] + cc[0];
+    blob_cell[b] = cell;
+    blob_rank[b] = atomicAdd(count + cell, 1);
+}
+
 // ------------------------------------------------------------------------------------------
 // Binning from the packed cells; loc[slot] = {hi, particle id} for the pair prefilter.
 __global__ void k_bin_count32(int64_t nb, const float4* __restrict__ A,
@@ -657,6 +738,21 @@ cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4*
     else
         k_interp32<2><<<nbk, 256, 0, st>>>(nb, A, B, v0, v1, box_of, g, bg, dt, A_base, B_base,
                                            A_out, B_out, u_out, order, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, const float* v0,
+                                  const float* v1, const int32_t* box_of, const GridGeo& g,
+                                  const BinGeo& bg, float dt, const float4* A_base,
+                                  const float4* B_base, float4* A_out, float4* B_out,
+                                  float4* Ah_out, float4* Bh_out, const int32_t* order,
+                                  int32_t* count, int32_t* blob_cell, int32_t* blob_rank)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_interp32_fused<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, v0, v1, box_of, g, bg, dt,
+                                                          A_base, B_base, A_out, B_out, Ah_out,
+                                                          Bh_out, order, count, blob_cell,
+                                                          blob_rank);
     return cudaGetLastError();
 }
 

@@ -134,7 +134,13 @@ struct mb_ctx {
         part_blobs, box_off, box_par, cell_count, cell_start, blob_cell, blob_rank, sorted,
         loc, scan_tmp, partial, staging_in, staging_out, mean_scratch;
     // FP32-grid mode blob state: positions as bin cell + float-float offset (q^n and midpoint)
-    DBuf sA, sB, hA, hB, F32, rec32, ext32, ext_sum, adj32;
+    DBuf sA, sB, hA[2], hB[2], F32, rec32, ext32, ext_sum, adj32;
+    // split midpoints: hA/hB[hcur] hold the predictor of the next step when pred_ready (the
+    // previous step's fused corrector wrote them); hlast is the buffer of the last step's
+    // midpoints (where its forces were evaluated)
+    int hcur = 0, hlast = 0;
+    bool pred_ready = false;
+    bool fuse_interp = true;
     bool ext_present = false;
     bool sorted_valid = false;     // `sorted` holds a permutation of the current blobs
     // spreading tile picked by timing candidate shapes on the first FP32-grid step
@@ -145,6 +151,7 @@ struct mb_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     bool graph_ext[2] = {false, false}, graph_body[2] = {false, false};
+    int graph_hcur[2] = {0, 0};
     int64_t graph_launches = 0;        // kernels per graph launch
     // adjoint scratch: blob vectors and grids (FP64 contexts)
     DBuf a_qn, a_u, a_qh, a_gq, a_guc, a_gqh, a_gF, a_gu, a_gk;
@@ -420,8 +427,10 @@ mb_status rebuild(mb_ctx* ctx)
     if (ctx->rsz == 4) {
         MB_TRY(ensure(ctx->sA, sizeof(float4) * nb, E, "split q"));
         MB_TRY(ensure(ctx->sB, sizeof(float4) * nb, E, "split q"));
-        MB_TRY(ensure(ctx->hA, sizeof(float4) * nb, E, "split q_half"));
-        MB_TRY(ensure(ctx->hB, sizeof(float4) * nb, E, "split q_half"));
+        for (int i = 0; i < 2; ++i) {
+            MB_TRY(ensure(ctx->hA[i], sizeof(float4) * nb, E, "split q_half"));
+            MB_TRY(ensure(ctx->hB[i], sizeof(float4) * nb, E, "split q_half"));
+        }
         MB_TRY(ensure(ctx->F32, sizeof(float4) * nb, E, "F32"));
         MB_TRY(ensure(ctx->rec32, 2 * sizeof(float4) * nb, E, "rec32"));
         MB_TRY(ensure(ctx->ext32, sizeof(float4) * nb, E, "ext32"));
@@ -441,6 +450,7 @@ mb_status rebuild(mb_ctx* ctx)
                              static_cast<float4*>(ctx->sA.p), static_cast<float4*>(ctx->sB.p)));
         ctx->ext_present = false;
         ctx->sorted_valid = false;
+        ctx->pred_ready = false;
         ctx->tuned = false;
     }
     // the host vectors die at return: make the copies complete first
@@ -641,6 +651,20 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
 
 // One time step of every box in FP32-grid mode: blob positions as bin cell + float-float
 // offset, forces and weights on the FP32 pipes, the k = 0 mode from the FP64 external force sum.
+// Host-side state after an FP32-grid step has been enqueued (directly or as a graph replay).
+void finish_fast_step(mb_ctx* ctx)
+{
+    ctx->cur ^= 1;
+    ctx->steps_taken++;
+    ctx->hlast = ctx->hcur;
+    if (ctx->nb > 0 && ctx->fuse_interp) {
+        ctx->hcur ^= 1;
+        ctx->pred_ready = true;
+    } else {
+        ctx->pred_ready = false;
+    }
+}
+
 mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
 {
     cudaStream_t st = ctx->st;
@@ -650,8 +674,8 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     float* vnext = static_cast<float*>(ctx->v[ctx->cur ^ 1].p);
     float4* sA = static_cast<float4*>(ctx->sA.p);
     float4* sB = static_cast<float4*>(ctx->sB.p);
-    float4* hA = static_cast<float4*>(ctx->hA.p);
-    float4* hB = static_cast<float4*>(ctx->hB.p);
+    float4* hA = static_cast<float4*>(ctx->hA[ctx->hcur].p);
+    float4* hB = static_cast<float4*>(ctx->hB[ctx->hcur].p);
     const int32_t* box_of = static_cast<const int32_t*>(ctx->box_of.p);
     const bool blobs = ctx->nb > 0;
     if (ctx->timing) {
@@ -661,7 +685,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     auto mark = [&](int i) { if (ctx->timing) cudaEventRecord(ctx->ev[i], st); };
     const float dt = (float)ctx->d.dt;
     mark(ST_INTERP_PREDICT);
-    if (blobs) {
+    if (blobs && !ctx->pred_ready) {
         // the predictor also bins the midpoint positions (counts per cell); the previous
         // step's cell order still groups neighbouring blobs
         MB_CUDA(cudaMemsetAsync(ctx->cell_count.p, 0, sizeof(int32_t) * B * ctx->bg.ncell, st));
@@ -730,14 +754,27 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
         ctx->launches += FLUID3_KERNELS;
     }
     if (blobs) {
-        MB_CUDA(launch_interp32(st, 2, ctx->nb, hA, hB, vcur, vnext, box_of, g, ctx->bg, dt, sA,
-                                sB, sA, sB, nullptr, static_cast<const int32_t*>(ctx->sorted.p)));
+        if (ctx->fuse_interp) {
+            // corrector of this step and predictor of the next (into the other midpoint buffer,
+            // with the bin counts the next step sorts by)
+            MB_CUDA(cudaMemsetAsync(ctx->cell_count.p, 0, sizeof(int32_t) * B * ctx->bg.ncell, st));
+            MB_CUDA(launch_interp32_fused(st, ctx->nb, hA, vcur, vnext, box_of, g, ctx->bg, dt, sA,
+                                          sB, sA, sB,
+                                          static_cast<float4*>(ctx->hA[ctx->hcur ^ 1].p),
+                                          static_cast<float4*>(ctx->hB[ctx->hcur ^ 1].p),
+                                          static_cast<const int32_t*>(ctx->sorted.p),
+                                          static_cast<int32_t*>(ctx->cell_count.p),
+                                          static_cast<int32_t*>(ctx->blob_cell.p),
+                                          static_cast<int32_t*>(ctx->blob_rank.p)));
+        } else {
+            MB_CUDA(launch_interp32(st, 2, ctx->nb, hA, hB, vcur, vnext, box_of, g, ctx->bg, dt,
+                                    sA, sB, sA, sB, nullptr,
+                                    static_cast<const int32_t*>(ctx->sorted.p)));
+        }
         ctx->launches += 1;
     }
     mark(NUM_STAGES);
     if (ctx->timing) ctx->ev_pending++;
-    ctx->cur ^= 1;
-    ctx->steps_taken++;
     return MB_OK;
 }
 
@@ -813,6 +850,8 @@ mb_status capture_graph(mb_ctx* ctx, bool ext, const double* body)
         MB_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     cudaStream_t user = ctx->st;
     const int64_t steps0 = ctx->steps_taken, l0 = ctx->launches;
+    const int hcur0 = ctx->hcur, hlast0 = ctx->hlast;
+    const bool ready0 = ctx->pred_ready;
     ctx->st = ctx->cap_stream;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal);
@@ -824,6 +863,9 @@ mb_status capture_graph(mb_ctx* ctx, bool ext, const double* body)
     ctx->st = user;
     ctx->cur = cur0;
     ctx->steps_taken = steps0;
+    ctx->hcur = hcur0;
+    ctx->hlast = hlast0;
+    ctx->pred_ready = ready0;
     ctx->graph_launches = ctx->launches - l0;
     ctx->launches = l0;
     if (s != MB_OK) {
@@ -845,6 +887,7 @@ mb_status capture_graph(mb_ctx* ctx, bool ext, const double* body)
     }
     ctx->graph_ext[cur0] = ext;
     ctx->graph_body[cur0] = body != nullptr;
+    ctx->graph_hcur[cur0] = hcur0;
     return MB_OK;
 }
 
@@ -853,17 +896,19 @@ mb_status run_fast_steps(mb_ctx* ctx, int n_steps, bool ext, const double* body)
 {
     const bool graphs = ctx->use_graph && !ctx->timing && ctx->nb > 0;
     for (int s = 0; s < n_steps; ++s) {
-        if (!graphs || !ctx->sorted_valid) {          // first step after a rebuild: direct
+        // first step after a rebuild, or after the state was set from outside: direct
+        if (!graphs || !ctx->sorted_valid || (ctx->fuse_interp && !ctx->pred_ready)) {
             MB_TRY(do_step_fast(ctx, ext, body));
+            finish_fast_step(ctx);
             if (!ctx->tuned) MB_TRY(autotune_spread(ctx));
             continue;
         }
         const int c = ctx->cur;
-        if (!ctx->graph_exec[c] || ctx->graph_ext[c] != ext || ctx->graph_body[c] != (body != nullptr))
+        if (!ctx->graph_exec[c] || ctx->graph_ext[c] != ext ||
+            ctx->graph_body[c] != (body != nullptr) || ctx->graph_hcur[c] != ctx->hcur)
             MB_TRY(capture_graph(ctx, ext, body));
         MB_CUDA(cudaGraphLaunch(ctx->graph_exec[c], ctx->st));
-        ctx->cur ^= 1;
-        ctx->steps_taken += 1;
+        finish_fast_step(ctx);
         ctx->launches += ctx->graph_launches;
     }
     return MB_OK;
@@ -950,7 +995,7 @@ void release(mb_ctx* ctx)
                    &ctx->s_F, &ctx->s_rec, &ctx->s_cell_count, &ctx->s_cell_start,
                    &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
                    &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out, &ctx->sA,
-                   &ctx->sB, &ctx->hA, &ctx->hB, &ctx->F32, &ctx->rec32, &ctx->ext32,
+                   &ctx->sB, &ctx->hA[0], &ctx->hA[1], &ctx->hB[0], &ctx->hB[1], &ctx->F32, &ctx->rec32, &ctx->ext32,
                    &ctx->ext_sum, &ctx->adj32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
                    &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk,
                    &ctx->a_vn, &ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvp, &ctx->a_gvn,
@@ -1082,6 +1127,7 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     if (const char* e = std::getenv("MB_FFT_PASSES")) ctx->fft_passes = std::atoi(e) == 5 ? 5 : 3;
     if (const char* e = std::getenv("MB_NO_GRAPH")) ctx->use_graph = std::atoi(e) == 0;
     if (const char* e = std::getenv("MB_NO_AUTOTUNE")) ctx->autotune = std::atoi(e) == 0;
+    if (const char* e = std::getenv("MB_NO_FUSE_INTERP")) ctx->fuse_interp = std::atoi(e) == 0;
     choose_bins(ctx, 0.0);
     pick_tile(ctx);
 
@@ -1228,8 +1274,8 @@ mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos)
     if (ctx->rsz == 4) {
         MB_CUDA(launch_forces_to_fp64(ctx->st, ctx->nb, static_cast<const float4*>(ctx->F32.p),
                                       static_cast<double*>(ctx->F.p)));
-        MB_CUDA(launch_unsplit(ctx->st, ctx->nb, static_cast<const float4*>(ctx->hA.p),
-                               static_cast<const float4*>(ctx->hB.p), ctx->g, ctx->bg,
+        MB_CUDA(launch_unsplit(ctx->st, ctx->nb, static_cast<const float4*>(ctx->hA[ctx->hlast].p),
+                               static_cast<const float4*>(ctx->hB[ctx->hlast].p), ctx->g, ctx->bg,
                                static_cast<double*>(ctx->qh.p)));
     }
     double* outs[2] = {blob_force, midpoint_pos};
@@ -1305,6 +1351,7 @@ mb_status mb_set_positions(mb_ctx* ctx, const double* pos)
         MB_CUDA(launch_split(ctx->st, ctx->nb, q, ctx->g, ctx->bg, static_cast<float4*>(ctx->sA.p),
                              static_cast<float4*>(ctx->sB.p)));
     ctx->sorted_valid = false;
+    ctx->pred_ready = false;
     ctx->steps_taken = 0;
     MB_CUDA(cudaStreamSynchronize(ctx->st));
     return MB_OK;
@@ -1634,6 +1681,7 @@ mb_status mb_set_velocity_field(mb_ctx* ctx, const void* grid_v)
     const void* src;
     MB_TRY(stage_in(ctx, grid_v, by, ctx->staging_in, &src, "grid_v"));
     MB_CUDA(cudaMemcpyAsync(ctx->v[ctx->cur].p, src, by, cudaMemcpyDeviceToDevice, ctx->st));
+    ctx->pred_ready = false;              // the next predictor must see the new field
     if (ctx->rsz == 4)
         MB_CUDA(launch_grid_mean<float>(ctx->st, ctx->B, ctx->g, static_cast<const float*>(ctx->v[ctx->cur].p),
                                         static_cast<double*>(ctx->vbar.p), nullptr));

@@ -158,6 +158,14 @@ cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4*
                             float4* B_out, double* u_out, const int32_t* order = nullptr,
                             int32_t* count = nullptr, int32_t* blob_cell = nullptr,
                             int32_t* blob_rank = nullptr);
+// Corrector of step n and predictor of step n + 1 in one pass (blob counts into `count`,
+// which must be zero).  Mode-2 + mode-1 semantics of launch_interp32.
+cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, const float* v0,
+                                  const float* v1, const int32_t* box_of, const GridGeo& g,
+                                  const BinGeo& bg, float dt, const float4* A_base,
+                                  const float4* B_base, float4* A_out, float4* B_out,
+                                  float4* Ah_out, float4* Bh_out, const int32_t* order,
+                                  int32_t* count, int32_t* blob_cell, int32_t* blob_rank);
 cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int32_t* box_of,
                          int Bx, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
                          int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
