@@ -129,6 +129,19 @@ __global__ void k_unsplit(int64_t nb, const float4* __restrict__ A, const float4
 
 // ------------------------------------------------------------------------------------------
 // Interpolation J from the split positions (mode 0: u only; 1: predictor; 2: corrector).
+// Per-dimension windows for both MAC shifts (0 along the component's own axis, 1/2 across).
+struct Win2 {
+    float w[2][3];
+    int i0[2];
+};
+__device__ __forceinline__ Win2 windows2(int c, int bs, float hi, float inv_h)
+{
+    Win2 r;
+    r.i0[0] = window32(c, bs, hi, inv_h, 0.0f, r.w[0]);
+    r.i0[1] = window32(c, bs, hi, inv_h, 0.5f, r.w[1]);
+    return r;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256)
 k_interp32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ Bl,
@@ -239,48 +252,66 @@ __device__ __forceinline__ void gather32(const int c[3], const float hi[3], cons
     }
 }
 
-// The corrector of step n followed by the predictor of step n + 1, one thread per blob:
+// The corrector of step n followed by the predictor of step n + 1 for the blob at sorted
+// position t:
 //   q^{n+1}   = q^n + dt J(q^{n+1/2}) (v^n + v^{n+1}) / 2       (A_base, B_base -> A_out, B_out)
 //   q^{n+3/2} = q^{n+1} + (dt/2) J(q^{n+1}) v^{n+1}             (-> Ah_out, Bh_out, binned)
-// The second gather reads the nodes the first has just brought into L1.  A/Bl (q^{n+1/2}) and
-// Ah_out/Bh_out may alias, as may A_base/B_base and A_out/B_out: each thread reads its blob's
-// entries before writing them.
-__global__ void __launch_bounds__(256)
-k_interp32_fused(int64_t nb, const float4* A, const float* __restrict__ v0,
-                 const float* __restrict__ v1, const int32_t* __restrict__ box_of, GridGeo g,
-                 BinGeo bg, float dt, const float4* A_base, const float4* B_base, float4* A_out,
-                 float4* B_out, float4* Ah_out, float4* Bh_out, const int32_t* __restrict__ order,
-                 int32_t* __restrict__ count, int32_t* __restrict__ blob_cell,
-                 int32_t* __restrict__ blob_rank)
+// The second gather reads the nodes the first has just brought into L1.  A (q^{n+1/2}) and
+// Ah_out may alias, as may A_base/B_base and A_out/B_out: each thread reads its blob's entries
+// before writing them.
+struct FusedArgs {
+    const float4* A;
+    const float* v0;
+    const float* v1;
+    const int32_t* box_of;
+    float dt;
+    const float4* A_base;
+    const float4* B_base;
+    float4* A_out;
+    float4* B_out;
+    float4* Ah_out;
+    float4* Bh_out;
+    const int32_t* order;
+    int32_t* count;
+    int32_t* blob_cell;
+    int32_t* blob_rank;
+};
+
+__device__ __forceinline__ void fused_blob(int64_t t, const FusedArgs& f, const Geo32& G)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= nb) return;
-    const int64_t b = order ? order[t] : t;
-    const Geo32 G = geo32(g, bg);
-    const int box = box_of ? box_of[b] : 0;
+    const int64_t b = f.order ? f.order[t] : t;
+    const int box = f.box_of ? f.box_of[b] : 0;
     const size_t box_base = (size_t)box * 3 * (size_t)G.N;
     float u[3];
     {
-        const float4 a = A[b];
+        const float4 a = f.A[b];
         const int pk = __float_as_int(a.w);
         const int c[3] = {cell_unpack(pk, 0), cell_unpack(pk, 1), cell_unpack(pk, 2)};
         const float hi[3] = {a.x, a.y, a.z};
-        gather32(c, hi, v0, v1, box_base, G, u);
+        gather32(c, hi, f.v0, f.v1, box_base, G, u);
     }
-    const float4 ab = A_base[b], lb = B_base[b];
+    const float4 ab = f.A_base[b], lb = f.B_base[b];
     int cc[3] = {cell_unpack(__float_as_int(ab.w), 0), cell_unpack(__float_as_int(ab.w), 1),
                  cell_unpack(__float_as_int(ab.w), 2)};
     float h2[3] = {ab.x, ab.y, ab.z}, l2[3] = {lb.x, lb.y, lb.z};
-    for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], dt * (0.5f * u[d]), G.w, G.nc[d]);
-    A_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
-    B_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
-    gather32(cc, h2, v1, nullptr, box_base, G, u);
-    for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], 0.5f * dt * u[d], G.w, G.nc[d]);
-    Ah_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
-    Bh_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
+    for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], f.dt * (0.5f * u[d]), G.w, G.nc[d]);
+    f.A_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
+    f.B_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
+    gather32(cc, h2, f.v1, nullptr, box_base, G, u);
+    for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], 0.5f * f.dt * u[d], G.w, G.nc[d]);
+    f.Ah_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
+    f.Bh_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
     const int cell = (int)(box * G.ncell) + (cc[2] * G.nc[1] + cc[1]) * G.nc[0] + cc[0];
-    blob_cell[b] = cell;
-    blob_rank[b] = atomicAdd(count + cell, 1);
+    f.blob_cell[b] = cell;
+    f.blob_rank[b] = atomicAdd(f.count + cell, 1);
+}
+
+__global__ void __launch_bounds__(256, 4)
+k_interp32_fused(int64_t nb, FusedArgs f, GridGeo g, BinGeo bg)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    fused_blob(t, f, geo32(g, bg));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -512,19 +543,6 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
 
 // ------------------------------------------------------------------------------------------
 // Spreading from the FP32 records.
-// Per-dimension windows for both MAC shifts (0 along the component's own axis, 1/2 across).
-struct Win2 {
-    float w[2][3];
-    int i0[2];
-};
-__device__ __forceinline__ Win2 windows2(int c, int bs, float hi, float inv_h)
-{
-    Win2 r;
-    r.i0[0] = window32(c, bs, hi, inv_h, 0.0f, r.w[0]);
-    r.i0[1] = window32(c, bs, hi, inv_h, 0.5f, r.w[1]);
-    return r;
-}
-
 // Spreading, one block per tile of TX x TY x TZ nodes (whole bin cells).  The block spreads the
 // blobs binned in its cells, each exactly once, into a shared-memory copy of the nodes their
 // windows can reach: x over [T0 - 4, T0 + TX + 4) in 16-byte chunks, y and z over
@@ -749,10 +767,9 @@ cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, 
                                   int32_t* count, int32_t* blob_cell, int32_t* blob_rank)
 {
     if (nb <= 0) return cudaSuccess;
-    k_interp32_fused<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, v0, v1, box_of, g, bg, dt,
-                                                          A_base, B_base, A_out, B_out, Ah_out,
-                                                          Bh_out, order, count, blob_cell,
-                                                          blob_rank);
+    const FusedArgs f{A, v0, v1, box_of, dt, A_base, B_base, A_out, B_out, Ah_out, Bh_out,
+                      order, count, blob_cell, blob_rank};
+    k_interp32_fused<<<blocks_for(nb, 256), 256, 0, st>>>(nb, f, g, bg);
     return cudaGetLastError();
 }
 

@@ -141,6 +141,7 @@ struct mb_ctx {
     int hcur = 0, hlast = 0;
     bool pred_ready = false;
     bool fuse_interp = true;
+
     bool ext_present = false;
     bool sorted_valid = false;     // `sorted` holds a permutation of the current blobs
     // spreading tile picked by timing candidate shapes on the first FP32-grid step
