@@ -332,18 +332,110 @@ __global__ void k_bin_count32(int64_t nb, const float4* __restrict__ A,
     blob_rank[b] = atomicAdd(count + cell, 1);
 }
 
-__global__ void k_bin_scatter32(int64_t nb, const int32_t* __restrict__ blob_cell,
-                                const int32_t* __restrict__ blob_rank,
-                                const int32_t* __restrict__ cell_start,
-                                int32_t* __restrict__ sorted, const float4* __restrict__ A,
-                                const int32_t* __restrict__ pid, float4* __restrict__ loc)
+
+// Counting sort in two launches.  k_bin_scan32: each block scans 4096 cell counts in place
+// (exclusive, block-local) and publishes its total; the last block to finish (atomic ticket
+// after a fence; no block waits for another) scans the block totals into tile offsets, writes
+// the grand total and resets the ticket for the next launch.  k_bin_place32: cell_start =
+// local scan + tile offset for every cell, and every blob's slot from the same two numbers.
+constexpr int BIN_SCAN_THREADS = 1024, BIN_SCAN_LOG = 12;          // 4096 cells per block
+
+__global__ void __launch_bounds__(BIN_SCAN_THREADS)
+k_bin_scan32(int32_t* __restrict__ c, int64_t n, int32_t* __restrict__ tile_off,
+             int32_t* __restrict__ total, unsigned* __restrict__ ticket)
 {
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    const int slot = cell_start[blob_cell[b]] + blob_rank[b];
-    sorted[slot] = (int32_t)b;
-    const float4 a = A[b];
-    loc[slot] = make_float4(a.x, a.y, a.z, __int_as_float(pid[b]));
+    __shared__ int32_t warp_tot[32];
+    __shared__ int32_t block_total;
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x << BIN_SCAN_LOG) + 4 * threadIdx.x;
+    int32_t v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = base + i < n ? c[base + i] : 0;
+    const int32_t s4 = v[0] + v[1] + v[2] + v[3];
+    int32_t x = s4;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    int32_t run = x - s4 + (warp > 0 ? warp_tot[warp - 1] : 0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (base + i < n) c[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == BIN_SCAN_THREADS - 1) block_total = run;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tile_off[blockIdx.x] = block_total;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    int32_t carry = 0;
+    for (int c0 = 0; c0 < (int)gridDim.x; c0 += BIN_SCAN_THREADS) {
+        const int i = c0 + threadIdx.x;
+        const int32_t t = i < (int)gridDim.x ? __ldcg(tile_off + i) : 0;
+        int32_t y0 = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, y0, o);
+            if (lane >= o) y0 += y;
+        }
+        __syncthreads();
+        if (lane == 31) warp_tot[warp] = y0;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t w = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_tot[lane] = w;
+        }
+        __syncthreads();
+        const int32_t excl = carry + y0 - t + (warp > 0 ? warp_tot[warp - 1] : 0);
+        if (i < (int)gridDim.x) tile_off[i] = excl;
+        carry += warp_tot[31];
+    }
+    if (threadIdx.x == 0) {
+        *total = carry;
+        *ticket = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_bin_place32(int64_t nb, int64_t ncells, const int32_t* __restrict__ local,
+              const int32_t* __restrict__ tile_off, int32_t* __restrict__ cell_start,
+              const int32_t* __restrict__ blob_cell, const int32_t* __restrict__ blob_rank,
+              int32_t* __restrict__ sorted, const float4* __restrict__ A,
+              const int32_t* __restrict__ pid, float4* __restrict__ loc)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < ncells) cell_start[i] = local[i] + tile_off[i >> BIN_SCAN_LOG];
+    if (i < nb) {
+        const int cell = blob_cell[i];
+        const int slot = local[cell] + tile_off[cell >> BIN_SCAN_LOG] + blob_rank[i];
+        sorted[slot] = (int32_t)i;
+        const float4 a = A[i];
+        loc[slot] = make_float4(a.x, a.y, a.z, __int_as_float(pid[i]));
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -787,11 +879,16 @@ cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int
             k_bin_count32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, box_of, bg, cell_count,
                                                                blob_cell, blob_rank);
     }
-    e = launch_exclusive_scan(st, cell_count, cell_start, ncells, scan_tmp);
-    if (e != cudaSuccess) return e;
-    if (nb > 0)
-        k_bin_scatter32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, blob_cell, blob_rank,
-                                                             cell_start, sorted, A, pid, loc);
+    // scan_tmp: [ntiles] tile offsets, then the ticket of the last-block scan (zero between
+    // launches)
+    const int ntiles = (int)((ncells + (1 << BIN_SCAN_LOG) - 1) >> BIN_SCAN_LOG);
+    k_bin_scan32<<<ntiles, BIN_SCAN_THREADS, 0, st>>>(cell_count, ncells, scan_tmp,
+                                                      cell_start + ncells,
+                                                      reinterpret_cast<unsigned*>(scan_tmp + ntiles));
+    const int64_t nthr = nb > ncells ? nb : ncells;
+    k_bin_place32<<<blocks_for(nthr, 256), 256, 0, st>>>(nb, ncells, cell_count, scan_tmp,
+                                                         cell_start, blob_cell, blob_rank, sorted,
+                                                         A, pid, loc);
     return cudaGetLastError();
 }
 

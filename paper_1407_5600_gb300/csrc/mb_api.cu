@@ -408,6 +408,8 @@ mb_status rebuild(mb_ctx* ctx)
     MB_TRY(ensure(ctx->sorted, sizeof(int32_t) * nb, E, "sorted"));
     MB_TRY(ensure(ctx->loc, sizeof(float4) * nb, E, "loc"));
     MB_TRY(ensure(ctx->scan_tmp, sizeof(int32_t) * (ncells / 4096 + 2), E, "scan_tmp"));
+    // the FP32 binning keeps a zero ticket after its tile offsets
+    MB_CUDA(cudaMemsetAsync(ctx->scan_tmp.p, 0, sizeof(int32_t) * (ncells / 4096 + 2), ctx->st));
     MB_TRY(ensure(ctx->partial, sizeof(double) * 3 * B * std::max(ctx->nchunk, 1), E, "partial"));
 
     cudaStream_t st = ctx->st;
@@ -710,7 +712,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                              static_cast<int32_t*>(ctx->scan_tmp.p),
                              static_cast<const int32_t*>(ctx->pid.p),
                              static_cast<float4*>(ctx->loc.p), true));
-        ctx->launches += 4;
+        ctx->launches += 2;
         ctx->sorted_valid = true;
     }
     mark(ST_FORCES);
