@@ -936,11 +936,14 @@ cudaError_t launch_spread32_t(cudaStream_t st, int Bx, const float4* rec, const 
 }
 
 cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
-                            const GridGeo& g, const BinGeo& bg, const int tile[3], float* f)
+                            const GridGeo& g, const BinGeo& bg, const int tile[3], float* f,
+                            bool f_is_zero)
 {
     if (!spread32_tile_ok(tile, g, bg)) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(f, 0, sizeof(float) * 3 * (size_t)Bx * g.N, st);
-    if (e != cudaSuccess) return e;
+    if (!f_is_zero) {
+        const cudaError_t e = cudaMemsetAsync(f, 0, sizeof(float) * 3 * (size_t)Bx * g.N, st);
+        if (e != cudaSuccess) return e;
+    }
     const int a = tile[0], b = tile[1], c = tile[2];
     if (a == 32 && b == 8 && c == 8) return launch_spread32_t<32, 8, 8>(st, Bx, rec, cell_start, g, bg, tile, f);
     if (a == 16 && b == 8 && c == 8) return launch_spread32_t<16, 8, 8>(st, Bx, rec, cell_start, g, bg, tile, f);

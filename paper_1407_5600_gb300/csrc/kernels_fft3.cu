@@ -239,6 +239,7 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     const R* pzp = vc + (size_t)((z + 1) & (nz - 1)) * ny * nx;
     const R* pzm = vc + (size_t)((z - 1) & (nz - 1)) * ny * nx;
     const R* pf = fc ? fc + (size_t)z * ny * nx : nullptr;
+    R* pclr = a.f_clear && fc ? a.f_clear + (size_t)bc * g.N + (size_t)z * ny * nx : nullptr;
     // each work unit: 4 consecutive x of the two rows 2p, 2p+1
     const int qx = nx / 4;
     for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
@@ -280,6 +281,11 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
             for (int i = 0; i < 4; ++i) r0[i] += t[i];
             load4(pf + (size_t)y1 * nx + x0, t);
             for (int i = 0; i < 4; ++i) r1[i] += t[i];
+            if (pclr) {                  // leave f zeroed for the next accumulation
+                const R zero[4] = {R(0), R(0), R(0), R(0)};
+                store4(pclr + (size_t)y0 * nx + x0, zero);
+                store4(pclr + (size_t)y1 * nx + x0, zero);
+            }
         }
         if (body) {
             for (int i = 0; i < 4; ++i) {

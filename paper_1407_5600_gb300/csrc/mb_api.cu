@@ -141,6 +141,7 @@ struct mb_ctx {
     int hcur = 0, hlast = 0;
     bool pred_ready = false;
     bool fuse_interp = true;
+    bool f_zero = false;        // ctx->f holds zeros (cleared by the last plane pass)
 
     bool ext_present = false;
     bool sorted_valid = false;     // `sorted` holds a permutation of the current blobs
@@ -153,6 +154,7 @@ struct mb_ctx {
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     bool graph_ext[2] = {false, false}, graph_body[2] = {false, false};
     int graph_hcur[2] = {0, 0};
+    bool graph_fz[2] = {false, false};
     int64_t graph_launches = 0;        // kernels per graph launch
     // adjoint scratch: blob vectors and grids (FP64 contexts)
     DBuf a_qn, a_u, a_qh, a_gq, a_guc, a_gqh, a_gF, a_gu, a_gk;
@@ -660,6 +662,7 @@ void finish_fast_step(mb_ctx* ctx)
     ctx->cur ^= 1;
     ctx->steps_taken++;
     ctx->hlast = ctx->hcur;
+    if (ctx->nb > 0) ctx->f_zero = ctx->fft_passes == 3;     // the plane pass cleared f
     if (ctx->nb > 0 && ctx->fuse_interp) {
         ctx->hcur ^= 1;
         ctx->pred_ready = true;
@@ -742,12 +745,13 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     if (blobs) {
         MB_CUDA(launch_spread32(st, B, static_cast<const float4*>(ctx->rec32.p),
                                 static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
-                                ctx->tile, static_cast<float*>(ctx->f.p)));
+                                ctx->tile, static_cast<float*>(ctx->f.p), ctx->f_zero));
         ctx->launches += 1;
     }
     const double* mean = ctx->d.mean_mode == 0 ? static_cast<const double*>(ctx->vbar.p) : nullptr;
     FluidArgs<float> fa = fluid_args<float>(ctx, vcur, blobs ? ctx->f.p : nullptr, vnext,
                                             ctx->body_prof.p, body, mean);
+    if (blobs && ctx->fft_passes == 3) fa.f_clear = static_cast<float*>(ctx->f.p);
     cudaEvent_t* fm = ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr;
     if (ctx->fft_passes == 5) {
         MB_CUDA(launch_fluid<float>(st, B, g, fa, fm));
@@ -837,6 +841,9 @@ mb_status autotune_spread(mb_ctx* ctx)
     cudaEventDestroy(e1);
     for (int d = 0; d < 3; ++d) ctx->tile[d] = best_t[d];
     ctx->tile_ms = best / 2;
+    // the timing runs left a spread grid in f: clear it for the next step
+    MB_CUDA(cudaMemsetAsync(ctx->f.p, 0, sizeof(float) * 3 * (size_t)ctx->B * ctx->g.N, ctx->st));
+    ctx->f_zero = true;
     std::lock_guard<std::mutex> lock(g_tile_mu);
     g_tile_cache[key] = {best_t[0], best_t[1], best_t[2]};
     return MB_OK;
@@ -891,6 +898,7 @@ mb_status capture_graph(mb_ctx* ctx, bool ext, const double* body)
     ctx->graph_ext[cur0] = ext;
     ctx->graph_body[cur0] = body != nullptr;
     ctx->graph_hcur[cur0] = hcur0;
+    ctx->graph_fz[cur0] = ctx->f_zero;
     return MB_OK;
 }
 
@@ -908,7 +916,8 @@ mb_status run_fast_steps(mb_ctx* ctx, int n_steps, bool ext, const double* body)
         }
         const int c = ctx->cur;
         if (!ctx->graph_exec[c] || ctx->graph_ext[c] != ext ||
-            ctx->graph_body[c] != (body != nullptr) || ctx->graph_hcur[c] != ctx->hcur)
+            ctx->graph_body[c] != (body != nullptr) || ctx->graph_hcur[c] != ctx->hcur ||
+            ctx->graph_fz[c] != ctx->f_zero)
             MB_TRY(capture_graph(ctx, ext, body));
         MB_CUDA(cudaGraphLaunch(ctx->graph_exec[c], ctx->st));
         finish_fast_step(ctx);

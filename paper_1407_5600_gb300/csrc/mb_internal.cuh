@@ -128,6 +128,7 @@ struct FluidArgs {
     const double* mean_override;   // [B][3] mean velocity to impose at k = 0, or null
     int mean_mode;
     double rho_dt, half_eta;
+    R* f_clear;            // three-pass FFT: f, zeroed as it is read (null = leave f alone)
 };
 // marks: null, or 6 events recorded before pass 1 and after each of the 5 passes.
 template <typename R>
@@ -177,12 +178,13 @@ cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t max_box_blobs, cons
                             const double* box_par, const int32_t* cell_start,
                             const int32_t* blob_cell, const float4* ext, float4* F, float4* rec,
                             const GridGeo& g, const BinGeo& bg);
-// f = S F from the binned records (zeroes f first).  The tile (nodes per block) must satisfy
+// f = S F from the binned records (zeroes f first unless the caller knows it is zero).  The tile (nodes per block) must satisfy
 // spread32_tile_ok: at least 4 and whole bin cells per side, dividing the grid, at most 64 rows
 // of cells, shared copy within 200 KiB; other tiles return cudaErrorInvalidValue.
 bool spread32_tile_ok(const int tile[3], const GridGeo& g, const BinGeo& bg);
 cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
-                            const GridGeo& g, const BinGeo& bg, const int tile[3], float* f);
+                            const GridGeo& g, const BinGeo& bg, const int tile[3], float* f,
+                            bool f_is_zero = false);
 // External forces to FP32 plus their per-box FP64 sums (partial: [B][chunks][3] scratch).
 cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t max_box_blobs,
                                const int64_t* box_off, const double* ext, float4* ext32,
