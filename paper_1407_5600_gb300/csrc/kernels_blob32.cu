@@ -483,14 +483,47 @@ __device__ __forceinline__ void spring32(const int cb[3], const float hb[3], con
     for (int d = 0; d < 3; ++d) F[d] += mag * rh[d];
 }
 
+// Spring forces, one thread per blob: the bonds of its adjacency list (entries with the sign
+// bit of j set are owned: the opposite force also goes to blob j).  Fs must be zero on entry;
+// every contribution is added atomically, a blob's own sum once.
+__global__ void __launch_bounds__(256)
+k_springs32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ Bv,
+            const int4* __restrict__ adj, const int32_t* __restrict__ adj_start,
+            const int32_t* __restrict__ box_of, const double* __restrict__ box_par, GridGeo g,
+            BinGeo bg, float* __restrict__ Fs)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int e0 = adj_start[b], e1 = adj_start[b + 1];
+    if (e0 == e1) return;
+    const Geo32 G = geo32(g, bg);
+    const float4 ab = A[b], lbv = Bv[b];
+    const int pk = __float_as_int(ab.w);
+    const int cb[3] = {cell_unpack(pk, 0), cell_unpack(pk, 1), cell_unpack(pk, 2)};
+    const float hb[3] = {ab.x, ab.y, ab.z}, lb[3] = {lbv.x, lbv.y, lbv.z};
+    const float k_spring = (float)box_par[3 * (box_of ? box_of[b] : 0)];
+    float F[3] = {0.f, 0.f, 0.f};
+#pragma unroll 2
+    for (int e = e0; e < e1; ++e) {
+        const int4 ad = adj[e];
+        const int j = ad.x & 0x7fffffff;
+        float f[3] = {0.f, 0.f, 0.f};
+        spring32(cb, hb, lb, A[j], Bv[j], __int_as_float(ad.y), __int_as_float(ad.z),
+                 __int_as_float(ad.w), k_spring, G, f);
+        for (int d = 0; d < 3; ++d) F[d] += f[d];
+        if (ad.x < 0)
+            for (int d = 0; d < 3; ++d) atomicAdd(Fs + 4 * (int64_t)j + d, -f[d]);
+    }
+    for (int d = 0; d < 3; ++d) atomicAdd(Fs + 4 * b + d, F[d]);
+}
+
 struct Force32Args {
     const int64_t* box_off;
     const int32_t* sorted;
     const float4* A;          // split midpoint positions (blob order)
     const float4* B;
     const float4* loc;        // [slot] hi + particle id
-    const int4* adj;          // per adjacency entry: j, r0, r0^2 hi, r0^2 lo (float bits)
-    const int32_t* adj_start;
+    const float4* Fs;         // [nb] spring forces (k_springs32)
     const double* box_par;    // [B][3] k_spring, k_rep, r_cut
     const int32_t* cell_start;
     const int32_t* blob_cell;
@@ -509,10 +542,9 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
     if (local >= cnt) return;
     const int64_t slot = s0 + local;
     const int b = a.sorted[slot];
-    const float4 ab = a.A[b], lbv = a.B[b];
+    const float4 ab = a.A[b];
     const int pk = __float_as_int(ab.w);
     const int cb[3] = {cell_unpack(pk, 0), cell_unpack(pk, 1), cell_unpack(pk, 2)};
-    const float hb[3] = {ab.x, ab.y, ab.z}, lb[3] = {lbv.x, lbv.y, lbv.z};
     float F[3] = {0.f, 0.f, 0.f};
     if (a.ext) {
         const float4 e = a.ext[b];
@@ -520,14 +552,13 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
         F[1] = e.y;
         F[2] = e.z;
     }
-    const float k_spring = (float)a.box_par[3 * box];
     const float k_rep = (float)a.box_par[3 * box + 1];
     const float r_cut = (float)a.box_par[3 * box + 2];
-#pragma unroll 2
-    for (int e = a.adj_start[b]; e < a.adj_start[b + 1]; ++e) {
-        const int4 ad = a.adj[e];
-        spring32(cb, hb, lb, a.A[ad.x], a.B[ad.x], __int_as_float(ad.y), __int_as_float(ad.z),
-                 __int_as_float(ad.w), k_spring, G, F);
+    {
+        const float4 fs = a.Fs[b];
+        F[0] += fs.x;
+        F[1] += fs.y;
+        F[2] += fs.z;
     }
     if (k_rep != 0.0f && r_cut > 0.0f) {
         const float4 me = a.loc[slot];
@@ -892,16 +923,20 @@ cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int
     return cudaGetLastError();
 }
 
-cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t max_box_blobs, const int64_t* box_off,
-                            const int32_t* sorted, const float4* A, const float4* B,
-                            const float4* loc, const int4* adj, const int32_t* adj_start,
+cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t nb, int64_t max_box_blobs,
+                            const int64_t* box_off, const int32_t* sorted, const float4* A,
+                            const float4* B, const float4* loc, const int4* adj,
+                            const int32_t* adj_start, const int32_t* box_of,
                             const double* box_par, const int32_t* cell_start,
-                            const int32_t* blob_cell, const float4* ext, float4* F, float4* rec,
-                            const GridGeo& g, const BinGeo& bg)
+                            const int32_t* blob_cell, const float4* ext, float4* Fs, float4* F,
+                            float4* rec, const GridGeo& g, const BinGeo& bg)
 {
     if (max_box_blobs <= 0) return cudaSuccess;
-    Force32Args a{box_off, sorted, A, B, loc, adj, adj_start, box_par, cell_start, blob_cell,
-                  ext, F, rec};
+    cudaError_t e = cudaMemsetAsync(Fs, 0, sizeof(float4) * nb, st);
+    if (e != cudaSuccess) return e;
+    k_springs32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, B, adj, adj_start, box_of, box_par, g,
+                                                    bg, reinterpret_cast<float*>(Fs));
+    Force32Args a{box_off, sorted, A, B, loc, Fs, box_par, cell_start, blob_cell, ext, F, rec};
     dim3 grid(blocks_for(max_box_blobs, 256), (unsigned)Bx);
     k_forces32<<<grid, 256, 0, st>>>(a, g, bg);
     return cudaGetLastError();

@@ -134,7 +134,7 @@ struct mb_ctx {
         part_blobs, box_off, box_par, cell_count, cell_start, blob_cell, blob_rank, sorted,
         loc, scan_tmp, partial, staging_in, staging_out, mean_scratch;
     // FP32-grid mode blob state: positions as bin cell + float-float offset (q^n and midpoint)
-    DBuf sA, sB, hA[2], hB[2], F32, rec32, ext32, ext_sum, adj32;
+    DBuf sA, sB, hA[2], hB[2], F32, rec32, ext32, ext_sum, adj32, adj32_start, Fs32;
     // split midpoints: hA/hB[hcur] hold the predictor of the next step when pred_ready (the
     // previous step's fused corrector wrote them); hlast is the buffer of the last step's
     // midpoints (where its forces were evaluated)
@@ -440,17 +440,37 @@ mb_status rebuild(mb_ctx* ctx)
         MB_TRY(ensure(ctx->rec32, 2 * sizeof(float4) * nb, E, "rec32"));
         MB_TRY(ensure(ctx->ext32, sizeof(float4) * nb, E, "ext32"));
         MB_TRY(ensure(ctx->ext_sum, sizeof(double) * 3 * B, E, "ext_sum"));
-        MB_TRY(ensure(ctx->adj32, sizeof(int4) * std::max<int64_t>(nadj, 1), E, "adj32"));
-        std::vector<int32_t> a32(4 * nadj);
-        for (int64_t e = 0; e < nadj; ++e) {
-            const double r0 = adj_rest[e], r0sq = r0 * r0;
-            const float h = (float)r0sq, l = (float)(r0sq - (double)h), rf = (float)r0;
-            a32[4 * e] = adj_j[e];
-            std::memcpy(&a32[4 * e + 1], &rf, 4);
-            std::memcpy(&a32[4 * e + 2], &h, 4);
-            std::memcpy(&a32[4 * e + 3], &l, 4);
+        // FP32 springs: a bond with one end of more than SPRING_LOCAL_MAX bonds (an
+        // icosahedron's centre) is evaluated once, by its other end, which also adds the
+        // opposite force to the heavy end; every other bond is evaluated at both ends.  So no
+        // thread of a warp iterates over more than SPRING_LOCAL_MAX + its owned bonds.
+        constexpr int SPRING_LOCAL_MAX = 6;
+        auto heavy = [&](int64_t i) { return adj_start[i + 1] - adj_start[i] > SPRING_LOCAL_MAX; };
+        std::vector<int32_t> s32(nb + 1, 0);
+        std::vector<int32_t> a32;
+        a32.reserve(4 * nadj);
+        for (int64_t i = 0; i < nb; ++i) {
+            for (int32_t e = adj_start[i]; e < adj_start[i + 1]; ++e) {
+                const int64_t j = adj_j[e];
+                const bool hi = heavy(i), hj = heavy(j);
+                if (hi && !hj) continue;                   // j evaluates this bond
+                const bool owned = hj && !hi;              // i adds the force to j as well
+                const double r0 = adj_rest[e], r0sq = r0 * r0;
+                const float h = (float)r0sq, l = (float)(r0sq - (double)h), rf = (float)r0;
+                int32_t w[4];
+                w[0] = (int32_t)((uint32_t)j | (owned ? 0x80000000u : 0u));
+                std::memcpy(&w[1], &rf, 4);
+                std::memcpy(&w[2], &h, 4);
+                std::memcpy(&w[3], &l, 4);
+                a32.insert(a32.end(), w, w + 4);
+            }
+            s32[i + 1] = (int32_t)(a32.size() / 4);
         }
-        MB_TRY(up(ctx->adj32, a32.data(), sizeof(int32_t) * 4 * nadj));
+        MB_TRY(ensure(ctx->adj32, sizeof(int32_t) * std::max<size_t>(a32.size(), 4), E, "adj32"));
+        MB_TRY(ensure(ctx->adj32_start, sizeof(int32_t) * (nb + 1), E, "adj32_start"));
+        MB_TRY(ensure(ctx->Fs32, sizeof(float4) * nb, E, "spring forces"));
+        MB_TRY(up(ctx->adj32, a32.data(), sizeof(int32_t) * a32.size()));
+        MB_TRY(up(ctx->adj32_start, s32.data(), sizeof(int32_t) * (nb + 1)));
         MB_CUDA(launch_split(st, nb, static_cast<const double*>(ctx->q.p), ctx->g, ctx->bg,
                              static_cast<float4*>(ctx->sA.p), static_cast<float4*>(ctx->sB.p)));
         ctx->ext_present = false;
@@ -720,18 +740,19 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     }
     mark(ST_FORCES);
     if (blobs) {
-        MB_CUDA(launch_forces32(st, B, ctx->max_box_blobs, static_cast<const int64_t*>(ctx->box_off.p),
+        MB_CUDA(launch_forces32(st, B, ctx->nb, ctx->max_box_blobs,
+                                static_cast<const int64_t*>(ctx->box_off.p),
                                 static_cast<const int32_t*>(ctx->sorted.p), hA, hB,
                                 static_cast<const float4*>(ctx->loc.p),
                                 static_cast<const int4*>(ctx->adj32.p),
-                                static_cast<const int32_t*>(ctx->adj_start.p),
+                                static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
                                 static_cast<const double*>(ctx->box_par.p),
                                 static_cast<const int32_t*>(ctx->cell_start.p),
                                 static_cast<const int32_t*>(ctx->blob_cell.p),
                                 ext ? static_cast<const float4*>(ctx->ext32.p) : nullptr,
-                                static_cast<float4*>(ctx->F32.p),
+                                static_cast<float4*>(ctx->Fs32.p), static_cast<float4*>(ctx->F32.p),
                                 static_cast<float4*>(ctx->rec32.p), g, ctx->bg));
-        ctx->launches += 1;
+        ctx->launches += 2;
     }
     mark(ST_FORCE_SUM);
     {
@@ -1008,7 +1029,7 @@ void release(mb_ctx* ctx)
                    &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
                    &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out, &ctx->sA,
                    &ctx->sB, &ctx->hA[0], &ctx->hA[1], &ctx->hB[0], &ctx->hB[1], &ctx->F32, &ctx->rec32, &ctx->ext32,
-                   &ctx->ext_sum, &ctx->adj32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
+                   &ctx->ext_sum, &ctx->adj32, &ctx->adj32_start, &ctx->Fs32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
                    &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk,
                    &ctx->a_vn, &ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvp, &ctx->a_gvn,
                    &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero};
