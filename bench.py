@@ -51,8 +51,9 @@ def stage_model(n, nb, rsz, ncell):
         "fluid_y_fwd": ("hbm", 0),                       # no kernel in the three-pass FFT
         "fluid_z_solve": ("hbm", 2 * spec),
         "fluid_y_inv": ("hbm", 0),                       # no kernel in the three-pass FFT
-        "fluid_x_inv": ("hbm", spec + grid),             # read spectrum; write v
-        # read v^n, v^{n+1}, q_half, q; write q^{n+1} and the next q_half
+        # read spectrum and v^n; write v^{n+1} and v^n + v^{n+1} (the corrector's grid)
+        "fluid_x_inv": ("hbm", spec + 3 * grid),
+        # read v^n + v^{n+1}, v^{n+1}, q_half, q; write q^{n+1} and the next q_half
         "interp_correct": ("hbm", 2 * grid + 4 * vec),
     }
 

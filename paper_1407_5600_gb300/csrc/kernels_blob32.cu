@@ -261,8 +261,9 @@ __device__ __forceinline__ void gather32(const int c[3], const float hi[3], cons
 // before writing them.
 struct FusedArgs {
     const float4* A;
-    const float* v0;
+    const float* v0;          // corrector: J of v0 (+ v1 when not null), halved
     const float* v1;
+    const float* vp;          // predictor of the next step: J of vp (= v^{n+1})
     const int32_t* box_of;
     float dt;
     const float4* A_base;
@@ -297,7 +298,7 @@ __device__ __forceinline__ void fused_blob(int64_t t, const FusedArgs& f, const 
     for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], f.dt * (0.5f * u[d]), G.w, G.nc[d]);
     f.A_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
     f.B_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
-    gather32(cc, h2, f.v1, nullptr, box_base, G, u);
+    gather32(cc, h2, f.vp, nullptr, box_base, G, u);
     for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], 0.5f * f.dt * u[d], G.w, G.nc[d]);
     f.Ah_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
     f.Bh_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
@@ -883,14 +884,15 @@ cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4*
 }
 
 cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, const float* v0,
-                                  const float* v1, const int32_t* box_of, const GridGeo& g,
+                                  const float* v1, const float* vp, const int32_t* box_of,
+                                  const GridGeo& g,
                                   const BinGeo& bg, float dt, const float4* A_base,
                                   const float4* B_base, float4* A_out, float4* B_out,
                                   float4* Ah_out, float4* Bh_out, const int32_t* order,
                                   int32_t* count, int32_t* blob_cell, int32_t* blob_rank)
 {
     if (nb <= 0) return cudaSuccess;
-    const FusedArgs f{A, v0, v1, box_of, dt, A_base, B_base, A_out, B_out, Ah_out, Bh_out,
+    const FusedArgs f{A, v0, v1, vp, box_of, dt, A_base, B_base, A_out, B_out, Ah_out, Bh_out,
                       order, count, blob_cell, blob_rank};
     k_interp32_fused<<<blocks_for(nb, 256), 256, 0, st>>>(nb, f, g, bg);
     return cudaGetLastError();

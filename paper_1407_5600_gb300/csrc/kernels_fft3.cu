@@ -552,6 +552,18 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
         }
         store4(out + (size_t)(2 * p) * nx + x0, r0);
         store4(out + (size_t)(2 * p + 1) * nx + x0, r1);
+        if (a.v_sum_out) {               // v^n + v^{n+1} for the corrector's single gather
+            const size_t o0 = (size_t)bc * g.N + (size_t)z * ny * nx + (size_t)(2 * p) * nx + x0;
+            R b0[4], b1[4];
+            load4(a.v_sum_base + o0, b0);
+            load4(a.v_sum_base + o0 + nx, b1);
+            for (int i = 0; i < 4; ++i) {
+                b0[i] += r0[i];
+                b1[i] += r1[i];
+            }
+            store4(a.v_sum_out + o0, b0);
+            store4(a.v_sum_out + o0 + nx, b1);
+        }
     }
 }
 

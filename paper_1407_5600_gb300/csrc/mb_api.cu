@@ -118,7 +118,7 @@ struct mb_ctx {
     int nxh = 0;
     int tile[3] = {8, 8, 8};
 
-    DBuf v[2], f, spec, vbar, fsum, tw[3], twf[3], sym, symr, body_prof, prof_scratch;
+    DBuf v[2], vsum, f, spec, vbar, fsum, tw[3], twf[3], sym, symr, body_prof, prof_scratch;
     int fft_passes = 3;     // 3: plane/z/plane pipeline; 5: one pass per axis (reference layout)
     int cur = 0;
     int64_t steps_taken = 0;
@@ -773,6 +773,11 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     FluidArgs<float> fa = fluid_args<float>(ctx, vcur, blobs ? ctx->f.p : nullptr, vnext,
                                             ctx->body_prof.p, body, mean);
     if (blobs && ctx->fft_passes == 3) fa.f_clear = static_cast<float*>(ctx->f.p);
+    const bool vsum = blobs && ctx->fuse_interp && ctx->fft_passes == 3;
+    if (vsum) {
+        fa.v_sum_base = vcur;
+        fa.v_sum_out = static_cast<float*>(ctx->vsum.p);
+    }
     cudaEvent_t* fm = ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr;
     if (ctx->fft_passes == 5) {
         MB_CUDA(launch_fluid<float>(st, B, g, fa, fm));
@@ -786,7 +791,8 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
             // corrector of this step and predictor of the next (into the other midpoint buffer,
             // with the bin counts the next step sorts by)
             MB_CUDA(cudaMemsetAsync(ctx->cell_count.p, 0, sizeof(int32_t) * B * ctx->bg.ncell, st));
-            MB_CUDA(launch_interp32_fused(st, ctx->nb, hA, vcur, vnext, box_of, g, ctx->bg, dt, sA,
+            MB_CUDA(launch_interp32_fused(st, ctx->nb, hA, vsum ? static_cast<const float*>(ctx->vsum.p) : vcur,
+                                          vsum ? nullptr : vnext, vnext, box_of, g, ctx->bg, dt, sA,
                                           sB, sA, sB,
                                           static_cast<float4*>(ctx->hA[ctx->hcur ^ 1].p),
                                           static_cast<float4*>(ctx->hB[ctx->hcur ^ 1].p),
@@ -1016,7 +1022,7 @@ void release(mb_ctx* ctx)
     drop_graph(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     ctx->cap_stream = nullptr;
-    DBuf* all[] = {&ctx->v[0], &ctx->v[1], &ctx->f, &ctx->spec, &ctx->vbar, &ctx->fsum,
+    DBuf* all[] = {&ctx->v[0], &ctx->v[1], &ctx->vsum, &ctx->f, &ctx->spec, &ctx->vbar, &ctx->fsum,
                    &ctx->tw[0], &ctx->tw[1], &ctx->tw[2], &ctx->twf[0], &ctx->twf[1],
                    &ctx->twf[2], &ctx->sym, &ctx->symr, &ctx->body_prof,
                    &ctx->prof_scratch, &ctx->q, &ctx->qh, &ctx->u, &ctx->F, &ctx->rec,
@@ -1175,6 +1181,7 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     mb_status s;
     if ((s = ensure(ctx->v[0], gb, ctx->err, "v")) != MB_OK) return fail(s);
     if ((s = ensure(ctx->v[1], gb, ctx->err, "v")) != MB_OK) return fail(s);
+    if (ctx->rsz == 4 && (s = ensure(ctx->vsum, gb, ctx->err, "v sum")) != MB_OK) return fail(s);
     if ((s = ensure(ctx->f, gb, ctx->err, "f")) != MB_OK) return fail(s);
     if ((s = ensure(ctx->spec, sb, ctx->err, "spectrum")) != MB_OK) return fail(s);
     if ((s = ensure(ctx->vbar, sizeof(double) * 3 * ctx->B, ctx->err, "vbar")) != MB_OK) return fail(s);

@@ -129,6 +129,8 @@ struct FluidArgs {
     int mean_mode;
     double rho_dt, half_eta;
     R* f_clear;            // three-pass FFT: f, zeroed as it is read (null = leave f alone)
+    const R* v_sum_base;   // three-pass FFT: v^n; with v_sum_out, also write v^n + v^{n+1}
+    R* v_sum_out;
 };
 // marks: null, or 6 events recorded before pass 1 and after each of the 5 passes.
 template <typename R>
@@ -160,9 +162,11 @@ cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4*
                             int32_t* count = nullptr, int32_t* blob_cell = nullptr,
                             int32_t* blob_rank = nullptr);
 // Corrector of step n and predictor of step n + 1 in one pass (blob counts into `count`,
-// which must be zero).  Mode-2 + mode-1 semantics of launch_interp32.
+// which must be zero).  Mode-2 + mode-1 semantics of launch_interp32: the corrector gathers
+// (v0 + v1) / 2 (v1 may be null when v0 already holds v^n + v^{n+1}), the predictor vp.
 cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, const float* v0,
-                                  const float* v1, const int32_t* box_of, const GridGeo& g,
+                                  const float* v1, const float* vp, const int32_t* box_of,
+                                  const GridGeo& g,
                                   const BinGeo& bg, float dt, const float4* A_base,
                                   const float4* B_base, float4* A_out, float4* B_out,
                                   float4* Ah_out, float4* Bh_out, const int32_t* order,
