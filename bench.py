@@ -285,7 +285,8 @@ def run_ours(args):
     ncell = (n // 2) ** 3
     model = stage_model(n, nb, 4, ncell)
     per_stage = {k: {"ms_per_step": v[0] / max(v[1], 1)} for k, v in stages.items()}
-    single_kernel = [k for k in per_stage if model[k][1] > 0 and k != "bin"]
+    # stages that are one kernel (binning and forces are two each)
+    single_kernel = [k for k in per_stage if model[k][1] > 0 and k not in ("bin", "forces")]
     dom = max(single_kernel, key=lambda k: per_stage[k]["ms_per_step"])
     peak, peak_kind = peaks()
     for k, d in per_stage.items():
