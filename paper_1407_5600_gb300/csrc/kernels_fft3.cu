@@ -179,6 +179,18 @@ __host__ __device__ __forceinline__ int pad_shift(int n)
 }
 __host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> pad_shift(n)); }
 
+// Asynchronous global-to-shared copy of one complex value (no register staging, so every copy
+// of a thread is in flight at once), and the wait for all of a thread's copies.
+template <typename T> __device__ __forceinline__ void async_copy(T* dst, const T* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T> __device__ __forceinline__ void load_table(T* dst, const T* src, int n)
 {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
@@ -394,11 +406,11 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     T* base = a.spec + (size_t)(box * 3) * cstride + (size_t)kx * ny + ky0;
     auto at = [=](int c, int z, int k) { return (c * nzp + z + (z >> sz)) * Cp + k; };
     const int total = 3 * nz * C;
-#pragma unroll 8
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {      // 8 loads in flight per thread
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
         const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
-        Bf[at(c, z, k)] = base[c * cstride + (size_t)z * zstride + k];
+        async_copy(&Bf[at(c, z, k)], &base[c * cstride + (size_t)z * zstride + k]);
     }
+    async_wait_all();
     __syncthreads();
     auto idx = [=](int l, int z) { return at(l / C, z, l % C); };
     lines_fft_n<false>(nz, Bf, 3 * C, idx, twz);
@@ -473,8 +485,8 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
         return (y >> 1) * S + j + (j >> sx);
     };
     const int ly = 31 - __clz(ny);
-#pragma unroll 8
-    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) P[col(i >> ly, i & (ny - 1))] = in[i];
+    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) async_copy(&P[col(i >> ly, i & (ny - 1))], &in[i]);
+    async_wait_all();
     __syncthreads();
     // columns k = 0 and k = nx/2 invert to real sequences: transform their Hermitian parts as
     // one complex column Z = herm(A) + i herm(B), whose inverse is Re(IFFT A) + i Re(IFFT B)
