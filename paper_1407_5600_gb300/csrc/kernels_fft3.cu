@@ -432,8 +432,16 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
         }
         if (kx == 0 && ky == 0 && kz == 0) {
             for (int c = 0; c < 3; ++c) {
-                if (a.mean_override) W[c] = T{R((double)g.N * a.mean_override[3 * box + c]), R(0)};
-                else if (a.mean_mode == 1) W[c] = T{R(0), R(0)};
+                if (a.mean_state) {              // the only thread of this box at k = 0
+                    double m = a.mean_state[3 * box + c];
+                    if (a.mean_force) m += a.mean_scale * a.mean_force[3 * box + c];
+                    a.mean_state[3 * box + c] = m;
+                    W[c] = T{R((double)g.N * m), R(0)};
+                } else if (a.mean_override) {
+                    W[c] = T{R((double)g.N * a.mean_override[3 * box + c]), R(0)};
+                } else if (a.mean_mode == 1) {
+                    W[c] = T{R(0), R(0)};
+                }
             }
         } else {
             // D_a = (e^{i th} - 1)/h, G_a = (1 - e^{-i th})/h, D.G = -lambda:

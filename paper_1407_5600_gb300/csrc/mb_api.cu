@@ -754,14 +754,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                                 static_cast<float4*>(ctx->rec32.p), g, ctx->bg));
         ctx->launches += 2;
     }
-    mark(ST_FORCE_SUM);
-    {
-        const double L3 = g.L[0] * g.L[1] * g.L[2];
-        MB_CUDA(launch_vbar_step(st, B, ext ? static_cast<const double*>(ctx->ext_sum.p) : nullptr,
-                                 ctx->d.dt / (ctx->d.rho * L3), ctx->d.mean_mode,
-                                 static_cast<double*>(ctx->vbar.p)));
-        ctx->launches += 1;
-    }
+    mark(ST_FORCE_SUM);                 // the mean momentum advances inside the z pass
     mark(ST_SPREAD);
     if (blobs) {
         MB_CUDA(launch_spread32(st, B, static_cast<const float4*>(ctx->rec32.p),
@@ -769,9 +762,22 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                                 ctx->tile, static_cast<float*>(ctx->f.p), ctx->f_zero));
         ctx->launches += 1;
     }
-    const double* mean = ctx->d.mean_mode == 0 ? static_cast<const double*>(ctx->vbar.p) : nullptr;
     FluidArgs<float> fa = fluid_args<float>(ctx, vcur, blobs ? ctx->f.p : nullptr, vnext,
-                                            ctx->body_prof.p, body, mean);
+                                            ctx->body_prof.p, body, nullptr);
+    if (ctx->d.mean_mode == 0) {
+        const double L3 = g.L[0] * g.L[1] * g.L[2];
+        if (ctx->fft_passes == 3) {
+            fa.mean_state = static_cast<double*>(ctx->vbar.p);
+            fa.mean_force = ext ? static_cast<const double*>(ctx->ext_sum.p) : nullptr;
+            fa.mean_scale = ctx->d.dt / (ctx->d.rho * L3);
+        } else {
+            MB_CUDA(launch_vbar_step(st, B, ext ? static_cast<const double*>(ctx->ext_sum.p) : nullptr,
+                                     ctx->d.dt / (ctx->d.rho * L3), 0,
+                                     static_cast<double*>(ctx->vbar.p)));
+            ctx->launches += 1;
+            fa.mean_override = static_cast<const double*>(ctx->vbar.p);
+        }
+    }
     if (blobs && ctx->fft_passes == 3) fa.f_clear = static_cast<float*>(ctx->f.p);
     const bool vsum = blobs && ctx->fuse_interp && ctx->fft_passes == 3;
     if (vsum) {

@@ -131,6 +131,11 @@ struct FluidArgs {
     R* f_clear;            // three-pass FFT: f, zeroed as it is read (null = leave f alone)
     const R* v_sum_base;   // three-pass FFT: v^n; with v_sum_out, also write v^n + v^{n+1}
     R* v_sum_out;
+    // three-pass FFT, mean_mode 0: the FP64 mean velocity [B][3], advanced in place by the
+    // k = 0 thread (mean_state += mean_scale * mean_force, force optional) and imposed at k = 0
+    double* mean_state;
+    const double* mean_force;
+    double mean_scale;
 };
 // marks: null, or 6 events recorded before pass 1 and after each of the 5 passes.
 template <typename R>
