@@ -276,6 +276,7 @@ struct FusedArgs {
     int32_t* count;
     int32_t* blob_cell;
     int32_t* blob_rank;
+    float4* u_out;            // J(q^{n+1}) v^{n+1}: the blob velocities of the new state
 };
 
 __device__ __forceinline__ void fused_blob(int64_t t, const FusedArgs& f, const Geo32& G)
@@ -299,6 +300,7 @@ __device__ __forceinline__ void fused_blob(int64_t t, const FusedArgs& f, const 
     f.A_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
     f.B_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
     gather32(cc, h2, f.vp, nullptr, box_base, G, u);
+    f.u_out[b] = make_float4(u[0], u[1], u[2], 0.0f);
     for (int d = 0; d < 3; ++d) ff_move(cc[d], h2[d], l2[d], 0.5f * f.dt * u[d], G.w, G.nc[d]);
     f.Ah_out[b] = make_float4(h2[0], h2[1], h2[2], __int_as_float(cell_pack(cc[0], cc[1], cc[2])));
     f.Bh_out[b] = make_float4(l2[0], l2[1], l2[2], 0.0f);
@@ -793,9 +795,11 @@ k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_star
 // reduced in a fixed order afterwards.
 __global__ void __launch_bounds__(256)
 k_ext_prepare(const int64_t* __restrict__ box_off, const double* __restrict__ ext,
-              float4* __restrict__ e32, int nchunk, double* __restrict__ partial)
+              float4* __restrict__ e32, int nchunk, double* __restrict__ partial,
+              double* __restrict__ ext_sum, unsigned* __restrict__ ticket)
 {
-    __shared__ double sh[3][8];
+    __shared__ double sh[3][256];
+    __shared__ bool last;
     const int box = blockIdx.y;
     const int64_t s0 = box_off[box], cnt = box_off[box + 1] - s0;
     const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -817,6 +821,31 @@ k_ext_prepare(const int64_t* __restrict__ box_off, const double* __restrict__ ex
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
         partial[((int64_t)box * nchunk + blockIdx.x) * 3 + threadIdx.x] = t;
     }
+    // the last block to finish (atomic ticket after a fence; no block waits) sums the partials
+    // of every box in a fixed order and resets the ticket
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int bx = 0; bx < (int)gridDim.y; ++bx) {
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int c = threadIdx.x; c < nchunk; c += blockDim.x)
+            for (int d = 0; d < 3; ++d) t[d] += __ldcg(partial + ((int64_t)bx * nchunk + c) * 3 + d);
+        for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] = t[d];
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w)
+                for (int d = 0; d < 3; ++d) sh[d][threadIdx.x] += sh[d][threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x < 3) ext_sum[3 * bx + threadIdx.x] = sh[threadIdx.x][0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // vbar += scale * sum (mean_mode 0) or 0 (mean_mode 1), per box and component.
@@ -889,11 +918,12 @@ cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, 
                                   const BinGeo& bg, float dt, const float4* A_base,
                                   const float4* B_base, float4* A_out, float4* B_out,
                                   float4* Ah_out, float4* Bh_out, const int32_t* order,
-                                  int32_t* count, int32_t* blob_cell, int32_t* blob_rank)
+                                  int32_t* count, int32_t* blob_cell, int32_t* blob_rank,
+                                  float4* u_out)
 {
     if (nb <= 0) return cudaSuccess;
     const FusedArgs f{A, v0, v1, vp, box_of, dt, A_base, B_base, A_out, B_out, Ah_out, Bh_out,
-                      order, count, blob_cell, blob_rank};
+                      order, count, blob_cell, blob_rank, u_out};
     k_interp32_fused<<<blocks_for(nb, 256), 256, 0, st>>>(nb, f, g, bg);
     return cudaGetLastError();
 }
@@ -992,15 +1022,14 @@ cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const in
 
 cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t max_box_blobs,
                                const int64_t* box_off, const double* ext, float4* ext32,
-                               double* partial, double* ext_sum)
+                               double* partial, double* ext_sum, unsigned* ticket)
 {
     const int nchunk = (int)((max_box_blobs + 255) / 256);
     if (nchunk <= 0) return cudaMemsetAsync(ext_sum, 0, sizeof(double) * 3 * Bx, st);
     k_ext_prepare<<<dim3((unsigned)nchunk, (unsigned)Bx), 256, 0, st>>>(box_off, ext, ext32,
-                                                                        nchunk, partial);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_force_sum(st, Bx, nchunk, partial, nullptr, 0.0, 0, ext_sum);
+                                                                        nchunk, partial, ext_sum,
+                                                                        ticket);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_vbar_step(cudaStream_t st, int Bx, const double* sum, double scale,

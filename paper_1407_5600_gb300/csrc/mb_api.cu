@@ -134,7 +134,7 @@ struct mb_ctx {
         part_blobs, box_off, box_par, cell_count, cell_start, blob_cell, blob_rank, sorted,
         loc, scan_tmp, partial, staging_in, staging_out, mean_scratch;
     // FP32-grid mode blob state: positions as bin cell + float-float offset (q^n and midpoint)
-    DBuf sA, sB, hA[2], hB[2], F32, rec32, ext32, ext_sum, adj32, adj32_start, Fs32;
+    DBuf sA, sB, hA[2], hB[2], F32, rec32, ext32, ext_sum, ext_ticket, adj32, adj32_start, Fs32, u32;
     // split midpoints: hA/hB[hcur] hold the predictor of the next step when pred_ready (the
     // previous step's fused corrector wrote them); hlast is the buffer of the last step's
     // midpoints (where its forces were evaluated)
@@ -440,6 +440,8 @@ mb_status rebuild(mb_ctx* ctx)
         MB_TRY(ensure(ctx->rec32, 2 * sizeof(float4) * nb, E, "rec32"));
         MB_TRY(ensure(ctx->ext32, sizeof(float4) * nb, E, "ext32"));
         MB_TRY(ensure(ctx->ext_sum, sizeof(double) * 3 * B, E, "ext_sum"));
+        MB_TRY(ensure(ctx->ext_ticket, sizeof(unsigned), E, "ext ticket"));
+        MB_CUDA(cudaMemsetAsync(ctx->ext_ticket.p, 0, sizeof(unsigned), ctx->st));
         // FP32 springs: a bond with one end of more than SPRING_LOCAL_MAX bonds (an
         // icosahedron's centre) is evaluated once, by its other end, which also adds the
         // opposite force to the heavy end; every other bond is evaluated at both ends.  So no
@@ -469,6 +471,7 @@ mb_status rebuild(mb_ctx* ctx)
         MB_TRY(ensure(ctx->adj32, sizeof(int32_t) * std::max<size_t>(a32.size(), 4), E, "adj32"));
         MB_TRY(ensure(ctx->adj32_start, sizeof(int32_t) * (nb + 1), E, "adj32_start"));
         MB_TRY(ensure(ctx->Fs32, sizeof(float4) * nb, E, "spring forces"));
+        MB_TRY(ensure(ctx->u32, sizeof(float4) * nb, E, "blob velocities"));
         MB_TRY(up(ctx->adj32, a32.data(), sizeof(int32_t) * a32.size()));
         MB_TRY(up(ctx->adj32_start, s32.data(), sizeof(int32_t) * (nb + 1)));
         MB_CUDA(launch_split(st, nb, static_cast<const double*>(ctx->q.p), ctx->g, ctx->bg,
@@ -805,7 +808,8 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                                           static_cast<const int32_t*>(ctx->sorted.p),
                                           static_cast<int32_t*>(ctx->cell_count.p),
                                           static_cast<int32_t*>(ctx->blob_cell.p),
-                                          static_cast<int32_t*>(ctx->blob_rank.p)));
+                                          static_cast<int32_t*>(ctx->blob_rank.p),
+                                          static_cast<float4*>(ctx->u32.p)));
         } else {
             MB_CUDA(launch_interp32(st, 2, ctx->nb, hA, hB, vcur, vnext, box_of, g, ctx->bg, dt,
                                     sA, sB, sA, sB, nullptr,
@@ -1041,7 +1045,7 @@ void release(mb_ctx* ctx)
                    &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
                    &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out, &ctx->sA,
                    &ctx->sB, &ctx->hA[0], &ctx->hA[1], &ctx->hB[0], &ctx->hB[1], &ctx->F32, &ctx->rec32, &ctx->ext32,
-                   &ctx->ext_sum, &ctx->adj32, &ctx->adj32_start, &ctx->Fs32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
+                   &ctx->ext_sum, &ctx->ext_ticket, &ctx->adj32, &ctx->adj32_start, &ctx->Fs32, &ctx->u32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
                    &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk,
                    &ctx->a_vn, &ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvp, &ctx->a_gvn,
                    &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero};
@@ -1291,16 +1295,22 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
     if (ext_blob_force && ctx->nb > 0) {
         const void* src = nullptr;
         MB_TRY(stage_in(ctx, ext_blob_force, sizeof(double) * 3 * ctx->nb, ctx->ext, &src, "ext"));
-        if (src != ctx->ext.p)
-            MB_CUDA(cudaMemcpyAsync(ctx->ext.p, src, sizeof(double) * 3 * ctx->nb,
-                                    cudaMemcpyDeviceToDevice, ctx->st));
-        ext = static_cast<const double*>(ctx->ext.p);
-        if (ctx->rsz == 4)
+        if (ctx->rsz == 4) {
+            // converted once into the library's FP32 copy (the steps never read `src`)
             MB_CUDA(launch_ext_prepare(ctx->st, ctx->B, ctx->max_box_blobs,
-                                       static_cast<const int64_t*>(ctx->box_off.p), ext,
+                                       static_cast<const int64_t*>(ctx->box_off.p),
+                                       static_cast<const double*>(src),
                                        static_cast<float4*>(ctx->ext32.p),
                                        static_cast<double*>(ctx->partial.p),
-                                       static_cast<double*>(ctx->ext_sum.p)));
+                                       static_cast<double*>(ctx->ext_sum.p),
+                                       static_cast<unsigned*>(ctx->ext_ticket.p)));
+            ext = static_cast<const double*>(ctx->ext.p);   // marks forces present
+        } else {
+            if (src != ctx->ext.p)
+                MB_CUDA(cudaMemcpyAsync(ctx->ext.p, src, sizeof(double) * 3 * ctx->nb,
+                                        cudaMemcpyDeviceToDevice, ctx->st));
+            ext = static_cast<const double*>(ctx->ext.p);
+        }
     }
     if (ctx->rsz == 4) return run_fast_steps(ctx, n_steps, ext != nullptr, body_force);
     for (int s = 0; s < n_steps; ++s) MB_TRY(do_step<double>(ctx, ext, body_force));
@@ -1632,7 +1642,10 @@ mb_status mb_get_counts(const mb_ctx* ctx, int64_t* total_blobs, int64_t* total_
 static mb_status blob_velocities(mb_ctx* ctx)
 {
     if (ctx->nb == 0) return MB_OK;
-    if (ctx->rsz == 4)
+    if (ctx->rsz == 4 && ctx->pred_ready)      // the last step's fused pass gathered them
+        MB_CUDA(launch_forces_to_fp64(ctx->st, ctx->nb, static_cast<const float4*>(ctx->u32.p),
+                                      static_cast<double*>(ctx->u.p)));
+    else if (ctx->rsz == 4)
         MB_CUDA(launch_interp32(ctx->st, 0, ctx->nb, static_cast<const float4*>(ctx->sA.p),
                                 static_cast<const float4*>(ctx->sB.p),
                                 static_cast<const float*>(ctx->v[ctx->cur].p), nullptr,
@@ -1654,13 +1667,19 @@ mb_status mb_get_velocities(mb_ctx* ctx, double* blob_vel, double* blob_pos, dou
     DeviceGuard dg(ctx->device);
     MB_TRY(ensure_ready(ctx));
     if (blob_pos || particle_U) MB_TRY(current_positions(ctx));
-    if (blob_vel || particle_U) MB_TRY(blob_velocities(ctx));
+    // FP32 grid after a fused step: the velocities were gathered by that step's last pass
+    const bool gathered = ctx->rsz == 4 && ctx->pred_ready;
+    if (particle_U || (blob_vel && !gathered)) MB_TRY(blob_velocities(ctx));
     if (blob_vel && ctx->nb > 0) {
         void* dst;
         bool host;
         const size_t by = sizeof(double) * 3 * ctx->nb;
         MB_TRY(out_target(ctx, blob_vel, by, ctx->staging_out, &dst, &host, "blob_vel"));
-        MB_CUDA(cudaMemcpyAsync(dst, ctx->u.p, by, cudaMemcpyDeviceToDevice, ctx->st));
+        if (gathered)
+            MB_CUDA(launch_forces_to_fp64(ctx->st, ctx->nb, static_cast<const float4*>(ctx->u32.p),
+                                          static_cast<double*>(dst)));
+        else
+            MB_CUDA(cudaMemcpyAsync(dst, ctx->u.p, by, cudaMemcpyDeviceToDevice, ctx->st));
         MB_TRY(finish_out(ctx, blob_vel, dst, by, host));
     }
     if (blob_pos && ctx->nb > 0) {

@@ -168,14 +168,16 @@ cudaError_t launch_interp32(cudaStream_t st, int mode, int64_t nb, const float4*
                             int32_t* blob_rank = nullptr);
 // Corrector of step n and predictor of step n + 1 in one pass (blob counts into `count`,
 // which must be zero).  Mode-2 + mode-1 semantics of launch_interp32: the corrector gathers
-// (v0 + v1) / 2 (v1 may be null when v0 already holds v^n + v^{n+1}), the predictor vp.
+// (v0 + v1) / 2 (v1 may be null when v0 already holds v^n + v^{n+1}), the predictor vp; the
+// predictor's velocities (those of the new state) go to u_out.
 cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, const float* v0,
                                   const float* v1, const float* vp, const int32_t* box_of,
                                   const GridGeo& g,
                                   const BinGeo& bg, float dt, const float4* A_base,
                                   const float4* B_base, float4* A_out, float4* B_out,
                                   float4* Ah_out, float4* Bh_out, const int32_t* order,
-                                  int32_t* count, int32_t* blob_cell, int32_t* blob_rank);
+                                  int32_t* count, int32_t* blob_cell, int32_t* blob_rank,
+                                  float4* u_out);
 cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int32_t* box_of,
                          int Bx, const BinGeo& bg, int32_t* cell_count, int32_t* cell_start,
                          int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
@@ -195,10 +197,11 @@ bool spread32_tile_ok(const int tile[3], const GridGeo& g, const BinGeo& bg);
 cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
                             const GridGeo& g, const BinGeo& bg, const int tile[3], float* f,
                             bool f_is_zero = false);
-// External forces to FP32 plus their per-box FP64 sums (partial: [B][chunks][3] scratch).
+// External forces to FP32 plus their per-box FP64 sums (partial: [B][chunks][3] scratch;
+// ticket: one zeroed unsigned, left zero), in one launch.
 cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t max_box_blobs,
                                const int64_t* box_off, const double* ext, float4* ext32,
-                               double* partial, double* ext_sum);
+                               double* partial, double* ext_sum, unsigned* ticket);
 cudaError_t launch_vbar_step(cudaStream_t st, int Bx, const double* sum, double scale,
                              int mean_mode, double* vbar);
 cudaError_t launch_forces_to_fp64(cudaStream_t st, int64_t nb, const float4* F, double* out);
