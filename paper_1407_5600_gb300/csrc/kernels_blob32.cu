@@ -802,13 +802,22 @@ k_ext_prepare(const int64_t* __restrict__ box_off, const double* __restrict__ ex
     __shared__ bool last;
     const int box = blockIdx.y;
     const int64_t s0 = box_off[box], cnt = box_off[box + 1] - s0;
-    const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x;       // first blob of the chunk
+    const int64_t local = first + threadIdx.x;
+    // the chunk's 3 x 256 doubles read contiguously (the source may be host memory read over
+    // the interconnect), then regrouped per blob through shared memory
+    const int64_t nval = 3 * (cnt - first < (int64_t)blockDim.x ? cnt - first : (int64_t)blockDim.x);
+    for (int k = 0; k < 3; ++k) {
+        const int e = k * (int)blockDim.x + (int)threadIdx.x;
+        (&sh[0][0])[e] = e < nval ? ext[3 * (s0 + first) + e] : 0.0;
+    }
+    __syncthreads();
     double v[3] = {0.0, 0.0, 0.0};
     if (local < cnt) {
-        const int64_t b = s0 + local;
-        for (int d = 0; d < 3; ++d) v[d] = ext[3 * b + d];
-        e32[b] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+        for (int d = 0; d < 3; ++d) v[d] = (&sh[0][0])[3 * threadIdx.x + d];
+        e32[s0 + local] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
     }
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = 0; d < 3; ++d) {
         double x = v[d];

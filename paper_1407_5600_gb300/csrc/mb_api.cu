@@ -95,6 +95,19 @@ bool is_device_ptr(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory (readable and writable by kernels over the
+// interconnect), or null for any other pointer.
+void* mapped_host_ptr(const void* p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 struct BoxData {
     bool set = false;
     std::vector<double> pos;
@@ -1294,7 +1307,11 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
     const double* ext = nullptr;
     if (ext_blob_force && ctx->nb > 0) {
         const void* src = nullptr;
-        MB_TRY(stage_in(ctx, ext_blob_force, sizeof(double) * 3 * ctx->nb, ctx->ext, &src, "ext"));
+        void* mapped = ctx->rsz == 4 ? mapped_host_ptr(ext_blob_force) : nullptr;
+        if (mapped)
+            src = mapped;         // page-locked host forces: the kernel reads them directly
+        else
+            MB_TRY(stage_in(ctx, ext_blob_force, sizeof(double) * 3 * ctx->nb, ctx->ext, &src, "ext"));
         if (ctx->rsz == 4) {
             // converted once into the library's FP32 copy (the steps never read `src`)
             MB_CUDA(launch_ext_prepare(ctx->st, ctx->B, ctx->max_box_blobs,
