@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 GRID_N = 128
 METRIC = "fluid cell-steps/s at 128^3 (FP32 grid); blob-steps/s and FP64 beside it"
 WORKLOAD = "dense suspension 128^3, a=2.2h, phi=0.40, 18808 particles x 13 blobs"
+DENSE128_BLOBS, DENSE128_PARTICLES = 244504, 18808      # the recipe's counts at seed 3
 
 # Algorithmic bytes moved by each stage per step, per unit (documented in the design doc):
 #   grid real = 4 B (FP32) / 8 B (FP64); half-spectrum complex = 2 reals; blob FP64 vec = 24 B.
@@ -56,6 +57,33 @@ def stage_model(n, nb, rsz, ncell):
         # read v^n + v^{n+1}, v^{n+1}, q_half, q; write q^{n+1} and the next q_half
         "interp_correct": ("hbm", 2 * grid + 4 * vec),
     }
+
+
+def base_config(nb=DENSE128_BLOBS, npart=DENSE128_PARTICLES, world=1):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": WORKLOAD, "grid": "128^3 MAC, h=rho=eta=1, dt=0.05",
+            "blobs": nb, "particles": npart, "precision":
+            "FP32 grid/spread/interp/FFT; FP64 positions, forces, mean mode",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "flushed between timed steps (256 MiB write outside the events)"}
+
+
+def reduce_max(x, dist=None, device=None):
+    """The largest of the ranks' values (x itself without a process group).  NCCL groups
+    reduce on the rank's GPU, gloo groups on the host."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    on = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=on)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, steps, world, ms_max):
+    """Whole-job throughput: every rank processes `units_per_rank` per step; the job takes the
+    slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max * 1e-3)
 
 
 def measured_traffic(stage):
@@ -89,6 +117,8 @@ def parse():
                     help="timed steps of the FP64 grid variant (default: min(steps, 10))")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--stage-json", default=None, help="also write per-stage times here")
+    ap.add_argument("--ref-seconds", type=float, default=None,
+                    help="CPU seconds of the reference arm's oracle sample (default 3 s a step)")
     return ap.parse_args()
 
 
@@ -185,7 +215,8 @@ def run_reference(args):
         return
     if args.warmup:
         oracle_sample(max_seconds=1.0, min_steps=1)
-    cps, bps, steps, el, nblobs = oracle_sample(max_seconds=max(10.0, 3.0 * args.steps),
+    budget = args.ref_seconds if args.ref_seconds else max(10.0, 3.0 * args.steps)
+    cps, bps, steps, el, nblobs = oracle_sample(max_seconds=budget,
                                                 min_steps=max(1, args.steps // 10))
     sample = (f"{steps} oracle steps of the same suspension recipe in a 64^3 box "
               f"({nblobs} blobs), {el:.1f} s")
@@ -193,7 +224,7 @@ def run_reference(args):
             "n_gpus": 0, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "64^3 box of the same recipe"},
+            "config": dict(base_config(), sample="64^3 box of the same recipe"),
             "blob_steps_per_s": bps,
             "cpu_baseline": {"value": cps, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
@@ -259,11 +290,7 @@ def run_ours(args):
         return ms, launches, stages
 
     def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, dev)
 
     # ---- FP32 grid (the headline): each step replays the library's captured CUDA graph ----
     sim = make(0)
@@ -276,8 +303,8 @@ def run_ours(args):
     tile, tile_ms = mb.get_tuning(sim.ctx)
     ms = max_over_ranks(ms)
     ms_step = ms / args.steps
-    value = world * cells * args.steps / (ms * 1e-3)
-    blob_value = world * nb * args.steps / (ms * 1e-3)
+    value = job_rate(cells, args.steps, world, ms)
+    blob_value = job_rate(nb, args.steps, world, ms)
     # ---- the same steps with per-stage CUDA events (direct launches) for the roofline -----
     ms_staged, _, stages = timed_steps(sim, args.steps, True)
 
@@ -360,12 +387,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "128^3 MAC, h=rho=eta=1, dt=0.05",
-                       "blobs": nb, "particles": s.n_particles, "precision":
-                       "FP32 grid/spread/interp/FFT; FP64 positions, forces, mean mode",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "flushed between timed steps (256 MiB write outside the events)",
-                       "spread_tile": list(tile)},
+            "config": dict(base_config(nb, s.n_particles, world), spread_tile=list(tile)),
             "blob_steps_per_s": blob_value,
             "step_hbm_frac": step_frac,
             "ms_per_step_stage_timed": ms_staged / args.steps,

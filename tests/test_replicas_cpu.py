@@ -1,0 +1,77 @@
+"""Replica runs across ranks (bench.py under torchrun): the job time is the slowest rank's and
+the throughput counts every rank's units.  Two gloo ranks on the host, no GPU."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        local_ms = [12.5, 20.0][rank]
+        ms = bench.reduce_max(local_ms, dist)
+        out[rank] = (ms, bench.job_rate(128 ** 3, 20, world, ms))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    world, port = 2, _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    for rank in range(world):
+        ms, rate = res[rank]
+        assert ms == 20.0
+        assert rate == pytest.approx(2 * 128 ** 3 * 20 / 20e-3)
+
+
+def test_single_process_is_its_own_maximum():
+    import bench
+    assert bench.reduce_max(3.5) == 3.5
+    assert bench.job_rate(10, 4, 1, 2.0) == pytest.approx(20000.0)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    """Under torchrun only rank 0 runs the reference arm; the others exit 0 and print nothing."""
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=os.path.dirname(os.path.dirname(__file__)) or ".",
+                       env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
+
+
+def test_reference_arm_line_on_rank_zero():
+    """Rank 0 prints one JSON line with the oracle's throughput and the shared workload."""
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--ref-seconds", "1"],
+                       cwd=os.path.dirname(os.path.dirname(__file__)) or ".", env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["workload"].startswith("dense suspension 128^3")
