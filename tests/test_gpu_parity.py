@@ -88,6 +88,7 @@ def _projected_field(shape, seed, scale=1.0):
     ((16, 16, 16), 1.0, 0, None), ((8, 16, 32), 0.5, 1, None),
     ((32, 32, 32), 1.0, 0, (1e-2, 0, 2, 1)), ((16, 8, 64), 1.3, 1, (0.3, 1, 0, 3)),
     ((4, 8, 4), 2.0, 0, (1.0, 2, 1, 1)),
+    ((8, 16, 128), 0.8, 0, (1e-2, 1, 0, 2)), ((4, 64, 128), 1.0, 1, (0.5, 0, 1, 1)),
 ])
 def test_fluid_update_parity(prec, shape, h, mean_mode, body):
     d = _desc(shape, prec, h=h, rho=1.3, eta=0.7, dt=0.05, mean_mode=mean_mode)
