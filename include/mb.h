@@ -15,9 +15,17 @@
  *    synchronises that stream before it returns.
  *  - Pointers: array arguments may be device pointers (on the context's device) or host
  *    pointers (pageable or pinned); the library finds out which with
- *    cudaPointerGetAttributes and stages host arrays through its own device buffers.  The
- *    caller owns every array it passes; the library never keeps a caller pointer after the
- *    call returns.
+ *    cudaPointerGetAttributes and stages host arrays through its own device buffers (the
+ *    FP32-grid mb_step reads page-locked external forces directly instead).  Input arrays in
+ *    device or page-locked memory are read in stream order, like cudaMemcpyAsync: keep them
+ *    unchanged until the stream has reached the call.  The caller owns every array it
+ *    passes; no caller pointer is used by work enqueued after the call returns.
+ *  - Environment (read when a context is created; for comparisons and tuning, the defaults
+ *    are the fast path): MB_FFT_PASSES=5 runs the fluid solve as five one-axis passes instead
+ *    of three; MB_NO_GRAPH=1 launches every FP32-grid step directly instead of replaying its
+ *    captured CUDA graph; MB_NO_AUTOTUNE=1 keeps the default spreading tile;
+ *    MB_NO_FUSE_INTERP=1 runs the corrector and the next predictor as separate passes.
+ *    MB_FAULT_ALLOC=k makes the k-th device allocation fail (tests of the error paths).
  *  - Layouts: blob arrays are [n][3] row-major FP64 (x, y, z).  A velocity or force grid of
  *    one box is 3 component arrays stored one after another, each [nz][ny][nx] with x
  *    fastest, in the context's grid precision (float for precision 0, double for 1); a
