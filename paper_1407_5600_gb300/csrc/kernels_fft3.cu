@@ -388,7 +388,7 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
 // Pass B.  CTA = (ky block of width C, kx, box); shared buffer [3][pad(nz)][C + 4].  C is a
 // compile-time width (16 FP32, 8 FP64) and the block has 3 C N2 threads, one round of lines.
 template <typename R, int C>
-__global__ void __launch_bounds__(3 * C * 8)
+__global__ void __launch_bounds__(3 * C * 8, sizeof(R) == 4 ? 768 / (3 * C * 8) : 1)
 k_zsolve(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<R>::T;
@@ -593,7 +593,7 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
 {
     using T = typename C2<R>::T;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
-    constexpr int CZ = sizeof(R) == 4 ? 16 : 8;      // ky columns per z-pass block
+    constexpr int CZ = 8;                             // ky columns per z-pass block
     static std::atomic<unsigned> attr{0};     // per instantiation
     if (first_on_device(attr)) {
         const int lim = 200 * 1024;
