@@ -24,6 +24,9 @@ template <typename T> __device__ __forceinline__ T cm(T a, T b)
     return T{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 template <typename T> __device__ __forceinline__ T cadd(T a, T b) { return T{a.x + b.x, a.y + b.y}; }
+// Correctly rounded reciprocals (the float one is a single intrinsic instead of a division).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 template <typename T> __device__ __forceinline__ T csub(T a, T b) { return T{a.x - b.x, a.y - b.y}; }
 
 __host__ __device__ constexpr int bitrev(int i, int bits)
@@ -424,7 +427,7 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
         const R cs[3] = {csx, sym[3 * 256 + ky], sym[6 * 256 + kz]};
         const R sn[3] = {snx, sym[4 * 256 + ky], sym[7 * 256 + kz]};
         const R lam = lx + sym[5 * 256 + ky] + sym[8 * 256 + kz];
-        const R cinv = R(1) / (rho_dt + half_eta * lam);
+        const R cinv = recip(rho_dt + half_eta * lam);
         T W[3];
         for (int c = 0; c < 3; ++c) {
             const T v = Bf[at(c, kz, k)];
@@ -452,7 +455,7 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
                 dr += Dr * W[c].x - Di * W[c].y;
                 di += Dr * W[c].y + Di * W[c].x;
             }
-            const R il = R(1) / lam;
+            const R il = recip(lam);
             dr *= il;
             di *= il;
             for (int c = 0; c < 3; ++c) {
