@@ -743,8 +743,12 @@ k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_star
     const float scale = bound > 0.f ? ldexpf(1.0f, 30 - e) : 1.0f;
     // origin of the shared copy in node coordinates
     const int ox = T0[0] - 4, oy = T0[1] - 1, oz = T0[2] - 1;
+    // the lanes of a warp take blobs total/32 apart in the cell order (different cell rows):
+    // their windows then rarely share shared-memory words or banks
+    const int stride = total >> 5, body32 = stride << 5;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int64_t slot = slot_of(t);
+        const int tp = t < body32 ? (t & 31) * stride + (t >> 5) : t;
+        const int64_t slot = slot_of(tp);
         const float4 pa = rec[2 * slot], fv = rec[2 * slot + 1];
         const int pk = __float_as_int(pa.w);
         const Win2 wx = windows2(cell_unpack(pk, 0), G.bs, pa.x, G.inv_h);
