@@ -66,7 +66,9 @@ typedef enum {
  *   deterministic  0 or 1.  With precision 1, 1 makes a run bitwise reproducible: blobs are
  *                ordered within their bin cells and spreading accumulates in 64-bit fixed point
  *                (order-independent sums); every other stage already has a fixed order.  In
- *                FP32-grid mode the flag only fixes the in-cell order.
+ *                FP32-grid mode the flag has no effect: the in-cell order, the spring sums at
+ *                an icosahedron's centre and the grid additions of neighbouring spreading
+ *                tiles follow the order of atomics, so runs agree to FP32 rounding.
  *   advection    must be 0: the convective term rho v v of Eq. (vf) is not provided (every
  *                measurement in the paper is at vanishing Reynolds number).
  *   mean_mode    0: the k = 0 fluid mode carries the net momentum, rho L^3 d(mean v)/dt =
