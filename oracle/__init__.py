@@ -64,6 +64,7 @@ def _load():
             "mbref_pair_forces": [G, I64, P, P, D, D, P],
             "mbref_pair_forces_subset": [G, I64, P, P, D, D, I64, P, P],
             "mbref_step": [G, ctypes.c_int, I64, P, P, P, I64, P, P, D, D, D, P, P],
+            "mbref_stokes_step": [G, ctypes.c_int, I64, P, P, P, I64, P, P, D, D, D, P, P],
             "mbref_particle_velocities": [G, I64, P, P, P, I64, P, P],
         }.items():
             fn = getattr(lib, name)
@@ -222,6 +223,25 @@ def step(g: Grid, nsteps, q, v, pid, bonds, rest, k_spring, k_rep=0.0, r_cut=0.0
     _check(_load().mbref_step(g._c(), int(nsteps), len(q), q.ctypes.data_as(ctypes.c_void_p),
                               v.ctypes.data_as(ctypes.c_void_p), pp, len(b), bp, rp,
                               float(k_spring), float(k_rep), float(r_cut), ep, bbp), "step")
+    return q, v
+
+
+def stokes_step(g: Grid, nsteps, q, pid, bonds, rest, k_spring, k_rep=0.0, r_cut=0.0,
+                ext=None, body=None):
+    """Run nsteps Stokes-limit steps (explicit midpoint, steady zero-mean Stokes flow of the
+    current forces); returns new (q, v) with v the last flow (inputs are not modified)."""
+    q = np.array(q, dtype=np.float64, order="C", copy=True)
+    v = g.zeros()
+    p, pp = _i32(pid)
+    b, bp = _i32(np.asarray(bonds).reshape(-1, 2))
+    r, rp = _d(rest)
+    e, ep = _d(ext) if ext is not None else (None, None)
+    bb, bbp = _body(body)
+    _check(_load().mbref_stokes_step(g._c(), int(nsteps), len(q),
+                                     q.ctypes.data_as(ctypes.c_void_p),
+                                     v.ctypes.data_as(ctypes.c_void_p), pp, len(b), bp, rp,
+                                     float(k_spring), float(k_rep), float(r_cut), ep, bbp),
+           "stokes_step")
     return q, v
 
 

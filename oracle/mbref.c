@@ -460,6 +460,62 @@ int mbref_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
     return 0;
 }
 
+/* Stokes limit (Sc -> infinity) of the blob-fluid coupling: the fluid momentum relaxes
+ * instantly, so the fluid velocity is the steady Stokes solution for the current forces,
+ * v = P (-eta L)^{-1} (S F + f_body) with zero mean (Sec. 3 with the inertia of fluid and
+ * particles removed, the regime of the paper's viscosity runs), and the blobs follow it,
+ * u = J v.  In time, the explicit midpoint rule (the deterministic part of the Stokes-limit
+ * integrator the paper cites): forces and solve at q^n give q^{n+1/2} = q^n + dt/2 u^n, forces
+ * and solve at q^{n+1/2} give q^{n+1} = q^n + dt u^{n+1/2}.  v returns the second solve. */
+static void all_forces(const mbref_grid* g, int64_t n, const double* x, const int32_t* pid,
+                       int64_t nbonds, const int32_t* bonds, const double* rest, double k_spring,
+                       double k_rep, double r_cut, const double* ext, double* F)
+{
+    for (int64_t c = 0; c < 3 * n; ++c) F[c] = ext ? ext[c] : 0.0;
+    mbref_bond_forces(g, n, x, nbonds, bonds, rest, k_spring, F);
+    mbref_pair_forces(g, n, x, pid, k_rep, r_cut, F);
+}
+
+int mbref_stokes_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
+                      const int32_t* pid, int64_t nbonds, const int32_t* bonds,
+                      const double* rest, double k_spring, double k_rep, double r_cut,
+                      const double* ext, const double* body)
+{
+    const int64_t N = (int64_t)g->nx * g->ny * g->nz;
+    const double L[3] = {g->nx * g->h, g->ny * g->h, g->nz * g->h};
+    const double dt = g->dt;
+    double* u = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double* qh = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double* F = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double* f = (double*)malloc(sizeof(double) * 3 * N);
+    if (!u || !qh || !F || !f) {
+        free(u); free(qh); free(F); free(f);
+        return 2;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        /* half step with the forces and the flow of q^n */
+        all_forces(g, n, q, pid, nbonds, bonds, rest, k_spring, k_rep, r_cut, ext, F);
+        mbref_spread(g, n, q, F, f);
+        if (body) add_body_force(g, body, f);
+        mbref_stokes_solve(g, f, v);
+        mbref_interp(g, n, q, v, u);
+        for (int64_t b = 0; b < n; ++b)
+            for (int a = 0; a < 3; ++a)
+                qh[3 * b + a] = wrap_pos(q[3 * b + a] + 0.5 * dt * u[3 * b + a], L[a]);
+        /* full step with the forces and the flow of q^{n+1/2} */
+        all_forces(g, n, qh, pid, nbonds, bonds, rest, k_spring, k_rep, r_cut, ext, F);
+        mbref_spread(g, n, qh, F, f);
+        if (body) add_body_force(g, body, f);
+        mbref_stokes_solve(g, f, v);
+        mbref_interp(g, n, qh, v, u);
+        for (int64_t b = 0; b < n; ++b)
+            for (int a = 0; a < 3; ++a)
+                q[3 * b + a] = wrap_pos(q[3 * b + a] + dt * u[3 * b + a], L[a]);
+    }
+    free(u); free(qh); free(F); free(f);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Particle observables (Sec. 2 and Sec. 3.2): U0 = (1/N) sum u_i;
  * Omega solves I0 Omega = sum_i s_i x (u_i - U0), I0 = sum_i (s_i^2 1 - s_i s_i). */

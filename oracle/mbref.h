@@ -75,6 +75,13 @@ int mbref_pair_forces_subset(const mbref_grid* g, int64_t n, const double* q,
 
 /* nsteps of the neutrally buoyant ICM step (midpoint blob update, CN fluid update),
  * updating q (wrapped into [0, L)) and v in place.  ext ([n][3]) and body may be NULL. */
+/* Stokes-limit steps (fluid inertia removed): explicit midpoint rule with the steady,
+ * zero-mean Stokes flow of the current forces; v receives the last flow.  Same arguments as
+ * mbref_step (rho and mean_mode of the grid are not used). */
+int mbref_stokes_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
+                      const int32_t* pid, int64_t nbonds, const int32_t* bonds,
+                      const double* rest, double k_spring, double k_rep, double r_cut,
+                      const double* ext, const double* body);
 int mbref_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
                const int32_t* pid, int64_t nbonds, const int32_t* bonds, const double* rest,
                double k_spring, double k_rep, double r_cut, const double* ext,

@@ -1,0 +1,139 @@
+"""Pins of the oracle's Stokes-limit step (fluid inertia removed, explicit midpoint rule) against
+what the paper and the mathematics fix (no GPU).
+
+- Table rad: the drift of one blob, and of a 13-blob particle under equal blob forces, equals
+  the force times the mobility of the tabulated hydrodynamic radius corrected to the periodic
+  box with Hasimoto's Eq. (rhinf) (grid variation as in Sec. 5.1).
+- A single Fourier mode of body force gives the closed-form Stokes flow f0 / (eta lambda_k).
+- Invariants: one-cell translation, force-free rest, zero-mean divergence-free flow.
+- The midpoint rule converges at second order in dt.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as mb
+from paper_1407_5600_gb300 import workloads as wl
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table():
+    t = json.load(open(os.path.join(GOLD, "table_rad.json")))
+    return {row[0]: row[1] for row in t["rows"]}
+
+
+def _box_mobility(RH_inf, eta, L):
+    """Translational mobility in a periodic cube of side L (Eq. rhinf inverted)."""
+    return (1.0 - 2.84 * RH_inf / L) / (6 * np.pi * eta * RH_inf)
+
+
+def _div(v, h):
+    return sum((np.roll(v[a], -1, axis=2 - a) - v[a]) / h for a in range(3))
+
+
+def test_single_blob_drift_matches_table_radius():
+    table = _table()
+    n, eta, dt = 32, 1.3, 0.02
+    g = mb.Grid(n, n, n, eta=eta, dt=dt, mean_mode=1)
+    rng = np.random.default_rng(5)
+    ratios = []
+    for _ in range(6):
+        q0 = rng.uniform(0, n, size=(1, 3))
+        e = rng.normal(size=3)
+        e /= np.linalg.norm(e)
+        F = 1e-3 * e[None, :]
+        q1, _ = mb.stokes_step(g, 1, q0, np.zeros(1, np.int32), np.zeros((0, 2), np.int32),
+                               np.zeros(0), 0.0, ext=F)
+        U = (q1 - q0)[0] / dt
+        ratios.append(U @ e / (1e-3 * _box_mobility(table[0.0], eta, float(n))))
+    assert abs(np.mean(ratios) - 1.0) < 0.03, ratios
+
+
+def test_particle_drift_matches_table_radius():
+    """d = 2h icosahedron, equal forces on its 13 blobs: once the springs have taken up the
+    constraint forces (time k mu_blob >> 1) it translates with the rigid-body mobility of
+    R_H(d = 2h) from Table rad."""
+    table = _table()
+    n, eta, dt, d = 64, 1.0, 0.05, 2.0
+    g = mb.Grid(n, n, n, eta=eta, dt=dt, mean_mode=1)
+    rng = np.random.default_rng(8)
+    a = d * np.sqrt(10 + 2 * np.sqrt(5)) / 4
+    s = wl.build_particles(rng.uniform(0, n, size=3), a, rng, g.L)
+    Ftot = np.array([1e-3, 0.0, 0.0])
+    ext = np.tile(Ftot / 13, (13, 1))
+    nsteps = 12
+    qa, _ = mb.stokes_step(g, 20, s.pos, s.pid, s.bonds, s.rest, 100.0, ext=ext)
+    q1, _ = mb.stokes_step(g, nsteps, qa, s.pid, s.bonds, s.rest, 100.0, ext=ext)
+    disp = q1 - qa
+    disp -= g.L * np.round(disp / g.L)
+    U = disp.mean(0) / (nsteps * dt)
+    mu = _box_mobility(table[d], eta, float(n))
+    assert abs(U[0] / (mu * Ftot[0]) - 1.0) < 0.02, U
+    assert np.max(np.abs(U[1:])) < 0.01 * abs(U[0])
+
+
+def test_body_force_mode_closed_form():
+    """No blob forces: the flow of f_x = f0 sin(2 pi z / L) is f0 / (eta lambda) sin(2 pi z / L)
+    on the v_x nodes (z = (k + 1/2) h), lambda = (4 / h^2) sin^2(pi h / L)."""
+    n, h, eta, f0 = 16, 0.7, 1.7, 0.3
+    g = mb.Grid(n, n, n, h=h, eta=eta, dt=0.1, mean_mode=1)
+    L = n * h
+    q = np.array([[1.3, 2.2, 3.1]])
+    _, v = mb.stokes_step(g, 1, q, np.zeros(1, np.int32), np.zeros((0, 2), np.int32),
+                          np.zeros(0), 0.0, body=(f0, 0, 2, 1))
+    z = (np.arange(n) + 0.5) * h
+    lam = 4.0 / h ** 2 * np.sin(np.pi * h / L) ** 2
+    want = (f0 / (eta * lam) * np.sin(2 * np.pi * z / L))[:, None, None] * np.ones((n, n, n))
+    assert np.max(np.abs(v[0] - want)) < 1e-13 * np.max(np.abs(want))
+    assert np.max(np.abs(v[1:])) < 1e-13 * np.max(np.abs(want))
+
+
+def test_translation_by_one_cell_and_flow_properties():
+    n = 16
+    g = mb.Grid(n, n, n, eta=1.0, dt=0.05, mean_mode=1)
+    rng = np.random.default_rng(3)
+    s = wl.build_particles(np.array([[5.0, 6.0, 7.0], [10.5, 6.4, 7.2]]), 1.6, rng, g.L)
+    s.pos = np.mod(s.pos + rng.normal(scale=0.05, size=s.pos.shape), g.L)
+    ext = rng.normal(scale=1e-3, size=s.pos.shape)
+    args = (s.pid, s.bonds, s.rest, 100.0, 50.0, 1.0)
+    q1, v1 = mb.stokes_step(g, 3, s.pos, *args, ext=ext)
+    q2, v2 = mb.stokes_step(g, 3, np.mod(s.pos + 1.0, g.L), *args, ext=ext)
+    d1 = q1 - s.pos
+    d2 = q2 - np.mod(s.pos + 1.0, g.L)
+    d1 -= g.L * np.round(d1 / g.L)
+    d2 -= g.L * np.round(d2 / g.L)
+    assert np.max(np.abs(d1 - d2)) < 1e-12 * np.max(np.abs(d1))
+    assert np.allclose(np.roll(v1, (1, 1, 1), axis=(1, 2, 3)), v2, rtol=0,
+                       atol=1e-12 * np.max(np.abs(v1)))
+    assert np.max(np.abs(_div(v1, g.h))) < 1e-12 * np.max(np.abs(v1))
+    assert np.max(np.abs(v1.mean((1, 2, 3)))) < 1e-14
+
+
+def test_force_free_particle_rests():
+    n = 16
+    g = mb.Grid(n, n, n, eta=1.0, dt=0.05, mean_mode=1)
+    rng = np.random.default_rng(4)
+    s = wl.build_particles(np.array([[7.0, 8.0, 9.0]]), 1.6, rng, g.L)
+    q1, v = mb.stokes_step(g, 5, s.pos, s.pid, s.bonds, s.rest, 100.0)
+    assert np.max(np.abs(q1 - s.pos)) < 1e-12
+    assert np.max(np.abs(v)) < 1e-12
+
+
+def test_midpoint_rule_is_second_order():
+    n = 16
+    g0 = dict(eta=1.0, mean_mode=1)
+    rng = np.random.default_rng(6)
+    s = wl.build_particles(np.array([[7.0, 8.0, 9.0]]), 1.6, rng, np.array([16.0] * 3))
+    q0 = np.mod(s.pos + rng.normal(scale=0.08, size=s.pos.shape), 16.0)   # stretched springs
+    T = 0.4
+    out = []
+    for m in (4, 8, 16):
+        g = mb.Grid(n, n, n, dt=T / m, **g0)
+        q, _ = mb.stokes_step(g, m, q0, s.pid, s.bonds, s.rest, 20.0)
+        out.append(q)
+    e1 = np.linalg.norm(out[0] - out[1])
+    e2 = np.linalg.norm(out[1] - out[2])
+    assert 3.2 < e1 / e2 < 4.8, (e1, e2)
