@@ -75,7 +75,17 @@ typedef enum {
  *                sum of blob forces (+ mean body force); 1: the k = 0 mode is held at zero
  *                (the frame of Hasimoto's periodic drag, Eq. rhinf).
  *   kT           must be 0 (no fluctuating stress).
- *   seed         reserved for the fluctuating stress. */
+ *   seed         reserved for the fluctuating stress.
+ *   integrator   0: the inertial coupling method (Sec. 3: fluid and blob inertia, midpoint
+ *                predictor/corrector for the blobs, Crank-Nicolson for the fluid).  1: its
+ *                Stokes limit (Sc -> infinity, the regime of the paper's viscosity runs): each
+ *                half step solves the steady zero-mean Stokes flow of the current forces,
+ *                v = P (-eta L)^{-1} (S F + f_body), and the blobs follow u = J v with the
+ *                explicit midpoint rule; rho is not used, mean_mode must be 1, and the velocity
+ *                field of the context is the flow of the last half step.  In either grid
+ *                precision the blob positions, forces and interpolated velocities are FP64
+ *                (the FP32 mode keeps only the grid and its FFTs in FP32); the step adjoint
+ *                is not provided for it. */
 typedef struct {
     int nx, ny, nz;
     int batch;
@@ -86,6 +96,7 @@ typedef struct {
     int mean_mode;
     double kT;
     uint64_t seed;
+    int integrator;
 } mb_grid_desc;
 
 /* Creates a context: validates *desc, allocates every grid buffer on the current CUDA
@@ -159,7 +170,10 @@ mb_status mb_interp(mb_ctx* ctx, int64_t n, const double* pos, const void* grid_
 /* Standalone fluid update of one box (Eq. vf with the viscous stress, Crank-Nicolson):
  *   (rho/dt - eta/2 L) v_out = P[(rho/dt + eta/2 L) v_in + f + f_body].
  * The k = 0 mode follows the grid (mean_mode 0) or is zeroed (mean_mode 1).  v_in, f and
- * v_out are one box grid each; body_force as in mb_step (HOST, or NULL). */
+ * v_out are one box grid each; body_force as in mb_step (HOST, or NULL).
+ * In a Stokes-limit context (integrator 1) it is the steady solve of that integrator,
+ *   -eta L v_out = P[f + f_body], k = 0 mode zero,
+ * and v_in is not read (may be NULL). */
 mb_status mb_fluid_update(mb_ctx* ctx, const void* v_in, const void* f,
                           const double* body_force, void* v_out);
 
@@ -202,7 +216,8 @@ mb_status mb_set_positions(mb_ctx* ctx, const double* pos);
  * and T (Eq. vf: the projection P, the Laplacian and the CN factors are symmetric and commute),
  * so its transpose reuses the forward solver; the blob-force transpose is the force Hessian
  * applied to the incoming gradient (forces derive from a potential).  Provided for FP64
- * contexts (precision 1) with batch 1; MB_EINVAL otherwise.  Arrays may be host or device. */
+ * contexts (precision 1) with batch 1 and integrator 0; MB_EINVAL otherwise.  Arrays may be
+ * host or device. */
 mb_status mb_adjoint_step(mb_ctx* ctx, const double* pos_n, const void* grid_v_n,
                           const double* ext_blob_force, const double* body_force,
                           double* grad_pos, void* grad_v, double* grad_k_spring);

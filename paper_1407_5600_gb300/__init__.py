@@ -43,7 +43,8 @@ class _Desc(ctypes.Structure):
                 ("batch", ctypes.c_int), ("h", ctypes.c_double), ("rho", ctypes.c_double),
                 ("eta", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("advection", ctypes.c_int),
-                ("mean_mode", ctypes.c_int), ("kT", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("mean_mode", ctypes.c_int), ("kT", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("integrator", ctypes.c_int)]
 
 
 @dataclass
@@ -62,11 +63,12 @@ class GridDesc:
     mean_mode: int = 0        # 0: conserve net momentum, 1: hold the mean at zero
     kT: float = 0.0
     seed: int = 0
+    integrator: int = 0       # 0: inertial coupling, 1: Stokes limit
 
     def _c(self):
         return _Desc(self.nx, self.ny, self.nz, self.batch, self.h, self.rho, self.eta, self.dt,
                      self.precision, self.deterministic, self.advection, self.mean_mode,
-                     self.kT, self.seed)
+                     self.kT, self.seed, self.integrator)
 
     @property
     def grid_dtype(self):
@@ -405,6 +407,6 @@ class Multiblob:
 
     def fluid_update(self, v, f=None, body_force=None):
         out = self.torch.empty(self.grid_shape(1), dtype=self.grid_dtype, device=self.device)
-        fluid_update(self.ctx, self._dev(v, self.grid_dtype),
+        fluid_update(self.ctx, self._dev(v, self.grid_dtype) if v is not None else None,
                      self._dev(f, self.grid_dtype) if f is not None else None, out, body_force)
         return out

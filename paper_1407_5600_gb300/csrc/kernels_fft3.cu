@@ -257,7 +257,34 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     R* pclr = a.f_clear && fc ? a.f_clear + (size_t)bc * g.N + (size_t)z * ny * nx : nullptr;
     // each work unit: 4 consecutive x of the two rows 2p, 2p+1
     const int qx = nx / 4;
-    for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
+    for (int u = threadIdx.x; u < qx * (ny / 2) && a.no_v; u += blockDim.x) {
+        // Stokes limit: the right-hand side is the force density (and body force) alone
+        const int x0 = 4 * (u % qx), p = u / qx;
+        const int y0 = 2 * p, y1 = y0 + 1;
+        R r0[4] = {R(0), R(0), R(0), R(0)}, r1[4] = {R(0), R(0), R(0), R(0)};
+        if (pf) {
+            load4(pf + (size_t)y0 * nx + x0, r0);
+            load4(pf + (size_t)y1 * nx + x0, r1);
+            if (pclr) {
+                const R zero[4] = {R(0), R(0), R(0), R(0)};
+                store4(pclr + (size_t)y0 * nx + x0, zero);
+                store4(pclr + (size_t)y1 * nx + x0, zero);
+            }
+        }
+        if (body) {
+            for (int i = 0; i < 4; ++i) {
+                const int x = x0 + i;
+                r0[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y0 : z)];
+                r1[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)];
+            }
+        }
+        T* row = P + p * S;
+        for (int i = 0; i < 4; ++i) {
+            const int j = x0 + i;
+            row[j + (j >> sx)] = T{r0[i], r1[i]};
+        }
+    }
+    for (int u = threadIdx.x; u < qx * (ny / 2) && !a.no_v; u += blockDim.x) {
         const int x0 = 4 * (u % qx), p = u / qx;
         const int y0 = 2 * p, y1 = y0 + 1;
         const int ym = (y0 - 1) & (ny - 1), yp = (y1 + 1) & (ny - 1);

@@ -690,6 +690,110 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
     return MB_OK;
 }
 
+// One Stokes-limit step of every box (integrator 1), FP64 blob positions in either grid
+// precision: two half steps, each binning the blobs, computing their forces, spreading them and
+// solving the steady zero-mean Stokes flow v = P (-eta L)^{-1} (S F + f_body) (the three-pass
+// FFT with the right-hand side f alone and the divide by eta lambda); then
+// q^{n+1/2} = q^n + dt/2 J(q^n) v(q^n) and q^{n+1} = q^n + dt J(q^{n+1/2}) v(q^{n+1/2}).
+template <typename R>
+mb_status do_step_stokes(mb_ctx* ctx, const double* ext, const double* body)
+{
+    cudaStream_t st = ctx->st;
+    const GridGeo& g = ctx->g;
+    const int B = ctx->B;
+    R* v_half = static_cast<R*>(ctx->v[ctx->cur ^ 1].p);
+    R* v_full = static_cast<R*>(ctx->v[ctx->cur].p);
+    double* q = static_cast<double*>(ctx->q.p);
+    double* qh = static_cast<double*>(ctx->qh.p);
+    const int32_t* box_of = static_cast<const int32_t*>(ctx->box_of.p);
+    const bool blobs = ctx->nb > 0;
+    if (ctx->timing) {
+        if (ctx->ev_pending == mb_ctx::EV_RING) MB_TRY(drain_stage_events(ctx));
+        ctx->ev = ctx->ev_ring.data() + (size_t)ctx->ev_pending * (NUM_STAGES + 1);
+    }
+    auto mark = [&](int i) { if (ctx->timing) cudaEventRecord(ctx->ev[i], st); };
+    // forces at x into ctx->f, then the Stokes flow into v_out (stage marks on the second half)
+    auto half = [&](const double* x, R* v_out, bool marks) -> mb_status {
+        if (marks) mark(ST_BIN);
+        if (blobs) {
+            MB_CUDA(launch_bin(st, ctx->nb, x, box_of, B, ctx->bg,
+                               static_cast<int32_t*>(ctx->cell_count.p),
+                               static_cast<int32_t*>(ctx->cell_start.p),
+                               static_cast<int32_t*>(ctx->blob_cell.p),
+                               static_cast<int32_t*>(ctx->blob_rank.p),
+                               static_cast<int32_t*>(ctx->sorted.p),
+                               static_cast<int32_t*>(ctx->scan_tmp.p), ctx->d.deterministic != 0,
+                               static_cast<const int32_t*>(ctx->pid.p),
+                               static_cast<float4*>(ctx->loc.p)));
+            ctx->launches += 5 + 2 * (ctx->d.deterministic != 0);
+        }
+        if (marks) mark(ST_FORCES);
+        if (blobs) {
+            ForceArgs fa{};
+            fa.box_off = static_cast<const int64_t*>(ctx->box_off.p);
+            fa.sorted = static_cast<const int32_t*>(ctx->sorted.p);
+            fa.q = x;
+            fa.pid = static_cast<const int32_t*>(ctx->pid.p);
+            fa.adj_start = static_cast<const int32_t*>(ctx->adj_start.p);
+            fa.adj_j = static_cast<const int32_t*>(ctx->adj_j.p);
+            fa.adj_rest = static_cast<const double*>(ctx->adj_rest.p);
+            fa.box_par = static_cast<const double*>(ctx->box_par.p);
+            fa.cell_start = static_cast<const int32_t*>(ctx->cell_start.p);
+            fa.blob_cell = static_cast<const int32_t*>(ctx->blob_cell.p);
+            fa.ext = ext;
+            fa.loc = static_cast<const float4*>(ctx->loc.p);
+            fa.F = static_cast<double*>(ctx->F.p);
+            fa.rec = static_cast<double*>(ctx->rec.p);
+            fa.partial = static_cast<double*>(ctx->partial.p);
+            fa.nchunk = ctx->nchunk;
+            MB_CUDA(launch_forces(st, B, ctx->max_box_blobs, fa, g, ctx->bg, ctx->rsz == 8));
+            ctx->launches += 1;
+        }
+        if (marks) mark(ST_FORCE_SUM);
+        if (marks) mark(ST_SPREAD);
+        if (blobs) {
+            if (ctx->d.deterministic && sizeof(R) == 8)
+                MB_CUDA(launch_spread_det(st, B, static_cast<const double*>(ctx->rec.p),
+                                          static_cast<const int32_t*>(ctx->cell_start.p), g,
+                                          ctx->bg, ctx->tile, reinterpret_cast<double*>(ctx->f.p)));
+            else
+                MB_CUDA(launch_spread<R>(st, B, static_cast<const double*>(ctx->rec.p),
+                                         static_cast<const int32_t*>(ctx->cell_start.p), g,
+                                         ctx->bg, ctx->tile, static_cast<R*>(ctx->f.p)));
+            ctx->launches += 1;
+        }
+        FluidArgs<R> fa = fluid_args<R>(ctx, v_out, blobs ? ctx->f.p : nullptr, v_out,
+                                        ctx->body_prof.p, body, nullptr);
+        fa.no_v = 1;                        // right-hand side S F + f_body
+        fa.rho_dt = 0.0;                    // divide by eta lambda: steady Stokes
+        fa.half_eta = ctx->d.eta;
+        fa.mean_mode = 1;
+        MB_CUDA(launch_fluid3<R>(st, B, g, fa, marks && ctx->timing ? ctx->ev + ST_FLUID_X_FWD
+                                                                     : nullptr));
+        ctx->launches += FLUID3_KERNELS;
+        return MB_OK;
+    };
+    mark(ST_INTERP_PREDICT);
+    MB_TRY(half(q, v_half, false));
+    if (blobs) {
+        // q^{n+1/2} = q^n + dt/2 J(q^n) v(q^n)
+        MB_CUDA(launch_interp<R>(st, 1, ctx->nb, q, nullptr, v_half, nullptr, box_of, g,
+                                 ctx->d.dt, nullptr, qh));
+        ctx->launches += 1;
+    }
+    MB_TRY(half(qh, v_full, true));
+    if (blobs) {
+        // q^{n+1} = q^n + dt J(q^{n+1/2}) v(q^{n+1/2})  (the mean of a field with itself)
+        MB_CUDA(launch_interp<R>(st, 2, ctx->nb, qh, q, v_full, v_full, box_of, g, ctx->d.dt,
+                                 nullptr, q));
+        ctx->launches += 1;
+    }
+    mark(NUM_STAGES);
+    if (ctx->timing) ctx->ev_pending++;
+    ctx->steps_taken++;
+    return MB_OK;
+}
+
 // One time step of every box in FP32-grid mode: blob positions as bin cell + float-float
 // offset, forces and weights on the FP32 pipes, the k = 0 mode from the FP64 external force sum.
 // Host-side state after an FP32-grid step has been enqueued (directly or as a graph replay).
@@ -979,7 +1083,7 @@ mb_status run_fast_steps(mb_ctx* ctx, int n_steps, bool ext, const double* body)
 // FP64 blob positions of the current state (from the split form in FP32-grid mode).
 mb_status current_positions(mb_ctx* ctx)
 {
-    if (ctx->rsz == 4 && ctx->nb > 0)
+    if (ctx->rsz == 4 && ctx->nb > 0 && ctx->d.integrator == 0)
         MB_CUDA(launch_unsplit(ctx->st, ctx->nb, static_cast<const float4*>(ctx->sA.p),
                                static_cast<const float4*>(ctx->sB.p), ctx->g, ctx->bg,
                                static_cast<double*>(ctx->q.p)));
@@ -1168,6 +1272,14 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
         g_create_error = "fluctuating hydrodynamics (kT != 0) is not provided; set kT = 0";
         return MB_EINVAL;
     }
+    if (d.integrator != 0 && d.integrator != 1) {
+        g_create_error = "integrator must be 0 (inertial coupling) or 1 (Stokes limit)";
+        return MB_EINVAL;
+    }
+    if (d.integrator == 1 && d.mean_mode != 1) {
+        g_create_error = "the Stokes limit has no steady mean flow under a net force: set mean_mode = 1";
+        return MB_EINVAL;
+    }
     mb_ctx* ctx = new (std::nothrow) mb_ctx();
     if (!ctx) {
         g_create_error = "out of host memory";
@@ -1305,6 +1417,21 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
         if (ctx->body_prof.p != before) drop_graph(ctx);   // captured steps hold the old buffer
     }
     const double* ext = nullptr;
+    if (ctx->d.integrator == 1) {
+        // Stokes limit: FP64 forces in both grid precisions, from the library's copy
+        if (ext_blob_force && ctx->nb > 0) {
+            const void* src = nullptr;
+            MB_TRY(stage_in(ctx, ext_blob_force, sizeof(double) * 3 * ctx->nb, ctx->ext, &src, "ext"));
+            if (src != ctx->ext.p)
+                MB_CUDA(cudaMemcpyAsync(ctx->ext.p, src, sizeof(double) * 3 * ctx->nb,
+                                        cudaMemcpyDeviceToDevice, ctx->st));
+            ext = static_cast<const double*>(ctx->ext.p);
+        }
+        for (int s = 0; s < n_steps; ++s)
+            MB_TRY(ctx->rsz == 4 ? do_step_stokes<float>(ctx, ext, body_force)
+                                 : do_step_stokes<double>(ctx, ext, body_force));
+        return MB_OK;
+    }
     if (ext_blob_force && ctx->nb > 0) {
         const void* src = nullptr;
         void* mapped = ctx->rsz == 4 ? mapped_host_ptr(ext_blob_force) : nullptr;
@@ -1344,7 +1471,7 @@ mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos)
     }
     const size_t by = sizeof(double) * 3 * ctx->nb;
     if (ctx->nb == 0) return MB_OK;
-    if (ctx->rsz == 4) {
+    if (ctx->rsz == 4 && ctx->d.integrator == 0) {
         MB_CUDA(launch_forces_to_fp64(ctx->st, ctx->nb, static_cast<const float4*>(ctx->F32.p),
                                       static_cast<double*>(ctx->F.p)));
         MB_CUDA(launch_unsplit(ctx->st, ctx->nb, static_cast<const float4*>(ctx->hA[ctx->hlast].p),
@@ -1505,6 +1632,8 @@ mb_status mb_adjoint_step(mb_ctx* ctx, const double* pos_n, const void* grid_v_n
     DeviceGuard dg(ctx->device);
     if (!pos_n || !grid_v_n || !grad_pos || !grad_v) return invalid(ctx, "null argument");
     MB_TRY(adjoint_preconditions(ctx));
+    if (ctx->d.integrator != 0)
+        return invalid(ctx, "the step adjoint is provided for the inertial coupling integrator");
     if (body_force) MB_TRY(set_body(ctx, body_force, ctx->prof_scratch, false));
     cudaStream_t st = ctx->st;
     const GridGeo& g = ctx->g;
@@ -1662,6 +1791,11 @@ static mb_status blob_velocities(mb_ctx* ctx)
     if (ctx->rsz == 4 && ctx->pred_ready)      // the last step's fused pass gathered them
         MB_CUDA(launch_forces_to_fp64(ctx->st, ctx->nb, static_cast<const float4*>(ctx->u32.p),
                                       static_cast<double*>(ctx->u.p)));
+    else if (ctx->rsz == 4 && ctx->d.integrator == 1)   // FP64 positions, FP32 field
+        MB_CUDA(launch_interp<float>(ctx->st, 0, ctx->nb, static_cast<const double*>(ctx->q.p),
+                                     nullptr, static_cast<const float*>(ctx->v[ctx->cur].p),
+                                     nullptr, static_cast<const int32_t*>(ctx->box_of.p),
+                                     ctx->g, ctx->d.dt, static_cast<double*>(ctx->u.p), nullptr));
     else if (ctx->rsz == 4)
         MB_CUDA(launch_interp32(ctx->st, 0, ctx->nb, static_cast<const float4*>(ctx->sA.p),
                                 static_cast<const float4*>(ctx->sB.p),
@@ -1834,22 +1968,31 @@ mb_status mb_fluid_update(mb_ctx* ctx, const void* v_in, const void* f, const do
 {
     if (!ctx) return MB_EINVAL;
     DeviceGuard dg(ctx->device);
-    if (!v_in || !v_out) return invalid(ctx, "v_in and v_out must be non-null");
+    const bool stokes = ctx->d.integrator == 1;
+    if ((!v_in && !stokes) || !v_out) return invalid(ctx, "v_in and v_out must be non-null");
     const size_t by = grid_bytes(ctx, 1);
     const void *vd = nullptr, *fd = nullptr;
-    MB_TRY(stage_in(ctx, v_in, by, ctx->s_g1, &vd, "v_in"));
+    if (!stokes) MB_TRY(stage_in(ctx, v_in, by, ctx->s_g1, &vd, "v_in"));
     if (f) MB_TRY(stage_in(ctx, f, by, ctx->s_g2, &fd, "f"));
     if (body_force) MB_TRY(set_body(ctx, body_force, ctx->prof_scratch, false));
     void* dst;
     bool host;
     MB_TRY(out_target(ctx, v_out, by, ctx->s_out, &dst, &host, "v_out"));
+    auto stokes_args = [&](auto& a) {
+        a.v = a.v_out;                      // unread: the right-hand side is f + f_body
+        a.no_v = 1;
+        a.rho_dt = 0.0;
+        a.half_eta = ctx->d.eta;
+    };
     if (ctx->rsz == 4) {
         FluidArgs<float> a = fluid_args<float>(ctx, vd, fd, dst, ctx->prof_scratch.p, body_force, nullptr);
-        if (ctx->fft_passes == 5) MB_CUDA(launch_fluid<float>(ctx->st, 1, ctx->g, a));
+        if (stokes) stokes_args(a);
+        if (ctx->fft_passes == 5 && !stokes) MB_CUDA(launch_fluid<float>(ctx->st, 1, ctx->g, a));
         else MB_CUDA(launch_fluid3<float>(ctx->st, 1, ctx->g, a));
     } else {
         FluidArgs<double> a = fluid_args<double>(ctx, vd, fd, dst, ctx->prof_scratch.p, body_force, nullptr);
-        if (ctx->fft_passes == 5) MB_CUDA(launch_fluid<double>(ctx->st, 1, ctx->g, a));
+        if (stokes) stokes_args(a);
+        if (ctx->fft_passes == 5 && !stokes) MB_CUDA(launch_fluid<double>(ctx->st, 1, ctx->g, a));
         else MB_CUDA(launch_fluid3<double>(ctx->st, 1, ctx->g, a));
     }
     return finish_out(ctx, v_out, dst, by, host);

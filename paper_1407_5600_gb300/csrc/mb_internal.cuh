@@ -136,6 +136,7 @@ struct FluidArgs {
     double* mean_state;
     const double* mean_force;
     double mean_scale;
+    int no_v;              // three-pass FFT: right-hand side f (+ body) only (Stokes limit)
 };
 // marks: null, or 6 events recorded before pass 1 and after each of the 5 passes.
 template <typename R>
