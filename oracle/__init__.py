@@ -43,6 +43,11 @@ class _Grid(ctypes.Structure):
                 ("dt", ctypes.c_double), ("mean_mode", ctypes.c_int)]
 
 
+class _Noise(ctypes.Structure):
+    _fields_ = [("kT", ctypes.c_double), ("seed", ctypes.c_uint64), ("step0", ctypes.c_uint64),
+                ("box", ctypes.c_int64)]
+
+
 def _load():
     global _lib
     if _lib is None:
@@ -54,6 +59,8 @@ def _load():
         G = ctypes.POINTER(_Grid)
         lib.mbref_phi.restype = D
         lib.mbref_phi.argtypes = [D]
+        lib.mbref_philox4x64.restype = None
+        lib.mbref_philox4x64.argtypes = [P, P, P]
         for name, args in {
             "mbref_spread": [G, I64, P, P, P],
             "mbref_interp": [G, I64, P, P, P],
@@ -63,7 +70,10 @@ def _load():
             "mbref_bond_forces": [G, I64, P, I64, P, P, D, P],
             "mbref_pair_forces": [G, I64, P, P, D, D, P],
             "mbref_pair_forces_subset": [G, I64, P, P, D, D, I64, P, P],
-            "mbref_step": [G, ctypes.c_int, I64, P, P, P, I64, P, P, D, D, D, P, P],
+            "mbref_step": [G, ctypes.c_int, I64, P, P, P, I64, P, P, D, D, D, P, P,
+                           ctypes.POINTER(_Noise)],
+            "mbref_stress_normals": [G, ctypes.c_uint64, ctypes.c_uint64, I64, P],
+            "mbref_stress_div": [G, P, P],
             "mbref_stokes_step": [G, ctypes.c_int, I64, P, P, P, I64, P, P, D, D, D, P, P],
             "mbref_particle_velocities": [G, I64, P, P, P, I64, P, P],
         }.items():
@@ -210,9 +220,36 @@ def pair_forces_subset(g: Grid, q, pid, k_rep, r_cut, idx):
     return F
 
 
+def philox4x64(counter, key):
+    """Philox4x64-10 block: four uint64 words of Philox(counter[4], key[2])."""
+    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint64).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64).reshape(2))
+    out = np.zeros(4, dtype=np.uint64)
+    _load().mbref_philox4x64(c.ctypes.data_as(ctypes.c_void_p), k.ctypes.data_as(ctypes.c_void_p),
+                             out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def stress_normals(g: Grid, seed, step, box=0):
+    """The standard normals W [9][nz][ny][nx] of the thermal stress at one step."""
+    W = np.zeros((9,) + g.shape)
+    _check(_load().mbref_stress_normals(g._c(), int(seed), int(step), int(box),
+                                        W.ctypes.data_as(ctypes.c_void_p)), "stress_normals")
+    return W
+
+
+def stress_div(g: Grid, W):
+    """D.W on the MAC faces for a stress field W [9][nz][ny][nx]; returns [3][nz][ny][nx]."""
+    W, Wp = _d(np.asarray(W).reshape((9,) + g.shape))
+    f = g.zeros()
+    _check(_load().mbref_stress_div(g._c(), Wp, f.ctypes.data_as(ctypes.c_void_p)), "stress_div")
+    return f
+
+
 def step(g: Grid, nsteps, q, v, pid, bonds, rest, k_spring, k_rep=0.0, r_cut=0.0,
-         ext=None, body=None):
-    """Run nsteps ICM steps; returns new (q, v) (inputs are not modified)."""
+         ext=None, body=None, kT=0.0, seed=0, step0=0, box=0):
+    """Run nsteps ICM steps; returns new (q, v) (inputs are not modified).  kT > 0 adds the
+    thermal stress of steps step0, step0 + 1, ... of box `box` drawn with `seed`."""
     q = np.array(q, dtype=np.float64, order="C", copy=True)
     v = np.array(v, dtype=np.float64, order="C", copy=True)
     p, pp = _i32(pid)
@@ -222,7 +259,9 @@ def step(g: Grid, nsteps, q, v, pid, bonds, rest, k_spring, k_rep=0.0, r_cut=0.0
     bb, bbp = _body(body)
     _check(_load().mbref_step(g._c(), int(nsteps), len(q), q.ctypes.data_as(ctypes.c_void_p),
                               v.ctypes.data_as(ctypes.c_void_p), pp, len(b), bp, rp,
-                              float(k_spring), float(k_rep), float(r_cut), ep, bbp), "step")
+                              float(k_spring), float(k_rep), float(r_cut), ep, bbp,
+                              ctypes.byref(_Noise(float(kT), int(seed), int(step0), int(box)))),
+           "step")
     return q, v
 
 

@@ -403,6 +403,117 @@ int mbref_pair_forces_subset(const mbref_grid* g, int64_t n, const double* q,
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Fluctuating stress (Sec. 3: the stress sigma~ of Eq. vf, Gaussian, following the
+ * staggered fluctuating hydrodynamics the paper cites).  It is a random 3x3 tensor field
+ * W_ab, non-symmetric, each component an independent standard normal per cell, scaled to
+ * sigma~ = sqrt(2 eta kT / (h^3 dt)) W; the fluid receives the force density -D.sigma~.
+ * Placement on the MAC grid: W_aa at cell centres, W_ab (b != a) on the edge whose a and b
+ * coordinates are the integer multiples i_a h, i_b h.  Its divergence on the faces of
+ * component a is a backward difference of W_aa and forward differences of W_ab, so that
+ * D D^T = -L for each component: the covariance of the noise force is (2 eta kT/(h^3 dt))
+ * (-L), which makes the Crank-Nicolson update sample Eq. (ef) exactly at any dt. */
+
+/* Philox4x64-10 (Salmon, Moraes, Dror and Shaw, SC'11): ten rounds of two 64x64->128-bit
+ * multiplications on a 256-bit counter with a 128-bit key bumped by Weyl constants. */
+void mbref_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        unsigned __int128 p0 = (unsigned __int128)M0 * c0;
+        unsigned __int128 p1 = (unsigned __int128)M1 * c2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Nine standard normals of cell m of box `box` at step `step`: two Philox blocks with key
+ * (seed, 0) and counters (m, step, box, 0) and (m, step, box, 1); the 64-bit words x0..x4
+ * give five Box-Muller pairs, pair p from x_p: u1 = (lo32 + 1/2)/2^32, u2 = (hi32 + 1/2)/2^32,
+ * r = sqrt(-2 ln u1), normals r cos(2 pi u2), r sin(2 pi u2).  The ten normals, in order,
+ * are W_xx, W_xy, W_xz, W_yx, W_yy, W_yz, W_zx, W_zy, W_zz (the tenth is unused). */
+static void cell_normals(uint64_t seed, uint64_t step, int64_t box, int64_t m, double z[10])
+{
+    const uint64_t key[2] = {seed, 0};
+    uint64_t x[8];
+    for (int j = 0; j < 2; ++j) {
+        const uint64_t ctr[4] = {(uint64_t)m, step, (uint64_t)box, (uint64_t)j};
+        mbref_philox4x64(ctr, key, x + 4 * j);
+    }
+    for (int p = 0; p < 5; ++p) {
+        double u1 = ((double)(x[p] & 0xffffffffull) + 0.5) / 4294967296.0;
+        double u2 = ((double)(x[p] >> 32) + 0.5) / 4294967296.0;
+        double r = sqrt(-2.0 * log(u1));
+        z[2 * p] = r * cos(2.0 * MBREF_PI * u2);
+        z[2 * p + 1] = r * sin(2.0 * MBREF_PI * u2);
+    }
+}
+
+int mbref_stress_normals(const mbref_grid* g, uint64_t seed, uint64_t step, int64_t box,
+                         double* W)
+{
+    const int64_t N = (int64_t)g->nx * g->ny * g->nz;
+    for (int64_t m = 0; m < N; ++m) {
+        double z[10];
+        cell_normals(seed, step, box, m, z);
+        for (int c = 0; c < 9; ++c) W[c * N + m] = z[c];
+    }
+    return 0;
+}
+
+int mbref_stress_div(const mbref_grid* g, const double* W, double* f)
+{
+    const int n[3] = {g->nx, g->ny, g->nz};
+    const int64_t N = (int64_t)n[0] * n[1] * n[2];
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < n[2]; ++k)
+            for (int j = 0; j < n[1]; ++j)
+                for (int i = 0; i < n[0]; ++i) {
+                    const int idx[3] = {i, j, k};
+                    double d = 0.0;
+                    for (int b = 0; b < 3; ++b) {
+                        /* the two stress nodes of component (a, b) around this face */
+                        int lo[3] = {idx[0], idx[1], idx[2]}, hi[3] = {idx[0], idx[1], idx[2]};
+                        if (b == a) lo[b] = (int)wrap_index(idx[b] - 1, n[b]);   /* centres */
+                        else hi[b] = (int)wrap_index(idx[b] + 1, n[b]);          /* edges */
+                        const double* Wab = W + (3 * a + b) * N;
+                        d += Wab[((int64_t)hi[2] * n[1] + hi[1]) * n[0] + hi[0]]
+                           - Wab[((int64_t)lo[2] * n[1] + lo[1]) * n[0] + lo[0]];
+                    }
+                    f[a * N + ((int64_t)k * n[1] + j) * n[0] + i] = d / g->h;
+                }
+    return 0;
+}
+
+/* f += -D.sigma~ for the step `step` (nothing when noise is NULL or kT = 0). */
+static int add_stress_noise(const mbref_grid* g, const mbref_noise* noise, uint64_t step,
+                            double* f)
+{
+    if (!noise || noise->kT == 0.0) return 0;
+    const int64_t N = (int64_t)g->nx * g->ny * g->nz;
+    double* W = (double*)malloc(sizeof(double) * 9 * N);
+    double* d = (double*)malloc(sizeof(double) * 3 * N);
+    if (!W || !d) { free(W); free(d); return 2; }
+    mbref_stress_normals(g, noise->seed, step, noise->box, W);
+    const double amp = sqrt(2.0 * g->eta * noise->kT / (g->h * g->h * g->h * g->dt));
+    for (int64_t c = 0; c < 9 * N; ++c) W[c] *= amp;
+    mbref_stress_div(g, W, d);
+    for (int64_t c = 0; c < 3 * N; ++c) f[c] -= d[c];
+    free(W);
+    free(d);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Time step. */
 
 /* Periodic wrap into [0, L) for a displacement smaller than L. */
@@ -420,7 +531,7 @@ static double wrap_pos(double x, double L)
 int mbref_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
                const int32_t* pid, int64_t nbonds, const int32_t* bonds, const double* rest,
                double k_spring, double k_rep, double r_cut, const double* ext,
-               const double* body)
+               const double* body, const mbref_noise* noise)
 {
     const int64_t N = (int64_t)g->nx * g->ny * g->nz;
     const double L[3] = {g->nx * g->h, g->ny * g->h, g->nz * g->h};
@@ -447,6 +558,11 @@ int mbref_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
         mbref_pair_forces(g, n, qh, pid, k_rep, r_cut, F);
         /* neutrally buoyant blobs (m_e = 0): lambda_i = -F_i, so the fluid receives S F */
         mbref_spread(g, n, qh, F, f);
+        /* thermal stress of this step (Sec. 3), when kT > 0 */
+        if (add_stress_noise(g, noise, (noise ? noise->step0 : 0) + (uint64_t)s, f)) {
+            free(u); free(qh); free(F); free(f); free(vn); free(vm);
+            return 2;
+        }
         mbref_fluid_update(g, v, f, body, vn);
         /* corrector: q^{n+1} = q^n + dt J(q^{n+1/2}) (v^n + v^{n+1})/2 */
         for (int64_t c = 0; c < 3 * N; ++c) vm[c] = 0.5 * (v[c] + vn[c]);

@@ -73,19 +73,44 @@ int mbref_pair_forces_subset(const mbref_grid* g, int64_t n, const double* q,
                              const int32_t* pid, double k_rep, double r_cut, int64_t m,
                              const int64_t* idx, double* F);
 
+/* Thermal stress of the fluctuating ICM (Sec. 3, the stress sigma~ of Eq. vf):
+ * kT > 0 adds -D.sigma~, sigma~ = sqrt(2 eta kT/(h^3 dt)) W, to the force density of every
+ * step; W is drawn per (seed, step index, box, cell) by mbref_stress_normals, the step index
+ * of the s-th step of a call being step0 + s. */
+typedef struct {
+    double kT;
+    uint64_t seed;
+    uint64_t step0;
+    int64_t box;
+} mbref_noise;
+
+/* Philox4x64-10 counter-based generator: out = Philox(ctr, key). */
+void mbref_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+
+/* W [9][nz][ny][nx]: the standard normals of every cell (components xx, xy, xz, yx, yy, yz,
+ * zx, zy, zz), from Philox keyed by (seed, step, box, cell) with Box-Muller. */
+int mbref_stress_normals(const mbref_grid* g, uint64_t seed, uint64_t step, int64_t box,
+                         double* W);
+
+/* f [3][nz][ny][nx] = D.W, the MAC divergence of a stress field W [9][nz][ny][nx] placed
+ * with W_aa at cell centres and W_ab on edges (overwrites f). */
+int mbref_stress_div(const mbref_grid* g, const double* W, double* f);
+
 /* nsteps of the neutrally buoyant ICM step (midpoint blob update, CN fluid update),
- * updating q (wrapped into [0, L)) and v in place.  ext ([n][3]) and body may be NULL. */
+ * updating q (wrapped into [0, L)) and v in place.  ext ([n][3]), body and noise may be
+ * NULL. */
+int mbref_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
+               const int32_t* pid, int64_t nbonds, const int32_t* bonds, const double* rest,
+               double k_spring, double k_rep, double r_cut, const double* ext,
+               const double* body, const mbref_noise* noise);
+
 /* Stokes-limit steps (fluid inertia removed): explicit midpoint rule with the steady,
  * zero-mean Stokes flow of the current forces; v receives the last flow.  Same arguments as
- * mbref_step (rho and mean_mode of the grid are not used). */
+ * mbref_step without the noise (rho and mean_mode of the grid are not used). */
 int mbref_stokes_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
                       const int32_t* pid, int64_t nbonds, const int32_t* bonds,
                       const double* rest, double k_spring, double k_rep, double r_cut,
                       const double* ext, const double* body);
-int mbref_step(const mbref_grid* g, int nsteps, int64_t n, double* q, double* v,
-               const int32_t* pid, int64_t nbonds, const int32_t* bonds, const double* rest,
-               double k_spring, double k_rep, double r_cut, const double* ext,
-               const double* body);
 
 /* Particle translational velocity U0 = mean of u_i (Sec. 2) and angular velocity
  * Omega = I0^-1 sum_i s_i x (u_i - U0) (Eqs. torque, miner0), for np particles whose
