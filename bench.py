@@ -35,7 +35,7 @@ DENSE128_BLOBS, DENSE128_PARTICLES = 244504, 18808      # the recipe's counts at
 
 # Algorithmic bytes moved by each stage per step, per unit (documented in the design doc):
 #   grid real = 4 B (FP32) / 8 B (FP64); half-spectrum complex = 2 reals; blob FP64 vec = 24 B.
-def stage_model(n, nb, rsz, ncell):
+def stage_model(n, nb, rsz, ncell, thermal=False):
     N = n ** 3
     grid = 3 * N * rsz                                  # one 3-component grid
     spec = 3 * n * n * (n // 2 + 1) * 2 * rsz           # one 3-component half spectrum
@@ -48,6 +48,8 @@ def stage_model(n, nb, rsz, ncell):
         "forces": ("hbm", nb * (24 + 4 + 4 + 2 * 42 / 13 * 12 + 24 + 48)),
         "force_sum": ("hbm", 0),
         "spread": ("hbm", 48 * nb + grid),               # sorted (q, F) records; write f
+        # thermal stress (kT > 0 only): write 9 stress grids, read them and f, write f
+        "thermal_noise": ("hbm", 3 * grid + 3 * grid + 2 * grid if thermal else 0),
         "fluid_x_fwd": ("hbm", 2 * grid + spec),         # read v, f; write spectrum
         "fluid_y_fwd": ("hbm", 0),                       # no kernel in the three-pass FFT
         "fluid_z_solve": ("hbm", 2 * spec),

@@ -74,8 +74,20 @@ typedef enum {
  *   mean_mode    0: the k = 0 fluid mode carries the net momentum, rho L^3 d(mean v)/dt =
  *                sum of blob forces (+ mean body force); 1: the k = 0 mode is held at zero
  *                (the frame of Hasimoto's periodic drag, Eq. rhinf).
- *   kT           must be 0 (no fluctuating stress).
- *   seed         reserved for the fluctuating stress.
+ *   kT           thermal energy, >= 0.  kT > 0 adds the fluctuating stress of Sec. 3 (the
+ *                Gaussian stress sigma~ of Eq. vf; integrator 0 only): every step the fluid
+ *                receives -D.sigma~ with sigma~ = sqrt(2 eta kT/(h^3 dt)) W, W a
+ *                non-symmetric 3x3 tensor of standard normals per cell (W_aa at cell
+ *                centres, W_ab on the edges at integer a and b coordinates), so that the
+ *                fluid velocity samples Eq. (ef), variance kT/(rho h^3) per projected mode.
+ *                The nine normals of cell m (x fastest) of box b at step index n come from
+ *                two Philox4x64-10 blocks, key (seed, 0), counters (m, n, b, 0) and
+ *                (m, n, b, 1); the 64-bit words x0..x4 give five Box-Muller pairs (from x_p:
+ *                u1 = (low 32 bits + 1/2)/2^32, u2 = (high 32 bits + 1/2)/2^32,
+ *                sqrt(-2 ln u1) (cos, sin)(2 pi u2)), whose first nine values are W_xx,
+ *                W_xy, W_xz, W_yx, W_yy, W_yz, W_zx, W_zy, W_zz.  No drift term is added
+ *                (neutrally buoyant blobs, m_e = 0).
+ *   seed         key of the thermal stress (see kT).
  *   integrator   0: the inertial coupling method (Sec. 3: fluid and blob inertia, midpoint
  *                predictor/corrector for the blobs, Crank-Nicolson for the fluid).  1: its
  *                Stokes limit (Sc -> infinity, the regime of the paper's viscosity runs): each
@@ -188,12 +200,21 @@ mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos);
  * disabling) resets the totals.  mb_get_stage_times waits for the recorded steps, then copies
  * up to max_stages totals (milliseconds) and call counts, and sets *n_stages to the number of
  * stages; mb_stage_name gives a stage's name ("" if out of range).
- * Stages, in launch order: interp_predict, bin, forces, force_sum, spread, fluid_x_fwd,
- * fluid_y_fwd, fluid_z_solve, fluid_y_inv, fluid_x_inv, interp_correct. */
+ * Stages, in launch order: interp_predict, bin, forces, force_sum, spread, thermal_noise,
+ * fluid_x_fwd, fluid_y_fwd, fluid_z_solve, fluid_y_inv, fluid_x_inv, interp_correct. */
 mb_status mb_set_stage_timing(mb_ctx* ctx, int enable);
 mb_status mb_get_stage_times(mb_ctx* ctx, int max_stages, double* ms_total,
                              int64_t* calls, int* n_stages);
 const char* mb_stage_name(int stage);
+
+/* The step index n that keys the thermal stress of the next step (see kT above).  It starts
+ * at 0 when the context is created and every step of a context with kT > 0 advances it by one;
+ * setting it, together with mb_set_positions and mb_set_velocity_field, resumes a
+ * fluctuating run from a checkpoint with the same noise.  The paper has no counterpart of
+ * this index: it fixes the random-number stream that its Gaussian stress (Sec. 3) leaves
+ * open.  mb_get_step_index waits for the context stream. */
+mb_status mb_set_step_index(mb_ctx* ctx, uint64_t step);
+mb_status mb_get_step_index(mb_ctx* ctx, uint64_t* step);
 
 /* Number of CUDA kernels the context's steps have launched so far. */
 mb_status mb_get_launch_count(const mb_ctx* ctx, int64_t* launches);

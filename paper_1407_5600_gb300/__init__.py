@@ -111,6 +111,8 @@ def load_library(path: str | None = None):
         "mb_velocity_adjoint": [P, P, P, P, P, P],
         "mb_get_stage_times": [P, I, P, P, ctypes.POINTER(I)],
         "mb_get_launch_count": [P, ctypes.POINTER(I64)],
+        "mb_set_step_index": [P, ctypes.c_uint64],
+        "mb_get_step_index": [P, ctypes.POINTER(ctypes.c_uint64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -260,6 +262,17 @@ def set_positions(ctx, pos):
     _check(ctx, load_library().mb_set_positions(ctx, _ptr(pos, np.float64)))
 
 
+def set_step_index(ctx, step):
+    """mb_set_step_index: the step index keying the next step's thermal stress."""
+    _check(ctx, load_library().mb_set_step_index(ctx, int(step)))
+
+
+def get_step_index(ctx):
+    n = ctypes.c_uint64()
+    _check(ctx, load_library().mb_get_step_index(ctx, ctypes.byref(n)))
+    return n.value
+
+
 def adjoint_step(ctx, pos_n, grid_v_n, ext_blob_force, body_force, grad_pos, grad_v,
                  grad_k_spring=None):
     """mb_adjoint_step: overwrites grad_pos and grad_v in place, adds to grad_k_spring[0]."""
@@ -393,6 +406,15 @@ class Multiblob:
 
     def set_velocity_field(self, v):
         set_velocity_field(self.ctx, self._dev(v, self.grid_dtype))
+
+    @property
+    def step_index(self):
+        """Index keying the next step's thermal stress (settable, for resuming a run)."""
+        return get_step_index(self.ctx)
+
+    @step_index.setter
+    def step_index(self, n):
+        set_step_index(self.ctx, n)
 
     def spread(self, pos, F):
         out = self.torch.empty(self.grid_shape(1), dtype=self.grid_dtype, device=self.device)

@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libmb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["mb_api.cu", "kernels_blob.cu", "kernels_blob32.cu", "kernels_fft.cu",
            "kernels_fft3.cu", "adjoint.cu",
-           "spread_static.cu"]
+           "spread_static.cu", "kernels_noise.cu"]
 
 
 def nvcc() -> str:

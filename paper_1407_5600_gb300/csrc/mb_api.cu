@@ -23,12 +23,13 @@ constexpr int SYM_LEN = 256;   // per-dimension symbol table length (n <= 128 to
 
 // Stages of one step, in launch order (names returned by mb_stage_name).
 enum Stage {
-    ST_INTERP_PREDICT, ST_BIN, ST_FORCES, ST_FORCE_SUM, ST_SPREAD, ST_FLUID_X_FWD,
+    ST_INTERP_PREDICT, ST_BIN, ST_FORCES, ST_FORCE_SUM, ST_SPREAD, ST_THERMAL, ST_FLUID_X_FWD,
     ST_FLUID_Y_FWD, ST_FLUID_Z_SOLVE, ST_FLUID_Y_INV, ST_FLUID_X_INV, ST_INTERP_CORRECT,
     NUM_STAGES
 };
 const char* const STAGE_NAMES[NUM_STAGES] = {
-    "interp_predict", "bin", "forces", "force_sum", "spread", "fluid_x_fwd", "fluid_y_fwd",
+    "interp_predict", "bin", "forces", "force_sum", "spread", "thermal_noise", "fluid_x_fwd",
+    "fluid_y_fwd",
     "fluid_z_solve", "fluid_y_inv", "fluid_x_inv", "interp_correct"};
 
 thread_local std::string g_create_error;
@@ -132,6 +133,11 @@ struct mb_ctx {
     int tile[3] = {8, 8, 8};
 
     DBuf v[2], vsum, f, spec, vbar, fsum, tw[3], twf[3], sym, symr, body_prof, prof_scratch;
+    // thermal stress (kT > 0): sigma~ of the current step [B][9][N] and the step index that
+    // keys its random numbers (device memory, advanced by the step itself)
+    bool thermal = false;
+    double thermal_amp = 0.0;
+    DBuf W, step_index;
     int fft_passes = 3;     // 3: plane/z/plane pipeline; 5: one pass per axis (reference layout)
     int cur = 0;
     int64_t steps_taken = 0;
@@ -666,8 +672,16 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
                                      ctx->tile, static_cast<R*>(ctx->f.p)));
         ctx->launches += 1;
     }
+    mark(ST_THERMAL);
+    if (ctx->thermal) {
+        MB_CUDA(launch_thermal_stress<R>(st, B, g, ctx->d.seed,
+                                         static_cast<uint64_t*>(ctx->step_index.p),
+                                         ctx->thermal_amp, static_cast<R*>(ctx->W.p),
+                                         static_cast<R*>(ctx->f.p), blobs));
+        ctx->launches += THERMAL_KERNELS;
+    }
     const double* mean = ctx->d.mean_mode == 0 ? static_cast<const double*>(ctx->vbar.p) : nullptr;
-    FluidArgs<R> fa = fluid_args<R>(ctx, vcur, blobs ? ctx->f.p : nullptr, vnext,
+    FluidArgs<R> fa = fluid_args<R>(ctx, vcur, blobs || ctx->thermal ? ctx->f.p : nullptr, vnext,
                                     ctx->body_prof.p, body, mean);
     cudaEvent_t* fm = ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr;
     if (ctx->fft_passes == 5) {
@@ -762,6 +776,7 @@ mb_status do_step_stokes(mb_ctx* ctx, const double* ext, const double* body)
                                          ctx->bg, ctx->tile, static_cast<R*>(ctx->f.p)));
             ctx->launches += 1;
         }
+        if (marks) mark(ST_THERMAL);       // no thermal stress in this integrator
         FluidArgs<R> fa = fluid_args<R>(ctx, v_out, blobs ? ctx->f.p : nullptr, v_out,
                                         ctx->body_prof.p, body, nullptr);
         fa.no_v = 1;                        // right-hand side S F + f_body
@@ -882,8 +897,16 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                                 ctx->tile, static_cast<float*>(ctx->f.p), ctx->f_zero));
         ctx->launches += 1;
     }
-    FluidArgs<float> fa = fluid_args<float>(ctx, vcur, blobs ? ctx->f.p : nullptr, vnext,
-                                            ctx->body_prof.p, body, nullptr);
+    mark(ST_THERMAL);
+    if (ctx->thermal) {
+        MB_CUDA(launch_thermal_stress<float>(st, B, g, ctx->d.seed,
+                                             static_cast<uint64_t*>(ctx->step_index.p),
+                                             ctx->thermal_amp, static_cast<float*>(ctx->W.p),
+                                             static_cast<float*>(ctx->f.p), blobs));
+        ctx->launches += THERMAL_KERNELS;
+    }
+    FluidArgs<float> fa = fluid_args<float>(ctx, vcur, blobs || ctx->thermal ? ctx->f.p : nullptr,
+                                            vnext, ctx->body_prof.p, body, nullptr);
     if (ctx->d.mean_mode == 0) {
         const double L3 = g.L[0] * g.L[1] * g.L[2];
         if (ctx->fft_passes == 3) {
@@ -1268,8 +1291,8 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
         g_create_error = "mean_mode must be 0 (conserve) or 1 (zero)";
         return MB_EINVAL;
     }
-    if (d.kT != 0.0) {
-        g_create_error = "fluctuating hydrodynamics (kT != 0) is not provided; set kT = 0";
+    if (!(d.kT >= 0.0 && std::isfinite(d.kT))) {
+        g_create_error = "kT must be finite and >= 0";
         return MB_EINVAL;
     }
     if (d.integrator != 0 && d.integrator != 1) {
@@ -1278,6 +1301,10 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     }
     if (d.integrator == 1 && d.mean_mode != 1) {
         g_create_error = "the Stokes limit has no steady mean flow under a net force: set mean_mode = 1";
+        return MB_EINVAL;
+    }
+    if (d.integrator == 1 && d.kT != 0.0) {
+        g_create_error = "the Stokes-limit integrator is deterministic: set kT = 0";
         return MB_EINVAL;
     }
     mb_ctx* ctx = new (std::nothrow) mb_ctx();
@@ -1321,6 +1348,12 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     if ((s = ensure(ctx->spec, sb, ctx->err, "spectrum")) != MB_OK) return fail(s);
     if ((s = ensure(ctx->vbar, sizeof(double) * 3 * ctx->B, ctx->err, "vbar")) != MB_OK) return fail(s);
     if ((s = ensure(ctx->fsum, sizeof(double) * 3 * ctx->B, ctx->err, "fsum")) != MB_OK) return fail(s);
+    if ((s = ensure(ctx->step_index, sizeof(uint64_t), ctx->err, "step index")) != MB_OK) return fail(s);
+    ctx->thermal = d.kT > 0.0;
+    if (ctx->thermal) {
+        if ((s = ensure(ctx->W, 3 * gb, ctx->err, "thermal stress")) != MB_OK) return fail(s);
+        ctx->thermal_amp = std::sqrt(2.0 * d.eta * d.kT / (d.h * d.h * d.h * d.dt));
+    }
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
         cudaGetLastError();
         ctx->err = "no CUDA device";
@@ -1328,7 +1361,8 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     }
     if (cudaMemsetAsync(ctx->v[0].p, 0, gb, ctx->st) != cudaSuccess ||
         cudaMemsetAsync(ctx->v[1].p, 0, gb, ctx->st) != cudaSuccess ||
-        cudaMemsetAsync(ctx->vbar.p, 0, sizeof(double) * 3 * ctx->B, ctx->st) != cudaSuccess) {
+        cudaMemsetAsync(ctx->vbar.p, 0, sizeof(double) * 3 * ctx->B, ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->step_index.p, 0, sizeof(uint64_t), ctx->st) != cudaSuccess) {
         cudaGetLastError();
         ctx->err = "cudaMemsetAsync failed";
         return fail(MB_ECUDA);
@@ -1525,6 +1559,29 @@ mb_status mb_get_stage_times(mb_ctx* ctx, int max_stages, double* ms_total,
 const char* mb_stage_name(int stage)
 {
     return stage >= 0 && stage < NUM_STAGES ? STAGE_NAMES[stage] : "";
+}
+
+mb_status mb_set_step_index(mb_ctx* ctx, uint64_t step)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    MB_CUDA(cudaMemcpyAsync(ctx->step_index.p, &step, sizeof(uint64_t), cudaMemcpyHostToDevice,
+                            ctx->st));
+    MB_CUDA(cudaStreamSynchronize(ctx->st));
+    return MB_OK;
+}
+
+mb_status mb_get_step_index(mb_ctx* ctx, uint64_t* step)
+{
+    if (!ctx) return MB_EINVAL;
+    if (!step) return invalid(ctx, "step must be non-null");
+    DeviceGuard dg(ctx->device);
+    uint64_t v = 0;
+    MB_CUDA(cudaMemcpyAsync(&v, ctx->step_index.p, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                            ctx->st));
+    MB_CUDA(cudaStreamSynchronize(ctx->st));
+    *step = v;
+    return MB_OK;
 }
 
 mb_status mb_get_launch_count(const mb_ctx* ctx, int64_t* launches)
