@@ -56,7 +56,8 @@ typedef enum {
 } mb_status;
 
 /* Grid and fluid description.
- *   nx, ny, nz   cells per box side: powers of two in [4, 128].
+ *   nx, ny, nz   cells per box side: powers of two in [4, 256].  Sides above 128 run the
+ *                fluid solve as five one-axis passes (see MB_FFT_PASSES above).
  *   batch        number of independent periodic boxes B >= 1 sharing the same geometry.
  *   h            mesh size (> 0); box side L_a = n_a h.
  *   rho, eta     fluid density and shear viscosity (> 0).

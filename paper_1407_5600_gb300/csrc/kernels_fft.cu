@@ -87,11 +87,14 @@ k_rhs_fft_x(FluidArgs<R> a, GridGeo g, int RP)
         const int y = 2 * yp0 + r;
         const int yp = (y + 1) & (ny - 1), ym = (y - 1) & (ny - 1);
         const int xp = (x + 1) & (nx - 1), xm = (x - 1) & (nx - 1);
-        const R vcen = vc[(z0 + y) * nx + x];
-        const R lap = ((vc[(z0 + y) * nx + xp] + vc[(z0 + y) * nx + xm]) +
-                       (vc[(z0 + yp) * nx + x] + vc[(z0 + ym) * nx + x]) +
-                       (vc[(zp + y) * nx + x] + vc[(zm + y) * nx + x]) - R(6) * vcen) * ih2;
-        R val = rho_dt * vcen + half_eta * lap;
+        R val = R(0);               // Stokes limit (no_v): the right-hand side is f + f_body
+        if (!a.no_v) {
+            const R vcen = vc[(z0 + y) * nx + x];
+            const R lap = ((vc[(z0 + y) * nx + xp] + vc[(z0 + y) * nx + xm]) +
+                           (vc[(z0 + yp) * nx + x] + vc[(z0 + ym) * nx + x]) +
+                           (vc[(zp + y) * nx + x] + vc[(zm + y) * nx + x]) - R(6) * vcen) * ih2;
+            val = rho_dt * vcen + half_eta * lap;
+        }
         if (fc) val += fc[(z0 + y) * nx + x];
         if (body) val += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y : z)];
         T* slot = sb + (r >> 1) * ld + x;

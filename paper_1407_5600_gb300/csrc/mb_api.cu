@@ -783,9 +783,14 @@ mb_status do_step_stokes(mb_ctx* ctx, const double* ext, const double* body)
         fa.rho_dt = 0.0;                    // divide by eta lambda: steady Stokes
         fa.half_eta = ctx->d.eta;
         fa.mean_mode = 1;
-        MB_CUDA(launch_fluid3<R>(st, B, g, fa, marks && ctx->timing ? ctx->ev + ST_FLUID_X_FWD
-                                                                     : nullptr));
-        ctx->launches += FLUID3_KERNELS;
+        cudaEvent_t* fm = marks && ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr;
+        if (ctx->fft_passes == 5) {
+            MB_CUDA(launch_fluid<R>(st, B, g, fa, fm));
+            ctx->launches += FLUID_KERNELS;
+        } else {
+            MB_CUDA(launch_fluid3<R>(st, B, g, fa, fm));
+            ctx->launches += FLUID3_KERNELS;
+        }
         return MB_OK;
     };
     mark(ST_INTERP_PREDICT);
@@ -1262,8 +1267,8 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     const mb_grid_desc& d = *desc;
     const int ns[3] = {d.nx, d.ny, d.nz};
     for (int a = 0; a < 3; ++a)
-        if (!is_pow2(ns[a]) || ns[a] < 4 || ns[a] > 128) {
-            g_create_error = "nx, ny, nz must be powers of two in [4, 128]";
+        if (!is_pow2(ns[a]) || ns[a] < 4 || ns[a] > 256) {
+            g_create_error = "nx, ny, nz must be powers of two in [4, 256]";
             return MB_EINVAL;
         }
     if (d.batch < 1 || d.batch > 65535) {
@@ -1326,6 +1331,9 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     ctx->nxh = ns[0] / 2 + 1;
     ctx->boxes.resize(ctx->B);
     if (const char* e = std::getenv("MB_FFT_PASSES")) ctx->fft_passes = std::atoi(e) == 5 ? 5 : 3;
+    // the three-pass pipeline holds whole planes and lines of up to 128 points on chip; longer
+    // sides take the five-pass pipeline (one radix-2 pass per axis, lines of up to 256 points)
+    if (ns[0] > 128 || ns[1] > 128 || ns[2] > 128) ctx->fft_passes = 5;
     if (const char* e = std::getenv("MB_NO_GRAPH")) ctx->use_graph = std::atoi(e) == 0;
     if (const char* e = std::getenv("MB_NO_AUTOTUNE")) ctx->autotune = std::atoi(e) == 0;
     if (const char* e = std::getenv("MB_NO_FUSE_INTERP")) ctx->fuse_interp = std::atoi(e) == 0;
@@ -2044,12 +2052,12 @@ mb_status mb_fluid_update(mb_ctx* ctx, const void* v_in, const void* f, const do
     if (ctx->rsz == 4) {
         FluidArgs<float> a = fluid_args<float>(ctx, vd, fd, dst, ctx->prof_scratch.p, body_force, nullptr);
         if (stokes) stokes_args(a);
-        if (ctx->fft_passes == 5 && !stokes) MB_CUDA(launch_fluid<float>(ctx->st, 1, ctx->g, a));
+        if (ctx->fft_passes == 5) MB_CUDA(launch_fluid<float>(ctx->st, 1, ctx->g, a));
         else MB_CUDA(launch_fluid3<float>(ctx->st, 1, ctx->g, a));
     } else {
         FluidArgs<double> a = fluid_args<double>(ctx, vd, fd, dst, ctx->prof_scratch.p, body_force, nullptr);
         if (stokes) stokes_args(a);
-        if (ctx->fft_passes == 5 && !stokes) MB_CUDA(launch_fluid<double>(ctx->st, 1, ctx->g, a));
+        if (ctx->fft_passes == 5) MB_CUDA(launch_fluid<double>(ctx->st, 1, ctx->g, a));
         else MB_CUDA(launch_fluid3<double>(ctx->st, 1, ctx->g, a));
     }
     return finish_out(ctx, v_out, dst, by, host);

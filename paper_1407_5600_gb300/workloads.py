@@ -185,6 +185,7 @@ class GridSpec:
     eta: float = 1.0
     dt: float = 0.05
     mean_mode: int = 0
+    kT: float = 0.0
 
 
 def single_particle(n=32, a=1.0, seed=1, force_x=1e-3, k_spring=100.0):
@@ -246,6 +247,19 @@ def dense_suspension(n=128, a=2.2, phi=0.40, seed=3, f0=1e-4, k_spring=100.0,
     s.meta = {"workload": f"dense suspension {n}^3 a={a}h phi={phi}", "seed": seed,
               "n_particles": n_particles}
     return GridSpec(n, n, n, dt=0.05, mean_mode=0), s
+
+
+def fluctuating_suspension(n=256, a=3.2, phi=0.30, kT=1e-3, seed=5, mc_sweeps=3,
+                           k_spring=100.0, k_rep=100.0, r_cut=1.0):
+    """Thermal suspension (fluctuating stress, Sec. 3 and Eq. ef): the dense-suspension recipe
+    at radius a and volume fraction phi, at rest (no body force), with thermal energy kT
+    (spec.kT) for the equipartition and velocity-autocorrelation runs."""
+    spec, s = dense_suspension(n=n, a=a, phi=phi, seed=seed, k_spring=k_spring, k_rep=k_rep,
+                               r_cut=r_cut, mc_sweeps=mc_sweeps)
+    s.body = None
+    s.meta["workload"] = f"fluctuating suspension {n}^3 a={a}h phi={phi} kT={kT}"
+    spec.kT = kT
+    return spec, s
 
 
 def dilute_random(n=64, n_particles=64, a=2.0, seed=4, k_spring=100.0):
