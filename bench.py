@@ -117,6 +117,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the FP64 grid variant (default: min(steps, 10))")
+    ap.add_argument("--other-steps", type=int, default=20,
+                    help="timed steps of the Stokes-limit and fluctuating 256^3 runs (0: skip)")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--stage-json", default=None, help="also write per-stage times here")
     ap.add_argument("--ref-seconds", type=float, default=None,
@@ -276,7 +278,7 @@ def run_ours(args):
         if dist:
             dist.barrier()
 
-    def timed_steps(sim, K, stage_timing):
+    def timed_steps(sim, K, stage_timing, body=s.body):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(K)]
         if stage_timing:
@@ -286,7 +288,7 @@ def run_ours(args):
         for i in range(K):
             flush.fill_(i & 0xFF)                     # evict L2 between timed steps
             evs[i][0].record(stream)
-            mb.step(sim.ctx, 1, None, s.body)
+            mb.step(sim.ctx, 1, None, body)
             evs[i][1].record(stream)
         barrier()
         ms = sum(a.elapsed_time(b) for a, b in evs)
@@ -379,6 +381,44 @@ def run_ours(args):
                 "ms_per_step": ms64 / K64, "steps": K64,
                 "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stages64.items()}}
 
+    # ---- the other integrators (FP32 grid), for the record: the Stokes limit on the same
+    # suspension, and the fluctuating 256^3 suspension (kT = 1e-3, five-pass FFT) ---------
+    others = None
+    if args.other_steps > 0:
+        K2 = args.other_steps
+        others = {}
+        simS = mb.Multiblob(mb.GridDesc(n, n, n, precision=0, dt=spec.dt, eta=spec.eta, h=spec.h,
+                                        mean_mode=1, integrator=1), stream=stream, device=dev)
+        simS.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut)
+        for _ in range(3):
+            mb.step(simS.ctx, 1, None, s.body)
+        msS, _, stS = timed_steps(simS, K2, True)
+        simS.close()
+        msS = max_over_ranks(msS)
+        others["stokes_limit_dense128"] = {
+            "value": world * cells * K2 / (msS * 1e-3), "unit": "cell-steps/s",
+            "ms_per_step": msS / K2, "steps": K2,
+            "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stS.items()}}
+        spec5, s5 = wl.fluctuating_suspension(n=256, a=3.2, phi=0.30, kT=1e-3, seed=5 + rank)
+        n5 = spec5.nx
+        sim5 = mb.Multiblob(mb.GridDesc(n5, n5, n5, precision=0, dt=spec5.dt, eta=spec5.eta,
+                                        h=spec5.h, mean_mode=spec5.mean_mode, kT=spec5.kT,
+                                        seed=17 + rank), stream=stream, device=dev)
+        sim5.set_particles(0, s5.pos, s5.pid, s5.bonds, s5.rest, s5.k_spring, s5.k_rep,
+                           s5.r_cut)
+        for _ in range(3):
+            mb.step(sim5.ctx, 1, None, None)
+        ms5, _, _ = timed_steps(sim5, K2, False, body=None)
+        _, _, st5 = timed_steps(sim5, K2, True, body=None)
+        sim5.close()
+        ms5 = max_over_ranks(ms5)
+        others["fluctuating_256"] = {
+            "workload": s5.meta["workload"] + f", {s5.n_particles} particles x 13 blobs",
+            "value": world * n5 ** 3 * K2 / (ms5 * 1e-3), "unit": "cell-steps/s",
+            "blob_steps_per_s": world * s5.n_blobs * K2 / (ms5 * 1e-3),
+            "ms_per_step": ms5 / K2, "steps": K2,
+            "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in st5.items()}}
+
     # ---- CPU baseline (oracle, rank 0, N = 1 only) ---------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
@@ -401,6 +441,7 @@ def run_ours(args):
             "roofline": roofline,
             "stages": per_stage,
             "fp64": fp64,
+            "other_integrators": others,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),

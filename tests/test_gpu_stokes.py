@@ -144,3 +144,28 @@ def test_stokes_invalid_configurations():
         with pytest.raises(mb.MBError, match="inertial coupling"):
             mb.adjoint_step(sim.ctx, s.pos.copy(), v, None, None, np.zeros_like(s.pos),
                             np.zeros_like(v))
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_torque_driven_rotation_parity(prec):
+    """A couple of blob forces on a d = 2h icosahedron (the rotlet experiment): the particle
+    angular velocity Omega and drift U0 follow the oracle."""
+    n = 32
+    rng = np.random.default_rng(3)
+    a = 2.0 * np.sqrt(10 + 2 * np.sqrt(5)) / 4
+    s = wl.build_particles(np.array([13.3, 15.1, 16.7]), a, rng, np.array([32.0] * 3))
+    r = s.pos - s.pos.mean(axis=0)
+    T = np.array([2e-4, -5e-4, 1e-3])
+    F = np.cross(T, r) / np.sum(r ** 2) * 1.5            # a couple (zero net force)
+    d = _desc((n, n, n), prec, dt=0.05)
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, 200.0)
+        sim.step(12, ext_blob_force=F)
+        U, W = (to_np(x) for x in sim.particle_velocities())
+        q = to_np(sim.blob_positions())
+    g = _oracle_grid(d)
+    q_ref, v_ref = oracle.stokes_step(g, 12, s.pos, s.pid, s.bonds, s.rest, 200.0, ext=F)
+    U_ref, W_ref = oracle.particle_velocities(g, q_ref, oracle.interp(g, q_ref, v_ref), s.pid, 1)
+    assert position_error(q, q_ref, s.pos, g.L, 12) < TOL[prec]
+    assert rel_l2(W, W_ref) < TOL[prec]
+    assert np.max(np.abs(U - U_ref)) < TOL[prec] * np.max(np.abs(W_ref)) * a

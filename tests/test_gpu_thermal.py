@@ -153,3 +153,33 @@ def test_fluid_equipartition_fp32():
 def test_stokes_integrator_rejects_kT():
     with pytest.raises(mb.MBError, match="deterministic"):
         mb.Multiblob(mb.GridDesc(8, 8, 8, integrator=1, mean_mode=1, kT=1e-3))
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_particle_velocity_autocorrelation_matches_oracle(prec):
+    """Thermal 32^3 run (the small-box check of the fluctuating suspension): the particle
+    velocities U0(t), and so their autocorrelation, follow the oracle step by step with the
+    same Philox stream."""
+    spec, s = wl.dilute_random(n=32, n_particles=6, a=2.0, seed=12)
+    d = mb.GridDesc(32, 32, 32, dt=0.05, precision=prec, mean_mode=0, kT=1e-3, seed=31)
+    T = 60
+    U_gpu = []
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring)
+        for _ in range(T):
+            sim.step(1)
+            U_gpu.append(to_np(sim.particle_velocities()[0]))
+    g = _oracle_grid(d)
+    q, v = s.pos.copy(), g.zeros()
+    U_ref = []
+    for t in range(T):
+        q, v = oracle.step(g, 1, q, v, s.pid, s.bonds, s.rest, s.k_spring, kT=d.kT,
+                           seed=d.seed, step0=t)
+        U_ref.append(oracle.particle_velocities(g, q, oracle.interp(g, q, v), s.pid,
+                                                s.n_particles)[0])
+    U_gpu, U_ref = np.array(U_gpu), np.array(U_ref)
+    assert rel_l2(U_gpu, U_ref) < TOL[prec]
+
+    def vaf(U):
+        return np.array([np.mean(np.sum(U[:T - k] * U[k:], axis=-1)) for k in range(T // 2)])
+    assert rel_l2(vaf(U_gpu), vaf(U_ref)) < 4 * TOL[prec]

@@ -137,3 +137,30 @@ def test_midpoint_rule_is_second_order():
     e1 = np.linalg.norm(out[0] - out[1])
     e2 = np.linalg.norm(out[1] - out[2])
     assert 3.2 < e1 / e2 < 4.8, (e1, e2)
+
+
+@pytest.mark.parametrize("d,tol", [(1.0, 0.04), (1.5, 0.04), (2.0, 0.05), (2.5, 0.04),
+                                   (3.0, 0.08)])
+def test_rotlet_radius_matches_table(d, tol):
+    """A couple of blob forces (torque T, no net force) on a relaxed icosahedron: the Stokes
+    rotation rate is T / (8 pi eta R_r^3), R_r the rotlet radius of Table rad (its finite-box
+    correction is O((R/L)^3), negligible at L = 32h).  The table's R_r comes from integrating
+    the angular-velocity autocorrelation of noisy runs, so the tolerances allow a few percent
+    (largest at d = 3h, where R_r sits between R_H and R_I)."""
+    t = json.load(open(os.path.join(GOLD, "table_rad.json")))["rotlet"]
+    R_r = {row[0]: row[1] for row in t["rows"]}[d]
+    n, eta = 32, 1.0
+    g = mb.Grid(n, n, n, eta=eta, dt=0.05, mean_mode=1)
+    rng = np.random.default_rng(3)
+    a = d * np.sqrt(10 + 2 * np.sqrt(5)) / 4
+    s = wl.build_particles(np.array([13.3, 15.1, 16.7]), a, rng, g.L)
+    r = s.pos - s.pos.mean(axis=0)
+    T = np.array([0.0, 0.0, 1e-3])
+    F = np.cross(T, r) / np.sum(r[:, :2] ** 2)          # sum F = 0, sum r x F = T
+    q, v = mb.stokes_step(g, 30, s.pos, s.pid, s.bonds, s.rest, 200.0, ext=F)
+    U, W = mb.particle_velocities(g, q, mb.interp(g, q, v), s.pid, 1)
+    R_fit = (T[2] / (8 * np.pi * eta * W[0, 2])) ** (1.0 / 3.0)
+    assert abs(R_fit / R_r - 1.0) < tol, R_fit
+    # rotation about the torque axis; the grid couples a little translation to it
+    assert np.max(np.abs(W[0, :2])) < 0.01 * abs(W[0, 2])
+    assert np.max(np.abs(U)) < 0.03 * abs(W[0, 2]) * a
