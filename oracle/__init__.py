@@ -40,7 +40,8 @@ def build(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_double), ("rho", ctypes.c_double), ("eta", ctypes.c_double),
-                ("dt", ctypes.c_double), ("mean_mode", ctypes.c_int)]
+                ("dt", ctypes.c_double), ("mean_mode", ctypes.c_int),
+                ("advection", ctypes.c_int)]
 
 
 class _Noise(ctypes.Structure):
@@ -74,6 +75,7 @@ def _load():
                            ctypes.POINTER(_Noise)],
             "mbref_stress_normals": [G, ctypes.c_uint64, ctypes.c_uint64, I64, P],
             "mbref_stress_div": [G, P, P],
+            "mbref_advection": [G, P, P],
             "mbref_stokes_step": [G, ctypes.c_int, I64, P, P, P, I64, P, P, D, D, D, P, P],
             "mbref_particle_velocities": [G, I64, P, P, P, I64, P, P],
         }.items():
@@ -95,6 +97,7 @@ class Grid:
     eta: float = 1.0
     dt: float = 0.05
     mean_mode: int = 0   # 0: mean momentum follows the net force; 1: mean held at zero
+    advection: int = 0   # 1: the convective stress rho v v, explicit at v^n
 
     @property
     def shape(self):
@@ -106,7 +109,7 @@ class Grid:
 
     def _c(self):
         return ctypes.byref(_Grid(self.nx, self.ny, self.nz, self.h, self.rho, self.eta,
-                                  self.dt, self.mean_mode))
+                                  self.dt, self.mean_mode, self.advection))
 
     def zeros(self):
         return np.zeros((3,) + self.shape)
@@ -244,6 +247,14 @@ def stress_div(g: Grid, W):
     f = g.zeros()
     _check(_load().mbref_stress_div(g._c(), Wp, f.ctypes.data_as(ctypes.c_void_p)), "stress_div")
     return f
+
+
+def advection(g: Grid, v):
+    """D.(v v), the convective term on the MAC faces; returns [3][nz][ny][nx]."""
+    v, vp = _d(v)
+    out = g.zeros()
+    _check(_load().mbref_advection(g._c(), vp, out.ctypes.data_as(ctypes.c_void_p)), "advection")
+    return out
 
 
 def step(g: Grid, nsteps, q, v, pid, bonds, rest, k_spring, k_rep=0.0, r_cut=0.0,

@@ -321,6 +321,14 @@ int mbref_fluid_update(const mbref_grid* g, const double* v, const double* f,
         for (int64_t c = 0; c < N; ++c)
             rhs[a * N + c] = g->rho / g->dt * v[a * N + c] + 0.5 * g->eta * lap[c] + f[a * N + c];
     }
+    if (g->advection) {
+        /* convective stress rho v v of Eq. (vf), explicit at v^n */
+        double* adv = (double*)malloc(sizeof(double) * 3 * N);
+        if (!adv) { free(rhs); free(lap); return 2; }
+        mbref_advection(g, v, adv);
+        for (int64_t c = 0; c < 3 * N; ++c) rhs[c] -= g->rho * adv[c];
+        free(adv);
+    }
     if (body) add_body_force(g, body, rhs);
     int rc = spectral_solve(g, rhs, g->rho / g->dt, 0.5 * g->eta, g->mean_mode == 1, v_out);
     free(rhs);
@@ -491,6 +499,48 @@ int mbref_stress_div(const mbref_grid* g, const double* W, double* f)
                     }
                     f[a * N + ((int64_t)k * n[1] + j) * n[0] + i] = d / g->h;
                 }
+    return 0;
+}
+
+/* The convective tensor M_ab = v_a v_b at the stress nodes: for a = b the square of the mean
+ * of the two v_a faces around the cell centre; for b != a, on the edge at integer a and b
+ * coordinates, the mean of the two v_a faces on either side along b times the mean of the two
+ * v_b faces on either side along a.  Its MAC divergence is the convective term. */
+int mbref_advection(const mbref_grid* g, const double* v, double* out)
+{
+    const int n[3] = {g->nx, g->ny, g->nz};
+    const int64_t N = (int64_t)n[0] * n[1] * n[2];
+    double* M = (double*)malloc(sizeof(double) * 9 * N);
+    if (!M) return 2;
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                const int idx[3] = {i, j, k};
+                const int64_t c = ((int64_t)k * n[1] + j) * n[0] + i;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        /* neighbour of this cell one step along dimension e, by s = +-1 */
+                        int64_t nb_a, nb_b;
+                        int t[3] = {idx[0], idx[1], idx[2]};
+                        if (a == b) {
+                            t[a] = (int)wrap_index(idx[a] + 1, n[a]);
+                            nb_a = ((int64_t)t[2] * n[1] + t[1]) * n[0] + t[0];
+                            const double m = 0.5 * (v[a * N + c] + v[a * N + nb_a]);
+                            M[(3 * a + b) * N + c] = m * m;
+                        } else {
+                            t[b] = (int)wrap_index(idx[b] - 1, n[b]);
+                            nb_b = ((int64_t)t[2] * n[1] + t[1]) * n[0] + t[0];
+                            int r[3] = {idx[0], idx[1], idx[2]};
+                            r[a] = (int)wrap_index(idx[a] - 1, n[a]);
+                            nb_a = ((int64_t)r[2] * n[1] + r[1]) * n[0] + r[0];
+                            const double va = 0.5 * (v[a * N + c] + v[a * N + nb_b]);
+                            const double vb = 0.5 * (v[b * N + c] + v[b * N + nb_a]);
+                            M[(3 * a + b) * N + c] = va * vb;
+                        }
+                    }
+            }
+    mbref_stress_div(g, M, out);
+    free(M);
     return 0;
 }
 

@@ -34,6 +34,7 @@ typedef struct {
     double eta;      /* shear viscosity */
     double dt;       /* time step */
     int mean_mode;   /* 0: the k=0 (mean) mode evolves with the net force; 1: it is held at 0 */
+    int advection;   /* 1: the convective stress rho v v of Eq. (vf), explicit at v^n */
 } mbref_grid;
 
 /* Three-point kernel Phi of Eq. (delta): the Roma-Peskin-Berger function. */
@@ -50,7 +51,8 @@ int mbref_interp(const mbref_grid* g, int64_t n, const double* q, const double* 
 int mbref_dft3(int nx, int ny, int nz, double* re, double* im, int inverse);
 
 /* One Crank-Nicolson + projection update of the fluid (Eq. vf with sigma = -eta E, m_e = 0):
- *   (rho/dt - eta/2 L) v_out = P [ (rho/dt + eta/2 L) v + f + f_body ].
+ *   (rho/dt - eta/2 L) v_out = P [ (rho/dt + eta/2 L) v + f + f_body - rho D.(v v) ],
+ * the last term only with g->advection (see mbref_advection).
  * body = {f0, axis, wave_dir, j} (force density f0 sin(2 pi j x_wave / L_wave) along axis)
  * or NULL. */
 int mbref_fluid_update(const mbref_grid* g, const double* v, const double* f,
@@ -95,6 +97,12 @@ int mbref_stress_normals(const mbref_grid* g, uint64_t seed, uint64_t step, int6
 /* f [3][nz][ny][nx] = D.W, the MAC divergence of a stress field W [9][nz][ny][nx] placed
  * with W_aa at cell centres and W_ab on edges (overwrites f). */
 int mbref_stress_div(const mbref_grid* g, const double* W, double* f);
+
+/* out = D.(v v): the divergence of the convective tensor v_a v_b on the MAC grid, placed like
+ * the thermal stress (v_a v_a at cell centres from the two face values of v_a averaged;
+ * v_a v_b on the (a, b) edges from v_a averaged along b and v_b averaged along a), the
+ * conservative centred form of the convective term of Eq. (vf). */
+int mbref_advection(const mbref_grid* g, const double* v, double* out);
 
 /* nsteps of the neutrally buoyant ICM step (midpoint blob update, CN fluid update),
  * updating q (wrapped into [0, L)) and v in place.  ext ([n][3]), body and noise may be
