@@ -48,8 +48,9 @@ def stage_model(n, nb, rsz, ncell, thermal=False):
         "forces": ("hbm", nb * (24 + 4 + 4 + 2 * 42 / 13 * 12 + 24 + 48)),
         "force_sum": ("hbm", 0),
         "spread": ("hbm", 48 * nb + grid),               # sorted (q, F) records; write f
-        # thermal stress (kT > 0 only): write 9 stress grids, read them and f, write f
-        "thermal_noise": ("hbm", 3 * grid + 3 * grid + 2 * grid if thermal else 0),
+        # thermal / convective stress (kT > 0 or advection only): write 9 stress grids, read
+        # them and f, write f
+        "fluid_stress": ("hbm", 3 * grid + 3 * grid + 2 * grid if thermal else 0),
         "fluid_x_fwd": ("hbm", 2 * grid + spec),         # read v, f; write spectrum
         "fluid_y_fwd": ("hbm", 0),                       # no kernel in the three-pass FFT
         "fluid_z_solve": ("hbm", 2 * spec),

@@ -70,8 +70,14 @@ typedef enum {
  *                FP32-grid mode the flag has no effect: the in-cell order, the spring sums at
  *                an icosahedron's centre and the grid additions of neighbouring spreading
  *                tiles follow the order of atomics, so runs agree to FP32 rounding.
- *   advection    must be 0: the convective term rho v v of Eq. (vf) is not provided (every
- *                measurement in the paper is at vanishing Reynolds number).
+ *   advection    0, or 1 for the convective stress rho v v of Eq. (vf) (integrator 0 only;
+ *                every measurement in the paper is at vanishing Reynolds number, so it is off
+ *                by default).  It enters the momentum right-hand side as -rho D.M(v^n)
+ *                (explicit in time), M placed like the thermal stress: M_aa at cell centres,
+ *                the square of the mean of the two v_a faces; M_ab (b != a) on the (a, b)
+ *                edges, v_a averaged along b times v_b averaged along a.  This centred
+ *                conservative form keeps momentum exactly and, for a divergence-free field,
+ *                kinetic energy.  mb_fluid_update includes it too.
  *   mean_mode    0: the k = 0 fluid mode carries the net momentum, rho L^3 d(mean v)/dt =
  *                sum of blob forces (+ mean body force); 1: the k = 0 mode is held at zero
  *                (the frame of Hasimoto's periodic drag, Eq. rhinf).
@@ -181,7 +187,8 @@ mb_status mb_interp(mb_ctx* ctx, int64_t n, const double* pos, const void* grid_
                     double* u_out);
 
 /* Standalone fluid update of one box (Eq. vf with the viscous stress, Crank-Nicolson):
- *   (rho/dt - eta/2 L) v_out = P[(rho/dt + eta/2 L) v_in + f + f_body].
+ *   (rho/dt - eta/2 L) v_out = P[(rho/dt + eta/2 L) v_in + f + f_body - rho D.M(v_in)],
+ * the last term only with advection = 1 (no thermal stress here).
  * The k = 0 mode follows the grid (mean_mode 0) or is zeroed (mean_mode 1).  v_in, f and
  * v_out are one box grid each; body_force as in mb_step (HOST, or NULL).
  * In a Stokes-limit context (integrator 1) it is the steady solve of that integrator,
@@ -201,7 +208,7 @@ mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos);
  * disabling) resets the totals.  mb_get_stage_times waits for the recorded steps, then copies
  * up to max_stages totals (milliseconds) and call counts, and sets *n_stages to the number of
  * stages; mb_stage_name gives a stage's name ("" if out of range).
- * Stages, in launch order: interp_predict, bin, forces, force_sum, spread, thermal_noise,
+ * Stages, in launch order: interp_predict, bin, forces, force_sum, spread, fluid_stress,
  * fluid_x_fwd, fluid_y_fwd, fluid_z_solve, fluid_y_inv, fluid_x_inv, interp_correct. */
 mb_status mb_set_stage_timing(mb_ctx* ctx, int enable);
 mb_status mb_get_stage_times(mb_ctx* ctx, int max_stages, double* ms_total,

@@ -13,9 +13,15 @@
 // -L per component: the fluctuation-dissipation partner of the viscous term.  The fluid
 // receives -D.sigma~.
 //
-// Two launches per step: k_stress draws sigma~ into a [B][9][N] buffer (each Philox block is
-// computed once), k_stress_div adds -D.sigma~ to the force-density grid and advances the
-// step index held in device memory, so captured CUDA graphs draw fresh noise on every replay.
+// The convective stress rho v v of Eq. (vf) (advection = 1) sits on the same nodes: rho v_a v_a
+// at the cell centre from the mean of the two v_a faces, rho v_a v_b on the (a, b) edge from
+// v_a averaged along b times v_b averaged along a (the conservative centred form), explicit
+// at v^n, so one divergence serves both stresses.
+//
+// Two launches per step: k_stress forms sigma~ + rho v v into a [B][9][N] buffer (each Philox
+// block is computed once), k_stress_div adds -D.(sigma~ + rho v v) to the force-density grid
+// and advances the step index held in device memory (when drawing noise), so captured CUDA
+// graphs draw fresh noise on every replay.
 #include "mb_internal.cuh"
 
 namespace mbk {
@@ -67,28 +73,74 @@ __device__ __forceinline__ void box_muller(uint64_t x, float& z0, float& z1)
     z1 = r * s;
 }
 
+// Periodic neighbours of cell m = i + nx (j + ny k) (the sizes are powers of two).
+struct Nbr {
+    int64_t xm, xp, ym, yp, zm, zp;
+    __device__ Nbr(const GridGeo& g, int64_t m)
+    {
+        const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+        const int i = (int)(m % nx), j = (int)((m / nx) % ny), k = (int)(m / ((int64_t)nx * ny));
+        const int64_t row = m - i, plane = m - (int64_t)j * nx - i;
+        xm = row + ((i - 1) & (nx - 1));
+        xp = row + ((i + 1) & (nx - 1));
+        ym = plane + (int64_t)((j - 1) & (ny - 1)) * nx + i;
+        yp = plane + (int64_t)((j + 1) & (ny - 1)) * nx + i;
+        zm = m + ((int64_t)((k - 1) & (nz - 1)) - k) * nx * ny;
+        zp = m + ((int64_t)((k + 1) & (nz - 1)) - k) * nx * ny;
+    }
+};
+
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_stress(int B, GridGeo g, uint64_t seed, const uint64_t* __restrict__ step_index, R amp,
-         R* __restrict__ W)
+         const R* __restrict__ v, R rho, R* __restrict__ W)
 {
-    const uint64_t n = *step_index;
+    const uint64_t n = amp != R(0) ? *step_index : 0;
     const int64_t total = (int64_t)B * g.N;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = t / g.N, m = t - b * g.N;
-        uint64_t x[8];
-        for (int j = 0; j < 2; ++j) {
-            uint64_t c[4] = {(uint64_t)m, n, (uint64_t)b, (uint64_t)j};
-            philox4x64_10(c, seed, 0);
-            for (int i = 0; i < 4; ++i) x[4 * j + i] = c[i];
-        }
-        R z[10];
+        R T[9];
 #pragma unroll
-        for (int p = 0; p < 5; ++p) box_muller(x[p], z[2 * p], z[2 * p + 1]);
+        for (int c = 0; c < 9; ++c) T[c] = R(0);
+        if (amp != R(0)) {
+            uint64_t x[8];
+            for (int j = 0; j < 2; ++j) {
+                uint64_t c[4] = {(uint64_t)m, n, (uint64_t)b, (uint64_t)j};
+                philox4x64_10(c, seed, 0);
+                for (int i = 0; i < 4; ++i) x[4 * j + i] = c[i];
+            }
+            R z[10];
+#pragma unroll
+            for (int p = 0; p < 5; ++p) box_muller(x[p], z[2 * p], z[2 * p + 1]);
+#pragma unroll
+            for (int c = 0; c < 9; ++c) T[c] = amp * z[c];
+        }
+        if (v) {
+            const Nbr nb(g, m);
+            const R* vx = v + (size_t)b * 3 * g.N;
+            const R* vy = vx + g.N;
+            const R* vz = vy + g.N;
+            const R x0 = __ldg(vx + m), y0 = __ldg(vy + m), z0 = __ldg(vz + m);
+            const R h = R(0.5);
+            const R cx = h * (x0 + __ldg(vx + nb.xp)), cy = h * (y0 + __ldg(vy + nb.yp)),
+                    cz = h * (z0 + __ldg(vz + nb.zp));
+            const R xy = (h * (x0 + __ldg(vx + nb.ym))) * (h * (y0 + __ldg(vy + nb.xm)));
+            const R xz = (h * (x0 + __ldg(vx + nb.zm))) * (h * (z0 + __ldg(vz + nb.xm)));
+            const R yz = (h * (y0 + __ldg(vy + nb.zm))) * (h * (z0 + __ldg(vz + nb.ym)));
+            T[0] += rho * (cx * cx);
+            T[1] += rho * xy;
+            T[2] += rho * xz;
+            T[3] += rho * xy;
+            T[4] += rho * (cy * cy);
+            T[5] += rho * yz;
+            T[6] += rho * xz;
+            T[7] += rho * yz;
+            T[8] += rho * (cz * cz);
+        }
         R* Wb = W + (size_t)b * 9 * g.N + m;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) Wb[(size_t)c * g.N] = amp * z[c];
+        for (int c = 0; c < 9; ++c) Wb[(size_t)c * g.N] = T[c];
     }
 }
 
@@ -98,20 +150,13 @@ __global__ void __launch_bounds__(256)
 k_stress_div(int B, GridGeo g, const R* __restrict__ W, R* __restrict__ f, int accumulate,
              uint64_t* __restrict__ step_index)
 {
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const R mih = R(-g.inv_h);
     const int64_t total = (int64_t)B * g.N;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = t / g.N, m = t - b * g.N;
-        const int i = (int)(m % nx), j = (int)((m / nx) % ny), k = (int)(m / ((int64_t)nx * ny));
-        const int64_t row = m - i, plane = m - (int64_t)j * nx - i;
-        // neighbouring cells (periodic; the sizes are powers of two)
-        const int64_t xm = row + ((i - 1) & (nx - 1)), xp = row + ((i + 1) & (nx - 1));
-        const int64_t ym = plane + (int64_t)((j - 1) & (ny - 1)) * nx + i;
-        const int64_t yp = plane + (int64_t)((j + 1) & (ny - 1)) * nx + i;
-        const int64_t zm = m + ((int64_t)((k - 1) & (nz - 1)) - k) * nx * ny;
-        const int64_t zp = m + ((int64_t)((k + 1) & (nz - 1)) - k) * nx * ny;
+        const Nbr nb(g, m);
+        const int64_t xm = nb.xm, xp = nb.xp, ym = nb.ym, yp = nb.yp, zm = nb.zm, zp = nb.zp;
         const R* Wb = W + (size_t)b * 9 * g.N;
         auto w = [&](int comp, int64_t cell) { return __ldg(Wb + (size_t)comp * g.N + cell); };
         R d[3];
@@ -125,7 +170,7 @@ k_stress_div(int B, GridGeo g, const R* __restrict__ W, R* __restrict__ f, int a
             fb[(size_t)a * g.N] = accumulate ? fb[(size_t)a * g.N] + add : add;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *step_index += 1;
+    if (step_index && blockIdx.x == 0 && threadIdx.x == 0) *step_index += 1;
 }
 
 unsigned noise_blocks(int64_t total)
@@ -144,19 +189,23 @@ unsigned noise_blocks(int64_t total)
 }  // namespace
 
 template <typename R>
-cudaError_t launch_thermal_stress(cudaStream_t st, int B, const GridGeo& g, uint64_t seed,
-                                  uint64_t* step_index, double amp, R* W, R* f, bool accumulate)
+cudaError_t launch_fluid_stress(cudaStream_t st, int B, const GridGeo& g, uint64_t seed,
+                                uint64_t* step_index, double amp, const R* v, double rho, R* W,
+                                R* f, bool accumulate)
 {
     const int64_t total = (int64_t)B * g.N;
     if (total <= 0) return cudaSuccess;
     const unsigned blocks = noise_blocks(total);
-    k_stress<R><<<blocks, 256, 0, st>>>(B, g, seed, step_index, R(amp), W);
-    k_stress_div<R><<<blocks, 256, 0, st>>>(B, g, W, f, accumulate ? 1 : 0, step_index);
+    k_stress<R><<<blocks, 256, 0, st>>>(B, g, seed, step_index, R(amp), v, R(rho), W);
+    k_stress_div<R><<<blocks, 256, 0, st>>>(B, g, W, f, accumulate ? 1 : 0,
+                                            amp != 0.0 ? step_index : nullptr);
     return cudaGetLastError();
 }
-template cudaError_t launch_thermal_stress<float>(cudaStream_t, int, const GridGeo&, uint64_t,
-                                                  uint64_t*, double, float*, float*, bool);
-template cudaError_t launch_thermal_stress<double>(cudaStream_t, int, const GridGeo&, uint64_t,
-                                                   uint64_t*, double, double*, double*, bool);
+template cudaError_t launch_fluid_stress<float>(cudaStream_t, int, const GridGeo&, uint64_t,
+                                                uint64_t*, double, const float*, double, float*,
+                                                float*, bool);
+template cudaError_t launch_fluid_stress<double>(cudaStream_t, int, const GridGeo&, uint64_t,
+                                                 uint64_t*, double, const double*, double,
+                                                 double*, double*, bool);
 
 }  // namespace mbk

@@ -23,12 +23,12 @@ constexpr int SYM_LEN = 256;   // per-dimension symbol table length (n <= 128 to
 
 // Stages of one step, in launch order (names returned by mb_stage_name).
 enum Stage {
-    ST_INTERP_PREDICT, ST_BIN, ST_FORCES, ST_FORCE_SUM, ST_SPREAD, ST_THERMAL, ST_FLUID_X_FWD,
+    ST_INTERP_PREDICT, ST_BIN, ST_FORCES, ST_FORCE_SUM, ST_SPREAD, ST_STRESS, ST_FLUID_X_FWD,
     ST_FLUID_Y_FWD, ST_FLUID_Z_SOLVE, ST_FLUID_Y_INV, ST_FLUID_X_INV, ST_INTERP_CORRECT,
     NUM_STAGES
 };
 const char* const STAGE_NAMES[NUM_STAGES] = {
-    "interp_predict", "bin", "forces", "force_sum", "spread", "thermal_noise", "fluid_x_fwd",
+    "interp_predict", "bin", "forces", "force_sum", "spread", "fluid_stress", "fluid_x_fwd",
     "fluid_y_fwd",
     "fluid_z_solve", "fluid_y_inv", "fluid_x_inv", "interp_correct"};
 
@@ -138,6 +138,7 @@ struct mb_ctx {
     bool thermal = false;
     double thermal_amp = 0.0;
     DBuf W, step_index;
+    bool advect = false;        // the convective stress rho v v (explicit at v^n)
     int fft_passes = 3;     // 3: plane/z/plane pipeline; 5: one pass per axis (reference layout)
     int cur = 0;
     int64_t steps_taken = 0;
@@ -672,16 +673,18 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
                                      ctx->tile, static_cast<R*>(ctx->f.p)));
         ctx->launches += 1;
     }
-    mark(ST_THERMAL);
-    if (ctx->thermal) {
-        MB_CUDA(launch_thermal_stress<R>(st, B, g, ctx->d.seed,
-                                         static_cast<uint64_t*>(ctx->step_index.p),
-                                         ctx->thermal_amp, static_cast<R*>(ctx->W.p),
-                                         static_cast<R*>(ctx->f.p), blobs));
-        ctx->launches += THERMAL_KERNELS;
+    mark(ST_STRESS);
+    const bool stress = ctx->thermal || ctx->advect;
+    if (stress) {
+        MB_CUDA(launch_fluid_stress<R>(st, B, g, ctx->d.seed,
+                                       static_cast<uint64_t*>(ctx->step_index.p),
+                                       ctx->thermal_amp, ctx->advect ? vcur : nullptr,
+                                       ctx->d.rho, static_cast<R*>(ctx->W.p),
+                                       static_cast<R*>(ctx->f.p), blobs));
+        ctx->launches += STRESS_KERNELS;
     }
     const double* mean = ctx->d.mean_mode == 0 ? static_cast<const double*>(ctx->vbar.p) : nullptr;
-    FluidArgs<R> fa = fluid_args<R>(ctx, vcur, blobs || ctx->thermal ? ctx->f.p : nullptr, vnext,
+    FluidArgs<R> fa = fluid_args<R>(ctx, vcur, blobs || stress ? ctx->f.p : nullptr, vnext,
                                     ctx->body_prof.p, body, mean);
     cudaEvent_t* fm = ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr;
     if (ctx->fft_passes == 5) {
@@ -776,7 +779,7 @@ mb_status do_step_stokes(mb_ctx* ctx, const double* ext, const double* body)
                                          ctx->bg, ctx->tile, static_cast<R*>(ctx->f.p)));
             ctx->launches += 1;
         }
-        if (marks) mark(ST_THERMAL);       // no thermal stress in this integrator
+        if (marks) mark(ST_STRESS);        // no thermal or convective stress in this integrator
         FluidArgs<R> fa = fluid_args<R>(ctx, v_out, blobs ? ctx->f.p : nullptr, v_out,
                                         ctx->body_prof.p, body, nullptr);
         fa.no_v = 1;                        // right-hand side S F + f_body
@@ -902,15 +905,17 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                                 ctx->tile, static_cast<float*>(ctx->f.p), ctx->f_zero));
         ctx->launches += 1;
     }
-    mark(ST_THERMAL);
-    if (ctx->thermal) {
-        MB_CUDA(launch_thermal_stress<float>(st, B, g, ctx->d.seed,
-                                             static_cast<uint64_t*>(ctx->step_index.p),
-                                             ctx->thermal_amp, static_cast<float*>(ctx->W.p),
-                                             static_cast<float*>(ctx->f.p), blobs));
-        ctx->launches += THERMAL_KERNELS;
+    mark(ST_STRESS);
+    const bool stress = ctx->thermal || ctx->advect;
+    if (stress) {
+        MB_CUDA(launch_fluid_stress<float>(st, B, g, ctx->d.seed,
+                                           static_cast<uint64_t*>(ctx->step_index.p),
+                                           ctx->thermal_amp, ctx->advect ? vcur : nullptr,
+                                           ctx->d.rho, static_cast<float*>(ctx->W.p),
+                                           static_cast<float*>(ctx->f.p), blobs));
+        ctx->launches += STRESS_KERNELS;
     }
-    FluidArgs<float> fa = fluid_args<float>(ctx, vcur, blobs || ctx->thermal ? ctx->f.p : nullptr,
+    FluidArgs<float> fa = fluid_args<float>(ctx, vcur, blobs || stress ? ctx->f.p : nullptr,
                                             vnext, ctx->body_prof.p, body, nullptr);
     if (ctx->d.mean_mode == 0) {
         const double L3 = g.L[0] * g.L[1] * g.L[2];
@@ -1288,8 +1293,8 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
         g_create_error = "deterministic must be 0 or 1";
         return MB_EINVAL;
     }
-    if (d.advection != 0) {
-        g_create_error = "advection (the rho v v term) is not provided; set advection = 0";
+    if (d.advection != 0 && d.advection != 1) {
+        g_create_error = "advection must be 0 or 1 (the rho v v stress)";
         return MB_EINVAL;
     }
     if (d.mean_mode != 0 && d.mean_mode != 1) {
@@ -1310,6 +1315,10 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     }
     if (d.integrator == 1 && d.kT != 0.0) {
         g_create_error = "the Stokes-limit integrator is deterministic: set kT = 0";
+        return MB_EINVAL;
+    }
+    if (d.integrator == 1 && d.advection != 0) {
+        g_create_error = "the Stokes limit has no convective term: set advection = 0";
         return MB_EINVAL;
     }
     mb_ctx* ctx = new (std::nothrow) mb_ctx();
@@ -1358,10 +1367,12 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     if ((s = ensure(ctx->fsum, sizeof(double) * 3 * ctx->B, ctx->err, "fsum")) != MB_OK) return fail(s);
     if ((s = ensure(ctx->step_index, sizeof(uint64_t), ctx->err, "step index")) != MB_OK) return fail(s);
     ctx->thermal = d.kT > 0.0;
-    if (ctx->thermal) {
-        if ((s = ensure(ctx->W, 3 * gb, ctx->err, "thermal stress")) != MB_OK) return fail(s);
+    ctx->advect = d.advection == 1;
+    if (ctx->thermal)
         ctx->thermal_amp = std::sqrt(2.0 * d.eta * d.kT / (d.h * d.h * d.h * d.dt));
-    }
+    if ((ctx->thermal || ctx->advect) &&
+        (s = ensure(ctx->W, 3 * gb, ctx->err, "fluid stress")) != MB_OK)
+        return fail(s);
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {
         cudaGetLastError();
         ctx->err = "no CUDA device";
@@ -2039,6 +2050,24 @@ mb_status mb_fluid_update(mb_ctx* ctx, const void* v_in, const void* f, const do
     const void *vd = nullptr, *fd = nullptr;
     if (!stokes) MB_TRY(stage_in(ctx, v_in, by, ctx->s_g1, &vd, "v_in"));
     if (f) MB_TRY(stage_in(ctx, f, by, ctx->s_g2, &fd, "f"));
+    if (ctx->advect) {
+        // f - rho D.(v_in v_in) in the library's own copy (the caller's f is not written)
+        MB_TRY(ensure(ctx->s_g2, by, ctx->err, "f"));
+        if (fd && fd != ctx->s_g2.p)
+            MB_CUDA(cudaMemcpyAsync(ctx->s_g2.p, fd, by, cudaMemcpyDeviceToDevice, ctx->st));
+        MB_TRY(ensure(ctx->W, 3 * by, ctx->err, "fluid stress"));
+        if (ctx->rsz == 4)
+            MB_CUDA(launch_fluid_stress<float>(ctx->st, 1, ctx->g, 0, nullptr, 0.0,
+                                               static_cast<const float*>(vd), ctx->d.rho,
+                                               static_cast<float*>(ctx->W.p),
+                                               static_cast<float*>(ctx->s_g2.p), fd != nullptr));
+        else
+            MB_CUDA(launch_fluid_stress<double>(ctx->st, 1, ctx->g, 0, nullptr, 0.0,
+                                                static_cast<const double*>(vd), ctx->d.rho,
+                                                static_cast<double*>(ctx->W.p),
+                                                static_cast<double*>(ctx->s_g2.p), fd != nullptr));
+        fd = ctx->s_g2.p;
+    }
     if (body_force) MB_TRY(set_body(ctx, body_force, ctx->prof_scratch, false));
     void* dst;
     bool host;

@@ -150,12 +150,14 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
                           cudaEvent_t* marks = nullptr);
 constexpr int FLUID3_KERNELS = 3;
 
-// Thermal stress (kernels_noise.cu): W = amp * normals of step *step_index, then
-// f (+)= -D.W / h, then *step_index += 1.  W is [B][9][N], f [B][3][N].
+// Thermal and convective stress (kernels_noise.cu): W = amp * normals of step *step_index
+// (amp != 0) + rho v v (v != NULL), then f (+)= -D.W, then *step_index += 1 (amp != 0).
+// W is [B][9][N], v and f [B][3][N].
 template <typename R>
-cudaError_t launch_thermal_stress(cudaStream_t st, int B, const GridGeo& g, uint64_t seed,
-                                  uint64_t* step_index, double amp, R* W, R* f, bool accumulate);
-constexpr int THERMAL_KERNELS = 2;
+cudaError_t launch_fluid_stress(cudaStream_t st, int B, const GridGeo& g, uint64_t seed,
+                                uint64_t* step_index, double amp, const R* v, double rho, R* W,
+                                R* f, bool accumulate);
+constexpr int STRESS_KERNELS = 2;
 
 // Exclusive scan of n ints into out[0..n] (out[n] = total); tile_tmp holds n/4096 + 2 ints.
 cudaError_t launch_exclusive_scan(cudaStream_t st, const int32_t* in, int32_t* out, int64_t n,

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
 @pytest.mark.parametrize("field,value,msg", [
     ("nx", 3, "powers of two"), ("ny", 512, "powers of two"), ("batch", 0, "batch"),
     ("h", 0.0, "positive"), ("eta", -1.0, "positive"), ("precision", 2, "precision"),
-    ("advection", 1, "advection"), ("kT", -1e-3, "kT"), ("kT", float("nan"), "kT"),
+    ("advection", 2, "advection"), ("kT", -1e-3, "kT"), ("kT", float("nan"), "kT"),
     ("mean_mode", 3, "mean_mode"), ("integrator", 2, "integrator"),
 ])
 def test_descriptor_validation_is_host_side(field, value, msg):
