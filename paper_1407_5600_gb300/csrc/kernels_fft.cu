@@ -9,68 +9,28 @@
 //           divergence/gradient symbols, set the k = 0 mode, inverse FFT along z
 //   pass 4  inverse FFT along y
 //   pass 5  complex-to-real inverse FFT along x, scale 1/N         -> v_out
-// Every pass stages its lines in shared memory and runs radix-2 butterflies there; global
-// traffic is one coalesced read and one write of the half spectrum per pass.
+// Every pass stages its lines in shared memory (padded against bank conflicts) and transforms
+// them with the register line FFTs of fft_lines.cuh; global traffic is one coalesced read and
+// one write of the half spectrum per pass.  This pipeline takes sides of up to 256 points.
 #include "mb_internal.cuh"
+#include "fft_lines.cuh"
 
 namespace mbk {
 
-template <typename T> __device__ __forceinline__ T cmul(T a, T b)
-{
-    return T{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
-
-__device__ __forceinline__ int ilog2(int n) { return 31 - __clz(n); }
-
-// In-place radix-2 decimation-in-time FFT of ngroups*cw lines held in shared memory.
-// Line (g, c) stores element j at buf[g*gstride + c + j*estride].  tw[m] = e^{-2 pi i m/n}.
-// Forward: X_k = sum_j x_j e^{-2 pi i jk/n}; inverse uses e^{+...} with no scaling.
-template <typename T>
-__device__ void smem_fft(T* buf, int n, int ngroups, int gstride, int cw, int estride,
-                         const T* __restrict__ tw, bool inverse)
-{
-    const int logn = ilog2(n);
-    const int nl = ngroups * cw;
-    for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
-        const int l = t % nl, j = t / nl;
-        const int r = (int)(__brev((unsigned)j) >> (32 - logn));
-        if (r > j) {
-            T* base = buf + (l / cw) * gstride + (l % cw);
-            const T tmp = base[j * estride];
-            base[j * estride] = base[r * estride];
-            base[r * estride] = tmp;
-        }
-    }
-    __syncthreads();
-    for (int s = 1; s <= logn; ++s) {
-        const int half = 1 << (s - 1);
-        for (int t = threadIdx.x; t < nl * (n >> 1); t += blockDim.x) {
-            const int l = t % nl, bf = t / nl;
-            const int m = bf & (half - 1);
-            const int i0 = ((bf >> (s - 1)) << s) + m;
-            T w = tw[m << (logn - s)];
-            if (inverse) w.y = -w.y;
-            T* base = buf + (l / cw) * gstride + (l % cw);
-            const T a = base[i0 * estride];
-            const T b = cmul(base[(i0 + half) * estride], w);
-            base[i0 * estride] = T{a.x + b.x, a.y + b.y};
-            base[(i0 + half) * estride] = T{a.x - b.x, a.y - b.y};
-        }
-        __syncthreads();
-    }
-}
+// Padded position of element j of a line of n points (one spare slot every 2^pad_shift).
+__device__ __forceinline__ int pj(int j, int sh) { return j + (j >> sh); }
 
 // ------------------------------------------------------------------------------------------
 // Pass 1: rhs stencil + R2C along x.  CTA = RP row pairs of one (box, component, z) plane.
 template <typename R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
 k_rhs_fft_x(FluidArgs<R> a, GridGeo g, int RP)
 {
     using T = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sb = reinterpret_cast<T*>(smem_raw);
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
-    const int ld = nx + 1;
+    const int sx = pad_shift(nx), ld = padded_len(nx) + 1;
     const int yp0 = blockIdx.x * RP;
     const int z = blockIdx.y;
     const int bc = blockIdx.z;
@@ -82,31 +42,69 @@ k_rhs_fft_x(FluidArgs<R> a, GridGeo g, int RP)
     const bool body = a.body_prof && comp == a.body_axis;
     const size_t zp = (size_t)((z + 1) & (nz - 1)) * ny, zm = (size_t)((z - 1) & (nz - 1)) * ny;
     const size_t z0 = (size_t)z * ny;
-    for (int t = threadIdx.x; t < 2 * RP * nx; t += blockDim.x) {
-        const int x = t % nx, r = t / nx;
-        const int y = 2 * yp0 + r;
-        const int yp = (y + 1) & (ny - 1), ym = (y - 1) & (ny - 1);
-        const int xp = (x + 1) & (nx - 1), xm = (x - 1) & (nx - 1);
-        R val = R(0);               // Stokes limit (no_v): the right-hand side is f + f_body
-        if (!a.no_v) {
-            const R vcen = vc[(z0 + y) * nx + x];
-            const R lap = ((vc[(z0 + y) * nx + xp] + vc[(z0 + y) * nx + xm]) +
-                           (vc[(z0 + yp) * nx + x] + vc[(z0 + ym) * nx + x]) +
-                           (vc[(zp + y) * nx + x] + vc[(zm + y) * nx + x]) - R(6) * vcen) * ih2;
-            val = rho_dt * vcen + half_eta * lap;
+    // each work unit: 4 consecutive x (one vector load) of the row pair 2p, 2p+1
+    const int qx = nx / 4;
+    const R* pz = vc + z0 * nx;
+    const R* pzp = vc + zp * nx;
+    const R* pzm = vc + zm * nx;
+    const R* pf = fc ? fc + z0 * nx : nullptr;
+    for (int u = threadIdx.x; u < qx * RP; u += blockDim.x) {
+        const int x0 = 4 * (u % qx), p = u / qx;
+        const int y0 = 2 * (yp0 + p), y1 = y0 + 1;
+        R r0[4] = {R(0), R(0), R(0), R(0)}, r1[4] = {R(0), R(0), R(0), R(0)}, t[4];
+        if (!a.no_v) {              // Stokes limit (no_v): the right-hand side is f + f_body
+            const int ym = (y0 - 1) & (ny - 1), yp = (y1 + 1) & (ny - 1);
+            R c0[4], c1[4], am[4], ap[4], l0[4], l1[4];
+            load4(pz + (size_t)y0 * nx + x0, c0);
+            load4(pz + (size_t)y1 * nx + x0, c1);
+            load4(pz + (size_t)ym * nx + x0, am);
+            load4(pz + (size_t)yp * nx + x0, ap);
+            for (int i = 0; i < 4; ++i) {
+                l0[i] = am[i] + c1[i] - R(6) * c0[i];
+                l1[i] = c0[i] + ap[i] - R(6) * c1[i];
+            }
+            load4(pzp + (size_t)y0 * nx + x0, t);
+            for (int i = 0; i < 4; ++i) l0[i] += t[i];
+            load4(pzm + (size_t)y0 * nx + x0, t);
+            for (int i = 0; i < 4; ++i) l0[i] += t[i];
+            load4(pzp + (size_t)y1 * nx + x0, t);
+            for (int i = 0; i < 4; ++i) l1[i] += t[i];
+            load4(pzm + (size_t)y1 * nx + x0, t);
+            for (int i = 0; i < 4; ++i) l1[i] += t[i];
+            const int xm = (x0 - 1) & (nx - 1), xq = (x0 + 4) & (nx - 1);
+            const R e0m = pz[(size_t)y0 * nx + xm], e0p = pz[(size_t)y0 * nx + xq];
+            const R e1m = pz[(size_t)y1 * nx + xm], e1p = pz[(size_t)y1 * nx + xq];
+            for (int i = 0; i < 4; ++i) {
+                l0[i] += (i == 0 ? e0m : c0[i - 1]) + (i == 3 ? e0p : c0[i + 1]);
+                l1[i] += (i == 0 ? e1m : c1[i - 1]) + (i == 3 ? e1p : c1[i + 1]);
+                r0[i] = rho_dt * c0[i] + half_eta * (l0[i] * ih2);
+                r1[i] = rho_dt * c1[i] + half_eta * (l1[i] * ih2);
+            }
         }
-        if (fc) val += fc[(z0 + y) * nx + x];
-        if (body) val += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y : z)];
-        T* slot = sb + (r >> 1) * ld + x;
-        if (r & 1) slot->y = val; else slot->x = val;
+        if (pf) {
+            load4(pf + (size_t)y0 * nx + x0, t);
+            for (int i = 0; i < 4; ++i) r0[i] += t[i];
+            load4(pf + (size_t)y1 * nx + x0, t);
+            for (int i = 0; i < 4; ++i) r1[i] += t[i];
+        }
+        if (body) {
+            for (int i = 0; i < 4; ++i) {
+                const int x = x0 + i;
+                r0[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y0 : z)];
+                r1[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)];
+            }
+        }
+        for (int i = 0; i < 4; ++i) sb[p * ld + pj(x0 + i, sx)] = T{r0[i], r1[i]};
     }
     __syncthreads();
-    smem_fft<T>(sb, nx, RP, ld, 1, 1, reinterpret_cast<const T*>(a.tw[0]), false);
+    lines_fft_n<false>(nx, sb, RP, [ld, sx](int l, int j) { return l * ld + pj(j, sx); },
+                       reinterpret_cast<const T*>(a.twf[0]));
+    __syncthreads();
     T* out = a.spec + ((size_t)bc * nz + z) * (size_t)ny * nxh;
     for (int t = threadIdx.x; t < RP * nxh; t += blockDim.x) {
         const int k = t % nxh, p = t / nxh;
-        const T Z = sb[p * ld + k];
-        const T Zr = sb[p * ld + ((nx - k) & (nx - 1))];
+        const T Z = sb[p * ld + pj(k, sx)];
+        const T Zr = sb[p * ld + pj((nx - k) & (nx - 1), sx)];
         // even row: (Z + conj Zr)/2 ; odd row: -i (Z - conj Zr)/2
         const T Xa{(Z.x + Zr.x) * R(0.5), (Z.y - Zr.y) * R(0.5)};
         const T Xb{(Z.y + Zr.y) * R(0.5), (Zr.x - Z.x) * R(0.5)};
@@ -117,9 +115,9 @@ k_rhs_fft_x(FluidArgs<R> a, GridGeo g, int RP)
 }
 
 // Pass 2 / 4: complex FFT along y.  CTA = C consecutive kx columns of one (box, comp, z).
-template <typename R>
-__global__ void __launch_bounds__(256)
-k_fft_y(typename C2<R>::T* spec, const R* twy, GridGeo g, int C, bool inverse)
+template <typename R, bool INV>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
+k_fft_y(typename C2<R>::T* spec, const R* twy, GridGeo g, int C)
 {
     using T = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -127,23 +125,29 @@ k_fft_y(typename C2<R>::T* spec, const R* twy, GridGeo g, int C, bool inverse)
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     const int kx0 = blockIdx.x * C;
     const int cw = min(C, nxh - kx0);
+    const int sy = pad_shift(ny), CL = C + 1;
     T* plane = spec + ((size_t)blockIdx.z * nz + blockIdx.y) * (size_t)ny * nxh + kx0;
+    // every copy of a thread in flight at once
     for (int t = threadIdx.x; t < ny * cw; t += blockDim.x) {
         const int y = t / cw, c = t % cw;
-        sb[y * C + c] = plane[(size_t)y * nxh + c];
+        async_copy(&sb[pj(y, sy) * CL + c], &plane[(size_t)y * nxh + c]);
     }
+    async_wait_all();
     __syncthreads();
-    smem_fft<T>(sb, ny, 1, 0, cw, C, reinterpret_cast<const T*>(twy), inverse);
+    auto idx = [CL, sy](int l, int j) { return pj(j, sy) * CL + l; };
+    const T* tw = reinterpret_cast<const T*>(twy);
+    lines_fft_n<INV>(ny, sb, cw, idx, tw);
+    __syncthreads();
     for (int t = threadIdx.x; t < ny * cw; t += blockDim.x) {
         const int y = t / cw, c = t % cw;
-        plane[(size_t)y * nxh + c] = sb[y * C + c];
+        plane[(size_t)y * nxh + c] = sb[pj(y, sy) * CL + c];
     }
 }
 
 // Pass 3: FFT along z, Crank-Nicolson divide, projection, k = 0 mode, inverse FFT along z.
 // CTA = C consecutive kx columns at one ky of one box, all three components.
 template <typename R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
 k_fft_z_solve(FluidArgs<R> a, GridGeo g, int C)
 {
     using T = typename C2<R>::T;
@@ -158,33 +162,42 @@ k_fft_z_solve(FluidArgs<R> a, GridGeo g, int C)
     T* col[3];
     for (int c = 0; c < 3; ++c)
         col[c] = a.spec + ((size_t)(box * 3 + c) * nz) * zstride + (size_t)ky * nxh + kx0;
+    const int sz = pad_shift(nz), PZ = padded_len(nz), CL = C + 1;
+    auto at = [=](int c, int z, int k) { return (c * PZ + pj(z, sz)) * CL + k; };
+    // z twiddles in shared memory, after the three component columns (ready at the barrier
+    // that follows the column copies)
+    T* twz = sb + 3 * PZ * CL;
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) twz[i] = reinterpret_cast<const T*>(a.twf[2])[i];
     for (int t = threadIdx.x; t < 3 * nz * cw; t += blockDim.x) {
         const int c = t / (nz * cw), rem = t % (nz * cw);
         const int z = rem / cw, k = rem % cw;
-        sb[(c * nz + z) * C + k] = col[c][(size_t)z * zstride + k];
+        async_copy(&sb[at(c, z, k)], &col[c][(size_t)z * zstride + k]);
     }
+    async_wait_all();
     __syncthreads();
-    const T* twz = reinterpret_cast<const T*>(a.tw[2]);
-    smem_fft<T>(sb, nz, 3, nz * C, cw, C, twz, false);
+    auto idx = [=](int l, int j) { return at(l / cw, j, l % cw); };
+    lines_fft_n<false>(nz, sb, 3 * cw, idx, twz);
+    __syncthreads();
 
-    const double* cosx = a.sym + 0 * 256;
-    const double* sinx = a.sym + 1 * 256;
-    const double* lamx = a.sym + 2 * 256;
-    const double* cosy = a.sym + 3 * 256;
-    const double* siny = a.sym + 4 * 256;
-    const double* lamy = a.sym + 5 * 256;
-    const double* cosz = a.sym + 6 * 256;
-    const double* sinz = a.sym + 7 * 256;
-    const double* lamz = a.sym + 8 * 256;
+    const R* sym = reinterpret_cast<const R*>(a.symr);      // [9][256] cos, sin, lambda
+    const R* cosx = sym + 0 * 256;
+    const R* sinx = sym + 1 * 256;
+    const R* lamx = sym + 2 * 256;
+    const R* cosy = sym + 3 * 256;
+    const R* siny = sym + 4 * 256;
+    const R* lamy = sym + 5 * 256;
+    const R* cosz = sym + 6 * 256;
+    const R* sinz = sym + 7 * 256;
+    const R* lamz = sym + 8 * 256;
     const R ih = R(g.inv_h);
     for (int t = threadIdx.x; t < nz * cw; t += blockDim.x) {
         const int kz = t / cw, k = t % cw;
         const int kx = kx0 + k;
         T W[3];
         const R lam = R(lamx[kx]) + R(lamy[ky]) + R(lamz[kz]);
-        const R cinv = R(1) / (R(a.rho_dt) + R(a.half_eta) * lam);
+        const R cinv = recip(R(a.rho_dt) + R(a.half_eta) * lam);
         for (int c = 0; c < 3; ++c) {
-            const T v = sb[(c * nz + kz) * C + k];
+            const T v = sb[at(c, kz, k)];
             W[c] = T{v.x * cinv, v.y * cinv};
         }
         if (kx == 0 && ky == 0 && kz == 0) {
@@ -203,7 +216,7 @@ k_fft_z_solve(FluidArgs<R> a, GridGeo g, int C)
                 dr += Dr * W[c].x - Di * W[c].y;
                 di += Dr * W[c].y + Di * W[c].x;
             }
-            const R il = R(1) / lam;
+            const R il = recip(lam);
             dr *= il;
             di *= il;
             for (int c = 0; c < 3; ++c) {
@@ -212,56 +225,67 @@ k_fft_z_solve(FluidArgs<R> a, GridGeo g, int C)
                 W[c].y += Gr * di + Gi * dr;
             }
         }
-        for (int c = 0; c < 3; ++c) sb[(c * nz + kz) * C + k] = W[c];
+        for (int c = 0; c < 3; ++c) sb[at(c, kz, k)] = W[c];
     }
     __syncthreads();
-    smem_fft<T>(sb, nz, 3, nz * C, cw, C, twz, true);
+    lines_fft_n<true>(nz, sb, 3 * cw, idx, twz);
+    __syncthreads();
     for (int t = threadIdx.x; t < 3 * nz * cw; t += blockDim.x) {
         const int c = t / (nz * cw), rem = t % (nz * cw);
         const int z = rem / cw, k = rem % cw;
-        col[c][(size_t)z * zstride + k] = sb[(c * nz + z) * C + k];
+        col[c][(size_t)z * zstride + k] = sb[at(c, z, k)];
     }
 }
 
 // Pass 5: C2R along x.  Two half-spectrum rows form Z = Xa + i Xb (Hermitian extension),
 // one inverse complex FFT gives both real rows.
 template <typename R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
 k_fft_x_c2r(FluidArgs<R> a, GridGeo g, int RP)
 {
     using T = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sb = reinterpret_cast<T*>(smem_raw);
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
-    const int ld = nx + 1;
+    const int sx = pad_shift(nx), ld = padded_len(nx) + 1;
     const int yp0 = blockIdx.x * RP;
     const int z = blockIdx.y;
     const int bc = blockIdx.z;
     const T* in = a.spec + ((size_t)bc * nz + z) * (size_t)ny * nxh;
+    #pragma unroll 4
     for (int t = threadIdx.x; t < RP * nx; t += blockDim.x) {
         const int k = t % nx, p = t / nx;
         const int y = 2 * (yp0 + p);
         T Xa, Xb;
         if (k <= nx / 2) {
-            Xa = in[(size_t)y * nxh + k];
-            Xb = in[(size_t)(y + 1) * nxh + k];
+            Xa = __ldg(in + (size_t)y * nxh + k);
+            Xb = __ldg(in + (size_t)(y + 1) * nxh + k);
             if (k == 0 || k == nx / 2) { Xa.y = R(0); Xb.y = R(0); }
         } else {
-            Xa = in[(size_t)y * nxh + (nx - k)];
-            Xb = in[(size_t)(y + 1) * nxh + (nx - k)];
+            Xa = __ldg(in + (size_t)y * nxh + (nx - k));
+            Xb = __ldg(in + (size_t)(y + 1) * nxh + (nx - k));
             Xa.y = -Xa.y;
             Xb.y = -Xb.y;
         }
-        sb[p * ld + k] = T{Xa.x - Xb.y, Xa.y + Xb.x};
+        sb[p * ld + pj(k, sx)] = T{Xa.x - Xb.y, Xa.y + Xb.x};
     }
     __syncthreads();
-    smem_fft<T>(sb, nx, RP, ld, 1, 1, reinterpret_cast<const T*>(a.tw[0]), true);
+    lines_fft_n<true>(nx, sb, RP, [ld, sx](int l, int j) { return l * ld + pj(j, sx); },
+                      reinterpret_cast<const T*>(a.twf[0]));
+    __syncthreads();
     const R scale = R(1.0 / (double)g.N);
     R* out = a.v_out + (size_t)bc * g.N + (size_t)z * ny * nx;
-    for (int t = threadIdx.x; t < 2 * RP * nx; t += blockDim.x) {
-        const int x = t % nx, r = t / nx;
-        const T zv = sb[(r >> 1) * ld + x];
-        out[(size_t)(2 * yp0 + r) * nx + x] = ((r & 1) ? zv.y : zv.x) * scale;
+    const int qx = nx / 4;
+    for (int u = threadIdx.x; u < qx * RP; u += blockDim.x) {
+        const int x0 = 4 * (u % qx), p = u / qx;
+        R r0[4], r1[4];
+        for (int i = 0; i < 4; ++i) {
+            const T zv = sb[p * ld + pj(x0 + i, sx)];
+            r0[i] = zv.x * scale;
+            r1[i] = zv.y * scale;
+        }
+        store4(out + (size_t)(2 * (yp0 + p)) * nx + x0, r0);
+        store4(out + (size_t)(2 * (yp0 + p) + 1) * nx + x0, r1);
     }
 }
 
@@ -271,29 +295,33 @@ cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidAr
 {
     using T = typename C2<R>::T;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
-    const int RP = ny / 2 < 4 ? ny / 2 : 4;
+    const int RP = ny / 2 < 16 ? ny / 2 : 16;
     const int C = sizeof(R) == 4 ? 16 : 8;
     static std::atomic<unsigned> attr{0};     // per instantiation
     if (first_on_device(attr)) {
         const int lim = 200 * 1024;
         cudaFuncSetAttribute(k_rhs_fft_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_fft_y<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_fft_y<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_fft_y<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_fft_z_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_fft_x_c2r<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     }
-    const size_t smem_x = (size_t)RP * (nx + 1) * sizeof(T);
-    const size_t smem_y = (size_t)ny * C * sizeof(T);
-    const size_t smem_z = (size_t)3 * nz * C * sizeof(T);
+    const size_t smem_x = (size_t)RP * (padded_len(nx) + 1) * sizeof(T);
+    const size_t smem_y = (size_t)padded_len(ny) * (C + 1) * sizeof(T);
+    // the z pass holds three components of its columns: 8 columns keep three blocks per SM
+    const int Cz = 8;
+    const size_t smem_z = ((size_t)3 * padded_len(nz) * (Cz + 1) + nz) * sizeof(T);
     const unsigned nchunk = (unsigned)((nxh + C - 1) / C);
+    const unsigned nchunk_z = (unsigned)((nxh + Cz - 1) / Cz);
     auto mark = [&](int i) { if (marks) cudaEventRecord(marks[i], st); };
     mark(0);
     k_rhs_fft_x<R><<<dim3(ny / 2 / RP, nz, 3 * B), 256, smem_x, st>>>(a, g, RP);
     mark(1);
-    k_fft_y<R><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.tw[1], g, C, false);
+    k_fft_y<R, false><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.twf[1], g, C);
     mark(2);
-    k_fft_z_solve<R><<<dim3(nchunk, ny, B), 256, smem_z, st>>>(a, g, C);
+    k_fft_z_solve<R><<<dim3(nchunk_z, ny, B), 256, smem_z, st>>>(a, g, Cz);
     mark(3);
-    k_fft_y<R><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.tw[1], g, C, true);
+    k_fft_y<R, true><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.twf[1], g, C);
     mark(4);
     k_fft_x_c2r<R><<<dim3(ny / 2 / RP, nz, 3 * B), 256, smem_x, st>>>(a, g, RP);
     mark(5);

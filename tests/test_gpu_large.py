@@ -132,3 +132,42 @@ def test_full_size_fluctuating_suspension(thermal256):
     disp = np.abs(min_image(q - s.pos, n * spec.h))
     assert np.max(disp) < 0.5 * spec.h
 
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (8, 16, 128), (4, 4, 4), (32, 8, 64),
+                                   (128, 4, 8)])
+def test_five_pass_fluid_update_parity(monkeypatch, prec, shape):
+    """The five-pass pipeline (the one sides above 128 take) on ordinary shapes, selected with
+    MB_FFT_PASSES=5."""
+    monkeypatch.setenv("MB_FFT_PASSES", "5")
+    nz, ny, nx = shape
+    d = mb.GridDesc(nx, ny, nz, h=1.1, rho=0.9, eta=0.7, dt=0.05, precision=prec, mean_mode=0)
+    g = _oracle_grid(d)
+    v = oracle.fluid_update(oracle.Grid(nx, ny, nz, rho=1.0, eta=0.0, dt=1.0), g.zeros(),
+                            wl.random_field(shape, 5))
+    v = v.astype(d.grid_dtype).astype(np.float64)
+    f = wl.random_field(shape, 6, scale=0.3).astype(d.grid_dtype).astype(np.float64)
+    body = (0.1, 0, 2, 1)
+    with mb.Multiblob(d) as sim:
+        vn = to_np(sim.fluid_update(v[None].astype(d.grid_dtype), f[None].astype(d.grid_dtype),
+                                    body_force=body))[0]
+    assert rel_l2(vn, oracle.fluid_update(g, v, f, body=body)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_five_pass_step_parity(monkeypatch, prec):
+    monkeypatch.setenv("MB_FFT_PASSES", "5")
+    spec, s = wl.dense_suspension(n=32, a=2.2, phi=0.40, seed=5, mc_sweeps=3)
+    d = mb.GridDesc(32, 32, 32, dt=spec.dt, precision=prec, mean_mode=0, kT=1e-3, seed=3)
+    rng = np.random.default_rng(4)
+    ext = rng.normal(scale=1e-3, size=s.pos.shape)
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut)
+        sim.step(3, ext_blob_force=ext, body_force=s.body)
+        q, v = to_np(sim.blob_positions()), to_np(sim.velocity_field()).astype(np.float64)
+    g = _oracle_grid(d)
+    q_ref, v_ref = oracle.step(g, 3, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
+                               s.k_rep, s.r_cut, ext=ext, body=s.body, kT=d.kT, seed=d.seed)
+    assert position_error(q, q_ref, s.pos, g.L, 3) < TOL[prec]
+    assert rel_l2(v[0], v_ref) < TOL[prec]
