@@ -87,13 +87,14 @@ typedef enum {
  *                non-symmetric 3x3 tensor of standard normals per cell (W_aa at cell
  *                centres, W_ab on the edges at integer a and b coordinates), so that the
  *                fluid velocity samples Eq. (ef), variance kT/(rho h^3) per projected mode.
- *                The nine normals of cell m (x fastest) of box b at step index n come from
- *                two Philox4x64-10 blocks, key (seed, 0), counters (m, n, b, 0) and
- *                (m, n, b, 1); the 64-bit words x0..x4 give five Box-Muller pairs (from x_p:
- *                u1 = (low 32 bits + 1/2)/2^32, u2 = (high 32 bits + 1/2)/2^32,
- *                sqrt(-2 ln u1) (cos, sin)(2 pi u2)), whose first nine values are W_xx,
- *                W_xy, W_xz, W_yx, W_yy, W_yz, W_zx, W_zy, W_zz.  No drift term is added
- *                (neutrally buoyant blobs, m_e = 0).
+ *                The normals of box b at step index n are drawn for groups of four cells
+ *                along x (cell m = 4 G + r, x fastest): five Philox4x64-10 blocks, key
+ *                (seed, 0), counters (G, n, b, j), j = 0..4, give the 64-bit words
+ *                x0..x19; word x_p gives the Box-Muller pair p (u1 = (low 32 bits + 1/2)/
+ *                2^32, u2 = (high 32 bits + 1/2)/2^32, normals z_2p, z_2p+1 =
+ *                sqrt(-2 ln u1) (cos, sin)(2 pi u2)), and cell r takes z_9r .. z_9r+8 as
+ *                W_xx, W_xy, W_xz, W_yx, W_yy, W_yz, W_zx, W_zy, W_zz.  No drift term is
+ *                added (neutrally buoyant blobs, m_e = 0).
  *   seed         key of the thermal stress (see kT).
  *   integrator   0: the inertial coupling method (Sec. 3: fluid and blob inertia, midpoint
  *                predictor/corrector for the blobs, Crank-Nicolson for the fluid).  1: its

@@ -444,25 +444,28 @@ void mbref_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Nine standard normals of cell m of box `box` at step `step`: two Philox blocks with key
- * (seed, 0) and counters (m, step, box, 0) and (m, step, box, 1); the 64-bit words x0..x4
- * give five Box-Muller pairs, pair p from x_p: u1 = (lo32 + 1/2)/2^32, u2 = (hi32 + 1/2)/2^32,
- * r = sqrt(-2 ln u1), normals r cos(2 pi u2), r sin(2 pi u2).  The ten normals, in order,
- * are W_xx, W_xy, W_xz, W_yx, W_yy, W_yz, W_zx, W_zy, W_zz (the tenth is unused). */
-static void cell_normals(uint64_t seed, uint64_t step, int64_t box, int64_t m, double z[10])
+/* Nine standard normals of cell m of box `box` at step `step`.  Cells are drawn in groups of
+ * four along x (m = 4 G + r, r < 4; rows hold a multiple of four cells): five Philox blocks
+ * with key (seed, 0) and counters (G, step, box, j), j = 0..4, give the 64-bit words
+ * x_0..x_19; word x_p gives the Box-Muller pair p: u1 = (lo32 + 1/2)/2^32,
+ * u2 = (hi32 + 1/2)/2^32, rho = sqrt(-2 ln u1), normals z_2p = rho cos(2 pi u2) and
+ * z_2p+1 = rho sin(2 pi u2).  Cell r takes z_9r .. z_9r+8 as W_xx, W_xy, W_xz, W_yx, W_yy,
+ * W_yz, W_zx, W_zy, W_zz (pairs 0..17; words 18 and 19 are unused). */
+static void cell_normals(uint64_t seed, uint64_t step, int64_t box, int64_t m, double z[9])
 {
     const uint64_t key[2] = {seed, 0};
-    uint64_t x[8];
-    for (int j = 0; j < 2; ++j) {
-        const uint64_t ctr[4] = {(uint64_t)m, step, (uint64_t)box, (uint64_t)j};
+    const int64_t G = m / 4, r = m % 4;
+    uint64_t x[20];
+    for (int j = 0; j < 5; ++j) {
+        const uint64_t ctr[4] = {(uint64_t)G, step, (uint64_t)box, (uint64_t)j};
         mbref_philox4x64(ctr, key, x + 4 * j);
     }
-    for (int p = 0; p < 5; ++p) {
+    for (int c = 0; c < 9; ++c) {
+        const int q = 9 * (int)r + c, p = q / 2;
         double u1 = ((double)(x[p] & 0xffffffffull) + 0.5) / 4294967296.0;
         double u2 = ((double)(x[p] >> 32) + 0.5) / 4294967296.0;
-        double r = sqrt(-2.0 * log(u1));
-        z[2 * p] = r * cos(2.0 * MBREF_PI * u2);
-        z[2 * p + 1] = r * sin(2.0 * MBREF_PI * u2);
+        double rho = sqrt(-2.0 * log(u1));
+        z[c] = q % 2 == 0 ? rho * cos(2.0 * MBREF_PI * u2) : rho * sin(2.0 * MBREF_PI * u2);
     }
 }
 
@@ -470,8 +473,9 @@ int mbref_stress_normals(const mbref_grid* g, uint64_t seed, uint64_t step, int6
                          double* W)
 {
     const int64_t N = (int64_t)g->nx * g->ny * g->nz;
+    if (g->nx % 4 != 0) return 1;
     for (int64_t m = 0; m < N; ++m) {
-        double z[10];
+        double z[9];
         cell_normals(seed, step, box, m, z);
         for (int c = 0; c < 9; ++c) W[c * N + m] = z[c];
     }

@@ -90,7 +90,8 @@ typedef struct {
 void mbref_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 
 /* W [9][nz][ny][nx]: the standard normals of every cell (components xx, xy, xz, yx, yy, yz,
- * zx, zy, zz), from Philox keyed by (seed, step, box, cell) with Box-Muller. */
+ * zx, zy, zz), from Philox keyed by (seed, step, box, group of four cells along x) with
+ * Box-Muller.  nx must be a multiple of four. */
 int mbref_stress_normals(const mbref_grid* g, uint64_t seed, uint64_t step, int64_t box,
                          double* W);
 

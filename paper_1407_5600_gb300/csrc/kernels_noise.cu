@@ -1,13 +1,14 @@
 // Thermal stress of the fluctuating inertial coupling method (Sec. 3: the Gaussian stress
 // sigma~ of Eq. vf, on the staggered grid of fluctuating hydrodynamics that the paper cites).
 //
-// Per box b, step index n and cell m (x fastest), nine standard normals come from two
-// Philox4x64-10 blocks (Salmon, Moraes, Dror and Shaw, SC'11) with key (seed, 0) and counters
-// (m, n, b, 0), (m, n, b, 1).  The 64-bit words x0..x4 give five Box-Muller pairs: from x_p,
-// u1 = (low 32 bits + 1/2) / 2^32 and u2 = (high 32 bits + 1/2) / 2^32, the normals
-// sqrt(-2 ln u1) cos(2 pi u2) and sqrt(-2 ln u1) sin(2 pi u2).  The first nine are the
-// components xx, xy, xz, yx, yy, yz, zx, zy, zz of a non-symmetric stress W (the tenth is
-// dropped); sigma~ = sqrt(2 eta kT / (h^3 dt)) W.  W_aa sits at the cell centre, W_ab (b != a)
+// Per box b and step index n, the cells are drawn in groups of four along x (m = 4 G + r;
+// the rows hold a multiple of four cells): five Philox4x64-10 blocks (Salmon, Moraes, Dror
+// and Shaw, SC'11) with key (seed, 0) and counters (G, n, b, j), j = 0..4, give the 64-bit
+// words x0..x19.  Word x_p gives the Box-Muller pair p: u1 = (low 32 bits + 1/2) / 2^32 and
+// u2 = (high 32 bits + 1/2) / 2^32, the normals z_2p = sqrt(-2 ln u1) cos(2 pi u2) and
+// z_2p+1 = sqrt(-2 ln u1) sin(2 pi u2).  Cell r takes z_9r .. z_9r+8 as the components xx,
+// xy, xz, yx, yy, yz, zx, zy, zz of a non-symmetric stress W (words 18 and 19 are unused);
+// sigma~ = sqrt(2 eta kT / (h^3 dt)) W.  W_aa sits at the cell centre, W_ab (b != a)
 // on the edge at integer a and b coordinates, so the divergence on the faces of component a
 // is a backward difference of W_aa plus forward differences of W_ab, and its covariance is
 // -L per component: the fluctuation-dissipation partner of the viscous term.  The fluid
@@ -18,11 +19,12 @@
 // v_a averaged along b times v_b averaged along a (the conservative centred form), explicit
 // at v^n, so one divergence serves both stresses.
 //
-// Two launches per step: k_stress forms sigma~ + rho v v into a [B][9][N] buffer (each Philox
-// block is computed once), k_stress_div adds -D.(sigma~ + rho v v) to the force-density grid
+// Two launches per step: k_stress forms sigma~ + rho v v into a [B][9][N] buffer (one thread
+// per group of four cells, each Philox block computed once, vector stores), k_stress_div adds -D.(sigma~ + rho v v) to the force-density grid
 // and advances the step index held in device memory (when drawing noise), so captured CUDA
 // graphs draw fresh noise on every replay.
 #include "mb_internal.cuh"
+#include "fft_lines.cuh"
 
 namespace mbk {
 
@@ -58,19 +60,20 @@ __device__ __forceinline__ void box_muller(uint64_t x, double& z0, double& z1)
     z1 = r * s;
 }
 
-// FP32: ln u1 from u1 itself below 1/2 and from 1 - u1 = (~lo + 1/2) / 2^32 above, so that
-// the logarithm keeps its relative accuracy as u1 -> 1.
+// FP32: the hardware logarithm and sine/cosine (absolute errors of a few 1e-7 on these
+// ranges, far inside the FP32 grid's tolerance).  The angle is taken as 2 pi (u2 - 1/2) in
+// [-pi, pi], where the fast sine and cosine keep that accuracy, and the pair is negated back:
+// cos(2 pi u2) = -cos(2 pi (u2 - 1/2)), likewise for the sine.
 __device__ __forceinline__ void box_muller(uint64_t x, float& z0, float& z1)
 {
     const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
-    const float ln_u1 = lo < 0x80000000u ? logf(((float)lo + 0.5f) * 0x1p-32f)
-                                         : log1pf(-(((float)(~lo) + 0.5f) * 0x1p-32f));
-    const float r = sqrtf(-2.0f * ln_u1);
-    const float u2 = ((float)hi + 0.5f) * 0x1p-32f;
+    const float u1 = ((float)lo + 0.5f) * 0x1p-32f;
+    const float r = sqrtf(-2.0f * __logf(u1));
+    const float th = 6.283185307179586f * ((float)((int32_t)(hi - 0x80000000u)) + 0.5f) * 0x1p-32f;
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    __sincosf(th, &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
 }
 
 // Periodic neighbours of cell m = i + nx (j + ny k) (the sizes are powers of two).
@@ -90,57 +93,75 @@ struct Nbr {
     }
 };
 
+// rho v v at the stress nodes of cell m (xx, xy, xz, yx, yy, yz, zx, zy, zz).
 template <typename R>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void convective(const GridGeo& g, const R* __restrict__ vx, int64_t m,
+                                           R rho, R T[9])
+{
+    const Nbr nb(g, m);
+    const R* vy = vx + g.N;
+    const R* vz = vy + g.N;
+    const R x0 = __ldg(vx + m), y0 = __ldg(vy + m), z0 = __ldg(vz + m);
+    const R h = R(0.5);
+    const R cx = h * (x0 + __ldg(vx + nb.xp)), cy = h * (y0 + __ldg(vy + nb.yp)),
+            cz = h * (z0 + __ldg(vz + nb.zp));
+    const R xy = (h * (x0 + __ldg(vx + nb.ym))) * (h * (y0 + __ldg(vy + nb.xm)));
+    const R xz = (h * (x0 + __ldg(vx + nb.zm))) * (h * (z0 + __ldg(vz + nb.xm)));
+    const R yz = (h * (y0 + __ldg(vy + nb.zm))) * (h * (z0 + __ldg(vz + nb.ym)));
+    T[0] += rho * (cx * cx);
+    T[1] += rho * xy;
+    T[2] += rho * xz;
+    T[3] += rho * xy;
+    T[4] += rho * (cy * cy);
+    T[5] += rho * yz;
+    T[6] += rho * xz;
+    T[7] += rho * yz;
+    T[8] += rho * (cz * cz);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, 2)
 k_stress(int B, GridGeo g, uint64_t seed, const uint64_t* __restrict__ step_index, R amp,
          const R* __restrict__ v, R rho, R* __restrict__ W)
 {
     const uint64_t n = amp != R(0) ? *step_index : 0;
-    const int64_t total = (int64_t)B * g.N;
+    const int64_t groups = g.N / 4, total = (int64_t)B * groups;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = t / g.N, m = t - b * g.N;
-        R T[9];
+        const int64_t b = t / groups, G = t - b * groups, m0 = 4 * G;
+        R T[4][9];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) T[c] = R(0);
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) T[r][c] = R(0);
         if (amp != R(0)) {
-            uint64_t x[8];
-            for (int j = 0; j < 2; ++j) {
-                uint64_t c[4] = {(uint64_t)m, n, (uint64_t)b, (uint64_t)j};
-                philox4x64_10(c, seed, 0);
-                for (int i = 0; i < 4; ++i) x[4 * j + i] = c[i];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                uint64_t x[4] = {(uint64_t)G, n, (uint64_t)b, (uint64_t)j};
+                philox4x64_10(x, seed, 0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int p = 4 * j + i;             // pair p: normals 2p and 2p + 1
+                    if (p < 18) {
+                        R z0, z1;
+                        box_muller(x[i], z0, z1);
+                        T[(2 * p) / 9][(2 * p) % 9] = amp * z0;
+                        T[(2 * p + 1) / 9][(2 * p + 1) % 9] = amp * z1;
+                    }
+                }
             }
-            R z[10];
-#pragma unroll
-            for (int p = 0; p < 5; ++p) box_muller(x[p], z[2 * p], z[2 * p + 1]);
-#pragma unroll
-            for (int c = 0; c < 9; ++c) T[c] = amp * z[c];
         }
         if (v) {
-            const Nbr nb(g, m);
             const R* vx = v + (size_t)b * 3 * g.N;
-            const R* vy = vx + g.N;
-            const R* vz = vy + g.N;
-            const R x0 = __ldg(vx + m), y0 = __ldg(vy + m), z0 = __ldg(vz + m);
-            const R h = R(0.5);
-            const R cx = h * (x0 + __ldg(vx + nb.xp)), cy = h * (y0 + __ldg(vy + nb.yp)),
-                    cz = h * (z0 + __ldg(vz + nb.zp));
-            const R xy = (h * (x0 + __ldg(vx + nb.ym))) * (h * (y0 + __ldg(vy + nb.xm)));
-            const R xz = (h * (x0 + __ldg(vx + nb.zm))) * (h * (z0 + __ldg(vz + nb.xm)));
-            const R yz = (h * (y0 + __ldg(vy + nb.zm))) * (h * (z0 + __ldg(vz + nb.ym)));
-            T[0] += rho * (cx * cx);
-            T[1] += rho * xy;
-            T[2] += rho * xz;
-            T[3] += rho * xy;
-            T[4] += rho * (cy * cy);
-            T[5] += rho * yz;
-            T[6] += rho * xz;
-            T[7] += rho * yz;
-            T[8] += rho * (cz * cz);
-        }
-        R* Wb = W + (size_t)b * 9 * g.N + m;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) Wb[(size_t)c * g.N] = T[c];
+            for (int r = 0; r < 4; ++r) convective(g, vx, m0 + r, rho, T[r]);
+        }
+        R* Wb = W + (size_t)b * 9 * g.N + m0;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const R q[4] = {T[0][c], T[1][c], T[2][c], T[3][c]};
+            store4(Wb + (size_t)c * g.N, q);
+        }
     }
 }
 
@@ -150,24 +171,59 @@ __global__ void __launch_bounds__(256)
 k_stress_div(int B, GridGeo g, const R* __restrict__ W, R* __restrict__ f, int accumulate,
              uint64_t* __restrict__ step_index)
 {
+    // four consecutive cells along x per thread: vector loads of the stress rows, scalar
+    // loads of the two x neighbours outside the four
     const R mih = R(-g.inv_h);
-    const int64_t total = (int64_t)B * g.N;
+    const int nx = g.n[0];
+    const int64_t groups = g.N / 4, total = (int64_t)B * groups;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = t / g.N, m = t - b * g.N;
+        const int64_t b = t / groups, m = 4 * (t - b * groups);
         const Nbr nb(g, m);
-        const int64_t xm = nb.xm, xp = nb.xp, ym = nb.ym, yp = nb.yp, zm = nb.zm, zp = nb.zp;
+        const int i0 = (int)(m % nx);
+        const int64_t row = m - i0;
+        const int64_t xl = row + ((i0 - 1) & (nx - 1)), xr = row + ((i0 + 4) & (nx - 1));
+        const int64_t dy = nb.yp - m, dz = nb.zp - m, ey = m - nb.ym, ez = m - nb.zm;
         const R* Wb = W + (size_t)b * 9 * g.N;
-        auto w = [&](int comp, int64_t cell) { return __ldg(Wb + (size_t)comp * g.N + cell); };
-        R d[3];
-        d[0] = (w(0, m) - w(0, xm)) + (w(1, yp) - w(1, m)) + (w(2, zp) - w(2, m));
-        d[1] = (w(3, xp) - w(3, m)) + (w(4, m) - w(4, ym)) + (w(5, zp) - w(5, m));
-        d[2] = (w(6, xp) - w(6, m)) + (w(7, yp) - w(7, m)) + (w(8, m) - w(8, zm));
+        auto row4 = [&](int comp, int64_t cell, R v[4]) { load4(Wb + (size_t)comp * g.N + cell, v); };
+        auto one = [&](int comp, int64_t cell) { return __ldg(Wb + (size_t)comp * g.N + cell); };
+        R c[4], e[4], d[3][4];
+        // x component: W_xx backward in x, W_xy forward in y, W_xz forward in z
+        row4(0, m, c);
+        const R xxl = one(0, xl);
+        for (int i = 0; i < 4; ++i) d[0][i] = c[i] - (i == 0 ? xxl : c[i - 1]);
+        row4(1, m, c);
+        row4(1, m + dy, e);
+        for (int i = 0; i < 4; ++i) d[0][i] += e[i] - c[i];
+        row4(2, m, c);
+        row4(2, m + dz, e);
+        for (int i = 0; i < 4; ++i) d[0][i] += e[i] - c[i];
+        // y component: W_yx forward in x, W_yy backward in y, W_yz forward in z
+        row4(3, m, c);
+        const R yxr = one(3, xr);
+        for (int i = 0; i < 4; ++i) d[1][i] = (i == 3 ? yxr : c[i + 1]) - c[i];
+        row4(4, m, c);
+        row4(4, m - ey, e);
+        for (int i = 0; i < 4; ++i) d[1][i] += c[i] - e[i];
+        row4(5, m, c);
+        row4(5, m + dz, e);
+        for (int i = 0; i < 4; ++i) d[1][i] += e[i] - c[i];
+        // z component: W_zx forward in x, W_zy forward in y, W_zz backward in z
+        row4(6, m, c);
+        const R zxr = one(6, xr);
+        for (int i = 0; i < 4; ++i) d[2][i] = (i == 3 ? zxr : c[i + 1]) - c[i];
+        row4(7, m, c);
+        row4(7, m + dy, e);
+        for (int i = 0; i < 4; ++i) d[2][i] += e[i] - c[i];
+        row4(8, m, c);
+        row4(8, m - ez, e);
+        for (int i = 0; i < 4; ++i) d[2][i] += c[i] - e[i];
         R* fb = f + (size_t)b * 3 * g.N + m;
-#pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const R add = mih * d[a];
-            fb[(size_t)a * g.N] = accumulate ? fb[(size_t)a * g.N] + add : add;
+            R out[4];
+            if (accumulate) load4(fb + (size_t)a * g.N, out);
+            for (int i = 0; i < 4; ++i) out[i] = accumulate ? out[i] + mih * d[a][i] : mih * d[a][i];
+            store4(fb + (size_t)a * g.N, out);
         }
     }
     if (step_index && blockIdx.x == 0 && threadIdx.x == 0) *step_index += 1;
