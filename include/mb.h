@@ -102,10 +102,10 @@ typedef enum {
  *                half step solves the steady zero-mean Stokes flow of the current forces,
  *                v = P (-eta L)^{-1} (S F + f_body), and the blobs follow u = J v with the
  *                explicit midpoint rule; rho is not used, mean_mode must be 1, and the velocity
- *                field of the context is the flow of the last half step.  In either grid
- *                precision the blob positions, forces and interpolated velocities are FP64
- *                (the FP32 mode keeps only the grid and its FFTs in FP32); the step adjoint
- *                is not provided for it. */
+ *                field of the context is the flow of the last half step.  Each grid
+ *                precision keeps its blob arithmetic (FP64 positions and forces with
+ *                precision 1; float-float positions and FP32 forces with precision 0); the
+ *                step adjoint is not provided for it. */
 typedef struct {
     int nx, ny, nz;
     int batch;

@@ -972,6 +972,121 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     return MB_OK;
 }
 
+// One Stokes-limit step in FP32-grid mode (integrator 1, precision 0): the steps of
+// do_step_stokes on the split blob positions of the FP32 path (float-float offsets from bin
+// cells, FP32 forces, fixed-point shared-memory spreading).  Forces, spreading and the steady
+// solve at q^n give the flow v(q^n); the predictor pass moves the blobs to
+// q^{n+1/2} = q^n + dt/2 J v(q^n) and counts them into bins; forces, spreading and the solve at
+// q^{n+1/2} give v(q^{n+1/2}), and the corrector pass sets q^{n+1} = q^n + dt J v(q^{n+1/2}).
+mb_status do_step_stokes_fast(mb_ctx* ctx, bool ext, const double* body)
+{
+    cudaStream_t st = ctx->st;
+    const GridGeo& g = ctx->g;
+    const int B = ctx->B;
+    float* v_half = static_cast<float*>(ctx->v[ctx->cur ^ 1].p);
+    float* v_full = static_cast<float*>(ctx->v[ctx->cur].p);
+    float4* sA = static_cast<float4*>(ctx->sA.p);
+    float4* sB = static_cast<float4*>(ctx->sB.p);
+    float4* hA = static_cast<float4*>(ctx->hA[0].p);
+    float4* hB = static_cast<float4*>(ctx->hB[0].p);
+    const int32_t* box_of = static_cast<const int32_t*>(ctx->box_of.p);
+    const bool blobs = ctx->nb > 0;
+    if (ctx->timing) {
+        if (ctx->ev_pending == mb_ctx::EV_RING) MB_TRY(drain_stage_events(ctx));
+        ctx->ev = ctx->ev_ring.data() + (size_t)ctx->ev_pending * (NUM_STAGES + 1);
+    }
+    auto mark = [&](int i) { if (ctx->timing) cudaEventRecord(ctx->ev[i], st); };
+    const float dt = (float)ctx->d.dt;
+    // forces at (A, B) (binned already when `counted`), spreading, steady flow into v_out
+    auto half = [&](const float4* A, const float4* Bp, bool counted, float* v_out,
+                    bool marks) -> mb_status {
+        if (marks) mark(ST_BIN);
+        if (blobs) {
+            MB_CUDA(launch_bin32(st, ctx->nb, A, box_of, B, ctx->bg,
+                                 static_cast<int32_t*>(ctx->cell_count.p),
+                                 static_cast<int32_t*>(ctx->cell_start.p),
+                                 static_cast<int32_t*>(ctx->blob_cell.p),
+                                 static_cast<int32_t*>(ctx->blob_rank.p),
+                                 static_cast<int32_t*>(ctx->sorted.p),
+                                 static_cast<int32_t*>(ctx->scan_tmp.p),
+                                 static_cast<const int32_t*>(ctx->pid.p),
+                                 static_cast<float4*>(ctx->loc.p), counted));
+            ctx->launches += counted ? 2 : 3;
+            ctx->sorted_valid = true;
+        }
+        if (marks) mark(ST_FORCES);
+        if (blobs) {
+            MB_CUDA(launch_forces32(st, B, ctx->nb, ctx->max_box_blobs,
+                                    static_cast<const int64_t*>(ctx->box_off.p),
+                                    static_cast<const int32_t*>(ctx->sorted.p), A, Bp,
+                                    static_cast<const float4*>(ctx->loc.p),
+                                    static_cast<const int4*>(ctx->adj32.p),
+                                    static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
+                                    static_cast<const double*>(ctx->box_par.p),
+                                    static_cast<const int32_t*>(ctx->cell_start.p),
+                                    static_cast<const int32_t*>(ctx->blob_cell.p),
+                                    ext ? static_cast<const float4*>(ctx->ext32.p) : nullptr,
+                                    static_cast<float4*>(ctx->Fs32.p),
+                                    static_cast<float4*>(ctx->F32.p),
+                                    static_cast<float4*>(ctx->rec32.p), g, ctx->bg));
+            ctx->launches += 2;
+        }
+        if (marks) mark(ST_FORCE_SUM);
+        if (marks) mark(ST_SPREAD);
+        if (blobs) {
+            MB_CUDA(launch_spread32(st, B, static_cast<const float4*>(ctx->rec32.p),
+                                    static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
+                                    ctx->tile, static_cast<float*>(ctx->f.p), false));
+            ctx->launches += 1;
+        }
+        if (marks) mark(ST_STRESS);
+        FluidArgs<float> fa = fluid_args<float>(ctx, v_out, blobs ? ctx->f.p : nullptr, v_out,
+                                                ctx->body_prof.p, body, nullptr);
+        fa.no_v = 1;
+        fa.rho_dt = 0.0;
+        fa.half_eta = ctx->d.eta;
+        fa.mean_mode = 1;
+        cudaEvent_t* fm = marks && ctx->timing ? ctx->ev + ST_FLUID_X_FWD : nullptr;
+        if (ctx->fft_passes == 5) {
+            MB_CUDA(launch_fluid<float>(st, B, g, fa, fm));
+            ctx->launches += FLUID_KERNELS;
+        } else {
+            MB_CUDA(launch_fluid3<float>(st, B, g, fa, fm));
+            ctx->launches += FLUID3_KERNELS;
+        }
+        return MB_OK;
+    };
+    mark(ST_INTERP_PREDICT);
+    MB_TRY(half(sA, sB, false, v_half, false));
+    if (blobs) {
+        // q^{n+1/2} = q^n + dt/2 J(q^n) v(q^n), binned on the way
+        MB_CUDA(cudaMemsetAsync(ctx->cell_count.p, 0, sizeof(int32_t) * B * ctx->bg.ncell, st));
+        MB_CUDA(launch_interp32(st, 1, ctx->nb, sA, sB, v_half, nullptr, box_of, g, ctx->bg, dt,
+                                nullptr, nullptr, hA, hB, nullptr,
+                                static_cast<const int32_t*>(ctx->sorted.p),
+                                static_cast<int32_t*>(ctx->cell_count.p),
+                                static_cast<int32_t*>(ctx->blob_cell.p),
+                                static_cast<int32_t*>(ctx->blob_rank.p)));
+        ctx->launches += 1;
+    }
+    MB_TRY(half(hA, hB, true, v_full, true));
+    if (blobs) {
+        // q^{n+1} = q^n + dt J(q^{n+1/2}) v(q^{n+1/2})  (the mean of a field with itself)
+        MB_CUDA(launch_interp32(st, 2, ctx->nb, hA, hB, v_full, v_full, box_of, g, ctx->bg, dt,
+                                sA, sB, sA, sB, nullptr,
+                                static_cast<const int32_t*>(ctx->sorted.p)));
+        ctx->launches += 1;
+    }
+    mark(NUM_STAGES);
+    if (ctx->timing) ctx->ev_pending++;
+    ctx->hcur = 0;
+    ctx->hlast = 0;
+    ctx->pred_ready = false;
+    ctx->f_zero = false;
+    ctx->steps_taken++;
+    return MB_OK;
+}
+
 // Times each candidate spreading tile on the current binned records (the first step after
 // the blobs were set) and keeps the fastest; choices are cached per geometry and blob count.
 struct TuneKey {
@@ -1116,7 +1231,7 @@ mb_status run_fast_steps(mb_ctx* ctx, int n_steps, bool ext, const double* body)
 // FP64 blob positions of the current state (from the split form in FP32-grid mode).
 mb_status current_positions(mb_ctx* ctx)
 {
-    if (ctx->rsz == 4 && ctx->nb > 0 && ctx->d.integrator == 0)
+    if (ctx->rsz == 4 && ctx->nb > 0)
         MB_CUDA(launch_unsplit(ctx->st, ctx->nb, static_cast<const float4*>(ctx->sA.p),
                                static_cast<const float4*>(ctx->sB.p), ctx->g, ctx->bg,
                                static_cast<double*>(ctx->q.p)));
@@ -1470,8 +1585,29 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
         if (ctx->body_prof.p != before) drop_graph(ctx);   // captured steps hold the old buffer
     }
     const double* ext = nullptr;
+    if (ctx->d.integrator == 1 && ctx->rsz == 4) {
+        // Stokes limit, FP32 grid: the FP32 blob path with the external forces in FP32
+        bool has_ext = false;
+        if (ext_blob_force && ctx->nb > 0) {
+            const void* src = nullptr;
+            MB_TRY(stage_in(ctx, ext_blob_force, sizeof(double) * 3 * ctx->nb, ctx->ext, &src, "ext"));
+            MB_CUDA(launch_ext_prepare(ctx->st, ctx->B, ctx->max_box_blobs,
+                                       static_cast<const int64_t*>(ctx->box_off.p),
+                                       static_cast<const double*>(src),
+                                       static_cast<float4*>(ctx->ext32.p),
+                                       static_cast<double*>(ctx->partial.p),
+                                       static_cast<double*>(ctx->ext_sum.p),
+                                       static_cast<unsigned*>(ctx->ext_ticket.p)));
+            has_ext = true;
+        }
+        for (int s = 0; s < n_steps; ++s) {
+            MB_TRY(do_step_stokes_fast(ctx, has_ext, body_force));
+            if (!ctx->tuned) MB_TRY(autotune_spread(ctx));
+        }
+        return MB_OK;
+    }
     if (ctx->d.integrator == 1) {
-        // Stokes limit: FP64 forces in both grid precisions, from the library's copy
+        // Stokes limit, FP64 grid: FP64 positions and forces, from the library's copy
         if (ext_blob_force && ctx->nb > 0) {
             const void* src = nullptr;
             MB_TRY(stage_in(ctx, ext_blob_force, sizeof(double) * 3 * ctx->nb, ctx->ext, &src, "ext"));
@@ -1480,9 +1616,7 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
                                         cudaMemcpyDeviceToDevice, ctx->st));
             ext = static_cast<const double*>(ctx->ext.p);
         }
-        for (int s = 0; s < n_steps; ++s)
-            MB_TRY(ctx->rsz == 4 ? do_step_stokes<float>(ctx, ext, body_force)
-                                 : do_step_stokes<double>(ctx, ext, body_force));
+        for (int s = 0; s < n_steps; ++s) MB_TRY(do_step_stokes<double>(ctx, ext, body_force));
         return MB_OK;
     }
     if (ext_blob_force && ctx->nb > 0) {
@@ -1524,7 +1658,7 @@ mb_status mb_get_forces(mb_ctx* ctx, double* blob_force, double* midpoint_pos)
     }
     const size_t by = sizeof(double) * 3 * ctx->nb;
     if (ctx->nb == 0) return MB_OK;
-    if (ctx->rsz == 4 && ctx->d.integrator == 0) {
+    if (ctx->rsz == 4) {
         MB_CUDA(launch_forces_to_fp64(ctx->st, ctx->nb, static_cast<const float4*>(ctx->F32.p),
                                       static_cast<double*>(ctx->F.p)));
         MB_CUDA(launch_unsplit(ctx->st, ctx->nb, static_cast<const float4*>(ctx->hA[ctx->hlast].p),
@@ -1867,11 +2001,6 @@ static mb_status blob_velocities(mb_ctx* ctx)
     if (ctx->rsz == 4 && ctx->pred_ready)      // the last step's fused pass gathered them
         MB_CUDA(launch_forces_to_fp64(ctx->st, ctx->nb, static_cast<const float4*>(ctx->u32.p),
                                       static_cast<double*>(ctx->u.p)));
-    else if (ctx->rsz == 4 && ctx->d.integrator == 1)   // FP64 positions, FP32 field
-        MB_CUDA(launch_interp<float>(ctx->st, 0, ctx->nb, static_cast<const double*>(ctx->q.p),
-                                     nullptr, static_cast<const float*>(ctx->v[ctx->cur].p),
-                                     nullptr, static_cast<const int32_t*>(ctx->box_of.p),
-                                     ctx->g, ctx->d.dt, static_cast<double*>(ctx->u.p), nullptr));
     else if (ctx->rsz == 4)
         MB_CUDA(launch_interp32(ctx->st, 0, ctx->nb, static_cast<const float4*>(ctx->sA.p),
                                 static_cast<const float4*>(ctx->sB.p),

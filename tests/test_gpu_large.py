@@ -48,12 +48,12 @@ def test_fluid_update_parity_on_256_sides(prec, shape):
     assert rel_l2(vn, oracle.fluid_update(g, v, f, body=body)) < TOL[prec]
 
 
-def _particle_in(shape, seed):
+def _particle_in(shape, seed, stretch=0.05):
     nz, ny, nx = shape
     rng = np.random.default_rng(seed)
     L = np.array([nx, ny, nz], dtype=np.float64)
     s = wl.build_particles(rng.uniform(0, 1, size=3) * L, 1.0, rng, L)
-    s.pos = np.mod(s.pos + rng.normal(scale=0.05, size=s.pos.shape), L)
+    s.pos = np.mod(s.pos + rng.normal(scale=stretch, size=s.pos.shape), L)
     s.ext = rng.normal(scale=1e-3, size=s.pos.shape)
     return s
 
@@ -76,11 +76,18 @@ def test_thermal_step_parity_on_256_sides(prec, shape):
     assert rel_l2(v[0], v_ref) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [1, 0])
-def test_stokes_step_parity_on_a_256_side(prec):
+@pytest.mark.parametrize("prec,stretch,tol", [(1, 0.05, TOL[1]), (0, 0.0, TOL[0]),
+                                               (0, 0.05, 5e-5)])
+def test_stokes_step_parity_on_a_256_side(prec, stretch, tol):
+    """A particle in an 8 x 256 x 8 box.  In the Stokes limit the flow answers the forces
+    directly, and in a long thin periodic box the response to a net force grows with the box
+    length.  The springs' internal forces cancel exactly only in exact arithmetic: stretched
+    by 0.05h (forces ~ k 0.05 against external forces of 1e-3), their FP32 rounding leaves a
+    spurious net force whose amplified flow reaches ~2e-5 of the field, so the FP32 grid is
+    held to 5e-5 there and to the usual 1e-5 with the particle at rest shape."""
     shape = (8, 256, 8)
     nz, ny, nx = shape
-    s = _particle_in(shape, 8)
+    s = _particle_in(shape, 8, stretch)
     d = mb.GridDesc(nx, ny, nz, dt=0.05, precision=prec, mean_mode=1, integrator=1)
     with mb.Multiblob(d) as sim:
         sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring)
@@ -89,8 +96,8 @@ def test_stokes_step_parity_on_a_256_side(prec):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.stokes_step(g, 3, s.pos, s.pid, s.bonds, s.rest, s.k_spring,
                                       ext=s.ext)
-    assert position_error(q, q_ref, s.pos, g.L, 3) < TOL[prec]
-    assert rel_l2(v[0], v_ref) < TOL[prec]
+    assert position_error(q, q_ref, s.pos, g.L, 3) < tol
+    assert rel_l2(v[0], v_ref) < tol
 
 
 @pytest.fixture(scope="module")
