@@ -43,13 +43,13 @@ k_rhs_fft_x(FluidArgs<R> a, GridGeo g, int RP)
     const size_t zp = (size_t)((z + 1) & (nz - 1)) * ny, zm = (size_t)((z - 1) & (nz - 1)) * ny;
     const size_t z0 = (size_t)z * ny;
     // each work unit: 4 consecutive x (one vector load) of the row pair 2p, 2p+1
-    const int qx = nx / 4;
+    const int qx = nx / 4, lq = 31 - __clz(qx);
     const R* pz = vc + z0 * nx;
     const R* pzp = vc + zp * nx;
     const R* pzm = vc + zm * nx;
     const R* pf = fc ? fc + z0 * nx : nullptr;
     for (int u = threadIdx.x; u < qx * RP; u += blockDim.x) {
-        const int x0 = 4 * (u % qx), p = u / qx;
+        const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
         const int y0 = 2 * (yp0 + p), y1 = y0 + 1;
         R r0[4] = {R(0), R(0), R(0), R(0)}, r1[4] = {R(0), R(0), R(0), R(0)}, t[4];
         if (!a.no_v) {              // Stokes limit (no_v): the right-hand side is f + f_body
@@ -101,24 +101,27 @@ k_rhs_fft_x(FluidArgs<R> a, GridGeo g, int RP)
                        reinterpret_cast<const T*>(a.twf[0]));
     __syncthreads();
     T* out = a.spec + ((size_t)bc * nz + z) * (size_t)ny * nxh;
-    for (int t = threadIdx.x; t < RP * nxh; t += blockDim.x) {
-        const int k = t % nxh, p = t / nxh;
+    // row p, frequency k <= nx/2: even row (Z + conj Zr)/2, odd row -i (Z - conj Zr)/2
+    auto emit = [&](int p, int k) {
         const T Z = sb[p * ld + pj(k, sx)];
         const T Zr = sb[p * ld + pj((nx - k) & (nx - 1), sx)];
-        // even row: (Z + conj Zr)/2 ; odd row: -i (Z - conj Zr)/2
         const T Xa{(Z.x + Zr.x) * R(0.5), (Z.y - Zr.y) * R(0.5)};
         const T Xb{(Z.y + Zr.y) * R(0.5), (Zr.x - Z.x) * R(0.5)};
         const int y = 2 * (yp0 + p);
         out[(size_t)y * nxh + k] = Xa;
         out[(size_t)(y + 1) * nxh + k] = Xb;
-    }
+    };
+    const int hx = nx / 2, lh = 31 - __clz(hx);
+    for (int t = threadIdx.x; t < RP * hx; t += blockDim.x) emit(t >> lh, t & (hx - 1));
+    for (int p = threadIdx.x; p < RP; p += blockDim.x) emit(p, hx);
 }
 
 // Pass 2 / 4: complex FFT along y.  CTA = C consecutive kx columns of one (box, comp, z).
-template <typename R, bool INV>
+template <typename R, bool INV, int C>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
-k_fft_y(typename C2<R>::T* spec, const R* twy, GridGeo g, int C)
+k_fft_y(typename C2<R>::T* spec, const R* twy, GridGeo g)
 {
+    constexpr int LC = C == 16 ? 4 : 3;
     using T = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sb = reinterpret_cast<T*>(smem_raw);
@@ -127,29 +130,31 @@ k_fft_y(typename C2<R>::T* spec, const R* twy, GridGeo g, int C)
     const int cw = min(C, nxh - kx0);
     const int sy = pad_shift(ny), CL = C + 1;
     T* plane = spec + ((size_t)blockIdx.z * nz + blockIdx.y) * (size_t)ny * nxh + kx0;
-    // every copy of a thread in flight at once
-    for (int t = threadIdx.x; t < ny * cw; t += blockDim.x) {
-        const int y = t / cw, c = t % cw;
-        async_copy(&sb[pj(y, sy) * CL + c], &plane[(size_t)y * nxh + c]);
+    // every copy of a thread in flight at once (index arithmetic in shifts: C and ny are
+    // powers of two; columns past the last kx are transformed as garbage and not stored)
+    for (int t = threadIdx.x; t < ny * C; t += blockDim.x) {
+        const int y = t >> LC, c = t & (C - 1);
+        if (c < cw) async_copy(&sb[pj(y, sy) * CL + c], &plane[(size_t)y * nxh + c]);
     }
     async_wait_all();
     __syncthreads();
     auto idx = [CL, sy](int l, int j) { return pj(j, sy) * CL + l; };
     const T* tw = reinterpret_cast<const T*>(twy);
-    lines_fft_n<INV>(ny, sb, cw, idx, tw);
+    lines_fft_n<INV>(ny, sb, C, idx, tw);
     __syncthreads();
-    for (int t = threadIdx.x; t < ny * cw; t += blockDim.x) {
-        const int y = t / cw, c = t % cw;
-        plane[(size_t)y * nxh + c] = sb[pj(y, sy) * CL + c];
+    for (int t = threadIdx.x; t < ny * C; t += blockDim.x) {
+        const int y = t >> LC, c = t & (C - 1);
+        if (c < cw) plane[(size_t)y * nxh + c] = sb[pj(y, sy) * CL + c];
     }
 }
 
 // Pass 3: FFT along z, Crank-Nicolson divide, projection, k = 0 mode, inverse FFT along z.
 // CTA = C consecutive kx columns at one ky of one box, all three components.
-template <typename R>
+template <typename R, int C>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
-k_fft_z_solve(FluidArgs<R> a, GridGeo g, int C)
+k_fft_z_solve(FluidArgs<R> a, GridGeo g)
 {
+    constexpr int LC = C == 16 ? 4 : 3;
     using T = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sb = reinterpret_cast<T*>(smem_raw);    // [3][nz][C]
@@ -168,15 +173,17 @@ k_fft_z_solve(FluidArgs<R> a, GridGeo g, int C)
     // that follows the column copies)
     T* twz = sb + 3 * PZ * CL;
     for (int i = threadIdx.x; i < nz; i += blockDim.x) twz[i] = reinterpret_cast<const T*>(a.twf[2])[i];
-    for (int t = threadIdx.x; t < 3 * nz * cw; t += blockDim.x) {
-        const int c = t / (nz * cw), rem = t % (nz * cw);
-        const int z = rem / cw, k = rem % cw;
-        async_copy(&sb[at(c, z, k)], &col[c][(size_t)z * zstride + k]);
+    const int lz = 31 - __clz(nz);
+    // index arithmetic in shifts (C and nz are powers of two); columns past the last kx are
+    // transformed as garbage and not stored
+    for (int t = threadIdx.x; t < 3 * nz * C; t += blockDim.x) {
+        const int k = t & (C - 1), z = (t >> LC) & (nz - 1), c = t >> (LC + lz);
+        if (k < cw) async_copy(&sb[at(c, z, k)], &col[c][(size_t)z * zstride + k]);
     }
     async_wait_all();
     __syncthreads();
-    auto idx = [=](int l, int j) { return at(l / cw, j, l % cw); };
-    lines_fft_n<false>(nz, sb, 3 * cw, idx, twz);
+    auto idx = [=](int l, int j) { return at(l >> LC, j, l & (C - 1)); };
+    lines_fft_n<false>(nz, sb, 3 * C, idx, twz);
     __syncthreads();
 
     const R* sym = reinterpret_cast<const R*>(a.symr);      // [9][256] cos, sin, lambda
@@ -190,8 +197,8 @@ k_fft_z_solve(FluidArgs<R> a, GridGeo g, int C)
     const R* sinz = sym + 7 * 256;
     const R* lamz = sym + 8 * 256;
     const R ih = R(g.inv_h);
-    for (int t = threadIdx.x; t < nz * cw; t += blockDim.x) {
-        const int kz = t / cw, k = t % cw;
+    for (int t = threadIdx.x; t < nz * C; t += blockDim.x) {
+        const int kz = t >> LC, k = t & (C - 1);
         const int kx = kx0 + k;
         T W[3];
         const R lam = R(lamx[kx]) + R(lamy[ky]) + R(lamz[kz]);
@@ -228,12 +235,11 @@ k_fft_z_solve(FluidArgs<R> a, GridGeo g, int C)
         for (int c = 0; c < 3; ++c) sb[at(c, kz, k)] = W[c];
     }
     __syncthreads();
-    lines_fft_n<true>(nz, sb, 3 * cw, idx, twz);
+    lines_fft_n<true>(nz, sb, 3 * C, idx, twz);
     __syncthreads();
-    for (int t = threadIdx.x; t < 3 * nz * cw; t += blockDim.x) {
-        const int c = t / (nz * cw), rem = t % (nz * cw);
-        const int z = rem / cw, k = rem % cw;
-        col[c][(size_t)z * zstride + k] = sb[at(c, z, k)];
+    for (int t = threadIdx.x; t < 3 * nz * C; t += blockDim.x) {
+        const int k = t & (C - 1), z = (t >> LC) & (nz - 1), c = t >> (LC + lz);
+        if (k < cw) col[c][(size_t)z * zstride + k] = sb[at(c, z, k)];
     }
 }
 
@@ -252,9 +258,10 @@ k_fft_x_c2r(FluidArgs<R> a, GridGeo g, int RP)
     const int z = blockIdx.y;
     const int bc = blockIdx.z;
     const T* in = a.spec + ((size_t)bc * nz + z) * (size_t)ny * nxh;
+    const int lx = 31 - __clz(nx);
     #pragma unroll 4
     for (int t = threadIdx.x; t < RP * nx; t += blockDim.x) {
-        const int k = t % nx, p = t / nx;
+        const int k = t & (nx - 1), p = t >> lx;
         const int y = 2 * (yp0 + p);
         T Xa, Xb;
         if (k <= nx / 2) {
@@ -275,9 +282,9 @@ k_fft_x_c2r(FluidArgs<R> a, GridGeo g, int RP)
     __syncthreads();
     const R scale = R(1.0 / (double)g.N);
     R* out = a.v_out + (size_t)bc * g.N + (size_t)z * ny * nx;
-    const int qx = nx / 4;
+    const int qx = nx / 4, lq = 31 - __clz(qx);
     for (int u = threadIdx.x; u < qx * RP; u += blockDim.x) {
-        const int x0 = 4 * (u % qx), p = u / qx;
+        const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
         R r0[4], r1[4];
         for (int i = 0; i < 4; ++i) {
             const T zv = sb[p * ld + pj(x0 + i, sx)];
@@ -296,20 +303,21 @@ cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidAr
     using T = typename C2<R>::T;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     const int RP = ny / 2 < 16 ? ny / 2 : 16;
-    const int C = sizeof(R) == 4 ? 16 : 8;
+    constexpr int CY = sizeof(R) == 4 ? 16 : 8, CZ5 = 8;
+    const int C = CY;
     static std::atomic<unsigned> attr{0};     // per instantiation
     if (first_on_device(attr)) {
         const int lim = 200 * 1024;
         cudaFuncSetAttribute(k_rhs_fft_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_fft_y<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_fft_y<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_fft_z_solve<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_fft_y<R, false, CY>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_fft_y<R, true, CY>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_fft_z_solve<R, CZ5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_fft_x_c2r<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     }
     const size_t smem_x = (size_t)RP * (padded_len(nx) + 1) * sizeof(T);
     const size_t smem_y = (size_t)padded_len(ny) * (C + 1) * sizeof(T);
     // the z pass holds three components of its columns: 8 columns keep three blocks per SM
-    const int Cz = 8;
+    const int Cz = CZ5;
     const size_t smem_z = ((size_t)3 * padded_len(nz) * (Cz + 1) + nz) * sizeof(T);
     const unsigned nchunk = (unsigned)((nxh + C - 1) / C);
     const unsigned nchunk_z = (unsigned)((nxh + Cz - 1) / Cz);
@@ -317,11 +325,11 @@ cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidAr
     mark(0);
     k_rhs_fft_x<R><<<dim3(ny / 2 / RP, nz, 3 * B), 256, smem_x, st>>>(a, g, RP);
     mark(1);
-    k_fft_y<R, false><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.twf[1], g, C);
+    k_fft_y<R, false, CY><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.twf[1], g);
     mark(2);
-    k_fft_z_solve<R><<<dim3(nchunk_z, ny, B), 256, smem_z, st>>>(a, g, Cz);
+    k_fft_z_solve<R, CZ5><<<dim3(nchunk_z, ny, B), 256, smem_z, st>>>(a, g);
     mark(3);
-    k_fft_y<R, true><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.twf[1], g, C);
+    k_fft_y<R, true, CY><<<dim3(nchunk, nz, 3 * B), 256, smem_y, st>>>(a.spec, a.twf[1], g);
     mark(4);
     k_fft_x_c2r<R><<<dim3(ny / 2 / RP, nz, 3 * B), 256, smem_x, st>>>(a, g, RP);
     mark(5);
