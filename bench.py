@@ -101,10 +101,14 @@ def measured_traffic(stage):
         f = line.split()
         if len(f) != 5 or f[0] != stage:
             continue
-        src = os.path.join(here, f[2])
-        if not os.path.exists(src):
+        # the kernel's source files, '+'-separated (the .cu and the headers it includes)
+        srcs = [os.path.join(here, x) for x in f[2].split("+")]
+        if not all(os.path.exists(x) for x in srcs):
             return None
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != f[3]:
+        h = hashlib.sha256()
+        for x in srcs:
+            h.update(open(x, "rb").read())
+        if h.hexdigest() != f[3]:
             return None
         return int(f[4])
     return None

@@ -58,10 +58,10 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     const R* pf = fc ? fc + (size_t)z * ny * nx : nullptr;
     R* pclr = a.f_clear && fc ? a.f_clear + (size_t)bc * g.N + (size_t)z * ny * nx : nullptr;
     // each work unit: 4 consecutive x of the two rows 2p, 2p+1
-    const int qx = nx / 4;
+    const int qx = nx / 4, lq = 31 - __clz(qx);   // nx is a power of two
     for (int u = threadIdx.x; u < qx * (ny / 2) && a.no_v; u += blockDim.x) {
         // Stokes limit: the right-hand side is the force density (and body force) alone
-        const int x0 = 4 * (u % qx), p = u / qx;
+        const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
         const int y0 = 2 * p, y1 = y0 + 1;
         R r0[4] = {R(0), R(0), R(0), R(0)}, r1[4] = {R(0), R(0), R(0), R(0)};
         if (pf) {
@@ -87,7 +87,7 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         }
     }
     for (int u = threadIdx.x; u < qx * (ny / 2) && !a.no_v; u += blockDim.x) {
-        const int x0 = 4 * (u % qx), p = u / qx;
+        const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
         const int y0 = 2 * p, y1 = y0 + 1;
         const int ym = (y0 - 1) & (ny - 1), yp = (y1 + 1) & (ny - 1);
         R c0[4], c1[4], am[4], ap[4], t[4];
@@ -392,9 +392,9 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     __syncthreads();
     const R scale = R(1.0 / (double)g.N);
     R* out = a.v_out + (size_t)bc * g.N + (size_t)z * ny * nx;
-    const int qx = nx / 4;
+    const int qx = nx / 4, lq = 31 - __clz(qx);   // nx is a power of two
     for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
-        const int x0 = 4 * (u % qx), p = u / qx;
+        const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
         R r0[4], r1[4];
         for (int i = 0; i < 4; ++i) {
             const int j = x0 + i;
