@@ -249,6 +249,7 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------------------------
 def run_ours(args):
+    import numpy as np
     import torch
 
     import paper_1407_5600_gb300 as mb
@@ -386,8 +387,9 @@ def run_ours(args):
                 "ms_per_step": ms64 / K64, "steps": K64,
                 "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stages64.items()}}
 
-    # ---- the other integrators (FP32 grid), for the record: the Stokes limit on the same
-    # suspension, and the fluctuating 256^3 suspension (kT = 1e-3, five-pass FFT) ---------
+    # ---- the other workloads (FP32 grid), for the record: the Stokes limit on the same
+    # suspension, the fluctuating 256^3 suspension (kT = 1e-3, five-pass FFT) and the batched
+    # gap sweep (32 boxes of 64^3 in one context) ------------------------------------------
     others = None
     if args.other_steps > 0:
         K2 = args.other_steps
@@ -423,6 +425,32 @@ def run_ours(args):
             "blob_steps_per_s": world * s5.n_blobs * K2 / (ms5 * 1e-3),
             "ms_per_step": ms5 / K2, "steps": K2,
             "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in st5.items()}}
+        nbx, n2 = 32, 64
+        sweep = [wl.gap_sweep_box(b, n_boxes=nbx, n=n2, a=1.6) for b in range(nbx)]
+        spec2 = sweep[0][0]
+        sim2 = mb.Multiblob(mb.GridDesc(n2, n2, n2, batch=nbx, precision=0, dt=spec2.dt,
+                                        eta=spec2.eta, h=spec2.h, mean_mode=spec2.mean_mode),
+                           stream=stream, device=dev)
+        for b, (_, sb) in enumerate(sweep):
+            sim2.set_particles(b, sb.pos, sb.pid, sb.bonds, sb.rest, sb.k_spring)
+        ext2 = torch.from_numpy(np.concatenate([sb.ext for _, sb in sweep])).to(dev)
+        for _ in range(3):
+            mb.step(sim2.ctx, 1, ext2, None)
+        evs2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        barrier()
+        evs2[0].record(stream)
+        mb.step(sim2.ctx, K2, ext2, None)
+        evs2[1].record(stream)
+        barrier()
+        ms2 = max_over_ranks(evs2[0].elapsed_time(evs2[1]))
+        nb2 = sum(sb.n_blobs for _, sb in sweep)
+        sim2.close()
+        others["gap_sweep_32x64"] = {
+            "workload": "batched gap sweep: 32 boxes of 64^3, two particles of a = 1.6h each",
+            "value": world * nbx * n2 ** 3 * K2 / (ms2 * 1e-3), "unit": "cell-steps/s",
+            "blob_steps_per_s": world * nb2 * K2 / (ms2 * 1e-3),
+            "ms_per_step": ms2 / K2, "steps": K2,
+            "l2": "not flushed: the grids (velocity pair, force, spectrum: ~0.4 GB) exceed L2"}
 
     # ---- CPU baseline (oracle, rank 0, N = 1 only) ---------------------------------------
     cpu = None
@@ -446,7 +474,7 @@ def run_ours(args):
             "roofline": roofline,
             "stages": per_stage,
             "fp64": fp64,
-            "other_integrators": others,
+            "other_workloads": others,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
