@@ -246,8 +246,8 @@ mb_status mb_set_positions(mb_ctx* ctx, const double* pos);
  * and T (Eq. vf: the projection P, the Laplacian and the CN factors are symmetric and commute),
  * so its transpose reuses the forward solver; the blob-force transpose is the force Hessian
  * applied to the incoming gradient (forces derive from a potential).  Provided for FP64
- * contexts (precision 1) with batch 1 and integrator 0; MB_EINVAL otherwise.  Arrays may be
- * host or device. */
+ * contexts (precision 1) with batch 1, integrator 0, kT = 0 and advection = 0; MB_EINVAL
+ * otherwise.  Arrays may be host or device. */
 mb_status mb_adjoint_step(mb_ctx* ctx, const double* pos_n, const void* grid_v_n,
                           const double* ext_blob_force, const double* body_force,
                           double* grad_pos, void* grad_v, double* grad_k_spring);

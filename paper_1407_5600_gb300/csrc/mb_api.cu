@@ -1844,6 +1844,8 @@ mb_status mb_adjoint_step(mb_ctx* ctx, const double* pos_n, const void* grid_v_n
     MB_TRY(adjoint_preconditions(ctx));
     if (ctx->d.integrator != 0)
         return invalid(ctx, "the step adjoint is provided for the inertial coupling integrator");
+    if (ctx->thermal || ctx->advect)
+        return invalid(ctx, "the step adjoint is provided without the thermal and convective stresses");
     if (body_force) MB_TRY(set_body(ctx, body_force, ctx->prof_scratch, false));
     cudaStream_t st = ctx->st;
     const GridGeo& g = ctx->g;

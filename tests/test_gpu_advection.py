@@ -81,3 +81,14 @@ def test_step_with_advection_parity(prec, kT):
 def test_stokes_integrator_rejects_advection():
     with pytest.raises(mb.MBError, match="convective"):
         mb.Multiblob(mb.GridDesc(8, 8, 8, integrator=1, mean_mode=1, advection=1))
+
+
+@pytest.mark.parametrize("kw", [dict(advection=1), dict(kT=1e-3)])
+def test_step_adjoint_rejects_convective_and_thermal_stress(kw):
+    spec, s = wl.single_particle(n=16, a=1.0, seed=2)
+    with mb.Multiblob(mb.GridDesc(16, 16, 16, precision=1, **kw)) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring)
+        v = np.zeros((3, 16, 16, 16))
+        with pytest.raises(mb.MBError, match="thermal and convective"):
+            mb.adjoint_step(sim.ctx, s.pos.copy(), v, None, None, np.zeros_like(s.pos),
+                            np.zeros_like(v))

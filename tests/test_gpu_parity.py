@@ -461,3 +461,31 @@ def test_deterministic_fp64_runs_are_bitwise_identical():
                                s.k_rep, s.r_cut, ext=ext, body=s.body)
     assert position_error(outs[0][0], q_ref, s.pos, g.L, 4) < TOL[1]
     assert rel_l2(outs[0][1][0], v_ref) < TOL[1]
+
+
+def test_single_particle_full_run_fp64_deterministic():
+    """The single-particle Stokeslet run at full length (32^3, 200 steps, FP64, deterministic):
+    the whole trajectory equals the oracle's (1e-10), and the drift approaches the
+    Hasimoto-corrected Stokes drift of Table rad's radius from below (the t^-1/2 approach of a
+    suddenly forced sphere is still under way at t = 10)."""
+    import json
+    import os
+    spec, s = wl.single_particle(n=32, a=1.0, seed=1)
+    d = mb.GridDesc(32, 32, 32, h=spec.h, rho=spec.rho, eta=spec.eta, dt=spec.dt,
+                    precision=1, deterministic=1, mean_mode=spec.mean_mode)
+    Us = []
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring)
+        for _ in range(4):
+            sim.step(50, ext_blob_force=s.ext)
+            Us.append(to_np(sim.particle_velocities()[0])[0, 0])
+        q = to_np(sim.blob_positions())
+    g = _oracle_grid(d)
+    q_ref, _ = oracle.step(g, 200, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
+                           ext=s.ext)
+    assert position_error(q, q_ref, s.pos, g.L, 200) < TOL[1]
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table_rad.json")))
+    RH = dict((r[0], r[1]) for r in gold["rows"])[1.0]
+    U_inf = 1e-3 * (1.0 - 2.84 * RH / 32.0) / (6 * np.pi * spec.eta * RH)
+    assert np.all(np.diff(Us) > 0)
+    assert 0.6 * U_inf < Us[-1] < 1.05 * U_inf, (Us, U_inf)
