@@ -1163,13 +1163,14 @@ mb_status capture_graph(mb_ctx* ctx, bool ext, const double* body)
     cudaStream_t user = ctx->st;
     const int64_t steps0 = ctx->steps_taken, l0 = ctx->launches;
     const int hcur0 = ctx->hcur, hlast0 = ctx->hlast;
-    const bool ready0 = ctx->pred_ready;
+    const bool ready0 = ctx->pred_ready, fz0 = ctx->f_zero;
     ctx->st = ctx->cap_stream;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal);
     mb_status s = MB_OK;
     if (e == cudaSuccess) {
-        s = do_step_fast(ctx, ext, body);
+        s = ctx->d.integrator == 1 ? do_step_stokes_fast(ctx, ext, body)
+                                   : do_step_fast(ctx, ext, body);
         e = cudaStreamEndCapture(ctx->st, &graph);
     }
     ctx->st = user;
@@ -1178,6 +1179,7 @@ mb_status capture_graph(mb_ctx* ctx, bool ext, const double* body)
     ctx->hcur = hcur0;
     ctx->hlast = hlast0;
     ctx->pred_ready = ready0;
+    ctx->f_zero = fz0;
     ctx->graph_launches = ctx->launches - l0;
     ctx->launches = l0;
     if (s != MB_OK) {
@@ -1223,6 +1225,33 @@ mb_status run_fast_steps(mb_ctx* ctx, int n_steps, bool ext, const double* body)
             MB_TRY(capture_graph(ctx, ext, body));
         MB_CUDA(cudaGraphLaunch(ctx->graph_exec[c], ctx->st));
         finish_fast_step(ctx);
+        ctx->launches += ctx->graph_launches;
+    }
+    return MB_OK;
+}
+
+// Stokes-limit steps in FP32-grid mode: direct launches until the spreading tile is tuned,
+// then replays of a captured graph of one step (keyed by external forces and body force).
+mb_status run_stokes_fast_steps(mb_ctx* ctx, int n_steps, bool ext, const double* body)
+{
+    const bool graphs = ctx->use_graph && !ctx->timing && ctx->nb > 0;
+    for (int s = 0; s < n_steps; ++s) {
+        if (!graphs || !ctx->tuned) {
+            MB_TRY(do_step_stokes_fast(ctx, ext, body));
+            if (!ctx->tuned) MB_TRY(autotune_spread(ctx));
+            continue;
+        }
+        const int c = ctx->cur;
+        if (!ctx->graph_exec[c] || ctx->graph_ext[c] != ext ||
+            ctx->graph_body[c] != (body != nullptr))
+            MB_TRY(capture_graph(ctx, ext, body));
+        MB_CUDA(cudaGraphLaunch(ctx->graph_exec[c], ctx->st));
+        // the state changes of do_step_stokes_fast
+        ctx->hcur = ctx->hlast = 0;
+        ctx->pred_ready = false;
+        ctx->f_zero = false;
+        ctx->sorted_valid = true;
+        ctx->steps_taken++;
         ctx->launches += ctx->graph_launches;
     }
     return MB_OK;
@@ -1600,11 +1629,7 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
                                        static_cast<unsigned*>(ctx->ext_ticket.p)));
             has_ext = true;
         }
-        for (int s = 0; s < n_steps; ++s) {
-            MB_TRY(do_step_stokes_fast(ctx, has_ext, body_force));
-            if (!ctx->tuned) MB_TRY(autotune_spread(ctx));
-        }
-        return MB_OK;
+        return run_stokes_fast_steps(ctx, n_steps, has_ext, body_force);
     }
     if (ctx->d.integrator == 1) {
         // Stokes limit, FP64 grid: FP64 positions and forces, from the library's copy
