@@ -987,6 +987,33 @@ cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t nb, int64_t max_box
     return cudaGetLastError();
 }
 
+cudaError_t launch_springs32(cudaStream_t st, int64_t nb, const float4* A, const float4* B,
+                             const int4* adj, const int32_t* adj_start, const int32_t* box_of,
+                             const double* box_par, const GridGeo& g, const BinGeo& bg, float4* Fs)
+{
+    if (nb <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(Fs, 0, sizeof(float4) * nb, st);
+    if (e != cudaSuccess) return e;
+    k_springs32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, B, adj, adj_start, box_of, box_par, g,
+                                                    bg, reinterpret_cast<float*>(Fs));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs32(cudaStream_t st, int Bx, int64_t max_box_blobs,
+                           const int64_t* box_off, const int32_t* sorted, const float4* A,
+                           const float4* B, const float4* loc, const int32_t* box_of,
+                           const double* box_par, const int32_t* cell_start,
+                           const int32_t* blob_cell, const float4* ext, const float4* Fs,
+                           float4* F, float4* rec, const GridGeo& g, const BinGeo& bg)
+{
+    (void)box_of;
+    if (max_box_blobs <= 0) return cudaSuccess;
+    Force32Args a{box_off, sorted, A, B, loc, Fs, box_par, cell_start, blob_cell, ext, F, rec};
+    dim3 grid(blocks_for(max_box_blobs, 256), (unsigned)Bx);
+    k_forces32<<<grid, 256, 0, st>>>(a, g, bg);
+    return cudaGetLastError();
+}
+
 size_t spread32_smem(const int tile[3])
 {
     return (size_t)3 * (tile[0] + 8) * (tile[1] + 3) * (tile[2] + 3) * sizeof(float);

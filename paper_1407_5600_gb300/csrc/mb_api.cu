@@ -171,6 +171,9 @@ struct mb_ctx {
     // CUDA graphs of one FP32-grid step, one per velocity-buffer parity
     bool use_graph = true;
     cudaStream_t cap_stream = nullptr;
+    // second stream for the spring forces, which overlap the binning (fork/join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork[2] = {nullptr, nullptr};
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     bool graph_ext[2] = {false, false}, graph_body[2] = {false, false};
     int graph_hcur[2] = {0, 0};
@@ -867,6 +870,24 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                                 static_cast<int32_t*>(ctx->blob_rank.p)));
         ctx->launches += 1;
     }
+    // the spring forces need only the midpoint positions: without stage timing they run on a
+    // second stream while the blobs are binned (fork/join events, also inside captured graphs)
+    const bool overlap = blobs && !ctx->timing;
+    if (overlap) {
+        if (!ctx->side) {
+            MB_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+            for (cudaEvent_t& e : ctx->fork)
+                MB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        MB_CUDA(cudaEventRecord(ctx->fork[0], st));
+        MB_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork[0], 0));
+        MB_CUDA(launch_springs32(ctx->side, ctx->nb, hA, hB,
+                                 static_cast<const int4*>(ctx->adj32.p),
+                                 static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
+                                 static_cast<const double*>(ctx->box_par.p), g, ctx->bg,
+                                 static_cast<float4*>(ctx->Fs32.p)));
+        MB_CUDA(cudaEventRecord(ctx->fork[1], ctx->side));
+    }
     mark(ST_BIN);
     if (blobs) {
         MB_CUDA(launch_bin32(st, ctx->nb, hA, box_of, B, ctx->bg,
@@ -883,18 +904,32 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     }
     mark(ST_FORCES);
     if (blobs) {
-        MB_CUDA(launch_forces32(st, B, ctx->nb, ctx->max_box_blobs,
-                                static_cast<const int64_t*>(ctx->box_off.p),
-                                static_cast<const int32_t*>(ctx->sorted.p), hA, hB,
-                                static_cast<const float4*>(ctx->loc.p),
-                                static_cast<const int4*>(ctx->adj32.p),
-                                static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
-                                static_cast<const double*>(ctx->box_par.p),
-                                static_cast<const int32_t*>(ctx->cell_start.p),
-                                static_cast<const int32_t*>(ctx->blob_cell.p),
-                                ext ? static_cast<const float4*>(ctx->ext32.p) : nullptr,
-                                static_cast<float4*>(ctx->Fs32.p), static_cast<float4*>(ctx->F32.p),
-                                static_cast<float4*>(ctx->rec32.p), g, ctx->bg));
+        const int64_t* box_off = static_cast<const int64_t*>(ctx->box_off.p);
+        const float4* ext4 = ext ? static_cast<const float4*>(ctx->ext32.p) : nullptr;
+        if (overlap) {
+            MB_CUDA(cudaStreamWaitEvent(st, ctx->fork[1], 0));
+            MB_CUDA(launch_pairs32(st, B, ctx->max_box_blobs, box_off,
+                                   static_cast<const int32_t*>(ctx->sorted.p), hA, hB,
+                                   static_cast<const float4*>(ctx->loc.p), box_of,
+                                   static_cast<const double*>(ctx->box_par.p),
+                                   static_cast<const int32_t*>(ctx->cell_start.p),
+                                   static_cast<const int32_t*>(ctx->blob_cell.p), ext4,
+                                   static_cast<float4*>(ctx->Fs32.p),
+                                   static_cast<float4*>(ctx->F32.p),
+                                   static_cast<float4*>(ctx->rec32.p), g, ctx->bg));
+        } else {
+            MB_CUDA(launch_forces32(st, B, ctx->nb, ctx->max_box_blobs, box_off,
+                                    static_cast<const int32_t*>(ctx->sorted.p), hA, hB,
+                                    static_cast<const float4*>(ctx->loc.p),
+                                    static_cast<const int4*>(ctx->adj32.p),
+                                    static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
+                                    static_cast<const double*>(ctx->box_par.p),
+                                    static_cast<const int32_t*>(ctx->cell_start.p),
+                                    static_cast<const int32_t*>(ctx->blob_cell.p), ext4,
+                                    static_cast<float4*>(ctx->Fs32.p),
+                                    static_cast<float4*>(ctx->F32.p),
+                                    static_cast<float4*>(ctx->rec32.p), g, ctx->bg));
+        }
         ctx->launches += 2;
     }
     mark(ST_FORCE_SUM);                 // the mean momentum advances inside the z pass
@@ -1326,6 +1361,11 @@ void release(mb_ctx* ctx)
     drop_graph(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     ctx->cap_stream = nullptr;
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    ctx->side = nullptr;
+    for (cudaEvent_t& e : ctx->fork)
+        if (e) cudaEventDestroy(e);
+    ctx->fork[0] = ctx->fork[1] = nullptr;
     DBuf* all[] = {&ctx->v[0], &ctx->v[1], &ctx->vsum, &ctx->f, &ctx->spec, &ctx->vbar, &ctx->fsum,
                    &ctx->tw[0], &ctx->tw[1], &ctx->tw[2], &ctx->twf[0], &ctx->twf[1],
                    &ctx->twf[2], &ctx->sym, &ctx->symr, &ctx->body_prof,
@@ -1342,7 +1382,7 @@ void release(mb_ctx* ctx)
                    &ctx->ext_sum, &ctx->ext_ticket, &ctx->adj32, &ctx->adj32_start, &ctx->Fs32, &ctx->u32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
                    &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk,
                    &ctx->a_vn, &ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvp, &ctx->a_gvn,
-                   &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero};
+                   &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero, &ctx->W, &ctx->step_index};
     for (DBuf* b : all) dfree(*b);
     for (cudaEvent_t& e : ctx->ev_ring)
         if (e) cudaEventDestroy(e);

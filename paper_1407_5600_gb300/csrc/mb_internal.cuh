@@ -200,6 +200,17 @@ cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t nb, int64_t max_box
                             const double* box_par, const int32_t* cell_start,
                             const int32_t* blob_cell, const float4* ext, float4* Fs, float4* F,
                             float4* rec, const GridGeo& g, const BinGeo& bg);
+// The two halves of launch_forces32, for running the springs on another stream: the spring
+// forces (Fs, zeroed first), then the pair forces, sums and sorted records.
+cudaError_t launch_springs32(cudaStream_t st, int64_t nb, const float4* A, const float4* B,
+                             const int4* adj, const int32_t* adj_start, const int32_t* box_of,
+                             const double* box_par, const GridGeo& g, const BinGeo& bg, float4* Fs);
+cudaError_t launch_pairs32(cudaStream_t st, int Bx, int64_t max_box_blobs,
+                           const int64_t* box_off, const int32_t* sorted, const float4* A,
+                           const float4* B, const float4* loc, const int32_t* box_of,
+                           const double* box_par, const int32_t* cell_start,
+                           const int32_t* blob_cell, const float4* ext, const float4* Fs,
+                           float4* F, float4* rec, const GridGeo& g, const BinGeo& bg);
 // f = S F from the binned records (zeroes f first unless the caller knows it is zero).  The tile (nodes per block) must satisfy
 // spread32_tile_ok: at least 4 and whole bin cells per side, dividing the grid, at most 64 rows
 // of cells, shared copy within 200 KiB; other tiles return cudaErrorInvalidValue.
