@@ -138,3 +138,17 @@ def test_momentum_bookkeeping_with_spread_forces():
     vn = mb.fluid_update(g, v, mb.spread(g, q, F))
     dP = g.rho * g.h ** 3 * (vn.sum((1, 2, 3)) - v.sum((1, 2, 3)))
     assert np.max(np.abs(dP - g.dt * F.sum(0))) < 1e-12 * np.max(np.abs(F.sum(0))) * 10
+
+
+def test_time_stepping_converges_to_the_steady_stokes_flow():
+    """A constant force density (a spread point force) held on the fluid: the Crank-Nicolson
+    steps converge to the steady zero-mean Stokes flow of the same force, the solve that the
+    mobility pins use (each mode relaxes by (1 - eta lam dt/(2 rho))/(1 + ...) per step)."""
+    g = mb.Grid(16, 8, 16, h=0.9, rho=1.0, eta=1.0, dt=1.0, mean_mode=1)
+    F = np.array([[0.3, -0.2, 0.5]])
+    f = mb.spread(g, np.array([[3.3, 2.1, 7.7]]), F)
+    v = g.zeros()
+    for _ in range(300):
+        v = mb.fluid_update(g, v, f)
+    ref = mb.stokes_solve(g, f)
+    assert np.linalg.norm(v - ref) < 1e-10 * np.linalg.norm(ref)
