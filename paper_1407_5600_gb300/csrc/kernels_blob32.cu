@@ -937,6 +937,9 @@ cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, 
     if (nb <= 0) return cudaSuccess;
     const FusedArgs f{A, v0, v1, vp, box_of, dt, A_base, B_base, A_out, B_out, Ah_out, Bh_out,
                       order, count, blob_cell, blob_rank, u_out};
+    static std::atomic<unsigned> attr{0};
+    if (first_on_device(attr))       // no shared memory: all of the SM's L1 for the gathers
+        cudaFuncSetAttribute(k_interp32_fused, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     k_interp32_fused<<<blocks_for(nb, 256), 256, 0, st>>>(nb, f, g, bg);
     return cudaGetLastError();
 }
