@@ -127,7 +127,7 @@ def parse():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--stage-json", default=None, help="also write per-stage times here")
     ap.add_argument("--ref-seconds", type=float, default=None,
-                    help="CPU seconds of the reference arm's oracle sample (default 3 s a step)")
+                    help="CPU seconds of the reference arm's oracle sample (default 3 s a step, at most 120 s)")
     return ap.parse_args()
 
 
@@ -229,9 +229,10 @@ def run_reference(args):
         return
     if args.warmup:
         oracle_sample(max_seconds=1.0, min_steps=1)
-    budget = args.ref_seconds if args.ref_seconds else max(10.0, 3.0 * args.steps)
+    # a bounded sample whatever --steps asks for: the whole run ends within a few minutes
+    budget = args.ref_seconds if args.ref_seconds else min(max(10.0, 3.0 * args.steps), 120.0)
     cps, bps, steps, el, nblobs = oracle_sample(max_seconds=budget,
-                                                min_steps=max(1, args.steps // 10))
+                                                min_steps=min(3, max(1, args.steps // 10)))
     sample = (f"{steps} oracle steps of the same suspension recipe in a 64^3 box "
               f"({nblobs} blobs), {el:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": cps, "unit": "cell-steps/s",
