@@ -231,13 +231,10 @@ k_stress_div(int B, GridGeo g, const R* __restrict__ W, R* __restrict__ f, int a
 
 unsigned noise_blocks(int64_t total)
 {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
     const int64_t want = (total + 255) / 256, cap = (int64_t)sms * 8;
     return (unsigned)(want < cap ? want : cap);
 }

@@ -874,11 +874,6 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     // second stream while the blobs are binned (fork/join events, also inside captured graphs)
     const bool overlap = blobs && !ctx->timing;
     if (overlap) {
-        if (!ctx->side) {
-            MB_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
-            for (cudaEvent_t& e : ctx->fork)
-                MB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        }
         MB_CUDA(cudaEventRecord(ctx->fork[0], st));
         MB_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork[0], 0));
         MB_CUDA(launch_springs32(ctx->side, ctx->nb, hA, hB,
@@ -1571,6 +1566,14 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
         return fail(MB_ECUDA);
     }
     if ((s = upload_tables(ctx)) != MB_OK) return fail(s);
+    // the side stream and fork/join events of the step (created here, never inside a capture)
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = "stream or event creation failed";
+        return fail(MB_ECUDA);
+    }
     *out = ctx;
     return MB_OK;
 }
