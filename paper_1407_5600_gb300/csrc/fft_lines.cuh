@@ -6,6 +6,7 @@
 // (X[k1 + N1 k2] = sum_n2 W_N2^{n2 k2} W_N^{n2 k1} sum_n1 x[N2 n1 + n2] W_N1^{n1 k1}).
 #pragma once
 #include "mb_internal.cuh"
+#include "dfloat.cuh"
 
 namespace mbk {
 namespace {
@@ -120,7 +121,7 @@ __device__ __forceinline__ void lines_fft(T* buf, int lines, Idx idx, const T* _
         const bool on = l < lines;
         T a[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) a[n1] = on ? buf[idx(l, N2 * n1 + t)] : T{0, 0};
+        for (int n1 = 0; n1 < N1; ++n1) a[n1] = on ? buf[idx(l, N2 * n1 + t)] : T{};
         reg_dft<N1, INV>(a);
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) {
@@ -139,7 +140,7 @@ __device__ __forceinline__ void lines_fft(T* buf, int lines, Idx idx, const T* _
         for (int m = 0; m < M; ++m)
 #pragma unroll
             for (int n2 = 0; n2 < N2; ++n2)
-                b[m][n2] = on ? buf[idx(l, (t + N2 * m) * N2 + n2)] : T{0, 0};
+                b[m][n2] = on ? buf[idx(l, (t + N2 * m) * N2 + n2)] : T{};
 #pragma unroll
         for (int m = 0; m < M; ++m) reg_dft<N2, INV>(b[m]);
         __syncwarp();
@@ -207,6 +208,18 @@ __device__ __forceinline__ void store4(double* p, const double v[4])
 {
     reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
     reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+// FP64 grids read into, and written from, double-float values.
+__device__ __forceinline__ void load4(const double* p, dfloat v[4])
+{
+    double d[4];
+    load4(p, d);
+    for (int i = 0; i < 4; ++i) v[i] = dfloat(d[i]);
+}
+__device__ __forceinline__ void store4(double* p, const dfloat v[4])
+{
+    const double d[4] = {(double)v[0], (double)v[1], (double)v[2], (double)v[3]};
+    store4(p, d);
 }
 
 }  // namespace

@@ -36,21 +36,21 @@ __host__ __device__ inline int plane_ld(int nx)
 // Pass A.  Plane buffer P[p][pad(j)], p < ny/2: first rows 2p, 2p+1 packed as re + i im; after
 // the row FFT and the in-place separation, logical slot 2k + e of row p holds X_{2p+e}[k],
 // k <= nx/2.  pad(j) = j + (j >> pad_shift(nx)).
-template <typename R>
+template <typename R, typename K>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
 k_plane_fwd(FluidArgs<R> a, GridGeo g)
 {
-    using T = typename C2<R>::T;
+    using T = typename C2<K>::T;     // K: arithmetic type (FP32, or double-float for FP64)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     const int S = plane_ld(nx), sx = pad_shift(nx);
     T* P = reinterpret_cast<T*>(smem_raw);
-    const T* twx = reinterpret_cast<const T*>(a.twf[0]);      // twiddles through L1
-    const T* twy = reinterpret_cast<const T*>(a.twf[1]);
+    const T* twx = reinterpret_cast<const T*>(a.twk[0]);      // twiddles through L1
+    const T* twy = reinterpret_cast<const T*>(a.twk[1]);
     const int z = blockIdx.x, bc = blockIdx.y, comp = bc % 3;
     const R* vc = a.v + (size_t)bc * g.N;
     const R* fc = a.f ? a.f + (size_t)bc * g.N : nullptr;
-    const R ih2 = R(g.inv_h * g.inv_h), rho_dt = R(a.rho_dt), half_eta = R(a.half_eta);
+    const K ih2 = K(g.inv_h * g.inv_h), rho_dt = K(a.rho_dt), half_eta = K(a.half_eta);
     const bool body = a.body_prof && comp == a.body_axis;
     const R* pz = vc + (size_t)z * ny * nx;
     const R* pzp = vc + (size_t)((z + 1) & (nz - 1)) * ny * nx;
@@ -63,12 +63,12 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         // Stokes limit: the right-hand side is the force density (and body force) alone
         const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
         const int y0 = 2 * p, y1 = y0 + 1;
-        R r0[4] = {R(0), R(0), R(0), R(0)}, r1[4] = {R(0), R(0), R(0), R(0)};
+        K r0[4] = {K(0), K(0), K(0), K(0)}, r1[4] = {K(0), K(0), K(0), K(0)};
         if (pf) {
             load4(pf + (size_t)y0 * nx + x0, r0);
             load4(pf + (size_t)y1 * nx + x0, r1);
             if (pclr) {
-                const R zero[4] = {R(0), R(0), R(0), R(0)};
+                const K zero[4] = {K(0), K(0), K(0), K(0)};
                 store4(pclr + (size_t)y0 * nx + x0, zero);
                 store4(pclr + (size_t)y1 * nx + x0, zero);
             }
@@ -76,8 +76,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         if (body) {
             for (int i = 0; i < 4; ++i) {
                 const int x = x0 + i;
-                r0[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y0 : z)];
-                r1[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)];
+                r0[i] += K(a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y0 : z)]);
+                r1[i] += K(a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)]);
             }
         }
         T* row = P + p * S;
@@ -90,15 +90,15 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
         const int y0 = 2 * p, y1 = y0 + 1;
         const int ym = (y0 - 1) & (ny - 1), yp = (y1 + 1) & (ny - 1);
-        R c0[4], c1[4], am[4], ap[4], t[4];
+        K c0[4], c1[4], am[4], ap[4], t[4];
         load4(pz + (size_t)y0 * nx + x0, c0);
         load4(pz + (size_t)y1 * nx + x0, c1);
         load4(pz + (size_t)ym * nx + x0, am);
         load4(pz + (size_t)yp * nx + x0, ap);
-        R l0[4], l1[4];
+        K l0[4], l1[4];
         for (int i = 0; i < 4; ++i) {
-            l0[i] = am[i] + c1[i] - R(6) * c0[i];
-            l1[i] = c0[i] + ap[i] - R(6) * c1[i];
+            l0[i] = am[i] + c1[i] - K(6) * c0[i];
+            l1[i] = c0[i] + ap[i] - K(6) * c1[i];
         }
         load4(pzp + (size_t)y0 * nx + x0, t);
         for (int i = 0; i < 4; ++i) l0[i] += t[i];
@@ -109,13 +109,13 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         load4(pzm + (size_t)y1 * nx + x0, t);
         for (int i = 0; i < 4; ++i) l1[i] += t[i];
         const int xm = (x0 - 1) & (nx - 1), xp = (x0 + 4) & (nx - 1);
-        const R e0m = pz[(size_t)y0 * nx + xm], e0p = pz[(size_t)y0 * nx + xp];
-        const R e1m = pz[(size_t)y1 * nx + xm], e1p = pz[(size_t)y1 * nx + xp];
+        const K e0m = K(pz[(size_t)y0 * nx + xm]), e0p = K(pz[(size_t)y0 * nx + xp]);
+        const K e1m = K(pz[(size_t)y1 * nx + xm]), e1p = K(pz[(size_t)y1 * nx + xp]);
         for (int i = 0; i < 4; ++i) {
             l0[i] += (i == 0 ? e0m : c0[i - 1]) + (i == 3 ? e0p : c0[i + 1]);
             l1[i] += (i == 0 ? e1m : c1[i - 1]) + (i == 3 ? e1p : c1[i + 1]);
         }
-        R r0[4], r1[4];
+        K r0[4], r1[4];
         for (int i = 0; i < 4; ++i) {
             r0[i] = rho_dt * c0[i] + half_eta * (l0[i] * ih2);
             r1[i] = rho_dt * c1[i] + half_eta * (l1[i] * ih2);
@@ -126,7 +126,7 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
             load4(pf + (size_t)y1 * nx + x0, t);
             for (int i = 0; i < 4; ++i) r1[i] += t[i];
             if (pclr) {                  // leave f zeroed for the next accumulation
-                const R zero[4] = {R(0), R(0), R(0), R(0)};
+                const K zero[4] = {K(0), K(0), K(0), K(0)};
                 store4(pclr + (size_t)y0 * nx + x0, zero);
                 store4(pclr + (size_t)y1 * nx + x0, zero);
             }
@@ -134,8 +134,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         if (body) {
             for (int i = 0; i < 4; ++i) {
                 const int x = x0 + i;
-                r0[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y0 : z)];
-                r1[i] += a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)];
+                r0[i] += K(a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y0 : z)]);
+                r1[i] += K(a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)]);
             }
         }
         T* row = P + p * S;
@@ -159,8 +159,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
                 if (k < nxh) {
                     const int kr = (nx - k) & (nx - 1);
                     const T Z = rowp[k + (k >> sx)], Zr = rowp[kr + (kr >> sx)];
-                    ev[r] = T{(Z.x + Zr.x) * R(0.5), (Z.y - Zr.y) * R(0.5)};
-                    od[r] = T{(Z.y + Zr.y) * R(0.5), (Zr.x - Z.x) * R(0.5)};
+                    ev[r] = T{(Z.x + Zr.x) * K(0.5), (Z.y - Zr.y) * K(0.5)};
+                    od[r] = T{(Z.y + Zr.y) * K(0.5), (Zr.x - Z.x) * K(0.5)};
                 }
             }
             __syncwarp();
@@ -196,8 +196,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
             const int k = threadIdx.x + 32 * r;
             if (k < ny) {
                 const T Zk = P[col(0, k)], Zr = P[col(0, (ny - k) & (ny - 1))];
-                av[r] = T{(Zk.x + Zr.x) * R(0.5), (Zk.y - Zr.y) * R(0.5)};
-                bv[r] = T{(Zk.y + Zr.y) * R(0.5), (Zr.x - Zk.x) * R(0.5)};
+                av[r] = T{(Zk.x + Zr.x) * K(0.5), (Zk.y - Zr.y) * K(0.5)};
+                bv[r] = T{(Zk.y + Zr.y) * K(0.5), (Zr.x - Zk.x) * K(0.5)};
             }
         }
         __syncwarp();
@@ -211,7 +211,7 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         }
     }
     __syncthreads();
-    T* out = a.spec + ((size_t)bc * nz + z) * (size_t)nxh * ny;
+    T* out = reinterpret_cast<T*>(a.spec) + ((size_t)bc * nz + z) * (size_t)nxh * ny;
     const int ly = 31 - __clz(ny);
     for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) out[i] = P[col(i >> ly, i & (ny - 1))];
 }
@@ -219,11 +219,11 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
 // ------------------------------------------------------------------------------------------
 // Pass B.  CTA = (ky block of width C, kx, box); shared buffer [3][pad(nz)][C + 4].  C is a
 // compile-time width (16 FP32, 8 FP64) and the block has 3 C N2 threads, one round of lines.
-template <typename R, int C>
+template <typename R, typename K, int C>
 __global__ void __launch_bounds__(3 * C * 8, sizeof(R) == 4 ? 768 / (3 * C * 8) : 1)
 k_zsolve(FluidArgs<R> a, GridGeo g)
 {
-    using T = typename C2<R>::T;
+    using T = typename C2<K>::T;
     constexpr int Cp = C + 4;                    // 4 z-rows x 4 lines per half-warp: distinct banks
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
@@ -231,11 +231,11 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     const int sz = pad_shift(nz), nzp = padded_len(nz);
     T* Bf = reinterpret_cast<T*>(smem_raw);
     T* twz = Bf + 3 * nzp * Cp;
-    load_table(twz, reinterpret_cast<const T*>(a.twf[2]), nz);
+    load_table(twz, reinterpret_cast<const T*>(a.twk[2]), nz);
     const int ky0 = blockIdx.x * C, kx = blockIdx.y, box = blockIdx.z;
     const size_t zstride = (size_t)nxh * ny;
     const size_t cstride = (size_t)nz * zstride;
-    T* base = a.spec + (size_t)(box * 3) * cstride + (size_t)kx * ny + ky0;
+    T* base = reinterpret_cast<T*>(a.spec) + (size_t)(box * 3) * cstride + (size_t)kx * ny + ky0;
     auto at = [=](int c, int z, int k) { return (c * nzp + z + (z >> sz)) * Cp + k; };
     const int total = 3 * nz * C;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
@@ -247,16 +247,16 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     auto idx = [=](int l, int z) { return at(l / C, z, l % C); };
     lines_fft_n<false>(nz, Bf, 3 * C, idx, twz);
     __syncthreads();
-    const R* sym = reinterpret_cast<const R*>(a.symr);     // [9][256] cos, sin, lambda
-    const R ih = R(g.inv_h);
-    const R csx = sym[0 * 256 + kx], snx = sym[1 * 256 + kx], lx = sym[2 * 256 + kx];
-    const R rho_dt = R(a.rho_dt), half_eta = R(a.half_eta);
+    const K* sym = reinterpret_cast<const K*>(a.symk);     // [9][256] cos, sin, lambda
+    const K ih = K(g.inv_h);
+    const K csx = sym[0 * 256 + kx], snx = sym[1 * 256 + kx], lx = sym[2 * 256 + kx];
+    const K rho_dt = K(a.rho_dt), half_eta = K(a.half_eta);
     for (int i = threadIdx.x; i < nz * C; i += blockDim.x) {
         const int k = i % C, kz = i / C, ky = ky0 + k;
-        const R cs[3] = {csx, sym[3 * 256 + ky], sym[6 * 256 + kz]};
-        const R sn[3] = {snx, sym[4 * 256 + ky], sym[7 * 256 + kz]};
-        const R lam = lx + sym[5 * 256 + ky] + sym[8 * 256 + kz];
-        const R cinv = recip(rho_dt + half_eta * lam);
+        const K cs[3] = {csx, sym[3 * 256 + ky], sym[6 * 256 + kz]};
+        const K sn[3] = {snx, sym[4 * 256 + ky], sym[7 * 256 + kz]};
+        const K lam = lx + sym[5 * 256 + ky] + sym[8 * 256 + kz];
+        const K cinv = recip(rho_dt + half_eta * lam);
         T W[3];
         for (int c = 0; c < 3; ++c) {
             const T v = Bf[at(c, kz, k)];
@@ -268,27 +268,27 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
                     double m = a.mean_state[3 * box + c];
                     if (a.mean_force) m += a.mean_scale * a.mean_force[3 * box + c];
                     a.mean_state[3 * box + c] = m;
-                    W[c] = T{R((double)g.N * m), R(0)};
+                    W[c] = T{K((double)g.N * m), K(0)};
                 } else if (a.mean_override) {
-                    W[c] = T{R((double)g.N * a.mean_override[3 * box + c]), R(0)};
+                    W[c] = T{K((double)g.N * a.mean_override[3 * box + c]), K(0)};
                 } else if (a.mean_mode == 1) {
-                    W[c] = T{R(0), R(0)};
+                    W[c] = T{K(0), K(0)};
                 }
             }
         } else {
             // D_a = (e^{i th} - 1)/h, G_a = (1 - e^{-i th})/h, D.G = -lambda:
             // P W = W + G (D.W) / lambda
-            R dr = R(0), di = R(0);
+            K dr = K(0), di = K(0);
             for (int c = 0; c < 3; ++c) {
-                const R Dr = (cs[c] - R(1)) * ih, Di = sn[c] * ih;
+                const K Dr = (cs[c] - K(1)) * ih, Di = sn[c] * ih;
                 dr += Dr * W[c].x - Di * W[c].y;
                 di += Dr * W[c].y + Di * W[c].x;
             }
-            const R il = recip(lam);
+            const K il = recip(lam);
             dr *= il;
             di *= il;
             for (int c = 0; c < 3; ++c) {
-                const R Gr = (R(1) - cs[c]) * ih, Gi = sn[c] * ih;
+                const K Gr = (K(1) - cs[c]) * ih, Gi = sn[c] * ih;
                 W[c].x += Gr * dr - Gi * di;
                 W[c].y += Gr * di + Gi * dr;
             }
@@ -307,19 +307,19 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
 // ------------------------------------------------------------------------------------------
 // Pass C.  Inverse of pass A: columns, then the packed rows Z = X_{2p} + i X_{2p+1} (with the
 // Hermitian extension X[nx - k] = conj X[k]), then the real rows, scaled by 1/N.
-template <typename R>
+template <typename R, typename K>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
 k_plane_inv(FluidArgs<R> a, GridGeo g)
 {
-    using T = typename C2<R>::T;
+    using T = typename C2<K>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     const int S = plane_ld(nx), sx = pad_shift(nx);
     T* P = reinterpret_cast<T*>(smem_raw);
-    const T* twx = reinterpret_cast<const T*>(a.twf[0]);      // twiddles through L1
-    const T* twy = reinterpret_cast<const T*>(a.twf[1]);
+    const T* twx = reinterpret_cast<const T*>(a.twk[0]);      // twiddles through L1
+    const T* twy = reinterpret_cast<const T*>(a.twk[1]);
     const int z = blockIdx.x, bc = blockIdx.y;
-    const T* in = a.spec + ((size_t)bc * nz + z) * (size_t)nxh * ny;
+    const T* in = reinterpret_cast<const T*>(a.spec) + ((size_t)bc * nz + z) * (size_t)nxh * ny;
     auto col = [S, sx](int k, int y) {
         const int j = 2 * k + (y & 1);
         return (y >> 1) * S + j + (j >> sx);
@@ -340,8 +340,8 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
                 const T A = P[col(0, k)], Ar = P[col(0, kr)];
                 const T Bv = P[col(nx / 2, k)], Br = P[col(nx / 2, kr)];
                 // herm(A) = (A_k + conj A_-k) / 2, herm(B) likewise; Z = herm(A) + i herm(B)
-                const T ha = T{(A.x + Ar.x) * R(0.5), (A.y - Ar.y) * R(0.5)};
-                const T hb = T{(Bv.x + Br.x) * R(0.5), (Bv.y - Br.y) * R(0.5)};
+                const T ha = T{(A.x + Ar.x) * K(0.5), (A.y - Ar.y) * K(0.5)};
+                const T hb = T{(Bv.x + Br.x) * K(0.5), (Bv.y - Br.y) * K(0.5)};
                 zv[r] = T{ha.x - hb.y, ha.y + hb.x};
             }
         }
@@ -357,8 +357,8 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     __syncthreads();
     for (int y = threadIdx.x; y < ny; y += blockDim.x) {
         const T zc = P[col(0, y)];
-        P[col(0, y)] = T{zc.x, R(0)};
-        P[col(nx / 2, y)] = T{zc.y, R(0)};
+        P[col(0, y)] = T{zc.x, K(0)};
+        P[col(nx / 2, y)] = T{zc.y, K(0)};
     }
     __syncthreads();
     {
@@ -373,7 +373,7 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
                     const int kk = k <= nx / 2 ? k : nx - k;
                     const int j0 = 2 * kk, j1 = 2 * kk + 1;
                     T e = rowp[j0 + (j0 >> sx)], o = rowp[j1 + (j1 >> sx)];
-                    if (k == 0 || k == nx / 2) { e.y = R(0); o.y = R(0); }
+                    if (k == 0 || k == nx / 2) { e.y = K(0); o.y = K(0); }
                     if (k > nx / 2) { e.y = -e.y; o.y = -o.y; }
                     zv[r] = T{e.x - o.y, e.y + o.x};
                 }
@@ -390,12 +390,12 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     __syncthreads();
     lines_fft_n<true>(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx);
     __syncthreads();
-    const R scale = R(1.0 / (double)g.N);
+    const K scale = K(1.0 / (double)g.N);
     R* out = a.v_out + (size_t)bc * g.N + (size_t)z * ny * nx;
     const int qx = nx / 4, lq = 31 - __clz(qx);   // nx is a power of two
     for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
         const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
-        R r0[4], r1[4];
+        K r0[4], r1[4];
         for (int i = 0; i < 4; ++i) {
             const int j = x0 + i;
             const T zv = P[p * S + j + (j >> sx)];
@@ -406,7 +406,7 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
         store4(out + (size_t)(2 * p + 1) * nx + x0, r1);
         if (a.v_sum_out) {               // v^n + v^{n+1} for the corrector's single gather
             const size_t o0 = (size_t)bc * g.N + (size_t)z * ny * nx + (size_t)(2 * p) * nx + x0;
-            R b0[4], b1[4];
+            K b0[4], b1[4];
             load4(a.v_sum_base + o0, b0);
             load4(a.v_sum_base + o0 + nx, b1);
             for (int i = 0; i < 4; ++i) {
@@ -423,30 +423,31 @@ template <typename R>
 cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a,
                           cudaEvent_t* marks)
 {
-    using T = typename C2<R>::T;
+    using K = typename FftCompute<R>::type;
+    using T = typename C2<K>::T;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     constexpr int CZ = 8;                             // ky columns per z-pass block
     static std::atomic<unsigned> attr{0};     // per instantiation
     if (first_on_device(attr)) {
         const int lim = 200 * 1024;
-        cudaFuncSetAttribute(k_plane_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_zsolve<R, CZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_zsolve<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_plane_inv<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_plane_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_zsolve<R, K, CZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_zsolve<R, K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_plane_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     }
     const size_t smem_plane = (size_t)(ny / 2) * plane_ld(nx) * sizeof(T);
     const int C = ny >= CZ ? CZ : 4;
     const size_t smem_z = ((size_t)3 * padded_len(nz) * (C + 4) + nz) * sizeof(T);
     auto mark = [&](int i) { if (marks) cudaEventRecord(marks[i], st); };
     mark(0);
-    k_plane_fwd<R><<<dim3(nz, 3 * B), 256, smem_plane, st>>>(a, g);
+    k_plane_fwd<R, K><<<dim3(nz, 3 * B), 256, smem_plane, st>>>(a, g);
     mark(1);
     mark(2);
-    if (C == CZ) k_zsolve<R, CZ><<<dim3(ny / C, nxh, B), 3 * CZ * 8, smem_z, st>>>(a, g);
-    else k_zsolve<R, 4><<<dim3(ny / 4, nxh, B), 3 * 4 * 8, smem_z, st>>>(a, g);
+    if (C == CZ) k_zsolve<R, K, CZ><<<dim3(ny / C, nxh, B), 3 * CZ * 8, smem_z, st>>>(a, g);
+    else k_zsolve<R, K, 4><<<dim3(ny / 4, nxh, B), 3 * 4 * 8, smem_z, st>>>(a, g);
     mark(3);
     mark(4);
-    k_plane_inv<R><<<dim3(nz, 3 * B), 256, smem_plane, st>>>(a, g);
+    k_plane_inv<R, K><<<dim3(nz, 3 * B), 256, smem_plane, st>>>(a, g);
     mark(5);
     return cudaGetLastError();
 }

@@ -133,6 +133,7 @@ struct mb_ctx {
     int tile[3] = {8, 8, 8};
 
     DBuf v[2], vsum, f, spec, vbar, fsum, tw[3], twf[3], sym, symr, body_prof, prof_scratch;
+    DBuf twk[3], symk;          // FP64 grids: twiddles and symbols in double-float
     // thermal stress (kT > 0): sigma~ of the current step [B][9][N] and the step index that
     // keys its random numbers (device memory, advanced by the step itself)
     bool thermal = false;
@@ -566,6 +567,8 @@ FluidArgs<R> fluid_args(mb_ctx* ctx, const void* v, const void* f, void* v_out,
     }
     a.sym = static_cast<const double*>(ctx->sym.p);
     a.symr = ctx->symr.p;
+    for (int d = 0; d < 3; ++d) a.twk[d] = ctx->rsz == 8 ? ctx->twk[d].p : ctx->twf[d].p;
+    a.symk = ctx->rsz == 8 ? ctx->symk.p : ctx->symr.p;
     a.body_prof = body ? static_cast<const R*>(prof) : nullptr;
     a.body_axis = body ? (int)body[1] : -1;
     a.body_dir = body ? (int)body[2] : 0;
@@ -1327,6 +1330,17 @@ mb_status upload_tables(mb_ctx* ctx)
         MB_TRY(ensure(ctx->twf[d], sizeof(double) * 2 * n, ctx->err, "twiddles"));
         const void* srcf = ctx->rsz == 8 ? (const void*)fd.data() : (const void*)ff.data();
         MB_CUDA(cudaMemcpyAsync(ctx->twf[d].p, srcf, ctx->rsz * 2 * n, cudaMemcpyHostToDevice, ctx->st));
+        // FP64 grids: the same table in double-float (hi, lo per part) for the three-pass FFT
+        std::vector<float> fk(ctx->rsz == 8 ? 4 * n : 0);
+        for (size_t i = 0; i < fk.size() / 2; ++i) {
+            fk[2 * i] = (float)fd[i];
+            fk[2 * i + 1] = (float)(fd[i] - (double)fk[2 * i]);
+        }
+        if (ctx->rsz == 8) {
+            MB_TRY(ensure(ctx->twk[d], sizeof(float) * 4 * n, ctx->err, "twiddles"));
+            MB_CUDA(cudaMemcpyAsync(ctx->twk[d].p, fk.data(), sizeof(float) * 4 * n,
+                                    cudaMemcpyHostToDevice, ctx->st));
+        }
         for (int k = 0; k < n; ++k) {
             const double th = 2.0 * M_PI * (double)k / (double)n;
             const double s = std::sin(0.5 * th);
@@ -1344,6 +1358,17 @@ mb_status upload_tables(mb_ctx* ctx)
     if (ctx->rsz == 8)
         MB_CUDA(cudaMemcpyAsync(ctx->symr.p, sym.data(), sizeof(double) * sym.size(),
                                 cudaMemcpyHostToDevice, ctx->st));
+    if (ctx->rsz == 8) {
+        std::vector<float> symd(2 * sym.size());
+        for (size_t i = 0; i < sym.size(); ++i) {
+            symd[2 * i] = (float)sym[i];
+            symd[2 * i + 1] = (float)(sym[i] - (double)symd[2 * i]);
+        }
+        MB_TRY(ensure(ctx->symk, sizeof(float) * symd.size(), ctx->err, "symbols"));
+        MB_CUDA(cudaMemcpyAsync(ctx->symk.p, symd.data(), sizeof(float) * symd.size(),
+                                cudaMemcpyHostToDevice, ctx->st));
+        MB_CUDA(cudaStreamSynchronize(ctx->st));
+    }
     else
         MB_CUDA(cudaMemcpyAsync(ctx->symr.p, symf.data(), sizeof(float) * symf.size(),
                                 cudaMemcpyHostToDevice, ctx->st));
@@ -1377,7 +1402,8 @@ void release(mb_ctx* ctx)
                    &ctx->ext_sum, &ctx->ext_ticket, &ctx->adj32, &ctx->adj32_start, &ctx->Fs32, &ctx->u32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
                    &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk,
                    &ctx->a_vn, &ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvp, &ctx->a_gvn,
-                   &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero, &ctx->W, &ctx->step_index};
+                   &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero, &ctx->W, &ctx->step_index,
+                   &ctx->twk[0], &ctx->twk[1], &ctx->twk[2], &ctx->symk};
     for (DBuf* b : all) dfree(*b);
     for (cudaEvent_t& e : ctx->ev_ring)
         if (e) cudaEventDestroy(e);

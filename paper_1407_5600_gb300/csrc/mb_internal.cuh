@@ -123,6 +123,10 @@ struct FluidArgs {
     const R* twf[3];       // full tables W_n^j, j < n, per dimension (interleaved re, im)
     const double* sym;     // [3 dims][3][256]: cos, sin, lambda of 2 pi k / n (FP64)
     const void* symr;      // the same tables in the grid precision R
+    // the full twiddle tables and the symbols in the three-pass FFT's arithmetic type (the
+    // grid precision, or double-float for FP64 grids)
+    const void* twk[3];
+    const void* symk;
     const R* body_prof;    // body-force profile along wave_dir (null = none)
     int body_axis, body_dir;
     const double* mean_override;   // [B][3] mean velocity to impose at k = 0, or null
