@@ -37,7 +37,7 @@ __host__ __device__ inline int plane_ld(int nx)
 // the row FFT and the in-place separation, logical slot 2k + e of row p holds X_{2p+e}[k],
 // k <= nx/2.  pad(j) = j + (j >> pad_shift(nx)).
 template <typename R, typename K>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 512, sizeof(R) == 4 ? 3 : 1)
 k_plane_fwd(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<K>::T;     // K: arithmetic type (FP32, or double-float for FP64)
@@ -308,7 +308,7 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
 // Pass C.  Inverse of pass A: columns, then the packed rows Z = X_{2p} + i X_{2p+1} (with the
 // Hermitian extension X[nx - k] = conj X[k]), then the real rows, scaled by 1/N.
 template <typename R, typename K>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 512, sizeof(R) == 4 ? 3 : 1)
 k_plane_inv(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<K>::T;
@@ -425,6 +425,8 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
 {
     using K = typename FftCompute<R>::type;
     using T = typename C2<K>::T;
+    // plane blocks: FP64 planes (one block per SM) take 512 threads to hide latency
+    constexpr int PT = sizeof(R) == 4 ? 256 : 512;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     constexpr int CZ = 8;                             // ky columns per z-pass block
     static std::atomic<unsigned> attr{0};     // per instantiation
@@ -440,14 +442,14 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
     const size_t smem_z = ((size_t)3 * padded_len(nz) * (C + 4) + nz) * sizeof(T);
     auto mark = [&](int i) { if (marks) cudaEventRecord(marks[i], st); };
     mark(0);
-    k_plane_fwd<R, K><<<dim3(nz, 3 * B), 256, smem_plane, st>>>(a, g);
+    k_plane_fwd<R, K><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
     mark(1);
     mark(2);
     if (C == CZ) k_zsolve<R, K, CZ><<<dim3(ny / C, nxh, B), 3 * CZ * 8, smem_z, st>>>(a, g);
     else k_zsolve<R, K, 4><<<dim3(ny / 4, nxh, B), 3 * 4 * 8, smem_z, st>>>(a, g);
     mark(3);
     mark(4);
-    k_plane_inv<R, K><<<dim3(nz, 3 * B), 256, smem_plane, st>>>(a, g);
+    k_plane_inv<R, K><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
     mark(5);
     return cudaGetLastError();
 }
