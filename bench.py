@@ -33,7 +33,7 @@ METRIC = "fluid cell-steps/s at 128^3 (FP32 grid); blob-steps/s and FP64 beside 
 WORKLOAD = "dense suspension 128^3, a=2.2h, phi=0.40, 18808 particles x 13 blobs"
 DENSE128_BLOBS, DENSE128_PARTICLES = 244504, 18808      # the recipe's counts at seed 3
 
-# Algorithmic bytes moved by each stage per step, per unit (documented in the design doc):
+# Algorithmic bytes moved by each stage per step, per unit:
 #   grid real = 4 B (FP32) / 8 B (FP64); half-spectrum complex = 2 reals; blob FP64 vec = 24 B.
 def stage_model(n, nb, rsz, ncell, thermal=False):
     N = n ** 3
