@@ -244,21 +244,22 @@ unsigned noise_blocks(int64_t total)
 template <typename R>
 cudaError_t launch_fluid_stress(cudaStream_t st, int B, const GridGeo& g, uint64_t seed,
                                 uint64_t* step_index, double amp, const R* v, double rho, R* W,
-                                R* f, bool accumulate)
+                                R* f, bool accumulate, int parts)
 {
     const int64_t total = (int64_t)B * g.N;
     if (total <= 0) return cudaSuccess;
     const unsigned blocks = noise_blocks(total);
-    k_stress<R><<<blocks, 256, 0, st>>>(B, g, seed, step_index, R(amp), v, R(rho), W);
-    k_stress_div<R><<<blocks, 256, 0, st>>>(B, g, W, f, accumulate ? 1 : 0,
-                                            amp != 0.0 ? step_index : nullptr);
+    if (parts & 1) k_stress<R><<<blocks, 256, 0, st>>>(B, g, seed, step_index, R(amp), v, R(rho), W);
+    if (parts & 2)
+        k_stress_div<R><<<blocks, 256, 0, st>>>(B, g, W, f, accumulate ? 1 : 0,
+                                                amp != 0.0 ? step_index : nullptr);
     return cudaGetLastError();
 }
 template cudaError_t launch_fluid_stress<float>(cudaStream_t, int, const GridGeo&, uint64_t,
                                                 uint64_t*, double, const float*, double, float*,
-                                                float*, bool);
+                                                float*, bool, int);
 template cudaError_t launch_fluid_stress<double>(cudaStream_t, int, const GridGeo&, uint64_t,
                                                  uint64_t*, double, const double*, double,
-                                                 double*, double*, bool);
+                                                 double*, double*, bool, int);
 
 }  // namespace mbk

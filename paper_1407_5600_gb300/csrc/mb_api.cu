@@ -174,7 +174,7 @@ struct mb_ctx {
     cudaStream_t cap_stream = nullptr;
     // second stream for the spring forces, which overlap the binning (fork/join events)
     cudaStream_t side = nullptr;
-    cudaEvent_t fork[2] = {nullptr, nullptr};
+    cudaEvent_t fork[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     bool graph_ext[2] = {false, false}, graph_body[2] = {false, false};
     int graph_hcur[2] = {0, 0};
@@ -885,6 +885,16 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                                  static_cast<const double*>(ctx->box_par.p), g, ctx->bg,
                                  static_cast<float4*>(ctx->Fs32.p)));
         MB_CUDA(cudaEventRecord(ctx->fork[1], ctx->side));
+        // the thermal / convective stress needs only the step index and v^n: it is drawn on the
+        // side stream too, behind the springs, while the blobs are binned, forced and spread
+        if (ctx->thermal || ctx->advect) {
+            MB_CUDA(launch_fluid_stress<float>(ctx->side, B, g, ctx->d.seed,
+                                               static_cast<uint64_t*>(ctx->step_index.p),
+                                               ctx->thermal_amp, ctx->advect ? vcur : nullptr,
+                                               ctx->d.rho, static_cast<float*>(ctx->W.p),
+                                               static_cast<float*>(ctx->f.p), blobs, 1));
+            MB_CUDA(cudaEventRecord(ctx->fork[2], ctx->side));
+        }
     }
     mark(ST_BIN);
     if (blobs) {
@@ -941,11 +951,13 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     mark(ST_STRESS);
     const bool stress = ctx->thermal || ctx->advect;
     if (stress) {
+        if (overlap) MB_CUDA(cudaStreamWaitEvent(st, ctx->fork[2], 0));
         MB_CUDA(launch_fluid_stress<float>(st, B, g, ctx->d.seed,
                                            static_cast<uint64_t*>(ctx->step_index.p),
                                            ctx->thermal_amp, ctx->advect ? vcur : nullptr,
                                            ctx->d.rho, static_cast<float*>(ctx->W.p),
-                                           static_cast<float*>(ctx->f.p), blobs));
+                                           static_cast<float*>(ctx->f.p), blobs,
+                                           overlap ? 2 : 3));
         ctx->launches += STRESS_KERNELS;
     }
     FluidArgs<float> fa = fluid_args<float>(ctx, vcur, blobs || stress ? ctx->f.p : nullptr,
@@ -1385,7 +1397,7 @@ void release(mb_ctx* ctx)
     ctx->side = nullptr;
     for (cudaEvent_t& e : ctx->fork)
         if (e) cudaEventDestroy(e);
-    ctx->fork[0] = ctx->fork[1] = nullptr;
+    ctx->fork[0] = ctx->fork[1] = ctx->fork[2] = nullptr;
     DBuf* all[] = {&ctx->v[0], &ctx->v[1], &ctx->vsum, &ctx->f, &ctx->spec, &ctx->vbar, &ctx->fsum,
                    &ctx->tw[0], &ctx->tw[1], &ctx->tw[2], &ctx->twf[0], &ctx->twf[1],
                    &ctx->twf[2], &ctx->sym, &ctx->symr, &ctx->body_prof,
@@ -1595,7 +1607,8 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     // the side stream and fork/join events of the step (created here, never inside a capture)
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->fork[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->fork[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->fork[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork[2], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         ctx->err = "stream or event creation failed";
         return fail(MB_ECUDA);

@@ -155,12 +155,12 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
 constexpr int FLUID3_KERNELS = 3;
 
 // Thermal and convective stress (kernels_noise.cu): W = amp * normals of step *step_index
-// (amp != 0) + rho v v (v != NULL), then f (+)= -D.W, then *step_index += 1 (amp != 0).
-// W is [B][9][N], v and f [B][3][N].
+// (amp != 0) + rho v v (v != NULL) [parts & 1], then f (+)= -D.W and *step_index += 1
+// (amp != 0) [parts & 2].  W is [B][9][N], v and f [B][3][N].
 template <typename R>
 cudaError_t launch_fluid_stress(cudaStream_t st, int B, const GridGeo& g, uint64_t seed,
                                 uint64_t* step_index, double amp, const R* v, double rho, R* W,
-                                R* f, bool accumulate);
+                                R* f, bool accumulate, int parts = 3);
 constexpr int STRESS_KERNELS = 2;
 
 // Exclusive scan of n ints into out[0..n] (out[n] = total); tile_tmp holds n/4096 + 2 ints.
