@@ -6,6 +6,14 @@
   grid variation the paper reports (Sec. 5.1: 5% at d = h, 2.8% at d = 1.5 h, smaller beyond).
 - Sec. 2: J P S ~ 1/(12 h^3) for one blob in the incompressible fluid, about 1% deviation.
 - Sec. 5.2: the self-mobility is nearly isotropic, lift below 1% for d >= 1.5 h.
+- Table rad, second column: radius of inertia R_I from I_t = (2/5) M R_I^2 with the inertia
+  tensor of Eq. (itnb), I_t = rho I I_c^-1 I (I of Eq. miner0, I_c of Eq. mict built from J_i P S_j
+  acting on the torque forces alpha x s_j), and the mass M = rho V_m with V_m^-1 = Jm P Sm; the
+  paper finds both operators isotropic to about 1% over the grid.
+- Sec. 6 (mass and volume): the multiblob volume carries the added mass of the incompressible
+  fluid, V_m(P) / V_m(P = 1) = 3/2, as for a single blob (12 h^3 against 8 h^3); without overlaps
+  (d = 6h) the compressible volume is exactly N * 8 h^3, since the three-point kernel's squares
+  sum to 1/2 at every offset.
 """
 import json
 import os
@@ -102,3 +110,59 @@ def test_JPS_single_blob_volume():
         v = mb.fluid_update(proj, g.zeros(), mb.spread(g, q, e[None, :]))
         vals.append(mb.interp(g, q, v)[0] @ e)
     assert abs(np.mean(vals) * h ** 3 - gold["value_times_h3"]) < 2 * gold["relative_deviation"] * gold["value_times_h3"]
+
+
+def _jps(g, proj, q, F):
+    """J P S F at the blobs q: spread, project (one inviscid unit step from rest), interpolate."""
+    return mb.interp(g, q, mb.fluid_update(proj, g.zeros(), mb.spread(g, q, F)))
+
+
+def _icosahedron(n, h, d, rng):
+    g = mb.Grid(n, n, n, h=h)
+    a = d * h * np.sqrt(10 + 2 * np.sqrt(5)) / 4          # vertex radius for edge d
+    q = wl.build_particles(rng.uniform(0, n * h, size=3), a, rng, g.L).pos
+    rel = q - q[0]
+    rel -= g.L * np.round(rel / g.L)
+    return g, q, rel - rel.mean(0)                        # s_i about the geometric centre
+
+
+@pytest.mark.parametrize("d", [1.0, 1.5, 2.0, 2.5, 3.0])
+def test_radius_of_inertia(d):
+    rows = json.load(open(os.path.join(GOLD, "table_rad.json")))["inertia"]["rows"]
+    want = dict((r[0], r[1]) for r in rows)[d]
+    rng = np.random.default_rng(int(100 * d))
+    for h in (1.0, 0.7):
+        g, q, s = _icosahedron(32, h, d, rng)
+        proj = mb.Grid(32, 32, 32, h=h, rho=1.0, eta=0.0, dt=1.0, mean_mode=0)
+        N = len(q)
+        JPS_m = np.zeros((3, 3))      # Jm P Sm = sum_ij J_i P S_j / N^2
+        Ic = np.zeros((3, 3))         # Eq. mict: Ic alpha = sum_i s_i x J_i P sum_j S_j (alpha x s_j)
+        for k in range(3):
+            e = np.eye(3)[k]
+            JPS_m[:, k] = _jps(g, proj, q, np.tile(e, (N, 1))).sum(0) / N ** 2
+            Ic[:, k] = np.cross(s, _jps(g, proj, q, np.cross(e, s))).sum(0)
+        I = (s ** 2).sum() * np.eye(3) - s.T @ s                 # Eq. miner0
+        It = I @ np.linalg.solve(Ic, I)                          # Eq. itnb, rho = 1
+        for A in (It, JPS_m):                                    # isotropic to ~1% (Sec. 6)
+            ev = np.linalg.eigvals(A).real
+            assert np.ptp(ev) < 0.05 * ev.mean(), ev
+        R_I = np.sqrt(2.5 * (np.trace(It) / 3) * (np.trace(JPS_m) / 3)) / h   # M = 1 / JPS_m
+        assert abs(R_I - want) < 0.025 * want, (d, h, R_I, want)
+
+
+def test_multiblob_volume_added_mass():
+    rng = np.random.default_rng(7)
+    for d in (1.0, 2.0, 3.0, 6.0):
+        for h in (1.0, 0.7):
+            g, q, _ = _icosahedron(32, h, d, rng)
+            proj = mb.Grid(32, 32, 32, h=h, rho=1.0, eta=0.0, dt=1.0, mean_mode=0)
+            N = len(q)
+            inv_p, inv_1 = 0.0, 0.0
+            for k in range(3):
+                F = np.tile(np.eye(3)[k], (N, 1))
+                inv_p += _jps(g, proj, q, F).sum(0)[k] / (3 * N ** 2)
+                inv_1 += mb.interp(g, q, mb.spread(g, q, F)).sum(0)[k] / (3 * N ** 2)
+            V_p, V_1 = 1.0 / inv_p / h ** 3, 1.0 / inv_1 / h ** 3
+            assert abs(V_p / V_1 - 1.5) < 0.015 * 1.5, (d, h, V_p, V_1)
+            if d == 6.0:    # every blob pair is >= 3h apart along some axis: no overlap
+                assert abs(V_1 - 8.0 * N) < 1e-9 * V_1, V_1
