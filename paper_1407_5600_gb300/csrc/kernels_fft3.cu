@@ -63,12 +63,14 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         // Stokes limit: the right-hand side is the force density (and body force) alone
         const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
         const int y0 = 2 * p, y1 = y0 + 1;
-        K r0[4] = {K(0), K(0), K(0), K(0)}, r1[4] = {K(0), K(0), K(0), K(0)};
+        const K z0 = kconst<K>(0.0f);
+        K r0[4] = {z0, z0, z0, z0}, r1[4] = {z0, z0, z0, z0};
         if (pf) {
             load4(pf + (size_t)y0 * nx + x0, r0);
             load4(pf + (size_t)y1 * nx + x0, r1);
             if (pclr) {
-                const K zero[4] = {K(0), K(0), K(0), K(0)};
+                const K zero[4] = {kconst<K>(0.0f), kconst<K>(0.0f), kconst<K>(0.0f),
+                                   kconst<K>(0.0f)};
                 store4(pclr + (size_t)y0 * nx + x0, zero);
                 store4(pclr + (size_t)y1 * nx + x0, zero);
             }
@@ -97,8 +99,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
         load4(pz + (size_t)yp * nx + x0, ap);
         K l0[4], l1[4];
         for (int i = 0; i < 4; ++i) {
-            l0[i] = am[i] + c1[i] - K(6) * c0[i];
-            l1[i] = c0[i] + ap[i] - K(6) * c1[i];
+            l0[i] = am[i] + c1[i] - kconst<K>(6.0f) * c0[i];
+            l1[i] = c0[i] + ap[i] - kconst<K>(6.0f) * c1[i];
         }
         load4(pzp + (size_t)y0 * nx + x0, t);
         for (int i = 0; i < 4; ++i) l0[i] += t[i];
@@ -126,7 +128,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
             load4(pf + (size_t)y1 * nx + x0, t);
             for (int i = 0; i < 4; ++i) r1[i] += t[i];
             if (pclr) {                  // leave f zeroed for the next accumulation
-                const K zero[4] = {K(0), K(0), K(0), K(0)};
+                const K zero[4] = {kconst<K>(0.0f), kconst<K>(0.0f), kconst<K>(0.0f),
+                                   kconst<K>(0.0f)};
                 store4(pclr + (size_t)y0 * nx + x0, zero);
                 store4(pclr + (size_t)y1 * nx + x0, zero);
             }
@@ -159,8 +162,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
                 if (k < nxh) {
                     const int kr = (nx - k) & (nx - 1);
                     const T Z = rowp[k + (k >> sx)], Zr = rowp[kr + (kr >> sx)];
-                    ev[r] = T{(Z.x + Zr.x) * K(0.5), (Z.y - Zr.y) * K(0.5)};
-                    od[r] = T{(Z.y + Zr.y) * K(0.5), (Zr.x - Z.x) * K(0.5)};
+                    ev[r] = T{(Z.x + Zr.x) * kconst<K>(0.5f), (Z.y - Zr.y) * kconst<K>(0.5f)};
+                    od[r] = T{(Z.y + Zr.y) * kconst<K>(0.5f), (Zr.x - Z.x) * kconst<K>(0.5f)};
                 }
             }
             __syncwarp();
@@ -196,8 +199,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
             const int k = threadIdx.x + 32 * r;
             if (k < ny) {
                 const T Zk = P[col(0, k)], Zr = P[col(0, (ny - k) & (ny - 1))];
-                av[r] = T{(Zk.x + Zr.x) * K(0.5), (Zk.y - Zr.y) * K(0.5)};
-                bv[r] = T{(Zk.y + Zr.y) * K(0.5), (Zr.x - Zk.x) * K(0.5)};
+                av[r] = T{(Zk.x + Zr.x) * kconst<K>(0.5f), (Zk.y - Zr.y) * kconst<K>(0.5f)};
+                bv[r] = T{(Zk.y + Zr.y) * kconst<K>(0.5f), (Zr.x - Zk.x) * kconst<K>(0.5f)};
             }
         }
         __syncwarp();
@@ -268,19 +271,19 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
                     double m = a.mean_state[3 * box + c];
                     if (a.mean_force) m += a.mean_scale * a.mean_force[3 * box + c];
                     a.mean_state[3 * box + c] = m;
-                    W[c] = T{K((double)g.N * m), K(0)};
+                    W[c] = T{K((double)g.N * m), kconst<K>(0.0f)};
                 } else if (a.mean_override) {
-                    W[c] = T{K((double)g.N * a.mean_override[3 * box + c]), K(0)};
+                    W[c] = T{K((double)g.N * a.mean_override[3 * box + c]), kconst<K>(0.0f)};
                 } else if (a.mean_mode == 1) {
-                    W[c] = T{K(0), K(0)};
+                    W[c] = T{kconst<K>(0.0f), kconst<K>(0.0f)};
                 }
             }
         } else {
             // D_a = (e^{i th} - 1)/h, G_a = (1 - e^{-i th})/h, D.G = -lambda:
             // P W = W + G (D.W) / lambda
-            K dr = K(0), di = K(0);
+            K dr = kconst<K>(0.0f), di = kconst<K>(0.0f);
             for (int c = 0; c < 3; ++c) {
-                const K Dr = (cs[c] - K(1)) * ih, Di = sn[c] * ih;
+                const K Dr = (cs[c] - kconst<K>(1.0f)) * ih, Di = sn[c] * ih;
                 dr += Dr * W[c].x - Di * W[c].y;
                 di += Dr * W[c].y + Di * W[c].x;
             }
@@ -288,7 +291,7 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
             dr *= il;
             di *= il;
             for (int c = 0; c < 3; ++c) {
-                const K Gr = (K(1) - cs[c]) * ih, Gi = sn[c] * ih;
+                const K Gr = (kconst<K>(1.0f) - cs[c]) * ih, Gi = sn[c] * ih;
                 W[c].x += Gr * dr - Gi * di;
                 W[c].y += Gr * di + Gi * dr;
             }
@@ -340,8 +343,8 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
                 const T A = P[col(0, k)], Ar = P[col(0, kr)];
                 const T Bv = P[col(nx / 2, k)], Br = P[col(nx / 2, kr)];
                 // herm(A) = (A_k + conj A_-k) / 2, herm(B) likewise; Z = herm(A) + i herm(B)
-                const T ha = T{(A.x + Ar.x) * K(0.5), (A.y - Ar.y) * K(0.5)};
-                const T hb = T{(Bv.x + Br.x) * K(0.5), (Bv.y - Br.y) * K(0.5)};
+                const T ha = T{(A.x + Ar.x) * kconst<K>(0.5f), (A.y - Ar.y) * kconst<K>(0.5f)};
+                const T hb = T{(Bv.x + Br.x) * kconst<K>(0.5f), (Bv.y - Br.y) * kconst<K>(0.5f)};
                 zv[r] = T{ha.x - hb.y, ha.y + hb.x};
             }
         }
@@ -357,8 +360,8 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     __syncthreads();
     for (int y = threadIdx.x; y < ny; y += blockDim.x) {
         const T zc = P[col(0, y)];
-        P[col(0, y)] = T{zc.x, K(0)};
-        P[col(nx / 2, y)] = T{zc.y, K(0)};
+        P[col(0, y)] = T{zc.x, kconst<K>(0.0f)};
+        P[col(nx / 2, y)] = T{zc.y, kconst<K>(0.0f)};
     }
     __syncthreads();
     {
@@ -373,7 +376,7 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
                     const int kk = k <= nx / 2 ? k : nx - k;
                     const int j0 = 2 * kk, j1 = 2 * kk + 1;
                     T e = rowp[j0 + (j0 >> sx)], o = rowp[j1 + (j1 >> sx)];
-                    if (k == 0 || k == nx / 2) { e.y = K(0); o.y = K(0); }
+                    if (k == 0 || k == nx / 2) { e.y = kconst<K>(0.0f); o.y = kconst<K>(0.0f); }
                     if (k > nx / 2) { e.y = -e.y; o.y = -o.y; }
                     zv[r] = T{e.x - o.y, e.y + o.x};
                 }
