@@ -236,7 +236,8 @@ def run_reference(args):
     sample = (f"{steps} oracle steps of the same suspension recipe in a 64^3 box "
               f"({nblobs} blobs), {el:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": cps, "unit": "cell-steps/s",
-            "n_gpus": 0, "steps": steps, "warmup": args.warmup,
+            "n_gpus": args.gpus, "hardware": "host cores only (the oracle uses no GPU)",
+            "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(base_config(), sample="64^3 box of the same recipe"),
