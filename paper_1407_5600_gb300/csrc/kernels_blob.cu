@@ -227,7 +227,7 @@ __global__ void k_bin_scatter(int64_t nb, const int32_t* __restrict__ blob_cell,
         const int local = (int)(cell % bg.ncell);
         const int c[3] = {local % bg.nc[0], (local / bg.nc[0]) % bg.nc[1],
                           local / (bg.nc[0] * bg.nc[1])};
-        const double w = 1.0 / bg.inv_w;   // cell side
+        const double w = bg.w;   // cell side
         float r[3];
         for (int d = 0; d < 3; ++d) r[d] = (float)(q[3 * b + d] - c[d] * w);
         loc[slot] = make_float4(r[0], r[1], r[2], __int_as_float(pid ? pid[b] : 0));
@@ -263,7 +263,7 @@ __global__ void k_fill_loc(int64_t nb, const int32_t* __restrict__ sorted,
     const int local = (int)(blob_cell[b] % bg.ncell);
     const int c[3] = {local % bg.nc[0], (local / bg.nc[0]) % bg.nc[1],
                       local / (bg.nc[0] * bg.nc[1])};
-    const double w = 1.0 / bg.inv_w;
+    const double w = bg.w;
     float r[3];
     for (int d = 0; d < 3; ++d) r[d] = (float)(q[3 * b + d] - c[d] * w);
     loc[t] = make_float4(r[0], r[1], r[2], __int_as_float(pid ? pid[b] : 0));
@@ -424,7 +424,7 @@ k_forces(ForceArgs a, GridGeo g, BinGeo bg)
             const int cell = a.blob_cell[b] - (int)(box * bg.ncell);
             const int c[3] = {cell % bg.nc[0], (cell / bg.nc[0]) % bg.nc[1],
                               cell / (bg.nc[0] * bg.nc[1])};
-            const float w = (float)(1.0 / bg.inv_w);
+            const float w = bg.w32;
             const float rcf = (float)r_cut;
             const float pre = rcf * rcf * 1.0001f + 1e-6f;     // conservative FP32 prefilter
             const bool wide = bg.nc[0] >= 3 && bg.nc[1] >= 3 && bg.nc[2] >= 3;

@@ -151,6 +151,7 @@ struct mb_ctx {
     int64_t nb = 0, np = 0, max_box_blobs = 0;
     int nchunk = 0;
     std::vector<int64_t> box_off_h, part_off_h;
+    std::vector<float> box_par32_h;                // float copy of the box parameters
     DBuf q, qh, u, F, rec, ext, pid, box_of, adj_start, adj_j, adj_rest, part_start,
         part_blobs, box_off, box_par, cell_count, cell_start, blob_cell, blob_rank, sorted,
         loc, scan_tmp, partial, staging_in, staging_out, mean_scratch;
@@ -310,6 +311,12 @@ __global__ void k_wrap(int64_t n, double* q, double L0, double L1, double L2)
     q[i] = y;
 }
 
+// The box parameters [B][3] rounded to float, stored after the doubles.
+const float* box_par32(const mb_ctx* ctx)
+{
+    return reinterpret_cast<const float*>(static_cast<const double*>(ctx->box_par.p) + 3 * ctx->B);
+}
+
 // Choose the bin cell side: a power of two of mesh cells, at least 2 and at least r_cut.
 void choose_bins(mb_ctx* ctx, double r_cut)
 {
@@ -321,6 +328,7 @@ void choose_bins(mb_ctx* ctx, double r_cut)
     for (int a = 0; a < 3; ++a) ctx->bg.nc[a] = ctx->g.n[a] / bs;
     ctx->bg.ncell = (int64_t)ctx->bg.nc[0] * ctx->bg.nc[1] * ctx->bg.nc[2];
     ctx->bg.inv_w = 1.0 / (bs * ctx->d.h);
+    set_float_geo(ctx->bg);
 }
 
 // Default spreading tile: {32, 8, 8} nodes, clamped to the grid and raised to whole bin cells.
@@ -426,7 +434,8 @@ mb_status rebuild(mb_ctx* ctx)
     MB_TRY(ensure(ctx->part_start, sizeof(int32_t) * (np + 1), E, "part_start"));
     MB_TRY(ensure(ctx->part_blobs, sizeof(int32_t) * nb, E, "part_blobs"));
     MB_TRY(ensure(ctx->box_off, sizeof(int64_t) * (B + 1), E, "box_off"));
-    MB_TRY(ensure(ctx->box_par, sizeof(double) * 3 * B, E, "box_par"));
+    // [B][3] doubles, then the same rounded to float for the FP32 blob kernels
+    MB_TRY(ensure(ctx->box_par, (sizeof(double) + sizeof(float)) * 3 * B, E, "box_par"));
     MB_TRY(ensure(ctx->cell_count, sizeof(int32_t) * ncells, E, "cell_count"));
     MB_TRY(ensure(ctx->cell_start, sizeof(int32_t) * (ncells + 1), E, "cell_start"));
     MB_TRY(ensure(ctx->blob_cell, sizeof(int32_t) * nb, E, "blob_cell"));
@@ -453,6 +462,9 @@ mb_status rebuild(mb_ctx* ctx)
     MB_TRY(up(ctx->part_blobs, part_blobs.data(), sizeof(int32_t) * nb));
     MB_TRY(up(ctx->box_off, off.data(), sizeof(int64_t) * (B + 1)));
     MB_TRY(up(ctx->box_par, par.data(), sizeof(double) * 3 * B));
+    ctx->box_par32_h.assign(par.begin(), par.end());
+    MB_CUDA(cudaMemcpyAsync(static_cast<double*>(ctx->box_par.p) + 3 * B, ctx->box_par32_h.data(),
+                            sizeof(float) * 3 * B, cudaMemcpyHostToDevice, st));
     if (ctx->rsz == 4) {
         MB_TRY(ensure(ctx->sA, sizeof(float4) * nb, E, "split q"));
         MB_TRY(ensure(ctx->sB, sizeof(float4) * nb, E, "split q"));
@@ -882,7 +894,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
         MB_CUDA(launch_springs32(ctx->side, ctx->nb, hA, hB,
                                  static_cast<const int4*>(ctx->adj32.p),
                                  static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
-                                 static_cast<const double*>(ctx->box_par.p), g, ctx->bg,
+                                 box_par32(ctx), g, ctx->bg,
                                  static_cast<float4*>(ctx->Fs32.p)));
         MB_CUDA(cudaEventRecord(ctx->fork[1], ctx->side));
         // the thermal / convective stress needs only the step index and v^n: it is drawn on the
@@ -919,7 +931,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
             MB_CUDA(launch_pairs32(st, B, ctx->max_box_blobs, box_off,
                                    static_cast<const int32_t*>(ctx->sorted.p), hA, hB,
                                    static_cast<const float4*>(ctx->loc.p), box_of,
-                                   static_cast<const double*>(ctx->box_par.p),
+                                   box_par32(ctx),
                                    static_cast<const int32_t*>(ctx->cell_start.p),
                                    static_cast<const int32_t*>(ctx->blob_cell.p), ext4,
                                    static_cast<float4*>(ctx->Fs32.p),
@@ -931,7 +943,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
                                     static_cast<const float4*>(ctx->loc.p),
                                     static_cast<const int4*>(ctx->adj32.p),
                                     static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
-                                    static_cast<const double*>(ctx->box_par.p),
+                                    box_par32(ctx),
                                     static_cast<const int32_t*>(ctx->cell_start.p),
                                     static_cast<const int32_t*>(ctx->blob_cell.p), ext4,
                                     static_cast<float4*>(ctx->Fs32.p),
@@ -1067,7 +1079,7 @@ mb_status do_step_stokes_fast(mb_ctx* ctx, bool ext, const double* body)
                                     static_cast<const float4*>(ctx->loc.p),
                                     static_cast<const int4*>(ctx->adj32.p),
                                     static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
-                                    static_cast<const double*>(ctx->box_par.p),
+                                    box_par32(ctx),
                                     static_cast<const int32_t*>(ctx->cell_start.p),
                                     static_cast<const int32_t*>(ctx->blob_cell.p),
                                     ext ? static_cast<const float4*>(ctx->ext32.p) : nullptr,
@@ -1439,6 +1451,7 @@ mb_status standalone_spread(mb_ctx* ctx, int64_t n, const double* qd, const doub
         for (int a = 0; a < 3; ++a) bg.nc[a] = ctx->g.n[a] / bs;
         bg.ncell = (int64_t)bg.nc[0] * bg.nc[1] * bg.nc[2];
         bg.inv_w = 1.0 / (bs * ctx->d.h);
+        set_float_geo(bg);
     }
     MB_TRY(ensure(ctx->s_q, sizeof(double) * 3 * n, E, "spread q"));
     MB_TRY(ensure(ctx->s_rec, sizeof(double) * 6 * n, E, "spread rec"));
@@ -1554,6 +1567,7 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     ctx->g.N = (int64_t)ns[0] * ns[1] * ns[2];
     ctx->g.h = d.h;
     ctx->g.inv_h = 1.0 / d.h;
+    set_float_geo(ctx->g);
     ctx->nxh = ns[0] / 2 + 1;
     ctx->boxes.resize(ctx->B);
     if (const char* e = std::getenv("MB_FFT_PASSES")) ctx->fft_passes = std::atoi(e) == 5 ? 5 : 3;

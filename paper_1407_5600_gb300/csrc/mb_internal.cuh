@@ -19,6 +19,8 @@ struct GridGeo {
     int64_t N;         // cells per box
     double h, inv_h;
     double L[3];
+    float inv_h32, L32[3];   // the same rounded to float on the host (FP32 blob kernels: no
+                             // per-thread conversions on GB300's narrow FP64 pipe)
 };
 
 struct BinGeo {
@@ -26,7 +28,21 @@ struct BinGeo {
     int64_t ncell;     // bin cells per box
     int bs;            // bin cell side in mesh cells
     double inv_w;      // 1 / (bs h)
+    double w;          // 1 / inv_w (the cell side), and its float rounding; set with inv_w
+    float w32;
 };
+
+// The float copies of the geometry, from the double fields.
+inline void set_float_geo(GridGeo& g)
+{
+    g.inv_h32 = (float)g.inv_h;
+    for (int d = 0; d < 3; ++d) g.L32[d] = (float)g.L[d];
+}
+inline void set_float_geo(BinGeo& bg)
+{
+    bg.w = 1.0 / bg.inv_w;
+    bg.w32 = (float)bg.w;
+}
 
 // True the first time it is called for the current device with this flag set (function
 // attributes such as the dynamic shared-memory limit are set once per device).
@@ -201,18 +217,18 @@ cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t nb, int64_t max_box
                             const int64_t* box_off, const int32_t* sorted, const float4* A,
                             const float4* B, const float4* loc, const int4* adj,
                             const int32_t* adj_start, const int32_t* box_of,
-                            const double* box_par, const int32_t* cell_start,
+                            const float* box_par, const int32_t* cell_start,
                             const int32_t* blob_cell, const float4* ext, float4* Fs, float4* F,
                             float4* rec, const GridGeo& g, const BinGeo& bg);
 // The two halves of launch_forces32, for running the springs on another stream: the spring
 // forces (Fs, zeroed first), then the pair forces, sums and sorted records.
 cudaError_t launch_springs32(cudaStream_t st, int64_t nb, const float4* A, const float4* B,
                              const int4* adj, const int32_t* adj_start, const int32_t* box_of,
-                             const double* box_par, const GridGeo& g, const BinGeo& bg, float4* Fs);
+                             const float* box_par, const GridGeo& g, const BinGeo& bg, float4* Fs);
 cudaError_t launch_pairs32(cudaStream_t st, int Bx, int64_t max_box_blobs,
                            const int64_t* box_off, const int32_t* sorted, const float4* A,
                            const float4* B, const float4* loc, const int32_t* box_of,
-                           const double* box_par, const int32_t* cell_start,
+                           const float* box_par, const int32_t* cell_start,
                            const int32_t* blob_cell, const float4* ext, const float4* Fs,
                            float4* F, float4* rec, const GridGeo& g, const BinGeo& bg);
 // f = S F from the binned records (zeroes f first unless the caller knows it is zero).  The tile (nodes per block) must satisfy
