@@ -37,8 +37,9 @@ k_rhs_fft_x(FluidArgs<R> a, GridGeo g, int RP)
     const int comp = bc % 3;
     const R* vc = a.v + (size_t)bc * g.N;
     const R* fc = a.f ? a.f + (size_t)bc * g.N : nullptr;
-    const R ih2 = R(g.inv_h * g.inv_h);
-    const R rho_dt = R(a.rho_dt), half_eta = R(a.half_eta);
+    const R ih2 = kparam<R>(a.inv_h2, a.inv_h2_32);
+    const R rho_dt = kparam<R>(a.rho_dt, a.rho_dt32);
+    const R half_eta = kparam<R>(a.half_eta, a.half_eta32);
     const bool body = a.body_prof && comp == a.body_axis;
     const size_t zp = (size_t)((z + 1) & (nz - 1)) * ny, zm = (size_t)((z - 1) & (nz - 1)) * ny;
     const size_t z0 = (size_t)z * ny;
@@ -196,13 +197,15 @@ k_fft_z_solve(FluidArgs<R> a, GridGeo g)
     const R* cosz = sym + 6 * 256;
     const R* sinz = sym + 7 * 256;
     const R* lamz = sym + 8 * 256;
-    const R ih = R(g.inv_h);
+    const R ih = kparam<R>(a.inv_h, a.inv_h32);
+    const R rho_dt = kparam<R>(a.rho_dt, a.rho_dt32);
+    const R half_eta = kparam<R>(a.half_eta, a.half_eta32);
     for (int t = threadIdx.x; t < nz * C; t += blockDim.x) {
         const int kz = t >> LC, k = t & (C - 1);
         const int kx = kx0 + k;
         T W[3];
         const R lam = R(lamx[kx]) + R(lamy[ky]) + R(lamz[kz]);
-        const R cinv = recip(R(a.rho_dt) + R(a.half_eta) * lam);
+        const R cinv = recip(rho_dt + half_eta * lam);
         for (int c = 0; c < 3; ++c) {
             const T v = sb[at(c, kz, k)];
             W[c] = T{v.x * cinv, v.y * cinv};
@@ -280,7 +283,7 @@ k_fft_x_c2r(FluidArgs<R> a, GridGeo g, int RP)
     lines_fft_n<true>(nx, sb, RP, [ld, sx](int l, int j) { return l * ld + pj(j, sx); },
                       reinterpret_cast<const T*>(a.twf[0]));
     __syncthreads();
-    const R scale = R(1.0 / (double)g.N);
+    const R scale = kparam<R>(a.inv_n, a.inv_n32);
     R* out = a.v_out + (size_t)bc * g.N + (size_t)z * ny * nx;
     const int qx = nx / 4, lq = 31 - __clz(qx);
     for (int u = threadIdx.x; u < qx * RP; u += blockDim.x) {
@@ -297,9 +300,10 @@ k_fft_x_c2r(FluidArgs<R> a, GridGeo g, int RP)
 }
 
 template <typename R>
-cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a,
+cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a_in,
                          cudaEvent_t* marks)
 {
+    const FluidArgs<R> a = with_derived(a_in, g);
     using T = typename C2<R>::T;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
     const int RP = ny / 2 < 16 ? ny / 2 : 16;

@@ -50,7 +50,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     const int z = blockIdx.x, bc = blockIdx.y, comp = bc % 3;
     const R* vc = a.v + (size_t)bc * g.N;
     const R* fc = a.f ? a.f + (size_t)bc * g.N : nullptr;
-    const K ih2 = K(g.inv_h * g.inv_h), rho_dt = K(a.rho_dt), half_eta = K(a.half_eta);
+    const K ih2 = kparam<K>(a.inv_h2, a.inv_h2_32), rho_dt = kparam<K>(a.rho_dt, a.rho_dt32),
+            half_eta = kparam<K>(a.half_eta, a.half_eta32);
     const bool body = a.body_prof && comp == a.body_axis;
     const R* pz = vc + (size_t)z * ny * nx;
     const R* pzp = vc + (size_t)((z + 1) & (nz - 1)) * ny * nx;
@@ -251,9 +252,10 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     lines_fft_n<false>(nz, Bf, 3 * C, idx, twz);
     __syncthreads();
     const K* sym = reinterpret_cast<const K*>(a.symk);     // [9][256] cos, sin, lambda
-    const K ih = K(g.inv_h);
+    const K ih = kparam<K>(a.inv_h, a.inv_h32);
     const K csx = sym[0 * 256 + kx], snx = sym[1 * 256 + kx], lx = sym[2 * 256 + kx];
-    const K rho_dt = K(a.rho_dt), half_eta = K(a.half_eta);
+    const K rho_dt = kparam<K>(a.rho_dt, a.rho_dt32);
+    const K half_eta = kparam<K>(a.half_eta, a.half_eta32);
     for (int i = threadIdx.x; i < nz * C; i += blockDim.x) {
         const int k = i % C, kz = i / C, ky = ky0 + k;
         const K cs[3] = {csx, sym[3 * 256 + ky], sym[6 * 256 + kz]};
@@ -393,7 +395,7 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     __syncthreads();
     lines_fft_n<true>(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx);
     __syncthreads();
-    const K scale = K(1.0 / (double)g.N);
+    const K scale = kparam<K>(a.inv_n, a.inv_n32);
     R* out = a.v_out + (size_t)bc * g.N + (size_t)z * ny * nx;
     const int qx = nx / 4, lq = 31 - __clz(qx);   // nx is a power of two
     for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
@@ -423,9 +425,10 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
 }
 
 template <typename R>
-cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a,
+cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a_in,
                           cudaEvent_t* marks)
 {
+    const FluidArgs<R> a = with_derived(a_in, g);
     using K = typename FftCompute<R>::type;
     using T = typename C2<K>::T;
     // plane blocks: FP64 planes (one block per SM) take 512 threads to hide latency

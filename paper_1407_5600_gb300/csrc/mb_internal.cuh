@@ -148,6 +148,10 @@ struct FluidArgs {
     const double* mean_override;   // [B][3] mean velocity to impose at k = 0, or null
     int mean_mode;
     double rho_dt, half_eta;
+    double inv_h, inv_h2, inv_n;          // 1/h, 1/h^2, 1/N (set by the launch functions)
+    // the five rounded to float on the host: FP32 kernels read these instead of converting
+    // per thread on GB300's narrow FP64 pipe
+    float rho_dt32, half_eta32, inv_h32, inv_h2_32, inv_n32;
     R* f_clear;            // three-pass FFT: f, zeroed as it is read (null = leave f alone)
     const R* v_sum_base;   // three-pass FFT: v^n; with v_sum_out, also write v^n + v^{n+1}
     R* v_sum_out;
@@ -159,6 +163,27 @@ struct FluidArgs {
     int no_v;              // three-pass FFT: right-hand side f (+ body) only (Stokes limit)
 };
 // marks: null, or 6 events recorded before pass 1 and after each of the 5 passes.
+// The derived launch constants of a FluidArgs (1/h, 1/h^2, 1/N and the float roundings), set
+// by the launch functions from the final rho_dt and half_eta.
+template <typename R> inline FluidArgs<R> with_derived(const FluidArgs<R>& in, const GridGeo& g)
+{
+    FluidArgs<R> a = in;
+    a.inv_h = g.inv_h;
+    a.inv_h2 = g.inv_h * g.inv_h;
+    a.inv_n = 1.0 / (double)g.N;
+    a.rho_dt32 = (float)a.rho_dt;
+    a.half_eta32 = (float)a.half_eta;
+    a.inv_h32 = (float)a.inv_h;
+    a.inv_h2_32 = (float)a.inv_h2;
+    a.inv_n32 = (float)a.inv_n;
+    return a;
+}
+
+// A per-launch constant in the arithmetic type K: the host's float rounding for FP32
+// arithmetic, otherwise converted from the double.
+template <typename K> __device__ __forceinline__ K kparam(double d, float) { return K(d); }
+template <> __device__ __forceinline__ float kparam<float>(double, float f) { return f; }
+
 template <typename R>
 cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a,
                          cudaEvent_t* marks = nullptr);
