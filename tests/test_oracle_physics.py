@@ -14,6 +14,9 @@
   fluid, V_m(P) / V_m(P = 1) = 3/2, as for a single blob (12 h^3 against 8 h^3); without overlaps
   (d = 6h) the compressible volume is exactly N * 8 h^3, since the three-point kernel's squares
   sum to 1/2 at every offset.
+- Eqs. u0 and rotnb: one oracle ICM step in an ideal fluid at rest gives the particle velocity
+  dt F0 / M of a pulled particle and the angular velocity dt I_t^-1 tau of a twisted one, with
+  M and I_t from the operators above (tests the step's wiring of forces, rho, dt and Omega).
 """
 import json
 import os
@@ -166,3 +169,43 @@ def test_multiblob_volume_added_mass():
             assert abs(V_p / V_1 - 1.5) < 0.015 * 1.5, (d, h, V_p, V_1)
             if d == 6.0:    # every blob pair is >= 3h apart along some axis: no overlap
                 assert abs(V_1 - 8.0 * N) < 1e-9 * V_1, V_1
+
+
+def test_one_ideal_fluid_step_gives_inertial_mass_and_inertia():
+    """Eq. u0 and Eq. rotnb in an ideal fluid at rest (eta = 0): one ICM step of the oracle gives
+    U = dt F0 / M with M = rho / (Jm P Sm), and Omega = dt I_t^-1 tau with the inertia tensor of
+    Eq. itnb, both built from the oracle's operators (the quantities pinned to Table rad above)."""
+    n, h, rho, dt, d = 32, 1.0, 1.3, 0.05, 2.0
+    rng = np.random.default_rng(41)
+    gs = mb.Grid(n, n, n, h=h, rho=rho, eta=0.0, dt=dt, mean_mode=0)
+    proj = mb.Grid(n, n, n, h=h, rho=1.0, eta=0.0, dt=1.0, mean_mode=0)
+    part = wl.build_particles(rng.uniform(0, n * h, size=3),
+                              d * h * np.sqrt(10 + 2 * np.sqrt(5)) / 4, rng, gs.L)
+    q, N = part.pos, len(part.pos)
+    rel = q - q[0]
+    rel -= gs.L * np.round(rel / gs.L)
+    s = rel - rel.mean(0)
+    pid = np.zeros(N, dtype=np.int32)
+
+    def one_step(ext):
+        q1, v1 = mb.step(gs, 1, q, gs.zeros(), pid, part.bonds, part.rest, 100.0, ext=ext)
+        return mb.particle_velocities(gs, q1, mb.interp(gs, q1, v1), pid, 1)
+
+    # pulled: F0 along x shared by the blobs
+    F0 = 1e-3
+    ext = np.zeros((N, 3))
+    ext[:, 0] = F0 / N
+    U1, _ = one_step(ext)
+    JPS_xx = _jps(gs, proj, q, ext / ext[0, 0]).sum(0)[0] / N ** 2
+    M = rho / JPS_xx
+    assert abs(U1[0, 0] - dt * F0 / M) < 1e-5 * abs(dt * F0 / M)
+    assert np.max(np.abs(U1[0, 1:])) < 0.02 * abs(U1[0, 0])          # lift below 2%
+    # twisted: f_j = alpha x s_j, torque tau = I alpha
+    alpha = np.array([0.3, -0.5, 0.8]) * 1e-3
+    _, W1 = one_step(np.cross(alpha, s))
+    Ic = np.array([np.cross(s, _jps(gs, proj, q, np.cross(np.eye(3)[k], s))).sum(0)
+                   for k in range(3)]).T
+    I = (s ** 2).sum() * np.eye(3) - s.T @ s
+    It = rho * I @ np.linalg.solve(Ic, I)
+    want = dt * np.linalg.solve(It, I @ alpha)
+    assert np.linalg.norm(W1[0] - want) < 1e-5 * np.linalg.norm(want)
