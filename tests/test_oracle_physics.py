@@ -17,6 +17,7 @@
 - Eqs. u0 and rotnb: one oracle ICM step in an ideal fluid at rest gives the particle velocity
   dt F0 / M of a pulled particle and the angular velocity dt I_t^-1 tau of a twisted one, with
   M and I_t from the operators above (tests the step's wiring of forces, rho, dt and Omega).
+- Sec. 6: the multiblob volume varies over the grid by about 1% or less for every d.
 """
 import json
 import os
@@ -209,3 +210,23 @@ def test_one_ideal_fluid_step_gives_inertial_mass_and_inertia():
     It = rho * I @ np.linalg.solve(Ic, I)
     want = dt * np.linalg.solve(It, I @ alpha)
     assert np.linalg.norm(W1[0] - want) < 1e-5 * np.linalg.norm(want)
+
+
+def test_multiblob_volume_varies_about_one_percent_over_the_grid():
+    """Sec. 6 (mass and volume): the multiblob volume V_m = 1 / (e . Jm P Sm e) varies over
+    grid positions, orientations and directions e by about 1% or less for every d."""
+    n = 32
+    g = mb.Grid(n, n, n)
+    proj = mb.Grid(n, n, n, rho=1.0, eta=0.0, dt=1.0, mean_mode=0)
+    rng = np.random.default_rng(5)
+    for d in (1.0, 1.5, 2.0, 3.0):
+        vals = []
+        for _ in range(12):
+            q = wl.build_particles(rng.uniform(0, n, size=3),
+                                   d * np.sqrt(10 + 2 * np.sqrt(5)) / 4, rng, g.L).pos
+            e = rng.normal(size=3)
+            e /= np.linalg.norm(e)
+            u = _jps(g, proj, q, np.tile(e, (len(q), 1)))
+            vals.append(len(q) ** 2 / (u.sum(0) @ e))
+        vals = np.array(vals)
+        assert vals.std() < 0.01 * vals.mean(), (d, vals.std() / vals.mean())
