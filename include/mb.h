@@ -63,7 +63,10 @@ typedef enum {
  *   rho, eta     fluid density and shear viscosity (> 0).
  *   dt           time step (> 0).
  *   precision    0: grid, spreading, interpolation and FFT in FP32 (blob positions, forces and
- *                the mean fluid momentum stay FP64); 1: everything FP64.
+ *                the mean fluid momentum stay FP64); 1: FP64 storage and arithmetic, except
+ *                that the FFT of grids with every side at most 128 computes in double-float
+ *                (a pair of floats, about 48 significant bits; its error stays near 1e-14
+ *                relative), where grid values below 2^-74 in magnitude keep 24 bits.
  *   deterministic  0 or 1.  With precision 1, 1 makes a run bitwise reproducible: blobs are
  *                ordered within their bin cells and spreading accumulates in 64-bit fixed point
  *                (order-independent sums); every other stage already has a fixed order.  In
