@@ -142,3 +142,66 @@ def test_particle_velocities_rigid_motion():
         u[sl] = U[p] + np.cross(W[p], sp)
     U2, W2 = mb.particle_velocities(g, s.pos, u, s.pid, 4)
     assert np.max(np.abs(U2 - U)) < 1e-12 and np.max(np.abs(W2 - W)) < 1e-12
+
+
+def _stretched_particle_in_flow(g):
+    """One particle of vertex radius 1.5h with every spring stretched by 10% (position-dependent
+    internal forces), a constant external pull, in a shear mode plus a projected random flow."""
+    rng = np.random.default_rng(11)
+    s = wl.build_particles(np.array([5.3, 6.1, 4.7]), 1.5, rng, g.L)
+    c = s.pos[0]
+    q0 = np.mod(c + 1.1 * _min_img(s.pos - c, g.L), g.L)
+    z = np.arange(g.nz) + 0.5
+    v0 = g.zeros()
+    v0[0] += 0.05 * np.sin(2 * np.pi * z / g.nz)[:, None, None]
+    v0 += mb.fluid_update(mb.Grid(g.nx, g.ny, g.nz, rho=1.0, eta=0.0, dt=1.0), g.zeros(),
+                          wl.random_field(g.shape, 3, scale=2e-2))
+    ext = np.zeros_like(q0)
+    ext[:, 1] = 2e-2
+    return s, q0, v0, ext
+
+
+def test_step_is_second_order_in_time():
+    """The midpoint predictor/corrector with Crank-Nicolson is second order in dt: halving dt
+    divides the change of the end state by 4.  Evaluating the forces or the corrector's J at q^n
+    instead of q^{n+1/2}, a full predictor step, or v^{n+1} alone in the corrector each make it
+    first order (ratio 2), so this pins where the step places its midpoint."""
+    T = 0.32
+    q, v = {}, {}
+    for dt in (0.02, 0.01, 0.005):
+        g = mb.Grid(12, 12, 12, dt=dt, mean_mode=0)
+        s, q0, v0, ext = _stretched_particle_in_flow(g)
+        q[dt], v[dt] = mb.step(g, int(round(T / dt)), q0, v0, s.pid, s.bonds, s.rest, 100.0,
+                               ext=ext)
+    L = g.L
+    dq1 = np.linalg.norm(_min_img(q[0.02] - q[0.01], L))
+    dq2 = np.linalg.norm(_min_img(q[0.01] - q[0.005], L))
+    dv1 = np.linalg.norm(v[0.02] - v[0.01])
+    dv2 = np.linalg.norm(v[0.01] - v[0.005])
+    assert 3.6 < dq1 / dq2 < 4.4, dq1 / dq2
+    assert 3.6 < dv1 / dv2 < 4.4, dv1 / dv2
+    # the particle moved by much more than the time-discretisation change
+    assert np.linalg.norm(_min_img(q[0.005] - q0, L)) > 1e3 * dq2
+
+
+def test_step_midpoint_uniform_flow_shift():
+    """A uniform flow U with U dt/2 = h carries the predictor exactly one cell, because J of a
+    constant field is that constant (the weights sum to one).  The step from (q, v = U) is then
+    the step from (q + h x_hat, v = 0) shifted by h x_hat in q and by U in v: the blob forces and
+    S act at q^{n+1/2}, the fluid update is linear with constant fields unchanged, and the
+    corrector applies J(q^{n+1/2}) to (v^n + v^{n+1})/2.  Forces or the corrector's J taken at
+    q^n, or a full-step predictor, break the relation."""
+    g = mb.Grid(12, 12, 12, dt=0.05, mean_mode=0)
+    s, q0, v0, ext = _stretched_particle_in_flow(g)
+    U = 2.0 * g.h / g.dt
+    vU = g.zeros()
+    vU[0] = U
+    qa, va = mb.step(g, 1, q0, vU, s.pid, s.bonds, s.rest, 100.0, ext=ext)
+    shift = np.array([g.h, 0.0, 0.0])
+    qb, vb = mb.step(g, 1, np.mod(q0 + shift, g.L), g.zeros(), s.pid, s.bonds, s.rest, 100.0,
+                     ext=ext)
+    vb[0] += U
+    scale = np.max(np.abs(vb - vU))
+    assert scale > 1e-4
+    assert np.max(np.abs(va - vb)) < 1e-10 * U
+    assert np.max(np.abs(_min_img(qa - (qb + shift), g.L))) < 1e-12 * U * g.dt * 10
