@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the benchmark's
 CPU-baseline leg may import this module.  The product library never does, and the two
 share no code: this wrapper loads ``oracle/_build/libmbref.so`` built from ``mbref.c`` with
-plain gcc (``-O2 -ffp-contract=off``, no fast-math), and marshals numpy arrays into it.
+plain gcc (``-O2 -ffp-contract=off``, no fast-math, OpenMP over independent loops when the
+compiler has it), and marshals numpy arrays into it.
 
 Parity status of each routine (what pins it) is listed in the tests under
 ``tests/test_oracle_*.py``; every routine here has at least one independent pin.
@@ -30,9 +31,12 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mbref.h"))
     ):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(
-            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-             "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                "-o", tmp, _SRC, "-lm"]
+        try:   # OpenMP threads over independent loops; results do not depend on them
+            subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -60,6 +64,8 @@ def _load():
         G = ctypes.POINTER(_Grid)
         lib.mbref_phi.restype = D
         lib.mbref_phi.argtypes = [D]
+        lib.mbref_set_threads.restype = ctypes.c_int
+        lib.mbref_set_threads.argtypes = [ctypes.c_int]
         lib.mbref_philox4x64.restype = None
         lib.mbref_philox4x64.argtypes = [P, P, P]
         for name, args in {
@@ -70,6 +76,7 @@ def _load():
             "mbref_stokes_solve": [G, P, P],
             "mbref_bond_forces": [G, I64, P, I64, P, P, D, P],
             "mbref_pair_forces": [G, I64, P, P, D, D, P],
+            "mbref_pair_forces_brute": [G, I64, P, P, D, D, P],
             "mbref_pair_forces_subset": [G, I64, P, P, D, D, I64, P, P],
             "mbref_step": [G, ctypes.c_int, I64, P, P, P, I64, P, P, D, D, D, P, P,
                            ctypes.POINTER(_Noise)],
@@ -128,6 +135,12 @@ def _i32(a):
 def _check(rc, name):
     if rc != 0:
         raise RuntimeError(f"{name} returned {rc}")
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads of the oracle's parallel loops (n <= 0: leave unchanged); returns the number
+    in effect.  No result depends on it."""
+    return _load().mbref_set_threads(int(n))
 
 
 def phi(r: float) -> float:
@@ -208,6 +221,17 @@ def pair_forces(g: Grid, q, pid, k_rep, r_cut):
     F = np.zeros((len(q), 3))
     _check(_load().mbref_pair_forces(g._c(), len(q), qp, pp, float(k_rep), float(r_cut),
                                      F.ctypes.data_as(ctypes.c_void_p)), "pair_forces")
+    return F
+
+
+def pair_forces_brute(g: Grid, q, pid, k_rep, r_cut):
+    """The repulsion by its definition (all pairs); pair_forces equals it to the bit."""
+    q, qp = _d(q)
+    p, pp = _i32(pid)
+    F = np.zeros((len(q), 3))
+    _check(_load().mbref_pair_forces_brute(g._c(), len(q), qp, pp, float(k_rep), float(r_cut),
+                                           F.ctypes.data_as(ctypes.c_void_p)),
+           "pair_forces_brute")
     return F
 
 

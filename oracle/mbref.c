@@ -12,6 +12,26 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads.  Loops whose iterations write disjoint outputs and read only inputs (blobs of J,
+ * pair forces of each blob, lines of the DFT, grid points of the stencils, cells of the noise,
+ * components of S) may run on several threads; every output is computed by the same
+ * operations in the same order as on one thread, so results do not depend on the thread
+ * count.  Sums whose order would change with the split (bond forces, the particle sums) stay
+ * serial. */
+int mbref_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 static const double MBREF_PI = 3.14159265358979323846264338327950288;
 
@@ -61,8 +81,9 @@ int mbref_spread(const mbref_grid* g, int64_t n, const double* q, const double* 
     const int64_t N = (int64_t)nx * ny * nz;
     const double inv_h3 = 1.0 / (g->h * g->h * g->h);
     memset(f, 0, sizeof(double) * 3 * N);
-    for (int64_t b = 0; b < n; ++b) {
-        for (int comp = 0; comp < 3; ++comp) {
+#pragma omp parallel for schedule(static)
+    for (int comp = 0; comp < 3; ++comp) {
+        for (int64_t b = 0; b < n; ++b) {
             int64_t ix[3], iy[3], iz[3];
             double wx[3], wy[3], wz[3];
             kernel_window(q[3 * b + 0], g->h, node_shift(comp, 0), nx, ix, wx);
@@ -86,6 +107,7 @@ int mbref_interp(const mbref_grid* g, int64_t n, const double* q, const double* 
 {
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     const int64_t N = (int64_t)nx * ny * nz;
+#pragma omp parallel for schedule(static)
     for (int64_t b = 0; b < n; ++b) {
         for (int comp = 0; comp < 3; ++comp) {
             int64_t ix[3], iy[3], iz[3];
@@ -168,27 +190,41 @@ int mbref_dft3(int nx, int ny, int nz, double* re, double* im, int inverse)
 {
     int nmax = nx > ny ? nx : ny;
     if (nz > nmax) nmax = nz;
-    double* tr = (double*)malloc(sizeof(double) * 2 * nmax);   /* line + twiddle scratch */
-    double* ti = (double*)malloc(sizeof(double) * 2 * nmax);
-    if (!tr || !ti) { free(tr); free(ti); return 2; }
-    for (int k = 0; k < nz; ++k)             /* along x */
-        for (int j = 0; j < ny; ++j) {
-            int64_t o = ((int64_t)k * ny + j) * nx;
-            dft_line(re + o, im + o, nx, 1, inverse, tr, ti);
+    int rc = 0;
+    /* every line is transformed on its own; each thread has its own line + twiddle scratch */
+#pragma omp parallel
+    {
+        double* tr = (double*)malloc(sizeof(double) * 2 * nmax);
+        double* ti = (double*)malloc(sizeof(double) * 2 * nmax);
+        if (!tr || !ti) {
+#pragma omp atomic write
+            rc = 2;
         }
-    for (int k = 0; k < nz; ++k)             /* along y */
-        for (int i = 0; i < nx; ++i) {
-            int64_t o = (int64_t)k * ny * nx + i;
-            dft_line(re + o, im + o, ny, nx, inverse, tr, ti);
+#pragma omp barrier
+        if (rc == 0) {
+#pragma omp for schedule(static)
+            for (int k = 0; k < nz; ++k)             /* along x */
+                for (int j = 0; j < ny; ++j) {
+                    int64_t o = ((int64_t)k * ny + j) * nx;
+                    dft_line(re + o, im + o, nx, 1, inverse, tr, ti);
+                }
+#pragma omp for schedule(static)
+            for (int k = 0; k < nz; ++k)             /* along y */
+                for (int i = 0; i < nx; ++i) {
+                    int64_t o = (int64_t)k * ny * nx + i;
+                    dft_line(re + o, im + o, ny, nx, inverse, tr, ti);
+                }
+#pragma omp for schedule(static)
+            for (int j = 0; j < ny; ++j)             /* along z */
+                for (int i = 0; i < nx; ++i) {
+                    int64_t o = (int64_t)j * nx + i;
+                    dft_line(re + o, im + o, nz, (int64_t)nx * ny, inverse, tr, ti);
+                }
         }
-    for (int j = 0; j < ny; ++j)             /* along z */
-        for (int i = 0; i < nx; ++i) {
-            int64_t o = (int64_t)j * nx + i;
-            dft_line(re + o, im + o, nz, (int64_t)nx * ny, inverse, tr, ti);
-        }
-    free(tr);
-    free(ti);
-    return 0;
+        free(tr);
+        free(ti);
+    }
+    return rc;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -199,6 +235,7 @@ static void laplacian(const mbref_grid* g, const double* v, double* out)
 {
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     const double ih2 = 1.0 / (g->h * g->h);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -241,6 +278,7 @@ static void solve_and_project(const mbref_grid* g, double a0, double a1, int mea
 {
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     const double h = g->h;
+#pragma omp parallel for schedule(static)
     for (int kz = 0; kz < nz; ++kz)
         for (int ky = 0; ky < ny; ++ky)
             for (int kx = 0; kx < nx; ++kx) {
@@ -368,46 +406,191 @@ int mbref_bond_forces(const mbref_grid* g, int64_t n, const double* q, int64_t n
     return 0;
 }
 
-static void pair_force_on(const mbref_grid* g, int64_t n, const double* q, const int32_t* pid,
-                          double k_rep, double r_cut, int64_t i, double out[3])
+/* Contribution of blob j to the repulsion on blob i: k_rep (r_cut - r) r_hat, r = q_i - q_j
+ * (minimum image), for r < r_cut and blobs of different particles. */
+static void add_pair(const double L[3], const double* q, const int32_t* pid, double k_rep,
+                     double r_cut, int64_t i, int64_t j, double out[3])
+{
+    if (j == i || pid[j] == pid[i]) return;
+    double r[3], r2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        r[a] = min_image(q[3 * i + a] - q[3 * j + a], L[a]);
+        r2 += r[a] * r[a];
+    }
+    if (r2 >= r_cut * r_cut || r2 == 0.0) return;
+    double len = sqrt(r2);
+    double mag = k_rep * (r_cut - len) / len;
+    for (int a = 0; a < 3; ++a) out[a] += mag * r[a];
+}
+
+/* The definition: every other blob j = 0 .. n-1 in turn. */
+static void pair_force_brute(const double L[3], int64_t n, const double* q, const int32_t* pid,
+                             double k_rep, double r_cut, int64_t i, double out[3])
+{
+    out[0] = out[1] = out[2] = 0.0;
+    for (int64_t j = 0; j < n; ++j) add_pair(L, q, pid, k_rep, r_cut, i, j, out);
+}
+
+/* Bins of side w_a = L_a / nb_a >= r_cut (1 + 1e-6) along each axis.  Two blobs closer than
+ * r_cut (minimum image) differ by less than w_a along every axis, so their bins are equal or
+ * adjacent (periodically); the margin keeps that true when a coordinate on a bin boundary is
+ * rounded into the next bin.  With at least three bins per axis the 27 bins around a blob are
+ * distinct, and visiting the blobs listed there in ascending index order adds the same
+ * non-zero terms, in the same order, as the definition: the result is the same to the bit
+ * (tested).  Fewer bins fall back to the definition. */
+typedef struct {
+    int nb[3];
+    int64_t* start;   /* [nbins + 1] */
+    int64_t* list;    /* [n] blob indices, ascending within each bin */
+} pair_bins;
+
+static int bin_coord(double x, double L, int nb)
+{
+    double y = fmod(x, L);
+    if (y < 0.0) y += L;
+    int c = (int)floor(y / L * nb);
+    return c < 0 ? 0 : (c >= nb ? nb - 1 : c);
+}
+
+static int64_t blob_bin(const pair_bins* B, const double L[3], const double* q, int64_t i)
+{
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = bin_coord(q[3 * i + a], L[a], B->nb[a]);
+    return ((int64_t)c[2] * B->nb[1] + c[1]) * B->nb[0] + c[0];
+}
+
+/* 0: bins built; 1: too few bins (use the definition); 2: out of memory */
+static int build_bins(pair_bins* B, const double L[3], int64_t n, const double* q, double r_cut)
+{
+    B->start = NULL;
+    B->list = NULL;
+    for (int a = 0; a < 3; ++a) {
+        double m = floor(L[a] / (r_cut * (1.0 + 1e-6)));
+        if (m < 3.0) return 1;
+        B->nb[a] = m > 1024.0 ? 1024 : (int)m;
+    }
+    const int64_t nbins = (int64_t)B->nb[0] * B->nb[1] * B->nb[2];
+    B->start = (int64_t*)calloc((size_t)nbins + 1, sizeof(int64_t));
+    B->list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)nbins);
+    if (!B->start || !B->list || !fill) {
+        free(B->start); free(B->list); free(fill);
+        return 2;
+    }
+    for (int64_t i = 0; i < n; ++i) B->start[blob_bin(B, L, q, i) + 1] += 1;
+    for (int64_t b = 0; b < nbins; ++b) B->start[b + 1] += B->start[b];
+    memcpy(fill, B->start, sizeof(int64_t) * (size_t)nbins);
+    for (int64_t i = 0; i < n; ++i) B->list[fill[blob_bin(B, L, q, i)]++] = i;
+    free(fill);
+    return 0;
+}
+
+static int cmp_i64(const void* x, const void* y)
+{
+    int64_t a = *(const int64_t*)x, b = *(const int64_t*)y;
+    return (a > b) - (a < b);
+}
+
+/* Repulsion on blob i from the blobs of the 27 bins around it, in ascending index order.
+ * *cand / *cap is a per-thread buffer, grown as needed; returns 2 if that fails. */
+static int pair_force_binned(const pair_bins* B, const double L[3], const double* q,
+                             const int32_t* pid, double k_rep, double r_cut, int64_t i,
+                             int64_t** cand, int64_t* cap, double out[3])
+{
+    int c[3];
+    for (int a = 0; a < 3; ++a) c[a] = bin_coord(q[3 * i + a], L[a], B->nb[a]);
+    int64_t m = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int bx = (c[0] + dx + B->nb[0]) % B->nb[0];
+                const int by = (c[1] + dy + B->nb[1]) % B->nb[1];
+                const int bz = (c[2] + dz + B->nb[2]) % B->nb[2];
+                const int64_t b = ((int64_t)bz * B->nb[1] + by) * B->nb[0] + bx;
+                const int64_t k = B->start[b + 1] - B->start[b];
+                if (m + k > *cap) {
+                    int64_t nc = 2 * (m + k) + 64;
+                    int64_t* p = (int64_t*)realloc(*cand, sizeof(int64_t) * (size_t)nc);
+                    if (!p) return 2;
+                    *cand = p;
+                    *cap = nc;
+                }
+                memcpy(*cand + m, B->list + B->start[b], sizeof(int64_t) * (size_t)k);
+                m += k;
+            }
+    qsort(*cand, (size_t)m, sizeof(int64_t), cmp_i64);
+    out[0] = out[1] = out[2] = 0.0;
+    for (int64_t t = 0; t < m; ++t) add_pair(L, q, pid, k_rep, r_cut, i, (*cand)[t], out);
+    return 0;
+}
+
+/* Repulsion on the m blobs idx[0..m) (all n blobs when idx is NULL), written to out [m][3]
+ * (added to it when accumulate is set). */
+static int pair_forces_on(const mbref_grid* g, int64_t n, const double* q, const int32_t* pid,
+                          double k_rep, double r_cut, int64_t m, const int64_t* idx,
+                          int accumulate, int brute, double* out)
 {
     const double L[3] = {g->nx * g->h, g->ny * g->h, g->nz * g->h};
-    out[0] = out[1] = out[2] = 0.0;
-    for (int64_t j = 0; j < n; ++j) {
-        if (j == i || pid[j] == pid[i]) continue;
-        double r[3], r2 = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            r[a] = min_image(q[3 * i + a] - q[3 * j + a], L[a]);
-            r2 += r[a] * r[a];
-        }
-        if (r2 >= r_cut * r_cut || r2 == 0.0) continue;
-        double len = sqrt(r2);
-        double mag = k_rep * (r_cut - len) / len;
-        for (int a = 0; a < 3; ++a) out[a] += mag * r[a];
+    pair_bins B;
+    int binned = 0;
+    if (!brute) {
+        int rc = build_bins(&B, L, n, q, r_cut);
+        if (rc == 2) return 2;
+        binned = rc == 0;
     }
+    int err = 0;
+#pragma omp parallel
+    {
+        int64_t* cand = NULL;
+        int64_t cap = 0;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t s = 0; s < m; ++s) {
+            const int64_t i = idx ? idx[s] : s;
+            double fi[3];
+            if (binned) {
+                if (pair_force_binned(&B, L, q, pid, k_rep, r_cut, i, &cand, &cap, fi)) {
+#pragma omp atomic write
+                    err = 2;
+                    fi[0] = fi[1] = fi[2] = 0.0;
+                }
+            } else {
+                pair_force_brute(L, n, q, pid, k_rep, r_cut, i, fi);
+            }
+            for (int a = 0; a < 3; ++a)
+                out[3 * s + a] = accumulate ? out[3 * s + a] + fi[a] : fi[a];
+        }
+        free(cand);
+    }
+    if (binned) {
+        free(B.start);
+        free(B.list);
+    }
+    return err;
 }
 
 int mbref_pair_forces(const mbref_grid* g, int64_t n, const double* q, const int32_t* pid,
                       double k_rep, double r_cut, double* F)
 {
     if (k_rep == 0.0 || r_cut <= 0.0) return 0;
-    for (int64_t i = 0; i < n; ++i) {
-        double fi[3];
-        pair_force_on(g, n, q, pid, k_rep, r_cut, i, fi);
-        for (int a = 0; a < 3; ++a) F[3 * i + a] += fi[a];
-    }
-    return 0;
+    return pair_forces_on(g, n, q, pid, k_rep, r_cut, n, NULL, 1, 0, F);
+}
+
+int mbref_pair_forces_brute(const mbref_grid* g, int64_t n, const double* q, const int32_t* pid,
+                            double k_rep, double r_cut, double* F)
+{
+    if (k_rep == 0.0 || r_cut <= 0.0) return 0;
+    return pair_forces_on(g, n, q, pid, k_rep, r_cut, n, NULL, 1, 1, F);
 }
 
 int mbref_pair_forces_subset(const mbref_grid* g, int64_t n, const double* q,
                              const int32_t* pid, double k_rep, double r_cut, int64_t m,
                              const int64_t* idx, double* F)
 {
-    for (int64_t s = 0; s < m; ++s) {
-        if (k_rep == 0.0 || r_cut <= 0.0) { F[3 * s] = F[3 * s + 1] = F[3 * s + 2] = 0.0; continue; }
-        pair_force_on(g, n, q, pid, k_rep, r_cut, idx[s], F + 3 * s);
+    if (k_rep == 0.0 || r_cut <= 0.0) {
+        memset(F, 0, sizeof(double) * 3 * (size_t)m);
+        return 0;
     }
-    return 0;
+    return pair_forces_on(g, n, q, pid, k_rep, r_cut, m, idx, 0, 0, F);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -474,6 +657,7 @@ int mbref_stress_normals(const mbref_grid* g, uint64_t seed, uint64_t step, int6
 {
     const int64_t N = (int64_t)g->nx * g->ny * g->nz;
     if (g->nx % 4 != 0) return 1;
+#pragma omp parallel for schedule(static)
     for (int64_t m = 0; m < N; ++m) {
         double z[9];
         cell_normals(seed, step, box, m, z);
@@ -486,6 +670,7 @@ int mbref_stress_div(const mbref_grid* g, const double* W, double* f)
 {
     const int n[3] = {g->nx, g->ny, g->nz};
     const int64_t N = (int64_t)n[0] * n[1] * n[2];
+#pragma omp parallel for collapse(2) schedule(static)
     for (int a = 0; a < 3; ++a)
         for (int k = 0; k < n[2]; ++k)
             for (int j = 0; j < n[1]; ++j)
@@ -516,6 +701,7 @@ int mbref_advection(const mbref_grid* g, const double* v, double* out)
     const int64_t N = (int64_t)n[0] * n[1] * n[2];
     double* M = (double*)malloc(sizeof(double) * 9 * N);
     if (!M) return 2;
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < n[2]; ++k)
         for (int j = 0; j < n[1]; ++j)
             for (int i = 0; i < n[0]; ++i) {

@@ -6,7 +6,8 @@
  * leg do.  It shares no source with the CUDA path.
  *
  * Every routine is written for clarity, not speed: fixed loop order, IEEE double,
- * no fast-math, no contraction (built with -ffp-contract=off).
+ * no fast-math, no contraction (built with -ffp-contract=off).  Independent loops may run on
+ * several host threads (OpenMP) without changing any result (mbref_set_threads).
  *
  * Paper: Vazquez-Quesada, Balboa Usabiaga, Delgado-Buscalioni, "A multiblob approach to
  * colloidal hydrodynamics with inherent lubrication" (arXiv:1407.5600).
@@ -37,6 +38,10 @@ typedef struct {
     int advection;   /* 1: the convective stress rho v v of Eq. (vf), explicit at v^n */
 } mbref_grid;
 
+/* Number of host threads the oracle's parallel loops use (n <= 0 leaves it unchanged);
+ * returns the number in effect (1 when built without OpenMP).  Results do not depend on it. */
+int mbref_set_threads(int n);
+
 /* Three-point kernel Phi of Eq. (delta): the Roma-Peskin-Berger function. */
 double mbref_phi(double r);
 
@@ -66,9 +71,14 @@ int mbref_bond_forces(const mbref_grid* g, int64_t n, const double* q, int64_t n
                       const int32_t* bonds, const double* rest, double k, double* F);
 
 /* F += soft blob-blob repulsion k_rep (r_cut - r) r_hat for r < r_cut, between blobs of
- * different particles, by brute force over all pairs. */
+ * different particles.  Each blob sums over the blobs of the bins around it in ascending index
+ * order, which gives the sum over all pairs (mbref_pair_forces_brute) to the bit. */
 int mbref_pair_forces(const mbref_grid* g, int64_t n, const double* q, const int32_t* pid,
                       double k_rep, double r_cut, double* F);
+
+/* The same repulsion by its definition: every blob sums over all other blobs in index order. */
+int mbref_pair_forces_brute(const mbref_grid* g, int64_t n, const double* q, const int32_t* pid,
+                            double k_rep, double r_cut, double* F);
 
 /* Same repulsion, evaluated only for the m blobs listed in idx (F is [m][3], overwritten). */
 int mbref_pair_forces_subset(const mbref_grid* g, int64_t n, const double* q,

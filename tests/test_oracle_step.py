@@ -76,6 +76,33 @@ def test_pair_forces_gradient_balance_and_subset():
     assert np.all(F1 == 0.0)
 
 
+@pytest.mark.parametrize("shape,h,r_cut,nblob", [
+    ((16, 16, 16), 1.0, 1.0, 3000),      # many bins, dense
+    ((8, 12, 20), 0.7, 1.3, 1500),       # non-cubic, h != 1
+    ((8, 8, 8), 1.0, 2.9, 400),          # two bins along each axis: the definition is used
+    ((32, 4, 16), 1.0, 0.5, 2000),       # thin box
+])
+def test_binned_repulsion_equals_all_pairs_to_the_bit(shape, h, r_cut, nblob):
+    """The bins only skip pairs farther apart than r_cut; the sum over the rest runs in the
+    definition's order, so the two agree exactly, also for blobs on and outside the box faces."""
+    nz, ny, nx = shape
+    g = mb.Grid(nx, ny, nz, h=h)
+    rng = np.random.default_rng(nblob)
+    q = rng.uniform(0, 1, size=(nblob, 3)) * g.L
+    q[:40] = q[:40] * 1e-3                                   # a cluster at the origin corner
+    q[40:60] = g.L - q[40:60] * 1e-3                         # and just below the far faces
+    q[60:70] += g.L                                          # outside the box
+    q[70:80] -= 2 * g.L
+    q[80:90, 0] = np.round(q[80:90, 0] / (r_cut * 1.000001)) * r_cut * 1.000001   # on bin faces
+    pid = (np.arange(nblob) // 13).astype(np.int32)
+    Fb = mb.pair_forces(g, q, pid, 75.0, r_cut)
+    Fa = mb.pair_forces_brute(g, q, pid, 75.0, r_cut)
+    assert np.count_nonzero(Fa) > 0
+    assert np.array_equal(Fa, Fb)
+    idx = rng.choice(nblob, 50, replace=False)
+    assert np.array_equal(mb.pair_forces_subset(g, q, pid, 75.0, r_cut, idx), Fa[idx])
+
+
 def _single(n=16, a=1.0, seed=1):
     spec, s = wl.single_particle(n=n, a=a, seed=seed)
     g = mb.Grid(spec.nx, spec.ny, spec.nz, h=spec.h, rho=spec.rho, eta=spec.eta, dt=spec.dt,
