@@ -261,6 +261,17 @@ mb_status mb_adjoint_step(mb_ctx* ctx, const double* pos_n, const void* grid_v_n
 mb_status mb_velocity_adjoint(mb_ctx* ctx, const double* pos, const void* grid_v,
                               const double* grad_u, double* grad_pos, void* grad_v);
 
+/* Adjoint of the particle velocities U0_p = (1/N_p) sum_{i in p} J_i(q) v (Sec. 2, the
+ * translational velocity of a particle as the mean of its blob velocities, with Eq. ju) at
+ * positions pos and field grid_v:
+ *   grad_pos [total blobs][3] += (dU0/dq)^T grad_U,
+ *   grad_v   one grid (context precision) += (dU0/dv)^T grad_U,
+ * grad_U being [total particles][3].  Equivalent to mb_velocity_adjoint with
+ * grad_u_i = grad_U_p(i) / N_p(i).  FP64 contexts with batch 1; arrays may be host or device;
+ * MB_EINVAL for null arrays or other contexts. */
+mb_status mb_particle_velocity_adjoint(mb_ctx* ctx, const double* pos, const void* grid_v,
+                                       const double* grad_U, double* grad_pos, void* grad_v);
+
 /* Spreading tile (nodes per block along x, y, z) in use and the time one spreading launch
  * took with it when it was chosen (0 if not timed).  In FP32-grid mode the first step after
  * mb_set_particles times a set of candidate tile shapes on the actual blob distribution and
@@ -279,9 +290,10 @@ mb_status mb_get_counts(const mb_ctx* ctx, int64_t* total_blobs, int64_t* total_
  * compiled into the library instead of buffers it would otherwise have to allocate.
  *   pos, F       [n][3] FP64 DEVICE arrays (positions are taken modulo the box).
  *   grid_out     one box grid (3 components, desc->precision) in DEVICE memory, overwritten.
- *   cuda_stream  stream the work is enqueued on (NULL = legacy default stream).
- * Limits: 0 <= n <= 262144 blobs, grids up to 128^3; larger sizes and host pointers are
- * rejected with MB_EINVAL.  The scratch array (about 5 MiB) is held by every GPU that loads
+ *   cuda_stream  stream of the current device the work is enqueued on (NULL = legacy default
+ *                stream); a stream of another device is rejected with MB_EINVAL.
+ * Limits: 0 <= n <= 262144 blobs, grids up to 128^3; larger sizes, host pointers and device
+ * pointers of a GPU other than the current device are rejected with MB_EINVAL.  The scratch array (about 5 MiB) is held by every GPU that loads
  * the library until the process exits.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) and caches it; make that first call before any stream
  * capture.  Every call reuses the same array, so calls that overlap on the GPU (on different

@@ -21,7 +21,8 @@ __all__ = [
     "get_velocities", "get_particle_velocities", "set_velocity_field", "spread", "spread_static",
     "interp",
     "fluid_update", "get_counts", "get_forces", "set_stage_timing", "get_stage_times",
-    "get_launch_count", "get_tuning", "set_positions", "adjoint_step", "velocity_adjoint", "last_error", "Multiblob",
+    "get_launch_count", "get_tuning", "set_positions", "adjoint_step", "velocity_adjoint",
+    "particle_velocity_adjoint", "last_error", "Multiblob",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -109,6 +110,7 @@ def load_library(path: str | None = None):
         "mb_get_tuning": [P, P, P],
         "mb_adjoint_step": [P, P, P, P, P, P, P, P],
         "mb_velocity_adjoint": [P, P, P, P, P, P],
+        "mb_particle_velocity_adjoint": [P, P, P, P, P, P],
         "mb_get_stage_times": [P, I, P, P, ctypes.POINTER(I)],
         "mb_get_launch_count": [P, ctypes.POINTER(I64)],
         "mb_set_step_index": [P, ctypes.c_uint64],
@@ -289,6 +291,13 @@ def velocity_adjoint(ctx, pos, grid_v, grad_u, grad_pos, grad_v):
     """mb_velocity_adjoint: grad_pos += (du/dq)^T grad_u, grad_v += J^T grad_u."""
     _check(ctx, load_library().mb_velocity_adjoint(
         ctx, _ptr(pos, np.float64), _ptr(grid_v), _ptr(grad_u, np.float64),
+        _ptr(grad_pos, np.float64), _ptr(grad_v)))
+
+
+def particle_velocity_adjoint(ctx, pos, grid_v, grad_U, grad_pos, grad_v):
+    """mb_particle_velocity_adjoint: grad_pos += (dU0/dq)^T grad_U, grad_v += (dU0/dv)^T grad_U."""
+    _check(ctx, load_library().mb_particle_velocity_adjoint(
+        ctx, _ptr(pos, np.float64), _ptr(grid_v), _ptr(grad_U, np.float64),
         _ptr(grad_pos, np.float64), _ptr(grad_v)))
 
 

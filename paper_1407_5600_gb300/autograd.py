@@ -3,7 +3,7 @@
 `rollout_particle_velocities(sim, q0, k_spring, ...)` runs K steps of one box from blob
 positions q0 (fluid at rest) with spring stiffness k_spring and returns the particle velocities
 U0 (Sec. 2: U0 = mean blob velocity) after the last step.  Its backward pass is the hand-written
-adjoint of the step (mb_adjoint_step, mb_velocity_adjoint): the state is checkpointed every
+adjoint of the step (mb_adjoint_step, mb_particle_velocity_adjoint): the state is checkpointed every
 `checkpoint` steps in the forward pass, and each segment is recomputed from its checkpoint in
 the backward pass, so memory holds at most `checkpoint` states at a time.
 
@@ -15,8 +15,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (Multiblob, adjoint_step, get_velocities, set_positions, set_velocity_field,
-               step, velocity_adjoint)
+from . import (Multiblob, adjoint_step, particle_velocity_adjoint, set_positions,
+               set_velocity_field, step)
 
 
 class _Rollout(torch.autograd.Function):
@@ -42,12 +42,11 @@ class _Rollout(torch.autograd.Function):
     @staticmethod
     def backward(fctx, gU):
         sim = fctx.sim
-        pid = torch.as_tensor(np.asarray(fctx.topo[0]), device=sim.device, dtype=torch.long)
-        counts = torch.bincount(pid).to(torch.float64)
-        gu = (gU.to(torch.float64) / counts[:, None])[pid].contiguous()
         gq = torch.zeros_like(fctx.qK)
         gv = torch.zeros_like(fctx.vK)
-        velocity_adjoint(sim.ctx, fctx.qK, fctx.vK, gu, gq, gv)
+        particle_velocity_adjoint(sim.ctx, fctx.qK, fctx.vK,
+                                  gU.to(dtype=torch.float64, device=sim.device).contiguous(),
+                                  gq, gv)
         gk = np.zeros(1, dtype=np.float64)
         K, chk_every = fctx.K, fctx.checkpoint
         for seg in reversed(range(len(fctx.chk))):

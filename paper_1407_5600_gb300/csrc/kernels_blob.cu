@@ -933,6 +933,36 @@ cudaError_t launch_particle_reduce(cudaStream_t st, int64_t np, const int32_t* p
     return cudaGetLastError();
 }
 
+// Transpose of the particle mean U0 = (1/N_p) sum_{i in p} u_i (Sec. 2): every blob of particle
+// p receives gU_p / N_p.  One thread per particle; blobs belong to one particle each, so the
+// writes are disjoint.
+__global__ void k_particle_mean_adjoint(int64_t np, const int32_t* __restrict__ part_start,
+                                        const int32_t* __restrict__ part_blobs,
+                                        const double* __restrict__ gU, double* __restrict__ gu)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int s = part_start[p], e = part_start[p + 1];
+    if (e <= s) return;
+    const double inv = 1.0 / (double)(e - s);
+    const double g0 = gU[3 * p] * inv, g1 = gU[3 * p + 1] * inv, g2 = gU[3 * p + 2] * inv;
+    for (int i = s; i < e; ++i) {
+        const int b = part_blobs[i];
+        gu[3 * b] = g0;
+        gu[3 * b + 1] = g1;
+        gu[3 * b + 2] = g2;
+    }
+}
+
+cudaError_t launch_particle_mean_adjoint(cudaStream_t st, int64_t np, const int32_t* part_start,
+                                         const int32_t* part_blobs, const double* gU, double* gu)
+{
+    if (np <= 0) return cudaSuccess;
+    k_particle_mean_adjoint<<<(unsigned)((np + 127) / 128), 128, 0, st>>>(np, part_start,
+                                                                         part_blobs, gU, gu);
+    return cudaGetLastError();
+}
+
 // ==========================================================================================
 // Mean of each component grid (FP64 accumulation, fixed order).
 template <typename R>

@@ -182,7 +182,7 @@ struct mb_ctx {
     bool graph_fz[2] = {false, false};
     int64_t graph_launches = 0;        // kernels per graph launch
     // adjoint scratch: blob vectors and grids (FP64 contexts)
-    DBuf a_qn, a_u, a_qh, a_gq, a_guc, a_gqh, a_gF, a_gu, a_gk;
+    DBuf a_qn, a_u, a_qh, a_gq, a_guc, a_gqh, a_gF, a_gu, a_gk, a_gU;
     DBuf a_vn, a_vp, a_w, a_gw, a_gvp, a_gvn, a_gf, a_tmp, a_zero;
     // standalone-operator scratch
     DBuf s_q, s_F, s_rec, s_cell_count, s_cell_start, s_blob_cell, s_blob_rank, s_sorted,
@@ -1424,7 +1424,7 @@ void release(mb_ctx* ctx)
                    &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out, &ctx->sA,
                    &ctx->sB, &ctx->hA[0], &ctx->hA[1], &ctx->hB[0], &ctx->hB[1], &ctx->F32, &ctx->rec32, &ctx->ext32,
                    &ctx->ext_sum, &ctx->ext_ticket, &ctx->adj32, &ctx->adj32_start, &ctx->Fs32, &ctx->u32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
-                   &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk,
+                   &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk, &ctx->a_gU,
                    &ctx->a_vn, &ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvp, &ctx->a_gvn,
                    &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero, &ctx->W, &ctx->step_index,
                    &ctx->twk[0], &ctx->twk[1], &ctx->twk[2], &ctx->symk};
@@ -1943,6 +1943,39 @@ mb_status mb_velocity_adjoint(mb_ctx* ctx, const double* pos, const void* grid_v
     MB_TRY(pull(ctx, ctx->a_gu, grad_u, bv, "adjoint gu"));
     MB_TRY(pull(ctx, ctx->a_gq, grad_pos, bv, "adjoint gq"));
     MB_TRY(pull(ctx, ctx->a_gvn, grad_v, bg, "adjoint gv"));
+    double* q = static_cast<double*>(ctx->a_qn.p);
+    k_wrap<<<(unsigned)((3 * nb + 255) / 256), 256, 0, ctx->st>>>(nb, q, ctx->g.L[0], ctx->g.L[1],
+                                                                 ctx->g.L[2]);
+    MB_CUDA(cudaGetLastError());
+    MB_TRY(velocity_adjoint_dev(ctx, q, static_cast<const double*>(ctx->a_vn.p),
+                                static_cast<const double*>(ctx->a_gu.p),
+                                static_cast<double*>(ctx->a_gq.p),
+                                static_cast<double*>(ctx->a_gvn.p)));
+    MB_TRY(push(ctx, grad_pos, ctx->a_gq, bv));
+    return push(ctx, grad_v, ctx->a_gvn, bg);
+}
+
+mb_status mb_particle_velocity_adjoint(mb_ctx* ctx, const double* pos, const void* grid_v,
+                                       const double* grad_U, double* grad_pos, void* grad_v)
+{
+    if (!ctx) return MB_EINVAL;
+    DeviceGuard dg(ctx->device);
+    if (!pos || !grid_v || !grad_U || !grad_pos || !grad_v) return invalid(ctx, "null argument");
+    MB_TRY(adjoint_preconditions(ctx));
+    const int64_t nb = ctx->nb, np = ctx->np;
+    const size_t bv = sizeof(double) * 3 * nb, bg = sizeof(double) * 3 * ctx->g.N;
+    MB_TRY(pull(ctx, ctx->a_qn, pos, bv, "adjoint q"));
+    MB_TRY(pull(ctx, ctx->a_vn, grid_v, bg, "adjoint v"));
+    MB_TRY(pull(ctx, ctx->a_gU, grad_U, sizeof(double) * 3 * (np > 0 ? np : 1), "adjoint gU"));
+    MB_TRY(pull(ctx, ctx->a_gq, grad_pos, bv, "adjoint gq"));
+    MB_TRY(pull(ctx, ctx->a_gvn, grad_v, bg, "adjoint gv"));
+    MB_TRY(ensure(ctx->a_gu, bv, ctx->err, "adjoint gu"));
+    MB_CUDA(cudaMemsetAsync(ctx->a_gu.p, 0, bv, ctx->st));
+    MB_CUDA(launch_particle_mean_adjoint(ctx->st, np,
+                                         static_cast<const int32_t*>(ctx->part_start.p),
+                                         static_cast<const int32_t*>(ctx->part_blobs.p),
+                                         static_cast<const double*>(ctx->a_gU.p),
+                                         static_cast<double*>(ctx->a_gu.p)));
     double* q = static_cast<double*>(ctx->a_qn.p);
     k_wrap<<<(unsigned)((3 * nb + 255) / 256), 256, 0, ctx->st>>>(nb, q, ctx->g.L[0], ctx->g.L[1],
                                                                  ctx->g.L[2]);

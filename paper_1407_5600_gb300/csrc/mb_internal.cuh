@@ -128,6 +128,11 @@ cudaError_t launch_particle_reduce(cudaStream_t st, int64_t np, const int32_t* p
                                    const double* q, const double* u, const GridGeo& g,
                                    double* U, double* Omega);
 
+// Adjoint of U0 = (1/N_p) sum_i u_i: gu[i] = gU[p(i)] / N_p for every blob of every particle.
+cudaError_t launch_particle_mean_adjoint(cudaStream_t st, int64_t np, const int32_t* part_start,
+                                         const int32_t* part_blobs, const double* gU,
+                                         double* gu);
+
 // Fluid update pipeline on B boxes.
 template <typename R>
 struct FluidArgs {

@@ -229,6 +229,8 @@ k_static_spread(const double* __restrict__ pos, const double* __restrict__ F,
 
 bool is_pow2_in(int n) { return n >= 4 && n <= 128 && (n & (n - 1)) == 0; }
 
+// Device memory of the current device, or managed memory.  Device memory of another GPU is
+// refused: the kernels run on the current device and would dereference a peer pointer.
 bool on_device(const void* p)
 {
     cudaPointerAttributes at;
@@ -236,7 +238,14 @@ bool on_device(const void* p)
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.device == dev;
 }
 
 mb_status fail(mb_status s, const std::string& msg)
@@ -304,8 +313,8 @@ extern "C" mb_status mb_spread_static(const mb_grid_desc* desc, int64_t n, const
     if (!grid_out || (n > 0 && (!pos || !F)))
         return fail(MB_EINVAL, "pos, F (when n > 0) and grid_out must be non-null");
     if (!on_device(grid_out) || (n > 0 && (!on_device(pos) || !on_device(F))))
-        return fail(MB_EINVAL, "pos, F and grid_out must be device pointers (host arrays would "
-                               "need a staging allocation)");
+        return fail(MB_EINVAL, "pos, F and grid_out must be device pointers on the current "
+                               "device (host arrays would need a staging allocation)");
     int32_t* scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);
     if (e != cudaSuccess) {
@@ -322,6 +331,14 @@ extern "C" mb_status mb_spread_static(const mb_grid_desc* desc, int64_t n, const
     g.inv_h = 1.0 / desc->h;
     g.inv_w = 1.0 / (2.0 * desc->h);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (st) {
+        int sdev = -1, dev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MB_EINVAL, "cuda_stream is not a valid stream");
+        }
+        if (sdev != dev) return fail(MB_EINVAL, "cuda_stream belongs to another device");
+    }
     if (desc->precision == 0)
         e = launch_all<float>(st, n, pos, F, scratch, g, (int)ncell, static_cast<float*>(grid_out));
     else

@@ -22,11 +22,22 @@ TOL = {0: 1e-5, 1: 1e-10}
 
 
 def position_error(q, q_ref, q0, L, nsteps):
-    """Relative L2 error of the displacement q - q0 against q_ref - q0 (minimum image), with
-    the rounding floor of FP64 positions: each step rounds a coordinate of magnitude <= L once,
-    so differences of a few ulps of L per step are representation error, not method error."""
+    """(|d|, |ref|, floor) for the displacement error d = q - q_ref (minimum image) against the
+    reference displacement ref = q_ref - q0, and the rounding floor of the positions: each step
+    rounds a coordinate of magnitude <= L once, in FP64 in the oracle and in FP64 or split
+    float pairs (finer than FP64 at these box sizes) on the GPU, so a few ulps of L per step
+    are representation error, not method error.  The floor does not depend on the tolerance."""
     L = np.asarray(L, dtype=np.float64)
     d = min_image(np.asarray(q) - q_ref, L)
     ref = min_image(np.asarray(q_ref) - q0, L)
     floor = 4.0 * max(nsteps, 1) * np.finfo(np.float64).eps * np.max(L) * np.sqrt(d.size)
-    return np.linalg.norm(d) / (np.linalg.norm(ref) + floor / 1e-10)
+    return np.linalg.norm(d), np.linalg.norm(ref), floor
+
+
+def assert_positions(q, q_ref, q0, L, nsteps, tol):
+    """Assert |q - q_ref| <= tol |q_ref - q0| + floor (relative L2 on the displacement, plus the
+    FP64 rounding floor of position_error)."""
+    err, ref, floor = position_error(q, q_ref, q0, L, nsteps)
+    assert err <= tol * ref + floor, (
+        f"position error {err:.3e} > {tol:.1e} x |displacement| {ref:.3e} + floor {floor:.2e}"
+        f" (relative {err / max(ref, 1e-300):.3e})")

@@ -1,7 +1,7 @@
 """Adjoint of the ICM step and of K-step rollouts against FP64 central finite differences.
 
 The gradient of a scalar loss with respect to every blob coordinate and the spring stiffness
-comes from the hand-written adjoint (mb_adjoint_step, mb_velocity_adjoint) through
+comes from the hand-written adjoint (mb_adjoint_step, mb_particle_velocity_adjoint) through
 torch.autograd; it is checked along seeded random directions against central differences of
 the FP64 GPU forward (step 1e-6 for positions, 1e-3 relative for the stiffness) and against
 central differences of the FP64 CPU oracle.
@@ -70,6 +70,37 @@ def test_single_step_adjoint_against_finite_differences():
         fd_v = (loss(q0, v0 + EPS * dv_dir) - loss(q0, v0 - EPS * dv_dir)) / (2 * EPS)
         an_v = float((gv * dv_dir).sum())
         assert abs(an_v - fd_v) < 1e-6 * max(1.0, abs(fd_v)), (an_v, fd_v)
+
+
+def test_particle_velocity_adjoint_against_oracle_differences():
+    """mb_particle_velocity_adjoint: the transpose of U0 = (1/N_p) sum J_i(q) v along random
+    directions in q and v, against central differences of the oracle's interpolation and
+    particle mean."""
+    s, _ = _two_particles()
+    d = mb.GridDesc(16, 16, 16, precision=1, dt=0.05, mean_mode=0)
+    g = oracle.Grid(16, 16, 16)
+    rng = np.random.default_rng(8)
+    v = rng.normal(size=(3, 16, 16, 16))
+    gU = rng.normal(size=(s.n_particles, 3))
+    dq = rng.normal(size=s.pos.shape)
+    dv = rng.normal(size=v.shape)
+
+    def U0(q, vv):
+        return oracle.particle_velocities(g, q, oracle.interp(g, q, vv), s.pid,
+                                          s.n_particles)[0]
+
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, 100.0)
+        gq = torch.zeros(s.pos.shape, dtype=torch.float64, device="cuda")
+        gv = torch.zeros((1, 3, 16, 16, 16), dtype=torch.float64, device="cuda")
+        mb.particle_velocity_adjoint(sim.ctx, torch.tensor(s.pos, device="cuda"),
+                                     torch.tensor(v[None], device="cuda"),
+                                     torch.tensor(gU, device="cuda"), gq, gv)
+        gq, gv = gq.cpu().numpy(), gv.cpu().numpy()[0]
+    fd_q = np.sum(gU * (U0(s.pos + EPS * dq, v) - U0(s.pos - EPS * dq, v))) / (2 * EPS)
+    fd_v = np.sum(gU * (U0(s.pos, v + dv) - U0(s.pos, v - dv))) / 2.0
+    assert abs(np.sum(gq * dq) - fd_q) < 1e-6 * max(1.0, abs(fd_q))
+    assert abs(np.sum(gv * dv) - fd_v) < 1e-12 * max(1.0, abs(fd_v))
 
 
 def _rollout_setup(n, seed):

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import TOL, position_error, rel_l2, to_np
+from helpers import TOL, assert_positions, rel_l2, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -74,7 +74,7 @@ def test_step_with_advection_parity(prec, kT):
     v0r = v0.astype(d.grid_dtype).astype(np.float64)
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, v0r, s.pid, s.bonds, s.rest, s.k_spring,
                                s.k_rep, s.r_cut, ext=ext, body=body, kT=kT, seed=d.seed)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[prec])
     assert rel_l2(v[0], v_ref) < TOL[prec]
 
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import TOL, position_error, to_np
+from helpers import TOL, assert_positions, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,7 @@ def test_gap_sweep_full_size(sweep):
         s = boxes[b]
         q_ref, _ = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
                                ext=s.ext)
-        assert position_error(q[off[b]:off[b + 1]], q_ref, s.pos, g.L, nsteps) < TOL[0]
+        assert_positions(q[off[b]:off[b + 1]], q_ref, s.pos, g.L, nsteps, TOL[0])
     # relative mobility after 100 steps: particle 0 is pushed +x, particle 1 -x
     F = boxes[0].ext[0, 0] * 13
     mob = np.array([(U[2 * b, 0] - U[2 * b + 1, 0]) / (2 * F) for b in range(B)])

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import TOL, min_image, position_error, rel_l2, to_np
+from helpers import TOL, min_image, assert_positions, rel_l2, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -72,7 +72,7 @@ def test_thermal_step_parity_on_256_sides(prec, shape):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest,
                                s.k_spring, ext=s.ext, kT=d.kT, seed=d.seed)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[prec])
     assert rel_l2(v[0], v_ref) < TOL[prec]
 
 
@@ -96,7 +96,7 @@ def test_stokes_step_parity_on_a_256_side(prec, stretch, tol):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.stokes_step(g, 3, s.pos, s.pid, s.bonds, s.rest, s.k_spring,
                                       ext=s.ext)
-    assert position_error(q, q_ref, s.pos, g.L, 3) < tol
+    assert_positions(q, q_ref, s.pos, g.L, 3, tol)
     assert rel_l2(v[0], v_ref) < tol
 
 
@@ -141,6 +141,30 @@ def test_full_size_fluctuating_suspension(thermal256):
 
 
 
+def test_full_size_fluctuating_steps_match_oracle(thermal256):
+    """The 256^3 fluctuating suspension (476,697 blobs, kT = 1e-3, FP32 grid, five-pass FFT),
+    element by element: two steps, positions, fluid and blob velocities against two oracle steps
+    drawing the same thermal stress (Philox keyed by seed 17, steps 0 and 1)."""
+    spec, s = thermal256
+    n = spec.nx
+    d = mb.GridDesc(n, n, n, h=spec.h, rho=spec.rho, eta=spec.eta, dt=spec.dt, precision=0,
+                    mean_mode=spec.mean_mode, kT=spec.kT, seed=17)
+    nsteps = 2
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut)
+        sim.step(nsteps)
+        q = to_np(sim.blob_positions())
+        v = to_np(sim.velocity_field())[0].astype(np.float64)
+        u = to_np(sim.blob_velocities())
+    g = oracle.Grid(n, n, n, h=spec.h, rho=spec.rho, eta=spec.eta, dt=spec.dt,
+                    mean_mode=spec.mean_mode)
+    q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
+                               s.k_rep, s.r_cut, kT=spec.kT, seed=17)
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[0])
+    assert rel_l2(v, v_ref) < TOL[0]
+    assert rel_l2(u, oracle.interp(g, q_ref, v_ref)) < TOL[0]
+
+
 @pytest.mark.parametrize("prec", [1, 0])
 @pytest.mark.parametrize("shape", [(16, 16, 16), (8, 16, 128), (4, 4, 4), (32, 8, 64),
                                    (128, 4, 8)])
@@ -176,5 +200,5 @@ def test_five_pass_step_parity(monkeypatch, prec):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.step(g, 3, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
                                s.k_rep, s.r_cut, ext=ext, body=s.body, kT=d.kT, seed=d.seed)
-    assert position_error(q, q_ref, s.pos, g.L, 3) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, 3, TOL[prec])
     assert rel_l2(v[0], v_ref) < TOL[prec]

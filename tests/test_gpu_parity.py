@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import TOL, min_image, position_error, rel_l2, to_np
+from helpers import TOL, min_image, assert_positions, rel_l2, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -131,7 +131,7 @@ def test_step_parity_single_particle(prec):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
                                ext=s.ext)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[prec])
     assert rel_l2(v[0], v_ref) < TOL[prec]
     u_ref = oracle.interp(g, q_ref, v_ref)
     assert rel_l2(u, u_ref) < TOL[prec]
@@ -161,7 +161,7 @@ def test_step_parity_dense_with_repulsion(prec):
     v0r = v0.astype(d.grid_dtype).astype(np.float64)
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, v0r, s.pid, s.bonds, s.rest, s.k_spring,
                                s.k_rep, s.r_cut, ext=ext, body=s.body)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[prec])
     assert rel_l2(v[0], v_ref) < TOL[prec]
 
 
@@ -202,7 +202,7 @@ def test_batched_boxes_match_independent_runs(prec):
         q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest,
                                    s.k_spring, ext=s.ext)
         qb = q[off:off + s.n_blobs]
-        assert position_error(qb, q_ref, s.pos, g.L, nsteps) < TOL[prec]
+        assert_positions(qb, q_ref, s.pos, g.L, nsteps, TOL[prec])
         assert rel_l2(v[b], v_ref) < TOL[prec]
         off += s.n_blobs
 
@@ -224,7 +224,7 @@ def test_empty_box_and_single_blob():
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.step(g, 4, single.pos, g.zeros(), single.pid, single.bonds,
                                single.rest, 0.0, ext=ext)
-    assert position_error(q, q_ref, single.pos, g.L, 4) < 1e-10
+    assert_positions(q, q_ref, single.pos, g.L, 4, 1e-10)
     assert rel_l2(v[0], v_ref) < 1e-10
     assert np.all(v[1] == 0.0)
 
@@ -302,7 +302,7 @@ def test_fp32_step_external_forces_from_any_memory(kind):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
                                s.k_rep, s.r_cut, ext=ext, body=s.body)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[0]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[0])
     assert rel_l2(u, oracle.interp(g, q_ref, v_ref)) < TOL[0]
 
 
@@ -367,6 +367,36 @@ def test_full_size_step_properties(dense128):
     assert np.all(np.isfinite(q)) and np.max(np.abs(r - s.rest) / s.rest) < 1e-2
 
 
+def test_full_size_bench_steps_match_oracle(dense128):
+    """The benchmarked workload itself, element by element: 128^3 FP32 grid, 244,504 blobs,
+    repulsion and body force, run as the benchmark runs it (first step direct with the spreading
+    tile autotuned after it, then graph replays of both velocity-buffer parities with the fused
+    corrector/predictor interpolation).  Positions, the fluid velocity, the blob velocities and
+    the particle velocities after three steps against three FP64 oracle steps."""
+    spec, s = dense128
+    assert s.n_blobs == 244504
+    nsteps = 3
+    d = mb.GridDesc(128, 128, 128, precision=0, mean_mode=0, dt=spec.dt)
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut)
+        sim.step(nsteps, body_force=s.body)
+        q = to_np(sim.blob_positions())
+        v = to_np(sim.velocity_field())[0].astype(np.float64)
+        u = to_np(sim.blob_velocities())
+        U, _ = (to_np(x) for x in sim.particle_velocities())
+        tile, _ = mb.get_tuning(sim.ctx)
+    assert tile in [(32, 8, 8), (16, 8, 8), (32, 16, 8), (16, 16, 8), (64, 8, 8)]
+    g = _oracle_grid(d)
+    q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
+                               s.k_rep, s.r_cut, body=s.body)
+    u_ref = oracle.interp(g, q_ref, v_ref)
+    U_ref, _ = oracle.particle_velocities(g, q_ref, u_ref, s.pid, s.n_particles)
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[0])
+    assert rel_l2(v, v_ref) < TOL[0]
+    assert rel_l2(u, u_ref) < TOL[0]
+    assert rel_l2(U, U_ref) < TOL[0]
+
+
 def test_graph_replay_matches_direct_launches(monkeypatch):
     """Steps replayed from the captured CUDA graph equal directly launched steps."""
     spec, s = _dense_small(seed=7)
@@ -384,7 +414,7 @@ def test_graph_replay_matches_direct_launches(monkeypatch):
     # FP32 shared-memory atomics add in a run-dependent order: the two runs agree to the
     # FP32-grid tolerance, not bitwise
     L = np.array([spec.nx, spec.ny, spec.nz], dtype=float)
-    assert position_error(out[0][0], out[1][0], s.pos, L, 8) < TOL[0]
+    assert_positions(out[0][0], out[1][0], s.pos, L, 8, TOL[0])
     assert rel_l2(out[0][1], out[1][1]) < TOL[0]
 
 
@@ -403,7 +433,7 @@ def test_fast_translation_in_uniform_flow():
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, v0, s.pid, s.bonds, s.rest, s.k_spring,
                                s.k_rep, s.r_cut, body=s.body)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[0]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[0])
     assert rel_l2(v[0], v_ref) < TOL[0]
 
 
@@ -437,8 +467,8 @@ def test_state_set_between_fp32_steps(monkeypatch, fuse):
         sim.step(2, body_force=s.body)
         q = to_np(sim.blob_positions())
         v = to_np(sim.velocity_field()).astype(np.float64)
-    assert position_error(q5, q_ref5, s.pos, g.L, 5) < TOL[0]
-    assert position_error(q, q_ref, q_set, g.L, 2) < TOL[0]
+    assert_positions(q5, q_ref5, s.pos, g.L, 5, TOL[0])
+    assert_positions(q, q_ref, q_set, g.L, 2, TOL[0])
     assert rel_l2(v[0], v_ref) < TOL[0]
 
 
@@ -459,7 +489,7 @@ def test_deterministic_fp64_runs_are_bitwise_identical():
     g = _oracle_grid(mb.GridDesc(spec.nx, spec.ny, spec.nz, dt=spec.dt, mean_mode=spec.mean_mode))
     q_ref, v_ref = oracle.step(g, 4, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
                                s.k_rep, s.r_cut, ext=ext, body=s.body)
-    assert position_error(outs[0][0], q_ref, s.pos, g.L, 4) < TOL[1]
+    assert_positions(outs[0][0], q_ref, s.pos, g.L, 4, TOL[1])
     assert rel_l2(outs[0][1][0], v_ref) < TOL[1]
 
 
@@ -483,7 +513,7 @@ def test_single_particle_full_run_fp64_deterministic():
     g = _oracle_grid(d)
     q_ref, _ = oracle.step(g, 200, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
                            ext=s.ext)
-    assert position_error(q, q_ref, s.pos, g.L, 200) < TOL[1]
+    assert_positions(q, q_ref, s.pos, g.L, 200, TOL[1])
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table_rad.json")))
     RH = dict((r[0], r[1]) for r in gold["rows"])[1.0]
     U_inf = 1e-3 * (1.0 - 2.84 * RH / 32.0) / (6 * np.pi * spec.eta * RH)

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import TOL, position_error, rel_l2, to_np
+from helpers import TOL, assert_positions, rel_l2, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -64,7 +64,7 @@ def test_stokes_step_single_particle(prec):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.stokes_step(g, nsteps, s.pos, s.pid, s.bonds, s.rest, s.k_spring,
                                       ext=s.ext)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[prec])
     assert rel_l2(v[0], v_ref) < TOL[prec]
     # the blob velocities read back are J(q^{n+1}) of the last flow
     assert rel_l2(u, oracle.interp(g, q_ref, v_ref)) < TOL[prec]
@@ -84,7 +84,7 @@ def test_stokes_step_dense_with_repulsion_and_body_force(prec):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.stokes_step(g, nsteps, s.pos, s.pid, s.bonds, s.rest, s.k_spring,
                                       s.k_rep, s.r_cut, ext=ext, body=s.body)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[prec])
     assert rel_l2(v[0], v_ref) < TOL[prec]
     assert np.max(np.abs(oracle.pair_forces(g, q_ref, s.pid, s.k_rep, s.r_cut))) > 0
 
@@ -101,7 +101,7 @@ def test_stokes_batched_boxes_match_independent_runs(prec):
     for b, s in enumerate(boxes):
         q_ref, v_ref = oracle.stokes_step(g, nsteps, s.pos, s.pid, s.bonds, s.rest, s.k_spring,
                                           ext=s.ext)
-        assert position_error(q[off:off + s.n_blobs], q_ref, s.pos, g.L, nsteps) < TOL[prec]
+        assert_positions(q[off:off + s.n_blobs], q_ref, s.pos, g.L, nsteps, TOL[prec])
         assert rel_l2(v[b], v_ref) < TOL[prec]
         off += s.n_blobs
 
@@ -129,7 +129,7 @@ def test_stokes_empty_box_and_single_blob_with_body_force():
         q, v, _, _ = _run(d, [empty, single], 3, ext=ext, body=body)
         assert rel_l2(v[0], v0_ref) < TOL[prec]
         assert rel_l2(v[1], v1_ref) < TOL[prec]
-        assert position_error(q, q1_ref, single.pos, g.L, 3) < TOL[prec]
+        assert_positions(q, q1_ref, single.pos, g.L, 3, TOL[prec])
 
 
 def test_stokes_invalid_configurations():
@@ -166,6 +166,6 @@ def test_torque_driven_rotation_parity(prec):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.stokes_step(g, 12, s.pos, s.pid, s.bonds, s.rest, 200.0, ext=F)
     U_ref, W_ref = oracle.particle_velocities(g, q_ref, oracle.interp(g, q_ref, v_ref), s.pid, 1)
-    assert position_error(q, q_ref, s.pos, g.L, 12) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, 12, TOL[prec])
     assert rel_l2(W, W_ref) < TOL[prec]
     assert np.max(np.abs(U - U_ref)) < TOL[prec] * np.max(np.abs(W_ref)) * a

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import TOL, position_error, rel_l2, to_np
+from helpers import TOL, assert_positions, rel_l2, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -70,7 +70,7 @@ def test_thermal_step_parity_single_particle(prec):
     g = _oracle_grid(d)
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest,
                                s.k_spring, ext=s.ext, kT=d.kT, seed=d.seed)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[prec])
     assert rel_l2(v[0], v_ref) < TOL[prec]
 
 
@@ -88,7 +88,7 @@ def test_thermal_step_parity_dense_with_repulsion_and_body_force(prec):
     q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest,
                                s.k_spring, s.k_rep, s.r_cut, ext=ext, body=s.body, kT=d.kT,
                                seed=d.seed)
-    assert position_error(q, q_ref, s.pos, g.L, nsteps) < TOL[prec]
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[prec])
     assert rel_l2(v[0], v_ref) < TOL[prec]
 
 
@@ -117,7 +117,7 @@ def test_step_index_resumes_the_noise(prec):
         qr, vr = to_np(sim.blob_positions()), to_np(sim.velocity_field()).astype(np.float64)
         assert sim.step_index == 6
     assert rel_l2(vr, v6) < tol
-    assert position_error(qr, q6, s.pos, np.array([16.0] * 3), 6) < tol
+    assert_positions(qr, q6, s.pos, np.array([16.0] * 3), 6, tol)
 
 
 def test_fluid_equipartition_fp32():
