@@ -33,13 +33,42 @@ METRIC = "fluid cell-steps/s at 128^3 (FP32 grid); blob-steps/s and FP64 beside 
 WORKLOAD = "dense suspension 128^3, a=2.2h, phi=0.40, 18808 particles x 13 blobs"
 DENSE128_BLOBS, DENSE128_PARTICLES = 244504, 18808      # the recipe's counts at seed 3
 
+# What bounds each FP64-grid kernel below the HBM roofline (ncu, dense 128^3 workload).
+FP64_LIMITERS = {
+    "spread": "FP64 shared-memory atomic adds (one per node contribution)",
+    "forces": "FP64 arithmetic of the bond and repulsion forces",
+    "fluid_x_fwd": "FP32-pipe issue of the double-float FFT arithmetic",
+    "fluid_z_solve": "FP32-pipe issue of the double-float FFT arithmetic",
+    "fluid_x_inv": "FP32-pipe issue of the double-float FFT arithmetic",
+    "interp_correct": "gather latency (L1 sectors per request)",
+    "interp_predict": "gather latency (L1 sectors per request)",
+}
+
 # Algorithmic bytes moved by each stage per step, per unit:
 #   grid real = 4 B (FP32) / 8 B (FP64); half-spectrum complex = 2 reals; blob FP64 vec = 24 B.
 def stage_model(n, nb, rsz, ncell, thermal=False):
+    """Algorithmic bytes per stage.  FP32 grids (rsz = 4) fuse the next step's predictor into
+    the corrector pass, whose grid v^n + v^{n+1} the inverse plane pass writes; FP64 grids
+    (rsz = 8) run the predictor as its own pass and the corrector reads v^n and v^{n+1}."""
     N = n ** 3
     grid = 3 * N * rsz                                  # one 3-component grid
     spec = 3 * n * n * (n // 2 + 1) * 2 * rsz           # one 3-component half spectrum
     vec = 24 * nb
+    if rsz == 8:
+        return {
+            "interp_predict": ("hbm", grid + 2 * vec),   # read v^n, q; write q_half
+            "bin": ("hbm", vec + 3 * 4 * nb + 4 * 4 * ncell),
+            "forces": ("hbm", nb * (24 + 4 + 4 + 2 * 42 / 13 * 12 + 24 + 48)),
+            "force_sum": ("hbm", 0),
+            "spread": ("hbm", 48 * nb + grid),
+            "fluid_stress": ("hbm", 8 * grid if thermal else 0),
+            "fluid_x_fwd": ("hbm", 2 * grid + spec),
+            "fluid_y_fwd": ("hbm", 0),
+            "fluid_z_solve": ("hbm", 2 * spec),
+            "fluid_y_inv": ("hbm", 0),
+            "fluid_x_inv": ("hbm", spec + grid),        # read spectrum; write v^{n+1}
+            "interp_correct": ("hbm", 2 * grid + 3 * vec),   # read v^n, v^{n+1}, q_half, q; write q
+        }
     return {
         # the predictor of step n+1 runs inside step n's corrector pass (same gathered nodes)
         "interp_predict": ("hbm", 0),
@@ -127,7 +156,10 @@ def parse():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--stage-json", default=None, help="also write per-stage times here")
     ap.add_argument("--ref-seconds", type=float, default=None,
-                    help="CPU seconds of the reference arm's oracle sample (default 3 s a step, at most 120 s)")
+                    help="at most this many seconds of timed oracle steps in the reference arm "
+                         "(default 120)")
+    ap.add_argument("--skip-accuracy", action="store_true",
+                    help="skip the error of each reported workload against the oracle")
     return ap.parse_args()
 
 
@@ -200,56 +232,196 @@ def peaks():
 
 
 # ----------------------------------------------------------------------------------------------
-def oracle_sample(max_seconds=20.0, min_steps=2):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload: the same
-    suspension recipe (a, phi, springs, repulsion, body force) in a 64^3 box, stepped until
-    about max_seconds of CPU time.  Returns (cell-steps/s, blob-steps/s, steps, seconds, blobs)."""
+def oracle_sample(threads, warmup=1, steps=3, max_seconds=None, spec_s=None):
+    """The FP64 CPU oracle, as it stands, on the benchmark's own inputs (the dense 128^3
+    suspension): `warmup` untimed steps, then up to `steps` timed steps (fewer if max_seconds
+    runs out, at least one), on `threads` host threads.  Returns (cell-steps/s, blob-steps/s,
+    steps, seconds, blobs, threads used)."""
     import oracle
     from paper_1407_5600_gb300 import workloads as wl
 
-    spec, s = wl.dense_suspension(n=64, seed=3)
+    spec, s = spec_s if spec_s is not None else wl.dense_suspension(n=GRID_N, seed=3)
     g = oracle.Grid(spec.nx, spec.ny, spec.nz, h=spec.h, rho=spec.rho, eta=spec.eta,
                     dt=spec.dt, mean_mode=spec.mean_mode)
-    q, v = s.pos, g.zeros()
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        q, v = oracle.step(g, 1, q, v, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut,
-                           body=s.body)
-        steps += 1
+    before = oracle.set_threads(0)
+    used = oracle.set_threads(threads)
+    try:
+        q, v = s.pos, g.zeros()
+        for _ in range(warmup):
+            q, v = oracle.step(g, 1, q, v, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep,
+                               s.r_cut, body=s.body)
+        done, t0 = 0, time.perf_counter()
+        while done < steps:
+            q, v = oracle.step(g, 1, q, v, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep,
+                               s.r_cut, body=s.body)
+            done += 1
+            if max_seconds is not None and time.perf_counter() - t0 >= max_seconds:
+                break
         el = time.perf_counter() - t0
-        if steps >= min_steps and el >= max_seconds * 0.5 or el >= max_seconds:
-            break
+    finally:
+        oracle.set_threads(before)
     cells = spec.nx * spec.ny * spec.nz
-    return cells * steps / el, s.n_blobs * steps / el, steps, el, s.n_blobs
+    return cells * done / el, s.n_blobs * done / el, done, el, s.n_blobs, used
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_record():
+    """The oracle on the benchmark's 128^3 inputs, 1 warm-up + 3 timed steps, on all host cores
+    and on one."""
+    from paper_1407_5600_gb300 import workloads as wl
+    spec_s = wl.dense_suspension(n=GRID_N, seed=3)
+    nproc = host_cores()
+    cps, bps, st, el, nbl, used = oracle_sample(nproc, spec_s=spec_s)
+    cps1, bps1, st1, el1, _, _ = oracle_sample(1, spec_s=spec_s)
+    return {"value": cps, "unit": "cell-steps/s", "cores": used, "nproc": nproc,
+            "kind": "oracle", "blob_steps_per_s": bps,
+            "sample": f"the benchmark's own 128^3 inputs ({nbl} blobs): 1 warm-up + {st} timed "
+                      f"FP64 oracle steps on {used} threads (OpenMP over independent loops), "
+                      f"{el:.1f} s",
+            "single_thread": {"value": cps1, "unit": "cell-steps/s", "cores": 1,
+                              "blob_steps_per_s": bps1,
+                              "sample": f"1 warm-up + {st1} timed steps on one thread, "
+                                        f"{el1:.1f} s"}}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.warmup:
-        oracle_sample(max_seconds=1.0, min_steps=1)
-    # a bounded sample whatever --steps asks for: the whole run ends within a few minutes
-    budget = args.ref_seconds if args.ref_seconds else min(max(10.0, 3.0 * args.steps), 120.0)
-    cps, bps, steps, el, nblobs = oracle_sample(max_seconds=budget,
-                                                min_steps=min(3, max(1, args.steps // 10)))
-    sample = (f"{steps} oracle steps of the same suspension recipe in a 64^3 box "
-              f"({nblobs} blobs), {el:.1f} s")
+    nproc = host_cores()
+    # the benchmark's own 128^3 inputs; W warm-up and up to K timed steps, bounded in time so
+    # that the whole run ends within a few minutes whatever --steps asks for
+    budget = args.ref_seconds if args.ref_seconds else 120.0
+    cps, bps, steps, el, nblobs, used = oracle_sample(
+        nproc, warmup=min(args.warmup, 3), steps=max(1, args.steps), max_seconds=budget)
+    sample = (f"{steps} FP64 oracle steps of the benchmark's own 128^3 inputs ({nblobs} blobs) "
+              f"on {used} host threads after {min(args.warmup, 3)} warm-up steps, {el:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": cps, "unit": "cell-steps/s",
             "n_gpus": args.gpus, "hardware": "host cores only (the oracle uses no GPU)",
-            "steps": steps, "warmup": args.warmup,
+            "steps": steps, "warmup": min(args.warmup, 3),
             "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(base_config(), sample="64^3 box of the same recipe"),
+            "config": base_config(),
             "blob_steps_per_s": bps,
-            "cpu_baseline": {"value": cps, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": cps, "unit": "cell-steps/s", "cores": used,
+                             "nproc": nproc, "kind": "oracle", "sample": sample},
             "e2e": {"value": cps, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ----------------------------------------------------------------------------------------------
+def _rel(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b)) / (nb if nb > 0 else 1.0)
+
+
+def _pos_rel(q, q_ref, q0, L):
+    """Relative L2 error of the displacement (minimum image)."""
+    d = q - q_ref
+    d -= L * np.round(d / L)
+    r = q_ref - q0
+    r -= L * np.round(r / L)
+    return float(np.linalg.norm(d) / max(np.linalg.norm(r), 1e-300))
+
+
+def accuracy_records(mb, wl, stream, dev, spec, s):
+    """Error of every reported workload against the FP64 oracle on the same inputs: relative L2
+    of the blob displacements, the fluid velocity and the blob velocities after a few steps from
+    rest.  The dense 128^3 runs (both grid precisions, both integrators) use the benchmark's own
+    inputs; the fluctuating suspension a 64^3 box of its recipe (same a, phi, kT, Philox seed);
+    the gap sweep three of its 32 boxes, stepped inside the batched context."""
+    import oracle
+    oracle.set_threads(host_cores())
+    n = spec.nx
+    L = np.array([n * spec.h] * 3)
+    out = {}
+
+    def gpu_run(desc, sets, nsteps, ext=None, body=None):
+        sim = mb.Multiblob(desc, stream=stream, device=dev)
+        try:
+            for b, sb in enumerate(sets):
+                sim.set_particles(b, sb.pos, sb.pid, sb.bonds, sb.rest, sb.k_spring, sb.k_rep,
+                                  sb.r_cut)
+            e = None if ext is None else sim._dev(ext, sim.torch.float64)
+            for _ in range(nsteps):
+                mb.step(sim.ctx, 1, e, body)
+            q = sim.blob_positions().cpu().numpy()
+            v = sim.velocity_field().cpu().numpy().astype(np.float64)
+            u = sim.blob_velocities().cpu().numpy()
+        finally:
+            sim.close()
+        return q, v, u
+
+    def ograd(sp, integrator=0):
+        return oracle.Grid(sp.nx, sp.ny, sp.nz, h=sp.h, rho=sp.rho, eta=sp.eta, dt=sp.dt,
+                           mean_mode=1 if integrator else sp.mean_mode)
+
+    # dense 128^3, ICM, both grid precisions: 3 steps (direct, then graph replays)
+    g = ograd(spec)
+    q_ref, v_ref = oracle.step(g, 3, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
+                               s.k_rep, s.r_cut, body=s.body)
+    u_ref = oracle.interp(g, q_ref, v_ref)
+    for prec in (0, 1):
+        d = mb.GridDesc(n, n, n, precision=prec, dt=spec.dt, rho=spec.rho, eta=spec.eta,
+                        h=spec.h, mean_mode=spec.mean_mode)
+        q, v, u = gpu_run(d, [s], 3, body=s.body)
+        out["dense128_fp32" if prec == 0 else "dense128_fp64"] = {
+            "steps": 3, "q_displacement_rel_l2": _pos_rel(q, q_ref, s.pos, L),
+            "v_rel_l2": _rel(v[0], v_ref), "u_rel_l2": _rel(u, u_ref),
+            "sample": "the benchmark's own 128^3 inputs, 3 steps from rest"}
+    # Stokes limit on the same inputs: 2 steps
+    gs = ograd(spec, 1)
+    qs_ref, vs_ref = oracle.stokes_step(gs, 2, s.pos, s.pid, s.bonds, s.rest, s.k_spring,
+                                        s.k_rep, s.r_cut, body=s.body)
+    d = mb.GridDesc(n, n, n, precision=0, dt=spec.dt, eta=spec.eta, h=spec.h, mean_mode=1,
+                    integrator=1)
+    q, v, _ = gpu_run(d, [s], 2, body=s.body)
+    out["stokes_limit_dense128"] = {
+        "steps": 2, "q_displacement_rel_l2": _pos_rel(q, qs_ref, s.pos, L),
+        "v_rel_l2": _rel(v[0], vs_ref), "sample": "the benchmark's own 128^3 inputs"}
+    del q_ref, v_ref, u_ref, qs_ref, vs_ref
+    # fluctuating suspension: a 64^3 box of the 256^3 recipe, 2 steps of thermal stress
+    spec5, s5 = wl.fluctuating_suspension(n=64, a=3.2, phi=0.30, kT=1e-3, seed=5)
+    g5 = ograd(spec5)
+    q5_ref, v5_ref = oracle.step(g5, 2, s5.pos, g5.zeros(), s5.pid, s5.bonds, s5.rest,
+                                 s5.k_spring, s5.k_rep, s5.r_cut, kT=spec5.kT, seed=17)
+    d = mb.GridDesc(64, 64, 64, precision=0, dt=spec5.dt, eta=spec5.eta, h=spec5.h,
+                    mean_mode=spec5.mean_mode, kT=spec5.kT, seed=17)
+    q, v, u = gpu_run(d, [s5], 2)
+    out["fluctuating_256"] = {
+        "steps": 2, "q_displacement_rel_l2": _pos_rel(q, q5_ref, s5.pos, np.array([64.0] * 3)),
+        "v_rel_l2": _rel(v[0], v5_ref), "u_rel_l2": _rel(u, oracle.interp(g5, q5_ref, v5_ref)),
+        "sample": f"64^3 box of the same recipe ({s5.n_blobs} blobs), kT = 1e-3, Philox seed 17"}
+    # gap sweep: the batched context of 32 boxes, boxes 0, 15 and 31 against the oracle
+    sweep = [wl.gap_sweep_box(b, n_boxes=32, n=64, a=1.6) for b in range(32)]
+    spec2 = sweep[0][0]
+    d = mb.GridDesc(64, 64, 64, batch=32, precision=0, dt=spec2.dt, eta=spec2.eta, h=spec2.h,
+                    mean_mode=spec2.mean_mode)
+    ext2 = np.concatenate([sb.ext for _, sb in sweep])
+    q, v, u = gpu_run(d, [sb for _, sb in sweep], 2, ext=ext2)
+    g2 = ograd(spec2)
+    errs = []
+    for b in (0, 15, 31):
+        sb = sweep[b][1]
+        qb_ref, vb_ref = oracle.step(g2, 2, sb.pos, g2.zeros(), sb.pid, sb.bonds, sb.rest,
+                                     sb.k_spring, ext=sb.ext)
+        sl = slice(26 * b, 26 * b + 26)
+        errs.append((_pos_rel(q[sl], qb_ref, sb.pos, np.array([64.0] * 3)),
+                     _rel(v[b], vb_ref), _rel(u[sl], oracle.interp(g2, qb_ref, vb_ref))))
+    e = np.max(np.array(errs), axis=0)
+    out["gap_sweep_32x64"] = {"steps": 2, "q_displacement_rel_l2": float(e[0]),
+                              "v_rel_l2": float(e[1]), "u_rel_l2": float(e[2]),
+                              "sample": "boxes 0, 15 and 31 of the batched run (largest error)"}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -384,10 +556,27 @@ def run_ours(args):
         ms64, _, stages64 = timed_steps(sim64, K64, True)
         ms64 = max_over_ranks(ms64)
         sim64.close()
+        model64 = stage_model(n, nb, 8, ncell)
+        st64 = {}
+        for k, v in stages64.items():
+            t = v[0] / max(v[1], 1)
+            byts = model64[k][1]
+            st64[k] = {"ms_per_step": t, "algorithmic_MB": byts / 1e6,
+                       "GBps": byts / (t * 1e-3) / 1e9 if t > 0 and byts else None}
+            st64[k]["frac_hbm"] = st64[k]["GBps"] / peak if st64[k]["GBps"] else None
+        dom64 = max((k for k in st64 if model64[k][1] > 0 and k not in ("bin", "forces")),
+                    key=lambda k: st64[k]["ms_per_step"])
         fp64 = {"value": world * cells * K64 / (ms64 * 1e-3), "unit": "cell-steps/s",
                 "blob_steps_per_s": world * nb * K64 / (ms64 * 1e-3),
                 "ms_per_step": ms64 / K64, "steps": K64,
-                "stages_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in stages64.items()}}
+                "step_hbm_frac": sum(m[1] for m in model64.values())
+                / (ms64 / K64 * 1e-3) / 1e9 / peak,
+                "roofline": {"bound": "hbm", "kernel": dom64, "achieved": st64[dom64]["GBps"],
+                             "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                             "frac": st64[dom64]["frac_hbm"], "traffic": None,
+                             "algorithmic_bytes": model64[dom64][1],
+                             "limiter": FP64_LIMITERS.get(dom64)},
+                "stages": st64}
 
     # ---- the other workloads (FP32 grid), for the record: the Stokes limit on the same
     # suspension, the fluctuating 256^3 suspension (kT = 1e-3, five-pass FFT) and the batched
@@ -456,13 +645,17 @@ def run_ours(args):
             "l2": "not flushed: the grids (velocity pair, force, spectrum: ~0.4 GB) exceed L2"}
 
     # ---- CPU baseline (oracle, rank 0, N = 1 only) ---------------------------------------
+    acc = None
+    if rank == 0 and not args.skip_accuracy:
+        acc = accuracy_records(mb, wl, stream, dev, spec, s)
+        if fp64 is not None:
+            fp64["error_vs_oracle"] = acc["dense128_fp64"]
+        for k in (others or {}):
+            if k in acc:
+                others[k]["error_vs_oracle"] = acc[k]
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
-        cps, bps, st, el, nbl = oracle_sample()
-        cpu = {"value": cps, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-               "blob_steps_per_s": bps,
-               "sample": f"{st} FP64 oracle steps (single thread) of the same suspension recipe "
-                         f"in a 64^3 box ({nbl} blobs), {el:.1f} s"}
+        cpu = cpu_baseline_record()
 
     if rank == 0:
         line = {
@@ -475,6 +668,7 @@ def run_ours(args):
             "step_hbm_frac": step_frac,
             "ms_per_step_stage_timed": ms_staged / args.steps,
             "roofline": roofline,
+            "error_vs_oracle": acc["dense128_fp32"] if acc else None,
             "stages": per_stage,
             "fp64": fp64,
             "other_workloads": others,
