@@ -152,3 +152,18 @@ def test_time_stepping_converges_to_the_steady_stokes_flow():
         v = mb.fluid_update(g, v, f)
     ref = mb.stokes_solve(g, f)
     assert np.linalg.norm(v - ref) < 1e-10 * np.linalg.norm(ref)
+
+
+def test_transient_viscosity_estimator_returns_eta_for_the_pure_fluid():
+    """Sec. 10 protocol before steady state: the Crank-Nicolson transient of the driven shear
+    mode, solved for eta, returns the fluid's viscosity after any number of oracle steps (the
+    mode is an eigenvector of L and unchanged by the projection)."""
+    from helpers import eta_from_transient, shear_amplitude
+    n, f0 = 16, 1e-3
+    for eta, rho, nsteps in ((1.0, 1.0, 40), (2.5, 5.0, 7), (0.3, 1.0, 120)):
+        g = mb.Grid(n, n, n, rho=rho, eta=eta, dt=0.05, mean_mode=0)
+        q, v = mb.step(g, nsteps, np.zeros((0, 3)), g.zeros(), np.zeros(0, dtype=np.int32),
+                       np.zeros((0, 2), dtype=np.int32), np.zeros(0), 0.0, body=(f0, 0, 2, 1))
+        lam = 4.0 * np.sin(np.pi / n) ** 2
+        est = eta_from_transient(shear_amplitude(v[0], n), f0, lam, rho, g.dt, nsteps)
+        assert abs(est / eta - 1.0) < 1e-10, (eta, est)
