@@ -11,6 +11,9 @@
 // Line FFTs: the register-resident line transforms of fft_lines.cuh (lines of up to 128
 // points here; the planes of longer sides do not fit in shared memory).
 // Real rows are packed two per complex row and separated after the row transform.
+#include <cstdlib>
+#include <string>
+
 #include "mb_internal.cuh"
 #include "fft_lines.cuh"
 
@@ -32,18 +35,122 @@ __host__ __device__ inline int plane_ld(int nx)
     return nx + 2 + ((nx + 1) >> pad_shift(nx));
 }
 
+// Plane layouts.  Element (packed row p, slot j) of the plane buffer is P[L.at(p, j)]; rows()
+// and cols() transform the ny/2 packed rows (slot j = x) and the nx/2 columns (element y of
+// column k is slot 2k + (y & 1) of packed row y >> 1).
+//
+// PadPlane: any power-of-two plane; one pad slot every 2^pad_shift(nx) slots.
+struct PadPlane {
+    int nx, ny, S, sx;
+    __device__ PadPlane(int nx_, int ny_) : nx(nx_), ny(ny_), S(plane_ld(nx_)), sx(pad_shift(nx_)) {}
+    __device__ __forceinline__ int at(int p, int j) const { return p * S + j + (j >> sx); }
+    template <bool INV, typename T> __device__ __forceinline__ void rows(T* P, const T* tw) const
+    {
+        const int S_ = S, sx_ = sx;
+        lines_fft_n<INV>(nx, P, ny / 2, [S_, sx_](int l, int j) { return l * S_ + j + (j >> sx_); }, tw);
+    }
+    template <bool INV, typename T> __device__ __forceinline__ void cols(T* P, const T* tw) const
+    {
+        const int S_ = S, sx_ = sx;
+        lines_fft_n<INV>(ny, P, nx / 2, [S_, sx_](int k, int y) {
+            const int j = 2 * k + (y & 1);
+            return (y >> 1) * S_ + j + (j >> sx_);
+        }, tw);
+    }
+};
+
+// Skew128: 128 x 128 planes of float2.  Rows of 148 slots, one pad slot every 16 and a skew of
+// SK[(p >> 2) & 7] slots per group of four packed rows, SK = {0, 6, 7, 9, 2, 7, 8, 1}.  A bank
+// model of every shared-memory access of the two plane passes (loads, the two stages of the
+// row and column line FFTs, the separation and the spectrum copies) puts this layout within 5%
+// of the fewest possible wavefronts, against 1.7x for the padded layout; 64 rows x 148 slots
+// x 8 B = 74 KiB keeps three planes per SM.  With 128-point lines split 16 x 8 (thread t of a
+// line holds elements 8 n1 + t, then 8 (t + 8 m) + n2) every address is a per-thread base plus
+// a compile-time offset, so the line FFTs spend no instructions on indexing.
+struct Skew128 {
+    static constexpr int S = 148;
+    static constexpr unsigned SKW = 0x18729760u;              // SK[i] = (SKW >> 4 i) & 15
+    __host__ __device__ static constexpr int sk(int i) { return (int)((SKW >> (4 * (i & 7))) & 15u); }
+    __device__ Skew128(int, int) {}
+    __device__ __forceinline__ int at(int p, int j) const { return p * S + sk(p >> 2) + j + (j >> 4); }
+    // One round: 8 warps x 4 lines; lane = 4 t + (line - l0).  b1 addresses element 8 n1 + t
+    // at offset c1(n1); b2 element 8 (t + 8 m) + n2 at c2(m, n2); b1 element (t + 8 m) + 16 k2
+    // at c3(m, k2).
+    template <bool INV, bool COL>
+    __device__ __forceinline__ static void line_round(float2* P, int l, int t, const float2* tw)
+    {
+        int b1, b2;
+        if (COL) {
+            b1 = 148 * (t >> 1) + 2 * l + (t & 1) + (l >> 3);
+            b2 = 592 * t + 2 * l + (l >> 3) + sk(t);
+        } else {
+            const int base = l * S + sk(l >> 2);
+            b1 = base + t;
+            b2 = base + 8 * t + (t >> 1);
+        }
+        auto c1 = [](int n1) { return COL ? 592 * n1 + sk(n1) : 8 * n1 + (n1 >> 1); };
+        auto c2 = [](int m, int n2) { return COL ? 4736 * m + 148 * (n2 >> 1) + (n2 & 1) : 68 * m + n2; };
+        auto c3 = [](int m, int k2) { return COL ? 1184 * k2 + 592 * m + sk(2 * k2 + m) : 8 * m + 17 * k2; };
+        float2 a[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) a[n1] = P[b1 + c1(n1)];
+        reg_dft<16, INV>(a);
+#pragma unroll
+        for (int k1 = 1; k1 < 16; ++k1) {
+            float2 w = tw[(t * k1) & 127];
+            if (INV) w.y = -w.y;
+            a[k1] = cm(a[k1], w);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) P[b1 + c1(k1)] = a[k1];
+        __syncwarp();
+        float2 b[2][8];
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int n2 = 0; n2 < 8; ++n2) b[m][n2] = P[b2 + c2(m, n2)];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) reg_dft<8, INV>(b[m]);
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) P[b1 + c3(m, k2)] = b[m][k2];
+        __syncwarp();
+    }
+    template <bool INV, bool COL> __device__ __forceinline__ static void lines(float2* P, const float2* tw)
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int sub = lane & 3, t = lane >> 2;
+        for (int l0 = warp * 4; l0 < 64; l0 += nw * 4) line_round<INV, COL>(P, l0 + sub, t, tw);
+    }
+    template <bool INV, typename T> __device__ __forceinline__ void rows(T* P, const T* tw) const
+    {
+        lines<INV, false>(P, tw);
+    }
+    template <bool INV, typename T> __device__ __forceinline__ void cols(T* P, const T* tw) const
+    {
+        lines<INV, true>(P, tw);
+    }
+};
+
+template <typename L> struct PlaneSlots;
+template <> struct PlaneSlots<PadPlane> { static size_t count(int nx, int ny) { return (size_t)(ny / 2) * plane_ld(nx); } };
+template <> struct PlaneSlots<Skew128> { static size_t count(int, int) { return 64 * (size_t)Skew128::S; } };
+
 // ------------------------------------------------------------------------------------------
 // Pass A.  Plane buffer P[p][pad(j)], p < ny/2: first rows 2p, 2p+1 packed as re + i im; after
 // the row FFT and the in-place separation, logical slot 2k + e of row p holds X_{2p+e}[k],
 // k <= nx/2.  pad(j) = j + (j >> pad_shift(nx)).
-template <typename R, typename K>
+template <typename R, typename K, typename L>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 512, sizeof(R) == 4 ? 3 : 1)
 k_plane_fwd(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<K>::T;     // K: arithmetic type (FP32, or double-float for FP64)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
-    const int S = plane_ld(nx), sx = pad_shift(nx);
+    const L lay(nx, ny);
     T* P = reinterpret_cast<T*>(smem_raw);
     const T* twx = reinterpret_cast<const T*>(a.twk[0]);      // twiddles through L1
     const T* twy = reinterpret_cast<const T*>(a.twk[1]);
@@ -83,11 +190,7 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
                 r1[i] += K(a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)]);
             }
         }
-        T* row = P + p * S;
-        for (int i = 0; i < 4; ++i) {
-            const int j = x0 + i;
-            row[j + (j >> sx)] = T{r0[i], r1[i]};
-        }
+        for (int i = 0; i < 4; ++i) P[lay.at(p, x0 + i)] = T{r0[i], r1[i]};
     }
     for (int u = threadIdx.x; u < qx * (ny / 2) && !a.no_v; u += blockDim.x) {
         const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
@@ -142,27 +245,22 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
                 r1[i] += K(a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)]);
             }
         }
-        T* row = P + p * S;
-        for (int i = 0; i < 4; ++i) {
-            const int j = x0 + i;
-            row[j + (j >> sx)] = T{r0[i], r1[i]};
-        }
+        for (int i = 0; i < 4; ++i) P[lay.at(p, x0 + i)] = T{r0[i], r1[i]};
     }
     __syncthreads();
-    lines_fft_n<false>(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx);
+    lay.template rows<false>(P, twx);
     __syncthreads();
     // separate the two real rows of each packed row (one warp per packed row, in place)
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int p = warp; p < ny / 2; p += nw) {
-            T* rowp = P + p * S;
             T ev[3], od[3];        // nx/2 + 1 <= 65 values: at most 3 per lane
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 const int k = lane + 32 * r;
                 if (k < nxh) {
                     const int kr = (nx - k) & (nx - 1);
-                    const T Z = rowp[k + (k >> sx)], Zr = rowp[kr + (kr >> sx)];
+                    const T Z = P[lay.at(p, k)], Zr = P[lay.at(p, kr)];
                     ev[r] = T{(Z.x + Zr.x) * kconst<K>(0.5f), (Z.y - Zr.y) * kconst<K>(0.5f)};
                     od[r] = T{(Z.y + Zr.y) * kconst<K>(0.5f), (Zr.x - Z.x) * kconst<K>(0.5f)};
                 }
@@ -172,25 +270,21 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
             for (int r = 0; r < 3; ++r) {
                 const int k = lane + 32 * r;
                 if (k < nxh) {
-                    const int j0 = 2 * k, j1 = 2 * k + 1;
-                    rowp[j0 + (j0 >> sx)] = ev[r];
-                    rowp[j1 + (j1 >> sx)] = od[r];
+                    P[lay.at(p, 2 * k)] = ev[r];
+                    P[lay.at(p, 2 * k + 1)] = od[r];
                 }
             }
             __syncwarp();
         }
     }
     __syncthreads();
-    auto col = [S, sx](int k, int y) {
-        const int j = 2 * k + (y & 1);
-        return (y >> 1) * S + j + (j >> sx);
-    };
+    auto col = [lay](int k, int y) { return lay.at(y >> 1, 2 * k + (y & 1)); };
     // columns k = 0 and k = nx/2 are real: transform them as one complex column
     // Z_y = X_y[0] + i X_y[nx/2], so that nx/2 column lines remain
     for (int y = threadIdx.x; y < ny; y += blockDim.x)
         P[col(0, y)] = T{P[col(0, y)].x, P[col(nx / 2, y)].x};
     __syncthreads();
-    lines_fft_n<false>(ny, P, nxh - 1, col, twy);
+    lay.template cols<false>(P, twy);
     __syncthreads();
     // A = FFT X[0] = (Z_k + conj Z_-k) / 2,  B = FFT X[nx/2] = (Z_k - conj Z_-k) / (2i)
     if (threadIdx.x < 32) {
@@ -312,23 +406,20 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
 // ------------------------------------------------------------------------------------------
 // Pass C.  Inverse of pass A: columns, then the packed rows Z = X_{2p} + i X_{2p+1} (with the
 // Hermitian extension X[nx - k] = conj X[k]), then the real rows, scaled by 1/N.
-template <typename R, typename K>
+template <typename R, typename K, typename L>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 512, sizeof(R) == 4 ? 3 : 1)
 k_plane_inv(FluidArgs<R> a, GridGeo g)
 {
     using T = typename C2<K>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
-    const int S = plane_ld(nx), sx = pad_shift(nx);
+    const L lay(nx, ny);
     T* P = reinterpret_cast<T*>(smem_raw);
     const T* twx = reinterpret_cast<const T*>(a.twk[0]);      // twiddles through L1
     const T* twy = reinterpret_cast<const T*>(a.twk[1]);
     const int z = blockIdx.x, bc = blockIdx.y;
     const T* in = reinterpret_cast<const T*>(a.spec) + ((size_t)bc * nz + z) * (size_t)nxh * ny;
-    auto col = [S, sx](int k, int y) {
-        const int j = 2 * k + (y & 1);
-        return (y >> 1) * S + j + (j >> sx);
-    };
+    auto col = [lay](int k, int y) { return lay.at(y >> 1, 2 * k + (y & 1)); };
     const int ly = 31 - __clz(ny);
     for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) async_copy(&P[col(i >> ly, i & (ny - 1))], &in[i]);
     async_wait_all();
@@ -358,7 +449,7 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
         }
     }
     __syncthreads();
-    lines_fft_n<true>(ny, P, nxh - 1, col, twy);
+    lay.template cols<true>(P, twy);
     __syncthreads();
     for (int y = threadIdx.x; y < ny; y += blockDim.x) {
         const T zc = P[col(0, y)];
@@ -369,15 +460,13 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int p = warp; p < ny / 2; p += nw) {
-            T* rowp = P + p * S;
             T zv[4];              // nx <= 128 values: at most 4 per lane
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int k = lane + 32 * r;
                 if (k < nx) {
                     const int kk = k <= nx / 2 ? k : nx - k;
-                    const int j0 = 2 * kk, j1 = 2 * kk + 1;
-                    T e = rowp[j0 + (j0 >> sx)], o = rowp[j1 + (j1 >> sx)];
+                    T e = P[lay.at(p, 2 * kk)], o = P[lay.at(p, 2 * kk + 1)];
                     if (k == 0 || k == nx / 2) { e.y = kconst<K>(0.0f); o.y = kconst<K>(0.0f); }
                     if (k > nx / 2) { e.y = -e.y; o.y = -o.y; }
                     zv[r] = T{e.x - o.y, e.y + o.x};
@@ -387,13 +476,13 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int k = lane + 32 * r;
-                if (k < nx) rowp[k + (k >> sx)] = zv[r];
+                if (k < nx) P[lay.at(p, k)] = zv[r];
             }
             __syncwarp();
         }
     }
     __syncthreads();
-    lines_fft_n<true>(nx, P, ny / 2, [S, sx](int l, int j) { return l * S + j + (j >> sx); }, twx);
+    lay.template rows<true>(P, twx);
     __syncthreads();
     const K scale = kparam<K>(a.inv_n, a.inv_n32);
     R* out = a.v_out + (size_t)bc * g.N + (size_t)z * ny * nx;
@@ -403,7 +492,7 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
         K r0[4], r1[4];
         for (int i = 0; i < 4; ++i) {
             const int j = x0 + i;
-            const T zv = P[p * S + j + (j >> sx)];
+            const T zv = P[lay.at(p, j)];
             r0[i] = zv.x * scale;
             r1[i] = zv.y * scale;
         }
@@ -438,24 +527,46 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
     static std::atomic<unsigned> attr{0};     // per instantiation
     if (first_on_device(attr)) {
         const int lim = 200 * 1024;
-        cudaFuncSetAttribute(k_plane_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_plane_fwd<R, K, PadPlane>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_zsolve<R, K, CZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_zsolve<R, K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_plane_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_plane_inv<R, K, PadPlane>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if constexpr (sizeof(R) == 4) {
+            cudaFuncSetAttribute(k_plane_fwd<R, K, Skew128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+            cudaFuncSetAttribute(k_plane_inv<R, K, Skew128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        }
     }
-    const size_t smem_plane = (size_t)(ny / 2) * plane_ld(nx) * sizeof(T);
+    // FP32 planes of 128 x 128 take the conflict-free layout (MB_PLANE_LAYOUT=pad keeps the
+    // padded one, for comparison)
+    static const bool skew_off = [] {
+        const char* e = std::getenv("MB_PLANE_LAYOUT");
+        return e && std::string(e) == "pad";
+    }();
+    const bool skew = sizeof(R) == 4 && nx == 128 && ny == 128 && !skew_off;
+    const size_t smem_plane = (skew ? PlaneSlots<Skew128>::count(nx, ny)
+                                    : PlaneSlots<PadPlane>::count(nx, ny)) * sizeof(T);
     const int C = ny >= CZ ? CZ : 4;
     const size_t smem_z = ((size_t)3 * padded_len(nz) * (C + 4) + nz) * sizeof(T);
     auto mark = [&](int i) { if (marks) cudaEventRecord(marks[i], st); };
     mark(0);
-    k_plane_fwd<R, K><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+    if constexpr (sizeof(R) == 4) {
+        if (skew) k_plane_fwd<R, K, Skew128><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+        else k_plane_fwd<R, K, PadPlane><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+    } else {
+        k_plane_fwd<R, K, PadPlane><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+    }
     mark(1);
     mark(2);
     if (C == CZ) k_zsolve<R, K, CZ><<<dim3(ny / C, nxh, B), 3 * CZ * 8, smem_z, st>>>(a, g);
     else k_zsolve<R, K, 4><<<dim3(ny / 4, nxh, B), 3 * 4 * 8, smem_z, st>>>(a, g);
     mark(3);
     mark(4);
-    k_plane_inv<R, K><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+    if constexpr (sizeof(R) == 4) {
+        if (skew) k_plane_inv<R, K, Skew128><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+        else k_plane_inv<R, K, PadPlane><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+    } else {
+        k_plane_inv<R, K, PadPlane><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+    }
     mark(5);
     return cudaGetLastError();
 }
