@@ -314,6 +314,50 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) out[i] = P[col(i >> ly, i & (ny - 1))];
 }
 
+// 128-point z-lines of the pass-B buffer (FP32, C = 8 columns): element z of line l (component
+// l / 8, column l % 8) is at ((l / 8) 144 + z + (z >> 3)) 12 + l % 8.  Same 16 x 8 split as
+// lines_fft; thread t of a line addresses a per-thread base plus compile-time offsets (z =
+// 8 n1 + t pads to 9 n1 + t, 8 (t + 8 m) + n2 to 9 t + 72 m + n2, t + 8 m + 16 k2 to
+// t + 9 m + 18 k2), so the transforms spend no instructions on indexing.
+template <bool INV>
+__device__ __forceinline__ void zlines128(float2* Bf, const float2* tw)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int sub = lane & 3, t = lane >> 2;
+    for (int l0 = warp * 4; l0 < 24; l0 += nw * 4) {
+        const int l = l0 + sub, c = l >> 3, k = l & 7;
+        float2* b1 = Bf + (c * 144 + t) * 12 + k;
+        float2* b2 = Bf + (c * 144 + 9 * t) * 12 + k;
+        float2 a[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) a[n1] = b1[108 * n1];
+        reg_dft<16, INV>(a);
+#pragma unroll
+        for (int k1 = 1; k1 < 16; ++k1) {
+            float2 w = tw[(t * k1) & 127];
+            if (INV) w.y = -w.y;
+            a[k1] = cm(a[k1], w);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) b1[108 * k1] = a[k1];
+        __syncwarp();
+        float2 b[2][8];
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int n2 = 0; n2 < 8; ++n2) b[m][n2] = b2[(72 * m + n2) * 12];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) reg_dft<8, INV>(b[m]);
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) b1[(9 * m + 18 * k2) * 12] = b[m][k2];
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // Pass B.  CTA = (ky block of width C, kx, box); shared buffer [3][pad(nz)][C + 4].  C is a
 // compile-time width (16 FP32, 8 FP64) and the block has 3 C N2 threads, one round of lines.
@@ -343,7 +387,13 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     async_wait_all();
     __syncthreads();
     auto idx = [=](int l, int z) { return at(l / C, z, l % C); };
-    lines_fft_n<false>(nz, Bf, 3 * C, idx, twz);
+    constexpr bool z128 = sizeof(T) == 8 && C == 8;     // FP32 complex, eight columns
+    if constexpr (z128) {
+        if (nz == 128) zlines128<false>(reinterpret_cast<float2*>(Bf), reinterpret_cast<const float2*>(twz));
+        else lines_fft_n<false>(nz, Bf, 3 * C, idx, twz);
+    } else {
+        lines_fft_n<false>(nz, Bf, 3 * C, idx, twz);
+    }
     __syncthreads();
     const K* sym = reinterpret_cast<const K*>(a.symk);     // [9][256] cos, sin, lambda
     const K ih = kparam<K>(a.inv_h, a.inv_h32);
@@ -395,7 +445,12 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
         for (int c = 0; c < 3; ++c) Bf[at(c, kz, k)] = W[c];
     }
     __syncthreads();
-    lines_fft_n<true>(nz, Bf, 3 * C, idx, twz);
+    if constexpr (z128) {
+        if (nz == 128) zlines128<true>(reinterpret_cast<float2*>(Bf), reinterpret_cast<const float2*>(twz));
+        else lines_fft_n<true>(nz, Bf, 3 * C, idx, twz);
+    } else {
+        lines_fft_n<true>(nz, Bf, 3 * C, idx, twz);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
         const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
