@@ -715,32 +715,43 @@ k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_star
                        ((int)blockIdx.x / (ntx * nty)) * TZ};
     const int ncx = TX / G.bs, ncy = TY / G.bs, ncz = TZ / G.bs;
     const int rows = ncy * ncz;
-    if (threadIdx.x < rows) {
+    // the tile's rows of cells (at most 64): start slot and length, and the exclusive prefix of
+    // the lengths, scanned by the first two warps (32 rows each, then the first warp's carry)
+    __shared__ int carry0;
+    if (threadIdx.x < 64) {
         const int r = threadIdx.x;
-        const int cz = T0[2] / G.bs + r / ncy, cy = T0[1] / G.bs + r % ncy;
-        const int64_t base = box * G.ncell + ((int64_t)cz * G.nc[1] + cy) * G.nc[0] + T0[0] / G.bs;
-        rb[r] = cell_start[base];
-        rp[r] = cell_start[base + ncx] - rb[r];
+        int len = 0;
+        if (r < rows) {
+            const int cz = T0[2] / G.bs + r / ncy, cy = T0[1] / G.bs + r % ncy;
+            const int64_t base = box * G.ncell + ((int64_t)cz * G.nc[1] + cy) * G.nc[0] + T0[0] / G.bs;
+            rb[r] = cell_start[base];
+            len = cell_start[base + ncx] - rb[r];
+        }
+        int x = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((r & 31) >= o) x += y;
+        }
+        rp[r] = x - len;                       // exclusive within the warp
+        if (r == 31) carry0 = x;
+        if (r == 63) rp[64] = x;               // the second warp's total (carry added below)
     }
     {
         int4* a4 = reinterpret_cast<int4*>(acc);
         for (int i = threadIdx.x; i < 3 * SN / 4; i += blockDim.x) a4[i] = make_int4(0, 0, 0, 0);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int r = 0; r < rows; ++r) {
-            const int len = rp[r];
-            rp[r] = run;
-            run += len;
-        }
-        rp[rows] = run;
-    }
+    if (threadIdx.x >= 32 && threadIdx.x < 65) rp[threadIdx.x] += carry0;
     __syncthreads();
     const int total = rp[rows];
+    // the row holding position t of the tile's blobs: the last r with rp[r] <= t (rows with no
+    // blobs share their start with the next row, so take the last of equal starts)
     auto slot_of = [&](int t) {
         int r = 0;
-        while (rp[r + 1] <= t) ++r;
+#pragma unroll
+        for (int step = 32; step > 0; step >>= 1)
+            if (r + step < rows && rp[r + step] <= t) r += step;
         return (int64_t)rb[r] + (t - rp[r]);
     };
     // the tile's fixed-point scale: 2^(30 - e) with 2^e >= n (2/3)^3 max|F| / h^3
