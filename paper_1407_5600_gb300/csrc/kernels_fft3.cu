@@ -60,16 +60,18 @@ struct PadPlane {
 };
 
 // Skew128: 128 x 128 planes of float2.  Rows of 148 slots, one pad slot every 16 and a skew of
-// SK[(p >> 2) & 7] slots per group of four packed rows, SK = {0, 6, 7, 9, 2, 7, 8, 1}.  A bank
-// model of every shared-memory access of the two plane passes (loads, the two stages of the
-// row and column line FFTs, the separation and the spectrum copies) puts this layout within 5%
-// of the fewest possible wavefronts, against 1.7x for the padded layout; 64 rows x 148 slots
-// x 8 B = 74 KiB keeps three planes per SM.  With 128-point lines split 16 x 8 (thread t of a
-// line holds elements 8 n1 + t, then 8 (t + 8 m) + n2) every address is a per-thread base plus
-// a compile-time offset, so the line FFTs spend no instructions on indexing.
+// SK[(p >> 2) & 7] slots per group of four packed rows, SK = {0, 6, 3, 9, 7, 5, 4, 0}; the row
+// lines take lane = 4 t + (line - l0), the column lines lane = 8 (line - l0) + t.  A model of the
+// shared-memory banks (8-byte accesses served per half-warp) over every access of the two plane
+// passes (loads, both stages of the row and column line FFTs, the separation, the spectrum
+// copies) gives this layout 0.63x the wavefronts of the padded one (1.2x the fewest possible);
+// 64 rows x 148 slots x 8 B = 74 KiB keeps three planes per SM.  With 128-point lines split
+// 16 x 8 (thread t of a line holds elements 8 n1 + t, then 8 (t + 8 m) + n2) every address is
+// a per-thread base plus a compile-time offset, so the line FFTs spend no instructions on
+// indexing.
 struct Skew128 {
     static constexpr int S = 148;
-    static constexpr unsigned SKW = 0x18729760u;              // SK[i] = (SKW >> 4 i) & 15
+    static constexpr unsigned SKW = 0x04579360u;              // SK[i] = (SKW >> 4 i) & 15
     __host__ __device__ static constexpr int sk(int i) { return (int)((SKW >> (4 * (i & 7))) & 15u); }
     __device__ Skew128(int, int) {}
     __device__ __forceinline__ int at(int p, int j) const { return p * S + sk(p >> 2) + j + (j >> 4); }
@@ -122,7 +124,7 @@ struct Skew128 {
     template <bool INV, bool COL> __device__ __forceinline__ static void lines(float2* P, const float2* tw)
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        const int sub = lane & 3, t = lane >> 2;
+        const int sub = COL ? lane >> 3 : lane & 3, t = COL ? lane & 7 : lane >> 2;
         for (int l0 = warp * 4; l0 < 64; l0 += nw * 4) line_round<INV, COL>(P, l0 + sub, t, tw);
     }
     template <bool INV, typename T> __device__ __forceinline__ void rows(T* P, const T* tw) const
