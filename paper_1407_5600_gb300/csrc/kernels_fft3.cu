@@ -382,14 +382,25 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     T* base = reinterpret_cast<T*>(a.spec) + (size_t)(box * 3) * cstride + (size_t)kx * ny + ky0;
     auto at = [=](int c, int z, int k) { return (c * nzp + z + (z >> sz)) * Cp + k; };
     const int total = 3 * nz * C;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
-        async_copy(&Bf[at(c, z, k)], &base[c * cstride + (size_t)z * zstride + k]);
+    constexpr bool z128 = sizeof(T) == 8 && C == 8;     // FP32 complex, eight columns
+    // 128-point z-lines with 192 threads: thread (zr = tid / 8, k = tid % 8) moves the elements
+    // (c = zr / 8, z = zr % 8 + 8 j, k), j < 16, at a fixed stride on both sides
+    const bool fast = z128 && nz == 128 && blockDim.x == 3 * 8 * C;
+    if (fast) {
+        const int k = threadIdx.x & 7, zr = threadIdx.x >> 3, c = zr >> 3, z0 = zr & 7;
+        T* sb = Bf + (c * 144 + z0) * 12 + k;
+        const T* gb = base + c * cstride + (size_t)z0 * zstride + k;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) async_copy(sb + 108 * j, gb + (size_t)(8 * j) * zstride);
+    } else {
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
+            async_copy(&Bf[at(c, z, k)], &base[c * cstride + (size_t)z * zstride + k]);
+        }
     }
     async_wait_all();
     __syncthreads();
     auto idx = [=](int l, int z) { return at(l / C, z, l % C); };
-    constexpr bool z128 = sizeof(T) == 8 && C == 8;     // FP32 complex, eight columns
     if constexpr (z128) {
         if (nz == 128) zlines128<false>(reinterpret_cast<float2*>(Bf), reinterpret_cast<const float2*>(twz));
         else lines_fft_n<false>(nz, Bf, 3 * C, idx, twz);
@@ -402,11 +413,16 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     const K csx = sym[0 * 256 + kx], snx = sym[1 * 256 + kx], lx = sym[2 * 256 + kx];
     const K rho_dt = kparam<K>(a.rho_dt, a.rho_dt32);
     const K half_eta = kparam<K>(a.half_eta, a.half_eta32);
+    // with blockDim a multiple of C a thread keeps its column k (and ky's symbols) throughout
+    const int kfix = threadIdx.x % C;
+    const K csy = sym[3 * 256 + ky0 + kfix], sny = sym[4 * 256 + ky0 + kfix];
+    const K lxy = lx + sym[5 * 256 + ky0 + kfix];
+    const bool colfix = blockDim.x % C == 0;
     for (int i = threadIdx.x; i < nz * C; i += blockDim.x) {
-        const int k = i % C, kz = i / C, ky = ky0 + k;
-        const K cs[3] = {csx, sym[3 * 256 + ky], sym[6 * 256 + kz]};
-        const K sn[3] = {snx, sym[4 * 256 + ky], sym[7 * 256 + kz]};
-        const K lam = lx + sym[5 * 256 + ky] + sym[8 * 256 + kz];
+        const int k = colfix ? kfix : i % C, kz = i / C, ky = ky0 + k;
+        const K cs[3] = {csx, colfix ? csy : sym[3 * 256 + ky], sym[6 * 256 + kz]};
+        const K sn[3] = {snx, colfix ? sny : sym[4 * 256 + ky], sym[7 * 256 + kz]};
+        const K lam = (colfix ? lxy : lx + sym[5 * 256 + ky]) + sym[8 * 256 + kz];
         const K cinv = recip(rho_dt + half_eta * lam);
         T W[3];
         for (int c = 0; c < 3; ++c) {
@@ -454,9 +470,17 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
         lines_fft_n<true>(nz, Bf, 3 * C, idx, twz);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
-        base[c * cstride + (size_t)z * zstride + k] = Bf[at(c, z, k)];
+    if (fast) {
+        const int k = threadIdx.x & 7, zr = threadIdx.x >> 3, c = zr >> 3, z0 = zr & 7;
+        const T* sb = Bf + (c * 144 + z0) * 12 + k;
+        T* gb = base + c * cstride + (size_t)z0 * zstride + k;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) gb[(size_t)(8 * j) * zstride] = sb[108 * j];
+    } else {
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            const int k = i % C, zc = i / C, z = zc & (nz - 1), c = zc >> lz;
+            base[c * cstride + (size_t)z * zstride + k] = Bf[at(c, z, k)];
+        }
     }
 }
 
