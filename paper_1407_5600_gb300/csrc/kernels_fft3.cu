@@ -43,6 +43,8 @@ __host__ __device__ inline int plane_ld(int nx)
 struct PadPlane {
     int nx, ny, S, sx;
     __device__ PadPlane(int nx_, int ny_) : nx(nx_), ny(ny_), S(plane_ld(nx_)), sx(pad_shift(nx_)) {}
+    __device__ __forceinline__ int row(int p) const { return p * S; }
+    __device__ __forceinline__ int off(int j) const { return j + (j >> sx); }
     __device__ __forceinline__ int at(int p, int j) const { return p * S + j + (j >> sx); }
     template <bool INV, typename T> __device__ __forceinline__ void rows(T* P, const T* tw) const
     {
@@ -74,6 +76,8 @@ struct Skew128 {
     static constexpr unsigned SKW = 0x04579360u;              // SK[i] = (SKW >> 4 i) & 15
     __host__ __device__ static constexpr int sk(int i) { return (int)((SKW >> (4 * (i & 7))) & 15u); }
     __device__ Skew128(int, int) {}
+    __device__ __forceinline__ int row(int p) const { return p * S + sk(p >> 2); }
+    __device__ __forceinline__ int off(int j) const { return j + (j >> 4); }
     __device__ __forceinline__ int at(int p, int j) const { return p * S + sk(p >> 2) + j + (j >> 4); }
     // One round: 8 warps x 4 lines; lane = 4 t + (line - l0).  b1 addresses element 8 n1 + t
     // at offset c1(n1); b2 element 8 (t + 8 m) + n2 at c2(m, n2); b1 element (t + 8 m) + 16 k2
@@ -192,7 +196,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
                 r1[i] += K(a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)]);
             }
         }
-        for (int i = 0; i < 4; ++i) P[lay.at(p, x0 + i)] = T{r0[i], r1[i]};
+        T* rowp = P + lay.row(p);
+        for (int i = 0; i < 4; ++i) rowp[lay.off(x0 + i)] = T{r0[i], r1[i]};
     }
     for (int u = threadIdx.x; u < qx * (ny / 2) && !a.no_v; u += blockDim.x) {
         const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
@@ -247,7 +252,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
                 r1[i] += K(a.body_prof[a.body_dir == 0 ? x : (a.body_dir == 1 ? y1 : z)]);
             }
         }
-        for (int i = 0; i < 4; ++i) P[lay.at(p, x0 + i)] = T{r0[i], r1[i]};
+        T* rowp = P + lay.row(p);
+        for (int i = 0; i < 4; ++i) rowp[lay.off(x0 + i)] = T{r0[i], r1[i]};
     }
     __syncthreads();
     lay.template rows<false>(P, twx);
@@ -256,13 +262,14 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int p = warp; p < ny / 2; p += nw) {
+            T* rowp = P + lay.row(p);
             T ev[3], od[3];        // nx/2 + 1 <= 65 values: at most 3 per lane
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 const int k = lane + 32 * r;
                 if (k < nxh) {
                     const int kr = (nx - k) & (nx - 1);
-                    const T Z = P[lay.at(p, k)], Zr = P[lay.at(p, kr)];
+                    const T Z = rowp[lay.off(k)], Zr = rowp[lay.off(kr)];
                     ev[r] = T{(Z.x + Zr.x) * kconst<K>(0.5f), (Z.y - Zr.y) * kconst<K>(0.5f)};
                     od[r] = T{(Z.y + Zr.y) * kconst<K>(0.5f), (Zr.x - Z.x) * kconst<K>(0.5f)};
                 }
@@ -272,8 +279,8 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
             for (int r = 0; r < 3; ++r) {
                 const int k = lane + 32 * r;
                 if (k < nxh) {
-                    P[lay.at(p, 2 * k)] = ev[r];
-                    P[lay.at(p, 2 * k + 1)] = od[r];
+                    rowp[lay.off(2 * k)] = ev[r];
+                    rowp[lay.off(2 * k + 1)] = od[r];
                 }
             }
             __syncwarp();
@@ -313,7 +320,14 @@ k_plane_fwd(FluidArgs<R> a, GridGeo g)
     __syncthreads();
     T* out = reinterpret_cast<T*>(a.spec) + ((size_t)bc * nz + z) * (size_t)nxh * ny;
     const int ly = 31 - __clz(ny);
-    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) out[i] = P[col(i >> ly, i & (ny - 1))];
+    if (blockDim.x % ny == 0) {
+        // a thread keeps its y (so its packed row and parity) and steps through k
+        const int y = threadIdx.x & (ny - 1), e = y & 1, dk = blockDim.x >> ly;
+        const T* rowp = P + lay.row(y >> 1);
+        for (int k = threadIdx.x >> ly; k < nxh; k += dk) out[k * ny + y] = rowp[lay.off(2 * k + e)];
+    } else {
+        for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) out[i] = P[col(i >> ly, i & (ny - 1))];
+    }
 }
 
 // 128-point z-lines of the pass-B buffer (FP32, C = 8 columns): element z of line l (component
@@ -502,7 +516,13 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     const T* in = reinterpret_cast<const T*>(a.spec) + ((size_t)bc * nz + z) * (size_t)nxh * ny;
     auto col = [lay](int k, int y) { return lay.at(y >> 1, 2 * k + (y & 1)); };
     const int ly = 31 - __clz(ny);
-    for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) async_copy(&P[col(i >> ly, i & (ny - 1))], &in[i]);
+    if (blockDim.x % ny == 0) {
+        const int y = threadIdx.x & (ny - 1), e = y & 1, dk = blockDim.x >> ly;
+        T* rowp = P + lay.row(y >> 1);
+        for (int k = threadIdx.x >> ly; k < nxh; k += dk) async_copy(&rowp[lay.off(2 * k + e)], &in[k * ny + y]);
+    } else {
+        for (int i = threadIdx.x; i < nxh * ny; i += blockDim.x) async_copy(&P[col(i >> ly, i & (ny - 1))], &in[i]);
+    }
     async_wait_all();
     __syncthreads();
     // columns k = 0 and k = nx/2 invert to real sequences: transform their Hermitian parts as
@@ -541,13 +561,14 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int p = warp; p < ny / 2; p += nw) {
+            T* rowp = P + lay.row(p);
             T zv[4];              // nx <= 128 values: at most 4 per lane
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int k = lane + 32 * r;
                 if (k < nx) {
                     const int kk = k <= nx / 2 ? k : nx - k;
-                    T e = P[lay.at(p, 2 * kk)], o = P[lay.at(p, 2 * kk + 1)];
+                    T e = rowp[lay.off(2 * kk)], o = rowp[lay.off(2 * kk + 1)];
                     if (k == 0 || k == nx / 2) { e.y = kconst<K>(0.0f); o.y = kconst<K>(0.0f); }
                     if (k > nx / 2) { e.y = -e.y; o.y = -o.y; }
                     zv[r] = T{e.x - o.y, e.y + o.x};
@@ -557,7 +578,7 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int k = lane + 32 * r;
-                if (k < nx) P[lay.at(p, k)] = zv[r];
+                if (k < nx) rowp[lay.off(k)] = zv[r];
             }
             __syncwarp();
         }
@@ -571,9 +592,9 @@ k_plane_inv(FluidArgs<R> a, GridGeo g)
     for (int u = threadIdx.x; u < qx * (ny / 2); u += blockDim.x) {
         const int x0 = 4 * (u & (qx - 1)), p = u >> lq;
         K r0[4], r1[4];
+        const T* rowp = P + lay.row(p);
         for (int i = 0; i < 4; ++i) {
-            const int j = x0 + i;
-            const T zv = P[lay.at(p, j)];
+            const T zv = rowp[lay.off(x0 + i)];
             r0[i] = zv.x * scale;
             r1[i] = zv.y * scale;
         }
