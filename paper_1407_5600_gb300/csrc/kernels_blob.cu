@@ -29,20 +29,26 @@ k_interp(int64_t nb, const double* __restrict__ q, const double* q_base,
         const size_t base = ((size_t)box * 3 + a) * (size_t)g.N;
         const R* c0 = v0 + base;
         const R* c1 = MODE == 2 ? v1 + base : nullptr;
+        // 32-bit offsets inside the component grid (at most 2^24 nodes), the wrapped node
+        // indices computed once per dimension
+        int xo[3], yo[3], zo[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xo[d] = (ix + d) & (nx - 1);
+            yo[d] = ((iy + d) & (ny - 1)) * nx;
+            zo[d] = ((iz + d) & (nz - 1)) * (ny * nx);
+        }
         R acc = R(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int zz = (iz + c) & (nz - 1);
 #pragma unroll
             for (int bb = 0; bb < 3; ++bb) {
-                const int yy = (iy + bb) & (ny - 1);
-                const size_t row = ((size_t)zz * ny + yy) * nx;
+                const int row = zo[c] + yo[bb];
                 R r = R(0);
 #pragma unroll
                 for (int aa = 0; aa < 3; ++aa) {
-                    const int xx = (ix + aa) & (nx - 1);
-                    R val = __ldg(c0 + row + xx);
-                    if (MODE == 2) val += __ldg(c1 + row + xx);
+                    R val = __ldg(c0 + (row + xo[aa]));
+                    if (MODE == 2) val += __ldg(c1 + (row + xo[aa]));
                     r += wx[aa] * val;
                 }
                 acc += wy[bb] * wz[c] * r;

@@ -189,20 +189,25 @@ k_interp32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ 
         const size_t base = ((size_t)box * 3 + comp) * (size_t)G.N;
         const float* c0 = v0 + base;
         const float* c1 = MODE == 2 ? v1 + base : nullptr;
+        // 32-bit offsets inside the component grid, wrapped indices once per dimension
+        int xo[3], yo[3], zo[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xo[d] = (ix + d) & (nx - 1);
+            yo[d] = ((iy + d) & (ny - 1)) * nx;
+            zo[d] = ((iz + d) & (nz - 1)) * (ny * nx);
+        }
         float acc = 0.0f;
 #pragma unroll
         for (int cz = 0; cz < 3; ++cz) {
-            const int zz = (iz + cz) & (nz - 1);
 #pragma unroll
             for (int cy = 0; cy < 3; ++cy) {
-                const int yy = (iy + cy) & (ny - 1);
-                const size_t row = ((size_t)zz * ny + yy) * nx;
+                const int row = zo[cz] + yo[cy];
                 float r = 0.0f;
 #pragma unroll
                 for (int cx = 0; cx < 3; ++cx) {
-                    const int xx = (ix + cx) & (nx - 1);
-                    float val = __ldg(c0 + row + xx);
-                    if (MODE == 2) val += __ldg(c1 + row + xx);
+                    float val = __ldg(c0 + (row + xo[cx]));
+                    if (MODE == 2) val += __ldg(c1 + (row + xo[cx]));
                     r += wx[cx] * val;
                 }
                 acc += wy[cy] * wz[cz] * r;
@@ -244,21 +249,29 @@ __device__ __forceinline__ void gather32(const int c[3], const float hi[3], cons
         const int ix = window32(c[0], G.bs, hi[0], G.inv_h, comp == 0 ? 0.f : 0.5f, wx);
         const int iy = window32(c[1], G.bs, hi[1], G.inv_h, comp == 1 ? 0.f : 0.5f, wy);
         const int iz = window32(c[2], G.bs, hi[2], G.inv_h, comp == 2 ? 0.f : 0.5f, wz);
+        // one 64-bit base per component grid, 32-bit offsets inside it (a box grid has at most
+        // 2^24 nodes), the wrapped node indices computed once per dimension
         const size_t base = box_base + (size_t)comp * (size_t)G.N;
+        const float* g0 = v0 + base;
+        const float* g1 = v1 ? v1 + base : nullptr;
+        int xo[3], yo[3], zo[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xo[d] = (ix + d) & (nx - 1);
+            yo[d] = ((iy + d) & (ny - 1)) * nx;
+            zo[d] = ((iz + d) & (nz - 1)) * (ny * nx);
+        }
         float acc = 0.0f;
 #pragma unroll
         for (int cz = 0; cz < 3; ++cz) {
-            const int zz = (iz + cz) & (nz - 1);
 #pragma unroll
             for (int cy = 0; cy < 3; ++cy) {
-                const int yy = (iy + cy) & (ny - 1);
-                const size_t row = base + ((size_t)zz * ny + yy) * nx;
+                const int row = zo[cz] + yo[cy];
                 float r = 0.0f;
 #pragma unroll
                 for (int cx = 0; cx < 3; ++cx) {
-                    const int xx = (ix + cx) & (nx - 1);
-                    float val = __ldg(v0 + row + xx);
-                    if (v1) val += __ldg(v1 + row + xx);
+                    float val = __ldg(g0 + (row + xo[cx]));
+                    if (v1) val += __ldg(g1 + (row + xo[cx]));
                     r += wx[cx] * val;
                 }
                 acc += wy[cy] * wz[cz] * r;
@@ -807,7 +820,9 @@ k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_star
     }
     __syncthreads();
     const int4* a4 = reinterpret_cast<const int4*>(acc);
-    const size_t comp_stride = (size_t)G.N;
+    // one 64-bit base for the box, 32-bit offsets inside its three grids (3 N < 2^26)
+    float* fb = f + (size_t)box * 3 * (size_t)G.N;
+    const int N32 = (int)G.N;
     const float unscale = 1.0f / scale;
     for (int i = threadIdx.x; i < 3 * SY * SZ * SXC; i += blockDim.x) {
         const int4 q = a4[i];
@@ -816,7 +831,7 @@ k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_star
         const int comp = row / (SY * SZ), rr = row - comp * (SY * SZ);
         const int sz = rr / SY, sy = rr - sz * SY;
         const int gx = (ox + 4 * cx) & (nx - 1), gy = (oy + sy) & (ny - 1), gz = (oz + sz) & (nz - 1);
-        float* dst = f + ((size_t)box * 3 + comp) * comp_stride + ((size_t)gz * ny + gy) * nx + gx;
+        float* dst = fb + (comp * N32 + (gz * ny + gy) * nx + gx);
         atomicAdd(reinterpret_cast<float4*>(dst),
                   make_float4(q.x * unscale, q.y * unscale, q.z * unscale, q.w * unscale));
     }
