@@ -683,6 +683,68 @@ k_spread(const double* __restrict__ rec, const int32_t* __restrict__ cell_start,
     }
 }
 
+// Blob-owner spreading with global atomics: one thread per sorted slot adds its 81 node
+// contributions straight into f (zeroed beforehand) with the native FP64 (or FP32) global
+// atomic add; the sorted order keeps a warp's nodes close together in L2.
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_spread_atomic(const double* __restrict__ rec, const int32_t* __restrict__ cell_start,
+                GridGeo g, BinGeo bg, R* __restrict__ f)
+{
+    const int box = blockIdx.y;
+    const int64_t s0 = cell_start[box * bg.ncell], s1 = cell_start[(box + 1) * bg.ncell];
+    const int64_t slot = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= s1) return;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const double* rr = rec + 6 * slot;
+    const double p[3] = {rr[0], rr[1], rr[2]};
+    const double inv_h3 = g.inv_h * g.inv_h * g.inv_h;
+    R* fb = f + (size_t)box * 3 * (size_t)g.N;
+    const int N32 = (int)g.N;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const R Fa = static_cast<R>(rr[3 + a] * inv_h3);
+        R wx[3], wy[3], wz[3];
+        const int ix = peskin_window<R>(p[0] * g.inv_h - mac_shift(a, 0), wx);
+        const int iy = peskin_window<R>(p[1] * g.inv_h - mac_shift(a, 1), wy);
+        const int iz = peskin_window<R>(p[2] * g.inv_h - mac_shift(a, 2), wz);
+        int xo[3], yo[3], zo[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xo[d] = (ix + d) & (nx - 1);
+            yo[d] = ((iy + d) & (ny - 1)) * nx;
+            zo[d] = ((iz + d) & (nz - 1)) * (ny * nx);
+        }
+        R* fa = fb + a * N32;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) {
+                const R wyz = wy[bb] * wz[c] * Fa;
+#pragma unroll
+                for (int aa = 0; aa < 3; ++aa) atomicAdd(fa + (zo[c] + yo[bb] + xo[aa]), wx[aa] * wyz);
+            }
+    }
+}
+
+template <typename R>
+cudaError_t launch_spread_atomic(cudaStream_t st, int B, int64_t max_box_blobs, const double* rec,
+                                 const int32_t* cell_start, const GridGeo& g, const BinGeo& bg,
+                                 R* f)
+{
+    cudaError_t e = cudaMemsetAsync(f, 0, sizeof(R) * 3 * (size_t)B * g.N, st);
+    if (e != cudaSuccess || max_box_blobs <= 0) return e;
+    dim3 grid((unsigned)((max_box_blobs + 255) / 256), (unsigned)B);
+    k_spread_atomic<R><<<grid, 256, 0, st>>>(rec, cell_start, g, bg, f);
+    return cudaGetLastError();
+}
+template cudaError_t launch_spread_atomic<double>(cudaStream_t, int, int64_t, const double*,
+                                                  const int32_t*, const GridGeo&, const BinGeo&,
+                                                  double*);
+template cudaError_t launch_spread_atomic<float>(cudaStream_t, int, int64_t, const double*,
+                                                 const int32_t*, const GridGeo&, const BinGeo&,
+                                                 float*);
+
 // Deterministic FP64 spreading: the same tile-owner scheme, accumulated in 64-bit fixed point
 // (shared-memory integer atomics are associative, so the sums do not depend on the order in
 // which threads add).  The tile's scale is a power of two chosen from its largest force so that

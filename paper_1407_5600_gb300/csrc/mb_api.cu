@@ -611,6 +611,17 @@ mb_status drain_stage_events(mb_ctx* ctx)
 }
 
 // One time step of every box (see mb_step in include/mb.h).
+// FP64-mode spreading by blob-owner global atomics (MB_SPREAD64=tile keeps the tile-owner
+// shared-memory kernel).
+bool spread_atomic64()
+{
+    static const bool on = [] {
+        const char* e = std::getenv("MB_SPREAD64");
+        return !(e && std::string(e) == "tile");
+    }();
+    return on;
+}
+
 template <typename R>
 mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
 {
@@ -685,6 +696,11 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
             MB_CUDA(launch_spread_det(st, B, static_cast<const double*>(ctx->rec.p),
                                       static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,
                                       ctx->tile, reinterpret_cast<double*>(ctx->f.p)));
+        else if (spread_atomic64())
+            MB_CUDA(launch_spread_atomic<R>(st, B, ctx->max_box_blobs,
+                                            static_cast<const double*>(ctx->rec.p),
+                                            static_cast<const int32_t*>(ctx->cell_start.p), g,
+                                            ctx->bg, static_cast<R*>(ctx->f.p)));
         else
             MB_CUDA(launch_spread<R>(st, B, static_cast<const double*>(ctx->rec.p),
                                      static_cast<const int32_t*>(ctx->cell_start.p), g, ctx->bg,

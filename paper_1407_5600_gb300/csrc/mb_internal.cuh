@@ -118,6 +118,12 @@ template <typename R>
 cudaError_t launch_spread(cudaStream_t st, int B, const double* rec, const int32_t* cell_start,
                           const GridGeo& g, const BinGeo& bg, const int tile[3], R* f);
 
+// Blob-owner spreading with global atomic adds into f (zeroed by the launcher).
+template <typename R>
+cudaError_t launch_spread_atomic(cudaStream_t st, int B, int64_t max_box_blobs, const double* rec,
+                                 const int32_t* cell_start, const GridGeo& g, const BinGeo& bg,
+                                 R* f);
+
 // Deterministic FP64 spreading (64-bit fixed-point shared-memory accumulation).
 cudaError_t launch_spread_det(cudaStream_t st, int B, const double* rec, const int32_t* cell_start,
                               const GridGeo& g, const BinGeo& bg, const int tile[3], double* f);
