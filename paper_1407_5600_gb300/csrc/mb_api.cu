@@ -175,7 +175,13 @@ struct mb_ctx {
     cudaStream_t cap_stream = nullptr;
     // second stream for the spring forces, which overlap the binning (fork/join events)
     cudaStream_t side = nullptr;
-    cudaEvent_t fork[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork[4] = {nullptr, nullptr, nullptr, nullptr};
+    // a second side stream: the conversion of a single-step call's external forces
+    cudaStream_t side2 = nullptr;
+    // device-readable external forces of the current single-step call, converted inside the
+    // step beside the binning (null: ext32 already holds them or there are none)
+    const double* ext_src = nullptr;
+    const double* graph_ext_src[2] = {nullptr, nullptr};
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     bool graph_ext[2] = {false, false}, graph_body[2] = {false, false};
     int graph_hcur[2] = {0, 0};
@@ -904,8 +910,30 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
     // the spring forces need only the midpoint positions: without stage timing they run on a
     // second stream while the blobs are binned (fork/join events, also inside captured graphs)
     const bool overlap = blobs && !ctx->timing;
+    // a single-step call's external forces (read from the caller's array, possibly page-locked
+    // host memory over the interconnect) are converted on a third stream beside the binning and
+    // the springs; they are first needed by the repulsion pass
+    auto ext_prepare = [&](cudaStream_t s2) {
+        return launch_ext_prepare(s2, B, ctx->max_box_blobs,
+                                  static_cast<const int64_t*>(ctx->box_off.p), ctx->ext_src,
+                                  static_cast<float4*>(ctx->ext32.p),
+                                  static_cast<double*>(ctx->partial.p),
+                                  static_cast<double*>(ctx->ext_sum.p),
+                                  static_cast<unsigned*>(ctx->ext_ticket.p));
+    };
+    const bool ext_in_step = blobs && ctx->ext_src != nullptr;
+    if (ext_in_step && !overlap) {
+        MB_CUDA(ext_prepare(st));
+        ctx->launches += 1;
+    }
     if (overlap) {
         MB_CUDA(cudaEventRecord(ctx->fork[0], st));
+        if (ext_in_step) {
+            MB_CUDA(cudaStreamWaitEvent(ctx->side2, ctx->fork[0], 0));
+            MB_CUDA(ext_prepare(ctx->side2));
+            MB_CUDA(cudaEventRecord(ctx->fork[3], ctx->side2));
+            ctx->launches += 1;
+        }
         MB_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork[0], 0));
         MB_CUDA(launch_springs32(ctx->side, ctx->nb, hA, hB,
                                  static_cast<const int4*>(ctx->adj32.p),
@@ -944,6 +972,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
         const float4* ext4 = ext ? static_cast<const float4*>(ctx->ext32.p) : nullptr;
         if (overlap) {
             MB_CUDA(cudaStreamWaitEvent(st, ctx->fork[1], 0));
+            if (ext_in_step) MB_CUDA(cudaStreamWaitEvent(st, ctx->fork[3], 0));
             MB_CUDA(launch_pairs32(st, B, ctx->max_box_blobs, box_off,
                                    static_cast<const int32_t*>(ctx->sorted.p), hA, hB,
                                    static_cast<const float4*>(ctx->loc.p), box_of,
@@ -1273,6 +1302,7 @@ mb_status capture_graph(mb_ctx* ctx, bool ext, const double* body)
         return MB_ECUDA;
     }
     ctx->graph_ext[cur0] = ext;
+    ctx->graph_ext_src[cur0] = ctx->ext_src;
     ctx->graph_body[cur0] = body != nullptr;
     ctx->graph_hcur[cur0] = hcur0;
     ctx->graph_fz[cur0] = ctx->f_zero;
@@ -1293,6 +1323,7 @@ mb_status run_fast_steps(mb_ctx* ctx, int n_steps, bool ext, const double* body)
         }
         const int c = ctx->cur;
         if (!ctx->graph_exec[c] || ctx->graph_ext[c] != ext ||
+            ctx->graph_ext_src[c] != ctx->ext_src ||
             ctx->graph_body[c] != (body != nullptr) || ctx->graph_hcur[c] != ctx->hcur ||
             ctx->graph_fz[c] != ctx->f_zero)
             MB_TRY(capture_graph(ctx, ext, body));
@@ -1423,9 +1454,12 @@ void release(mb_ctx* ctx)
     ctx->cap_stream = nullptr;
     if (ctx->side) cudaStreamDestroy(ctx->side);
     ctx->side = nullptr;
-    for (cudaEvent_t& e : ctx->fork)
+    if (ctx->side2) cudaStreamDestroy(ctx->side2);
+    ctx->side2 = nullptr;
+    for (cudaEvent_t& e : ctx->fork) {
         if (e) cudaEventDestroy(e);
-    ctx->fork[0] = ctx->fork[1] = ctx->fork[2] = nullptr;
+        e = nullptr;
+    }
     DBuf* all[] = {&ctx->v[0], &ctx->v[1], &ctx->vsum, &ctx->f, &ctx->spec, &ctx->vbar, &ctx->fsum,
                    &ctx->tw[0], &ctx->tw[1], &ctx->tw[2], &ctx->twf[0], &ctx->twf[1],
                    &ctx->twf[2], &ctx->sym, &ctx->symr, &ctx->body_prof,
@@ -1636,9 +1670,11 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     if ((s = upload_tables(ctx)) != MB_OK) return fail(s);
     // the side stream and fork/join events of the step (created here, never inside a capture)
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->fork[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->fork[1], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->fork[2], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->fork[2], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork[3], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         ctx->err = "stream or event creation failed";
         return fail(MB_ECUDA);
@@ -1763,7 +1799,12 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
             src = mapped;         // page-locked host forces: the kernel reads them directly
         else
             MB_TRY(stage_in(ctx, ext_blob_force, sizeof(double) * 3 * ctx->nb, ctx->ext, &src, "ext"));
-        if (ctx->rsz == 4) {
+        if (ctx->rsz == 4 && n_steps == 1) {
+            // one step: converted inside it, beside the binning (the pointer is not kept past
+            // this call)
+            ctx->ext_src = static_cast<const double*>(src);
+            ext = static_cast<const double*>(ctx->ext.p);   // marks forces present
+        } else if (ctx->rsz == 4) {
             // converted once into the library's FP32 copy (the steps never read `src`)
             MB_CUDA(launch_ext_prepare(ctx->st, ctx->B, ctx->max_box_blobs,
                                        static_cast<const int64_t*>(ctx->box_off.p),
@@ -1780,7 +1821,11 @@ mb_status mb_step(mb_ctx* ctx, int n_steps, const double* ext_blob_force,
             ext = static_cast<const double*>(ctx->ext.p);
         }
     }
-    if (ctx->rsz == 4) return run_fast_steps(ctx, n_steps, ext != nullptr, body_force);
+    if (ctx->rsz == 4) {
+        const mb_status st = run_fast_steps(ctx, n_steps, ext != nullptr, body_force);
+        ctx->ext_src = nullptr;
+        return st;
+    }
     for (int s = 0; s < n_steps; ++s) MB_TRY(do_step<double>(ctx, ext, body_force));
     return MB_OK;
 }

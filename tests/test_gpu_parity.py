@@ -101,6 +101,25 @@ def test_fluid_update_parity(prec, shape, h, mean_mode, body):
     assert rel_l2(vn, ref) < TOL[prec]
 
 
+def test_fp64_fluid_update_on_tiny_fields():
+    """FP64 grids transform in double-float arithmetic; values below 2^-74 in magnitude take a
+    float-only path and keep 24 bits (documented in include/mb.h).  A field scaled into that
+    range matches the oracle to float precision, and the same field at unit scale to 1e-10."""
+    shape = (16, 16, 16)
+    d = _desc(shape, 1, rho=1.3, eta=0.7, dt=0.05, mean_mode=0)
+    v = _projected_field(shape, 31)
+    f = wl.random_field(shape, 32, scale=0.5)
+    g = _oracle_grid(d)
+    for scale, tol in ((1.0, TOL[1]), (2.0 ** -90, 1e-6)):
+        with mb.Multiblob(d) as sim:
+            vn = to_np(sim.fluid_update((scale * v)[None], (scale * f)[None]))[0]
+        ref = oracle.fluid_update(g, scale * v, scale * f)
+        err = rel_l2(vn, ref)
+        assert err < tol, (scale, err)
+        if scale < 1.0:
+            assert err > 1e-12      # the float-only path is in use: not FP64 accuracy
+
+
 # ------------------------------------------------------------------------------------------
 # Full step
 
@@ -395,6 +414,36 @@ def test_full_size_bench_steps_match_oracle(dense128):
     assert rel_l2(v, v_ref) < TOL[0]
     assert rel_l2(u, u_ref) < TOL[0]
     assert rel_l2(U, U_ref) < TOL[0]
+
+
+def test_single_step_calls_with_changing_external_forces():
+    """FP32 steps called one at a time with new external forces every step, from page-locked
+    host memory (converted inside the step graph, beside the binning), from pageable host
+    memory, from device memory, and from a multi-step call, against oracle steps with the
+    same forces."""
+    spec, s = _dense_small(seed=21)
+    d = mb.GridDesc(spec.nx, spec.ny, spec.nz, precision=0, dt=spec.dt, mean_mode=0)
+    g = _oracle_grid(d)
+    rng = np.random.default_rng(22)
+    forces = [rng.normal(scale=1e-3, size=s.pos.shape) for _ in range(7)]
+    pinned = [torch.empty(s.pos.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    with mb.Multiblob(d) as sim:
+        sim.set_particles(0, s.pos, s.pid, s.bonds, s.rest, s.k_spring, s.k_rep, s.r_cut)
+        for k in range(5):                       # same page-locked buffer, then the other one
+            buf = pinned[0] if k < 3 else pinned[1]
+            buf.copy_(torch.from_numpy(forces[k]))
+            mb.step(sim.ctx, 1, buf.numpy(), s.body)
+        mb.step(sim.ctx, 1, np.ascontiguousarray(forces[5]), s.body)      # pageable
+        mb.step(sim.ctx, 1, torch.from_numpy(forces[6]).cuda(), s.body)   # device
+        mb.step(sim.ctx, 2, torch.from_numpy(forces[6]).cuda(), s.body)   # two steps, one call
+        q = to_np(sim.blob_positions())
+        v = to_np(sim.velocity_field())[0].astype(np.float64)
+    q_ref, v_ref = s.pos, g.zeros()
+    for k in list(range(7)) + [6, 6]:
+        q_ref, v_ref = oracle.step(g, 1, q_ref, v_ref, s.pid, s.bonds, s.rest, s.k_spring,
+                                   s.k_rep, s.r_cut, ext=forces[k], body=s.body)
+    assert_positions(q, q_ref, s.pos, g.L, 9, TOL[0])
+    assert rel_l2(v, v_ref) < TOL[0]
 
 
 def test_graph_replay_matches_direct_launches(monkeypatch):
