@@ -145,6 +145,49 @@ __global__ void k_unsplit(int64_t nb, const float4* __restrict__ A, const float4
 
 // ------------------------------------------------------------------------------------------
 // Interpolation J from the split positions (mode 0: u only; 1: predictor; 2: corrector).
+// The x nodes ix, ix + 1, ix + 2 (periodic) of a window lie in the two aligned node pairs that
+// start at a = ix & ~1 and at (a + 2) mod nx: each row of a window is read with two 8-byte loads
+// instead of three 4-byte ones (a third fewer L1 sector lookups per gather), and the three
+// weights are laid over the four loaded nodes, the spare node weighted by zero.  The row sum
+// keeps the order of the three-term sum, so adding zero times the spare (finite) node changes
+// no bit.  Component grids start 8-byte aligned: device allocations, and N and nx are even.
+struct XPair {
+    int a0, a1;
+    float w[4];
+};
+__device__ __forceinline__ XPair xpair(int ix, int nx, const float wx[3])
+{
+    XPair p;
+    const int i = ix & (nx - 1);
+    const bool odd = (i & 1) != 0;
+    p.a0 = i & ~1;
+    p.a1 = (p.a0 + 2) & (nx - 1);
+    p.w[0] = odd ? 0.0f : wx[0];
+    p.w[1] = odd ? wx[0] : wx[1];
+    p.w[2] = odd ? wx[1] : wx[2];
+    p.w[3] = odd ? wx[2] : 0.0f;
+    return p;
+}
+// One row of a window: sum of the x weights times the grid g0 (+ g1 when not null).
+__device__ __forceinline__ float xrow(const float* g0, const float* g1, int row, const XPair& p)
+{
+    float2 lo = __ldg(reinterpret_cast<const float2*>(g0 + row + p.a0));
+    float2 hi = __ldg(reinterpret_cast<const float2*>(g0 + row + p.a1));
+    if (g1) {
+        const float2 lo1 = __ldg(reinterpret_cast<const float2*>(g1 + row + p.a0));
+        const float2 hi1 = __ldg(reinterpret_cast<const float2*>(g1 + row + p.a1));
+        lo.x += lo1.x;
+        lo.y += lo1.y;
+        hi.x += hi1.x;
+        hi.y += hi1.y;
+    }
+    float r = p.w[0] * lo.x;
+    r += p.w[1] * lo.y;
+    r += p.w[2] * hi.x;
+    r += p.w[3] * hi.y;
+    return r;
+}
+
 // Per-dimension windows for both MAC shifts (0 along the component's own axis, 1/2 across).
 struct Win2 {
     float w[2][3];
@@ -190,10 +233,10 @@ k_interp32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ 
         const float* c0 = v0 + base;
         const float* c1 = MODE == 2 ? v1 + base : nullptr;
         // 32-bit offsets inside the component grid, wrapped indices once per dimension
-        int xo[3], yo[3], zo[3];
+        const XPair xp = xpair(ix, nx, wx);
+        int yo[3], zo[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            xo[d] = (ix + d) & (nx - 1);
             yo[d] = ((iy + d) & (ny - 1)) * nx;
             zo[d] = ((iz + d) & (nz - 1)) * (ny * nx);
         }
@@ -202,14 +245,7 @@ k_interp32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__ 
         for (int cz = 0; cz < 3; ++cz) {
 #pragma unroll
             for (int cy = 0; cy < 3; ++cy) {
-                const int row = zo[cz] + yo[cy];
-                float r = 0.0f;
-#pragma unroll
-                for (int cx = 0; cx < 3; ++cx) {
-                    float val = __ldg(c0 + (row + xo[cx]));
-                    if (MODE == 2) val += __ldg(c1 + (row + xo[cx]));
-                    r += wx[cx] * val;
-                }
+                const float r = xrow(c0, MODE == 2 ? c1 : nullptr, zo[cz] + yo[cy], xp);
                 acc += wy[cy] * wz[cz] * r;
             }
         }
@@ -254,10 +290,10 @@ __device__ __forceinline__ void gather32(const int c[3], const float hi[3], cons
         const size_t base = box_base + (size_t)comp * (size_t)G.N;
         const float* g0 = v0 + base;
         const float* g1 = v1 ? v1 + base : nullptr;
-        int xo[3], yo[3], zo[3];
+        const XPair xp = xpair(ix, nx, wx);
+        int yo[3], zo[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            xo[d] = (ix + d) & (nx - 1);
             yo[d] = ((iy + d) & (ny - 1)) * nx;
             zo[d] = ((iz + d) & (nz - 1)) * (ny * nx);
         }
@@ -266,14 +302,7 @@ __device__ __forceinline__ void gather32(const int c[3], const float hi[3], cons
         for (int cz = 0; cz < 3; ++cz) {
 #pragma unroll
             for (int cy = 0; cy < 3; ++cy) {
-                const int row = zo[cz] + yo[cy];
-                float r = 0.0f;
-#pragma unroll
-                for (int cx = 0; cx < 3; ++cx) {
-                    float val = __ldg(g0 + (row + xo[cx]));
-                    if (v1) val += __ldg(g1 + (row + xo[cx]));
-                    r += wx[cx] * val;
-                }
+                const float r = xrow(g0, g1, zo[cz] + yo[cy], xp);
                 acc += wy[cy] * wz[cz] * r;
             }
         }
@@ -341,6 +370,8 @@ __device__ __forceinline__ void fused_blob(int64_t t, const FusedArgs& f, const 
 __global__ void __launch_bounds__(256, 4)
 k_interp32_fused(int64_t nb, FusedArgs f, GridGeo g, BinGeo bg)
 {
+    dep_wait();
+    dep_release();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nb) return;
     fused_blob(t, f, geo32(g, bg));
@@ -376,6 +407,8 @@ __global__ void __launch_bounds__(BIN_SCAN_THREADS)
 k_bin_scan32(int32_t* __restrict__ c, int64_t n, int32_t* __restrict__ tile_off,
              int32_t* __restrict__ total, unsigned* __restrict__ ticket)
 {
+    dep_wait();
+    dep_release();
     __shared__ int32_t warp_tot[32];
     __shared__ int32_t block_total;
     __shared__ bool last;
@@ -459,6 +492,8 @@ k_bin_place32(int64_t nb, int64_t ncells, const int32_t* __restrict__ local,
               int32_t* __restrict__ sorted, const float4* __restrict__ A,
               const int32_t* __restrict__ pid, float4* __restrict__ loc)
 {
+    dep_wait();
+    dep_release();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < ncells) cell_start[i] = local[i] + tile_off[i >> BIN_SCAN_LOG];
     if (i < nb) {
@@ -524,6 +559,8 @@ k_springs32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__
             const int32_t* __restrict__ box_of, const float* __restrict__ box_par, GridGeo g,
             BinGeo bg, float* __restrict__ Fs)
 {
+    dep_wait();
+    dep_release();
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nb) return;
     const int e0 = adj_start[b], e1 = adj_start[b + 1];
@@ -549,6 +586,62 @@ k_springs32(int64_t nb, const float4* __restrict__ A, const float4* __restrict__
     for (int d = 0; d < 3; ++d) atomicAdd(Fs + 4 * b + d, F[d]);
 }
 
+// Spring forces when every particle shares one bond pattern (Springs32::tmpl).  A block holds
+// whole particles (blockDim = ppb m threads, one per blob, in blob order).  Every bond is
+// evaluated once, by the end its evaluation list names, which adds the force to its own sum
+// and leaves the opposite force in one of its shared-memory slots; after a barrier each thread
+// adds the slots of its collection list.  The pattern spreads the evaluations evenly (an
+// icosahedron's 42 bonds: none by the centre, at most 4 by a vertex), no per-blob list is read,
+// and each blob's sum has a fixed order and is stored once: no atomics and no zeroing pass.
+//   tmpl entries: evaluation {offset | (slot + 1) << 16, r0, r0^2 hi, lo}, collection
+//   {offset, slot, 0, 0}; tstart[2l], tstart[2l + 1], tstart[2l + 2] bound blob l's two lists.
+__global__ void __launch_bounds__(256)
+k_springs32_shared(int nb, int m, int S, const float4* __restrict__ A,
+                   const float4* __restrict__ Bv, const int4* __restrict__ tmpl,
+                   const int32_t* __restrict__ tstart, const int32_t* __restrict__ box_of,
+                   const float* __restrict__ box_par, GridGeo g, BinGeo bg,
+                   float4* __restrict__ Fs)
+{
+    extern __shared__ float slot_f[];                    // [blockDim][S][3]
+    dep_wait();
+    dep_release();
+    const int tid = threadIdx.x;
+    const int b = blockIdx.x * blockDim.x + tid;
+    const bool live = b < nb;
+    const int l = tid % m;
+    float F[3] = {0.f, 0.f, 0.f};
+    if (live) {
+        const Geo32 G = geo32(g, bg);
+        const float4 ab = A[b], lbv = Bv[b];
+        const int pk = __float_as_int(ab.w);
+        const int cb[3] = {cell_unpack(pk, 0), cell_unpack(pk, 1), cell_unpack(pk, 2)};
+        const float hb[3] = {ab.x, ab.y, ab.z}, lb[3] = {lbv.x, lbv.y, lbv.z};
+        const float k_spring = box_par[3 * (box_of ? box_of[b] : 0)];
+        const int e0 = __ldg(tstart + 2 * l), e1 = __ldg(tstart + 2 * l + 1);
+        for (int e = e0; e < e1; ++e) {
+            const int4 ad = __ldg(tmpl + e);
+            const int j = b + (int)(short)(ad.x & 0xffff);
+            const int slot = (ad.x >> 16) - 1;
+            float f[3] = {0.f, 0.f, 0.f};
+            spring32(cb, hb, lb, A[j], Bv[j], __int_as_float(ad.y), __int_as_float(ad.z),
+                     __int_as_float(ad.w), k_spring, G, f);
+            for (int d = 0; d < 3; ++d) {
+                F[d] += f[d];
+                slot_f[(tid * S + slot) * 3 + d] = -f[d];
+            }
+        }
+    }
+    __syncthreads();
+    if (!live) return;
+    const int c0 = __ldg(tstart + 2 * l + 1), c1 = __ldg(tstart + 2 * l + 2);
+    for (int e = c0; e < c1; ++e) {
+        const int4 ad = __ldg(tmpl + e);
+        const int p = tid + ad.x;
+        for (int d = 0; d < 3; ++d) F[d] += slot_f[(p * S + ad.y) * 3 + d];
+    }
+    Fs[b] = make_float4(F[0], F[1], F[2], 0.0f);
+}
+
 struct Force32Args {
     const int64_t* box_off;
     const int32_t* sorted;
@@ -567,6 +660,8 @@ struct Force32Args {
 __global__ void __launch_bounds__(256)
 k_forces32(Force32Args a, GridGeo g, BinGeo bg)
 {
+    dep_wait();
+    dep_release();
     const Geo32 G = geo32(g, bg);
     const int box = blockIdx.y;
     const int64_t s0 = a.box_off[box], cnt = a.box_off[box + 1] - s0;
@@ -713,6 +808,8 @@ __global__ void __launch_bounds__(256)
 k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_start, GridGeo g,
            BinGeo bg, int TXr, int TYr, int TZr, float* __restrict__ f)
 {
+    dep_wait();
+    dep_release();
     const int TX = TXc ? TXc : TXr, TY = TYc ? TYc : TYr, TZ = TZc ? TZc : TZr;
     const int SXC = TX / 4 + 2, SX = 4 * SXC, SY = TY + 3, SZ = TZ + 3;
     const int SN = SX * SY * SZ;
@@ -845,6 +942,8 @@ k_ext_prepare(const int64_t* __restrict__ box_off, const double* __restrict__ ex
               float4* __restrict__ e32, int nchunk, double* __restrict__ partial,
               double* __restrict__ ext_sum, unsigned* __restrict__ ticket)
 {
+    dep_wait();
+    dep_release();
     __shared__ double sh[3][256];
     __shared__ bool last;
     const int box = blockIdx.y;
@@ -983,8 +1082,7 @@ cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, 
     static std::atomic<unsigned> attr{0};
     if (first_on_device(attr))       // no shared memory: all of the SM's L1 for the gathers
         cudaFuncSetAttribute(k_interp32_fused, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    k_interp32_fused<<<blocks_for(nb, 256), 256, 0, st>>>(nb, f, g, bg);
-    return cudaGetLastError();
+    return launch_dep(k_interp32_fused, dim3(blocks_for(nb, 256)), dim3(256), 0, st, nb, f, g, bg);
 }
 
 cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int32_t* box_of,
@@ -1004,45 +1102,47 @@ cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int
     // scan_tmp: [ntiles] tile offsets, then the ticket of the last-block scan (zero between
     // launches)
     const int ntiles = (int)((ncells + (1 << BIN_SCAN_LOG) - 1) >> BIN_SCAN_LOG);
-    k_bin_scan32<<<ntiles, BIN_SCAN_THREADS, 0, st>>>(cell_count, ncells, scan_tmp,
-                                                      cell_start + ncells,
-                                                      reinterpret_cast<unsigned*>(scan_tmp + ntiles));
+    e = launch_dep(k_bin_scan32, dim3(ntiles), dim3(BIN_SCAN_THREADS), 0, st, cell_count,
+                   ncells, scan_tmp, cell_start + ncells,
+                   reinterpret_cast<unsigned*>(scan_tmp + ntiles));
+    if (e != cudaSuccess) return e;
     const int64_t nthr = nb > ncells ? nb : ncells;
-    k_bin_place32<<<blocks_for(nthr, 256), 256, 0, st>>>(nb, ncells, cell_count, scan_tmp,
-                                                         cell_start, blob_cell, blob_rank, sorted,
-                                                         A, pid, loc);
-    return cudaGetLastError();
+    return launch_dep(k_bin_place32, dim3(blocks_for(nthr, 256)), dim3(256), 0, st, nb, ncells,
+                      (const int32_t*)cell_count, (const int32_t*)scan_tmp, cell_start,
+                      (const int32_t*)blob_cell, (const int32_t*)blob_rank, sorted, A, pid, loc);
 }
 
 cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t nb, int64_t max_box_blobs,
                             const int64_t* box_off, const int32_t* sorted, const float4* A,
-                            const float4* B, const float4* loc, const int4* adj,
-                            const int32_t* adj_start, const int32_t* box_of,
+                            const float4* B, const float4* loc, const Springs32& sp,
+                            const int32_t* box_of,
                             const float* box_par, const int32_t* cell_start,
                             const int32_t* blob_cell, const float4* ext, float4* Fs, float4* F,
                             float4* rec, const GridGeo& g, const BinGeo& bg)
 {
     if (max_box_blobs <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(Fs, 0, sizeof(float4) * nb, st);
+    cudaError_t e = launch_springs32(st, nb, A, B, sp, box_of, box_par, g, bg, Fs);
     if (e != cudaSuccess) return e;
-    k_springs32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, B, adj, adj_start, box_of, box_par, g,
-                                                    bg, reinterpret_cast<float*>(Fs));
     Force32Args a{box_off, sorted, A, B, loc, Fs, box_par, cell_start, blob_cell, ext, F, rec};
     dim3 grid(blocks_for(max_box_blobs, 256), (unsigned)Bx);
-    k_forces32<<<grid, 256, 0, st>>>(a, g, bg);
-    return cudaGetLastError();
+    return launch_dep(k_forces32, grid, dim3(256), 0, st, a, g, bg);
 }
 
 cudaError_t launch_springs32(cudaStream_t st, int64_t nb, const float4* A, const float4* B,
-                             const int4* adj, const int32_t* adj_start, const int32_t* box_of,
+                             const Springs32& sp, const int32_t* box_of,
                              const float* box_par, const GridGeo& g, const BinGeo& bg, float4* Fs)
 {
     if (nb <= 0) return cudaSuccess;
+    if (sp.tmpl) {
+        const int threads = (256 / sp.m) * sp.m;          // whole particles per block
+        return launch_dep(k_springs32_shared, dim3(blocks_for(nb, threads)), dim3(threads),
+                          sizeof(float) * 3 * threads * sp.slots, st, (int)nb, sp.m, sp.slots,
+                          A, B, sp.tmpl, sp.tstart, box_of, box_par, g, bg, Fs);
+    }
     cudaError_t e = cudaMemsetAsync(Fs, 0, sizeof(float4) * nb, st);
     if (e != cudaSuccess) return e;
-    k_springs32<<<blocks_for(nb, 256), 256, 0, st>>>(nb, A, B, adj, adj_start, box_of, box_par, g,
-                                                    bg, reinterpret_cast<float*>(Fs));
-    return cudaGetLastError();
+    return launch_dep(k_springs32, dim3(blocks_for(nb, 256)), dim3(256), 0, st, nb, A, B, sp.adj,
+                      sp.adj_start, box_of, box_par, g, bg, reinterpret_cast<float*>(Fs));
 }
 
 cudaError_t launch_pairs32(cudaStream_t st, int Bx, int64_t max_box_blobs,
@@ -1056,8 +1156,7 @@ cudaError_t launch_pairs32(cudaStream_t st, int Bx, int64_t max_box_blobs,
     if (max_box_blobs <= 0) return cudaSuccess;
     Force32Args a{box_off, sorted, A, B, loc, Fs, box_par, cell_start, blob_cell, ext, F, rec};
     dim3 grid(blocks_for(max_box_blobs, 256), (unsigned)Bx);
-    k_forces32<<<grid, 256, 0, st>>>(a, g, bg);
-    return cudaGetLastError();
+    return launch_dep(k_forces32, grid, dim3(256), 0, st, a, g, bg);
 }
 
 size_t spread32_smem(const int tile[3])
@@ -1083,9 +1182,8 @@ cudaError_t launch_spread32_t(cudaStream_t st, int Bx, const float4* rec, const 
         cudaFuncSetAttribute(k_spread32<TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
     const int ntiles = (g.n[0] / tile[0]) * (g.n[1] / tile[1]) * (g.n[2] / tile[2]);
-    k_spread32<TX, TY, TZ><<<dim3((unsigned)ntiles, (unsigned)Bx), 256, smem, st>>>(
-        rec, cell_start, g, bg, tile[0], tile[1], tile[2], f);
-    return cudaGetLastError();
+    return launch_dep(k_spread32<TX, TY, TZ>, dim3((unsigned)ntiles, (unsigned)Bx), dim3(256),
+                      smem, st, rec, cell_start, g, bg, tile[0], tile[1], tile[2], f);
 }
 
 cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
@@ -1112,10 +1210,8 @@ cudaError_t launch_ext_prepare(cudaStream_t st, int Bx, int64_t max_box_blobs,
 {
     const int nchunk = (int)((max_box_blobs + 255) / 256);
     if (nchunk <= 0) return cudaMemsetAsync(ext_sum, 0, sizeof(double) * 3 * Bx, st);
-    k_ext_prepare<<<dim3((unsigned)nchunk, (unsigned)Bx), 256, 0, st>>>(box_off, ext, ext32,
-                                                                        nchunk, partial, ext_sum,
-                                                                        ticket);
-    return cudaGetLastError();
+    return launch_dep(k_ext_prepare, dim3((unsigned)nchunk, (unsigned)Bx), dim3(256), 0, st,
+                      box_off, ext, ext32, nchunk, partial, ext_sum, ticket);
 }
 
 cudaError_t launch_vbar_step(cudaStream_t st, int Bx, const double* sum, double scale,

@@ -153,6 +153,8 @@ template <typename R, typename K, typename L>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 512, sizeof(R) == 4 ? 3 : 1)
 k_plane_fwd(FluidArgs<R> a, GridGeo g)
 {
+    dep_wait();
+    dep_release();
     using T = typename C2<K>::T;     // K: arithmetic type (FP32, or double-float for FP64)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
@@ -389,7 +391,9 @@ k_zsolve(FluidArgs<R> a, GridGeo g)
     const int sz = pad_shift(nz), nzp = padded_len(nz);
     T* Bf = reinterpret_cast<T*>(smem_raw);
     T* twz = Bf + 3 * nzp * Cp;
-    load_table(twz, reinterpret_cast<const T*>(a.twk[2]), nz);
+    load_table(twz, reinterpret_cast<const T*>(a.twk[2]), nz);   // set up once: no wait
+    dep_wait();
+    dep_release();
     const int ky0 = blockIdx.x * C, kx = blockIdx.y, box = blockIdx.z;
     const size_t zstride = (size_t)nxh * ny;
     const size_t cstride = (size_t)nz * zstride;
@@ -505,6 +509,8 @@ template <typename R, typename K, typename L>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 512, sizeof(R) == 4 ? 3 : 1)
 k_plane_inv(FluidArgs<R> a, GridGeo g)
 {
+    dep_wait();
+    dep_release();
     using T = typename C2<K>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
@@ -651,24 +657,29 @@ cudaError_t launch_fluid3(cudaStream_t st, int B, const GridGeo& g, const FluidA
     const size_t smem_z = ((size_t)3 * padded_len(nz) * (C + 4) + nz) * sizeof(T);
     auto mark = [&](int i) { if (marks) cudaEventRecord(marks[i], st); };
     mark(0);
+    cudaError_t e;
+    const dim3 gp(nz, 3 * B), gz(ny / C, nxh, B);
     if constexpr (sizeof(R) == 4) {
-        if (skew) k_plane_fwd<R, K, Skew128><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
-        else k_plane_fwd<R, K, PadPlane><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+        if (skew) e = launch_dep(k_plane_fwd<R, K, Skew128>, gp, dim3(PT), smem_plane, st, a, g);
+        else e = launch_dep(k_plane_fwd<R, K, PadPlane>, gp, dim3(PT), smem_plane, st, a, g);
     } else {
-        k_plane_fwd<R, K, PadPlane><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+        e = launch_dep(k_plane_fwd<R, K, PadPlane>, gp, dim3(PT), smem_plane, st, a, g);
     }
+    if (e != cudaSuccess) return e;
     mark(1);
     mark(2);
-    if (C == CZ) k_zsolve<R, K, CZ><<<dim3(ny / C, nxh, B), 3 * CZ * 8, smem_z, st>>>(a, g);
-    else k_zsolve<R, K, 4><<<dim3(ny / 4, nxh, B), 3 * 4 * 8, smem_z, st>>>(a, g);
+    if (C == CZ) e = launch_dep(k_zsolve<R, K, CZ>, gz, dim3(3 * CZ * 8), smem_z, st, a, g);
+    else e = launch_dep(k_zsolve<R, K, 4>, gz, dim3(3 * 4 * 8), smem_z, st, a, g);
+    if (e != cudaSuccess) return e;
     mark(3);
     mark(4);
     if constexpr (sizeof(R) == 4) {
-        if (skew) k_plane_inv<R, K, Skew128><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
-        else k_plane_inv<R, K, PadPlane><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+        if (skew) e = launch_dep(k_plane_inv<R, K, Skew128>, gp, dim3(PT), smem_plane, st, a, g);
+        else e = launch_dep(k_plane_inv<R, K, PadPlane>, gp, dim3(PT), smem_plane, st, a, g);
     } else {
-        k_plane_inv<R, K, PadPlane><<<dim3(nz, 3 * B), PT, smem_plane, st>>>(a, g);
+        e = launch_dep(k_plane_inv<R, K, PadPlane>, gp, dim3(PT), smem_plane, st, a, g);
     }
+    if (e != cudaSuccess) return e;
     mark(5);
     return cudaGetLastError();
 }

@@ -17,6 +17,15 @@
 
 using namespace mbk;
 
+bool mbk::pdl_enabled()
+{
+    static const bool on = [] {
+        const char* e = std::getenv("MB_PDL");
+        return !(e && std::atoi(e) == 0);
+    }();
+    return on;
+}
+
 namespace {
 
 constexpr int SYM_LEN = 256;   // per-dimension symbol table length (n <= 128 today)
@@ -157,6 +166,9 @@ struct mb_ctx {
         loc, scan_tmp, partial, staging_in, staging_out, mean_scratch;
     // FP32-grid mode blob state: positions as bin cell + float-float offset (q^n and midpoint)
     DBuf sA, sB, hA[2], hB[2], F32, rec32, ext32, ext_sum, ext_ticket, adj32, adj32_start, Fs32, u32;
+    // the bond pattern common to all particles (tmpl_m blobs each), when there is one
+    DBuf tmpl32, tstart32;
+    int tmpl_m = 0, tmpl_slots = 0;
     // split midpoints: hA/hB[hcur] hold the predictor of the next step when pred_ready (the
     // previous step's fused corrector wrote them); hlast is the buffer of the last step's
     // midpoints (where its forces were evaluated)
@@ -175,7 +187,9 @@ struct mb_ctx {
     cudaStream_t cap_stream = nullptr;
     // second stream for the spring forces, which overlap the binning (fork/join events)
     cudaStream_t side = nullptr;
-    cudaEvent_t fork[4] = {nullptr, nullptr, nullptr, nullptr};
+    // fork[0] step start, [1] springs done, [2] stress drawn, [3] external forces converted,
+    // [4] blobs binned, [5] bin counts cleared for the next step's predictor
+    cudaEvent_t fork[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // a second side stream: the conversion of a single-step call's external forces
     cudaStream_t side2 = nullptr;
     // device-readable external forces of the current single-step call, converted inside the
@@ -317,10 +331,31 @@ __global__ void k_wrap(int64_t n, double* q, double L0, double L1, double L2)
     q[i] = y;
 }
 
+// MB_SPRINGS=list keeps the per-blob bond lists even where all particles share one pattern.
+bool springs_per_blob()
+{
+    static const bool on = [] {
+        const char* e = std::getenv("MB_SPRINGS");
+        return e && std::string(e) == "list";
+    }();
+    return on;
+}
+
 // The box parameters [B][3] rounded to float, stored after the doubles.
 const float* box_par32(const mb_ctx* ctx)
 {
     return reinterpret_cast<const float*>(static_cast<const double*>(ctx->box_par.p) + 3 * ctx->B);
+}
+
+// The bonds of the FP32 spring kernels: the per-blob lists, and the common pattern if any.
+Springs32 springs32(const mb_ctx* ctx)
+{
+    const bool t = ctx->tmpl_m > 0 && !springs_per_blob();
+    return Springs32{static_cast<const int4*>(ctx->adj32.p),
+                     static_cast<const int32_t*>(ctx->adj32_start.p),
+                     t ? static_cast<const int4*>(ctx->tmpl32.p) : nullptr,
+                     t ? static_cast<const int32_t*>(ctx->tstart32.p) : nullptr, ctx->tmpl_m,
+                     ctx->tmpl_slots};
 }
 
 // Choose the bin cell side: a power of two of mesh cells, at least 2 and at least r_cut.
@@ -488,7 +523,6 @@ mb_status rebuild(mb_ctx* ctx)
         // icosahedron's centre) is evaluated once, by its other end, which also adds the
         // opposite force to the heavy end; every other bond is evaluated at both ends.  So no
         // thread of a warp iterates over more than SPRING_LOCAL_MAX + its owned bonds.
-        constexpr int SPRING_LOCAL_MAX = 6;
         auto heavy = [&](int64_t i) { return adj_start[i + 1] - adj_start[i] > SPRING_LOCAL_MAX; };
         std::vector<int32_t> s32(nb + 1, 0);
         std::vector<int32_t> a32;
@@ -509,6 +543,69 @@ mb_status rebuild(mb_ctx* ctx)
                 a32.insert(a32.end(), w, w + 4);
             }
             s32[i + 1] = (int32_t)(a32.size() / 4);
+        }
+        // one bond pattern shared by every particle: m blobs each, blob l of particle p
+        // numbered p m + l, the same partners (as offsets inside the particle) and the same
+        // rest lengths, compared exactly; the pattern is then stored once (Springs32::tmpl)
+        std::vector<int32_t> t_start, t32;
+        ctx->tmpl_m = 0;
+        if (np > 0 && nb % np == 0 && nb / np <= 64) {
+            const int64_t m = nb / np;
+            bool same = true;
+            for (int64_t i = 0; i < nb && same; ++i) same = pid[i] == (int32_t)(i / m);
+            for (int64_t i = 0; i < nb && same; ++i) {
+                const int64_t l = i % m, base = i - l;
+                const int32_t cnt = adj_start[i + 1] - adj_start[i];
+                same = cnt == adj_start[l + 1] - adj_start[l];
+                for (int32_t k = 0; k < cnt && same; ++k) {
+                    const int64_t e = adj_start[i] + k, e0 = adj_start[l] + k;
+                    const int64_t off = adj_j[e] - base;
+                    same = off >= 0 && off < m && off == adj_j[e0] &&
+                           std::memcmp(&adj_rest[e], &adj_rest[e0], sizeof(double)) == 0;
+                }
+            }
+            if (same) {
+                // every bond is evaluated once, by one end, which leaves the opposite force in
+                // one of its slots for the other end to collect: by the light end of a bond to a
+                // heavy blob, otherwise by the end with fewer evaluations so far (the lower
+                // index on a tie), so that no blob evaluates many more than the mean
+                std::vector<std::vector<std::array<int32_t, 4>>> ev(m), co(m);
+                std::vector<int> nslot(m, 0);
+                for (int64_t l = 0; l < m; ++l) {
+                    for (int32_t e = adj_start[l]; e < adj_start[l + 1]; ++e) {
+                        const int64_t j = adj_j[e];
+                        if (j < l) continue;                  // met from its lower end
+                        const bool hl = heavy(l), hj = heavy(j);
+                        const int64_t x = hl && !hj ? j
+                                          : (hj && !hl ? l : (nslot[l] <= nslot[j] ? l : j));
+                        const int64_t y = x == l ? j : l;
+                        const int slot = nslot[x]++;
+                        co[y].push_back({(int32_t)(x - y), slot, 0, 0});
+                        const double r0 = adj_rest[e], r0sq = r0 * r0;
+                        const float h = (float)r0sq, lo = (float)(r0sq - (double)h), rf = (float)r0;
+                        std::array<int32_t, 4> w;
+                        w[0] = (int32_t)(((uint32_t)(y - x) & 0xffffu) | ((uint32_t)(slot + 1) << 16));
+                        std::memcpy(&w[1], &rf, 4);
+                        std::memcpy(&w[2], &h, 4);
+                        std::memcpy(&w[3], &lo, 4);
+                        ev[x].push_back(w);
+                    }
+                }
+                t_start.assign(2 * m + 1, 0);
+                for (int64_t l = 0; l < m; ++l) {
+                    for (const auto& w : ev[l]) t32.insert(t32.end(), w.begin(), w.end());
+                    t_start[2 * l + 1] = (int32_t)(t32.size() / 4);
+                    for (const auto& w : co[l]) t32.insert(t32.end(), w.begin(), w.end());
+                    t_start[2 * l + 2] = (int32_t)(t32.size() / 4);
+                }
+                ctx->tmpl_m = (int)m;
+                ctx->tmpl_slots = *std::max_element(nslot.begin(), nslot.end());
+                MB_TRY(ensure(ctx->tmpl32, sizeof(int32_t) * std::max<size_t>(t32.size(), 4), E,
+                              "bond pattern"));
+                MB_TRY(ensure(ctx->tstart32, sizeof(int32_t) * (2 * m + 1), E, "bond pattern"));
+                MB_TRY(up(ctx->tmpl32, t32.data(), sizeof(int32_t) * t32.size()));
+                MB_TRY(up(ctx->tstart32, t_start.data(), sizeof(int32_t) * (2 * m + 1)));
+            }
         }
         MB_TRY(ensure(ctx->adj32, sizeof(int32_t) * std::max<size_t>(a32.size(), 4), E, "adj32"));
         MB_TRY(ensure(ctx->adj32_start, sizeof(int32_t) * (nb + 1), E, "adj32_start"));
@@ -935,9 +1032,7 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
             ctx->launches += 1;
         }
         MB_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork[0], 0));
-        MB_CUDA(launch_springs32(ctx->side, ctx->nb, hA, hB,
-                                 static_cast<const int4*>(ctx->adj32.p),
-                                 static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
+        MB_CUDA(launch_springs32(ctx->side, ctx->nb, hA, hB, springs32(ctx), box_of,
                                  box_par32(ctx), g, ctx->bg,
                                  static_cast<float4*>(ctx->Fs32.p)));
         MB_CUDA(cudaEventRecord(ctx->fork[1], ctx->side));
@@ -966,6 +1061,17 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
         ctx->launches += 2;
         ctx->sorted_valid = true;
     }
+    // the fused corrector pass counts the next step's midpoints into cell_count, which the
+    // placement has now read: with the side stream it is cleared there, off the step's chain of
+    // kernels (whose launches may then overlap one another's first and last blocks)
+    const bool clear_side = overlap && ctx->fuse_interp;
+    if (clear_side) {
+        MB_CUDA(cudaEventRecord(ctx->fork[4], st));
+        MB_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork[4], 0));
+        MB_CUDA(cudaMemsetAsync(ctx->cell_count.p, 0, sizeof(int32_t) * B * ctx->bg.ncell,
+                                ctx->side));
+        MB_CUDA(cudaEventRecord(ctx->fork[5], ctx->side));
+    }
     mark(ST_FORCES);
     if (blobs) {
         const int64_t* box_off = static_cast<const int64_t*>(ctx->box_off.p);
@@ -985,9 +1091,8 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
         } else {
             MB_CUDA(launch_forces32(st, B, ctx->nb, ctx->max_box_blobs, box_off,
                                     static_cast<const int32_t*>(ctx->sorted.p), hA, hB,
-                                    static_cast<const float4*>(ctx->loc.p),
-                                    static_cast<const int4*>(ctx->adj32.p),
-                                    static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
+                                    static_cast<const float4*>(ctx->loc.p), springs32(ctx),
+                                    box_of,
                                     box_par32(ctx),
                                     static_cast<const int32_t*>(ctx->cell_start.p),
                                     static_cast<const int32_t*>(ctx->blob_cell.p), ext4,
@@ -1051,7 +1156,8 @@ mb_status do_step_fast(mb_ctx* ctx, bool ext, const double* body)
         if (ctx->fuse_interp) {
             // corrector of this step and predictor of the next (into the other midpoint buffer,
             // with the bin counts the next step sorts by)
-            MB_CUDA(cudaMemsetAsync(ctx->cell_count.p, 0, sizeof(int32_t) * B * ctx->bg.ncell, st));
+            if (clear_side) MB_CUDA(cudaStreamWaitEvent(st, ctx->fork[5], 0));
+            else MB_CUDA(cudaMemsetAsync(ctx->cell_count.p, 0, sizeof(int32_t) * B * ctx->bg.ncell, st));
             MB_CUDA(launch_interp32_fused(st, ctx->nb, hA, vsum ? static_cast<const float*>(ctx->vsum.p) : vcur,
                                           vsum ? nullptr : vnext, vnext, box_of, g, ctx->bg, dt, sA,
                                           sB, sA, sB,
@@ -1121,9 +1227,8 @@ mb_status do_step_stokes_fast(mb_ctx* ctx, bool ext, const double* body)
             MB_CUDA(launch_forces32(st, B, ctx->nb, ctx->max_box_blobs,
                                     static_cast<const int64_t*>(ctx->box_off.p),
                                     static_cast<const int32_t*>(ctx->sorted.p), A, Bp,
-                                    static_cast<const float4*>(ctx->loc.p),
-                                    static_cast<const int4*>(ctx->adj32.p),
-                                    static_cast<const int32_t*>(ctx->adj32_start.p), box_of,
+                                    static_cast<const float4*>(ctx->loc.p), springs32(ctx),
+                                    box_of,
                                     box_par32(ctx),
                                     static_cast<const int32_t*>(ctx->cell_start.p),
                                     static_cast<const int32_t*>(ctx->blob_cell.p),
@@ -1473,7 +1578,7 @@ void release(mb_ctx* ctx)
                    &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
                    &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out, &ctx->sA,
                    &ctx->sB, &ctx->hA[0], &ctx->hA[1], &ctx->hB[0], &ctx->hB[1], &ctx->F32, &ctx->rec32, &ctx->ext32,
-                   &ctx->ext_sum, &ctx->ext_ticket, &ctx->adj32, &ctx->adj32_start, &ctx->Fs32, &ctx->u32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
+                   &ctx->ext_sum, &ctx->ext_ticket, &ctx->adj32, &ctx->adj32_start, &ctx->tmpl32, &ctx->tstart32, &ctx->Fs32, &ctx->u32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
                    &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk, &ctx->a_gU,
                    &ctx->a_vn, &ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvp, &ctx->a_gvn,
                    &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero, &ctx->W, &ctx->step_index,
@@ -1671,10 +1776,12 @@ mb_status mb_create_grid(const mb_grid_desc* desc, void* cuda_stream, mb_ctx** o
     // the side stream and fork/join events of the step (created here, never inside a capture)
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->side2, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->fork[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->fork[1], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->fork[2], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->fork[3], cudaEventDisableTiming) != cudaSuccess) {
+        [&] {
+            for (cudaEvent_t& e : ctx->fork)
+                if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                    return true;
+            return false;
+        }()) {
         cudaGetLastError();
         ctx->err = "stream or event creation failed";
         return fail(MB_ECUDA);

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/mb.h"
@@ -195,6 +196,40 @@ template <typename R> inline FluidArgs<R> with_derived(const FluidArgs<R>& in, c
 template <typename K> __device__ __forceinline__ K kparam(double d, float) { return K(d); }
 template <> __device__ __forceinline__ float kparam<float>(double, float f) { return f; }
 
+// ------------------------------------------------------------------------------------------
+// Programmatic dependent launch for the chain of kernels of one step.  A kernel launched with
+// launch_dep may be scheduled while the kernel before it on the stream is still draining its
+// last blocks; it must call dep_wait() before its first access to global memory (and before
+// any early return), which returns once every prerequisite grid has completed and its writes
+// are visible.  dep_release() lets the next kernel of the chain be scheduled once every block
+// of this one has started: its blocks then occupy only the slots this kernel's finished blocks
+// free, and wait there.  Both are no-ops for a kernel launched the ordinary way, so the same
+// kernels serve direct launches.  MB_PDL=0 launches the chain the ordinary way.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_release()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+bool pdl_enabled();
+
+template <typename... P, typename... A>
+inline cudaError_t launch_dep(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, A&&... args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 template <typename R>
 cudaError_t launch_fluid(cudaStream_t st, int B, const GridGeo& g, const FluidArgs<R>& a,
                          cudaEvent_t* marks = nullptr);
@@ -249,17 +284,37 @@ cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int
                          int32_t* blob_cell, int32_t* blob_rank, int32_t* sorted,
                          int32_t* scan_tmp, const int32_t* pid, float4* loc,
                          bool counted = false);
+// The bonds of the FP32 spring kernels.  A bond between a blob of at most SPRING_LOCAL_MAX
+// bonds and a heavier one (an icosahedron's vertex and centre) is evaluated by the light end
+// only, which also supplies the heavy end's opposite force.
+//   adj / adj_start: per-blob lists {j (sign bit: also add the opposite force to j), r0,
+//   r0^2 as float hi + lo}; bonds between two light or two heavy blobs are evaluated at both
+//   ends.
+//   tmpl / tstart: when every particle has the same m blobs under one bond pattern (blob l of
+//   particle p is blob p m + l; the same partners, as offsets inside the particle, and the same
+//   rest lengths in every particle), the pattern once, each bond evaluated once: per local
+//   blob l an evaluation list and a collection list (k_springs32_shared), and `slots`
+//   evaluations per blob at most.
+constexpr int SPRING_LOCAL_MAX = 6;
+struct Springs32 {
+    const int4* adj;
+    const int32_t* adj_start;
+    const int4* tmpl;          // null: no common pattern
+    const int32_t* tstart;     // [2 m + 1]
+    int m;
+    int slots;
+};
 cudaError_t launch_forces32(cudaStream_t st, int Bx, int64_t nb, int64_t max_box_blobs,
                             const int64_t* box_off, const int32_t* sorted, const float4* A,
-                            const float4* B, const float4* loc, const int4* adj,
-                            const int32_t* adj_start, const int32_t* box_of,
+                            const float4* B, const float4* loc, const Springs32& sp,
+                            const int32_t* box_of,
                             const float* box_par, const int32_t* cell_start,
                             const int32_t* blob_cell, const float4* ext, float4* Fs, float4* F,
                             float4* rec, const GridGeo& g, const BinGeo& bg);
 // The two halves of launch_forces32, for running the springs on another stream: the spring
-// forces (Fs, zeroed first), then the pair forces, sums and sorted records.
+// forces (Fs), then the pair forces, sums and sorted records.
 cudaError_t launch_springs32(cudaStream_t st, int64_t nb, const float4* A, const float4* B,
-                             const int4* adj, const int32_t* adj_start, const int32_t* box_of,
+                             const Springs32& sp, const int32_t* box_of,
                              const float* box_par, const GridGeo& g, const BinGeo& bg, float4* Fs);
 cudaError_t launch_pairs32(cudaStream_t st, int Bx, int64_t max_box_blobs,
                            const int64_t* box_off, const int32_t* sorted, const float4* A,

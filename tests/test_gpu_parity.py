@@ -4,6 +4,8 @@ Tolerances are relative L2 errors: 1e-10 for the FP64 grid path and 1e-5 for the
 (FP64 blobs) path.  Sizes span several spreading tiles and ragged blob counts; the full 128^3
 dense workload is checked operator by operator and through properties of one step.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -203,6 +205,41 @@ def test_forces_parity_after_step(prec):
     assert np.max(np.abs(F - F_ref)) < (1e-12 if prec == 1 else TOL[0]) * np.max(np.abs(F_ref))
     # repulsion was active
     assert np.max(np.abs(oracle.pair_forces(g, qh, s.pid, s.k_rep, s.r_cut))) > 0
+
+
+def test_fp32_springs_with_and_without_a_common_bond_pattern():
+    """FP32 grid: the icosahedra in particle order share one bond pattern (stored once); the same
+    suspension with its blobs shuffled has none (per-blob bond lists).  Both give the oracle's
+    forces and trajectory."""
+    spec, s = _dense_small(seed=7)
+    d = mb.GridDesc(spec.nx, spec.ny, spec.nz, h=spec.h, rho=spec.rho, eta=spec.eta,
+                    dt=spec.dt, precision=0, mean_mode=spec.mean_mode)
+    rng = np.random.default_rng(13)
+    s.pos = np.mod(s.pos + rng.normal(scale=0.08, size=s.pos.shape), s.L)
+    ext = rng.normal(scale=1e-3, size=s.pos.shape)
+    perm = rng.permutation(s.n_blobs)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(s.n_blobs)
+    shuffled = dataclasses.replace(s, pos=s.pos[perm].copy(), pid=s.pid[perm].copy(),
+                                   bonds=inv[s.bonds].astype(s.bonds.dtype))
+    g = _oracle_grid(d)
+    nsteps = 3
+    for susp, e, back in ((s, ext, np.arange(s.n_blobs)), (shuffled, ext[perm], inv)):
+        with mb.Multiblob(d) as sim:
+            sim.set_particles(0, susp.pos, susp.pid, susp.bonds, susp.rest, susp.k_spring,
+                              susp.k_rep, susp.r_cut)
+            sim.step(1, ext_blob_force=e)
+            F, qh = (to_np(x)[back] for x in sim.last_forces())
+            sim.step(nsteps - 1, ext_blob_force=e, body_force=s.body)
+            q = to_np(sim.blob_positions())[back]
+        F_ref = ext + oracle.bond_forces(g, qh, s.bonds, s.rest, s.k_spring) \
+            + oracle.pair_forces(g, qh, s.pid, s.k_rep, s.r_cut)
+        assert np.max(np.abs(F - F_ref)) < TOL[0] * np.max(np.abs(F_ref))
+        q_ref1, v_ref1 = oracle.step(g, 1, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
+                                     s.k_rep, s.r_cut, ext=ext)
+        q_ref, _ = oracle.step(g, nsteps - 1, q_ref1, v_ref1, s.pid, s.bonds, s.rest,
+                               s.k_spring, s.k_rep, s.r_cut, ext=ext, body=s.body)
+        assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[0])
 
 
 @pytest.mark.parametrize("prec", [1, 0])
