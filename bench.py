@@ -73,8 +73,10 @@ def stage_model(n, nb, rsz, ncell, thermal=False):
         # the predictor of step n+1 runs inside step n's corrector pass (same gathered nodes)
         "interp_predict": ("hbm", 0),
         "bin": ("hbm", vec + 3 * 4 * nb + 4 * 4 * ncell), # q_half; cell, rank, slot; counts/scan
-        # q_half, slot, pid, 42/13 bonds x 2 ends x (index + rest); write F and (q, F) record
-        "forces": ("hbm", nb * (24 + 4 + 4 + 2 * 42 / 13 * 12 + 24 + 48)),
+        # q_half, slot, pid; write F and the (q, F) record.  The icosahedra share one bond
+        # pattern, which the springs read once, not per blob (per-blob lists would add
+        # 42/13 bonds x 2 ends x (index + rest) = 78 B a blob)
+        "forces": ("hbm", nb * (24 + 4 + 4 + 24 + 48)),
         "force_sum": ("hbm", 0),
         "spread": ("hbm", 48 * nb + grid),               # sorted (q, F) records; write f
         # thermal / convective stress (kT > 0 or advection only): write 9 stress grids, read
