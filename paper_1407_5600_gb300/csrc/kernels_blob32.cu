@@ -799,10 +799,13 @@ k_forces32(Force32Args a, GridGeo g, BinGeo bg)
 // windows can reach: x over [T0 - 4, T0 + TX + 4) in 16-byte chunks, y and z over
 // [T0 - 1, T0 + T + 1] (a blob in the tile has its window start in [T0 - 1, T0 + T - 1]).  The
 // copy holds 32-bit fixed-point sums (integer shared-memory atomics), scaled per tile by a power
-// of two from a bound on its largest node value (blob count x largest force component x the
-// kernel's largest weight (2/3)^3).  The block then adds the copy to f (zeroed beforehand) with
-// vector atomics, skipping all-zero chunks; nodes shared with neighbouring tiles receive every
-// tile's part.  TXc = 0 takes the tile from the arguments (small grids).
+// of two from a bound on its largest node value: a node receives only blobs within 1.5 h of it
+// along each axis, which lie in at most three consecutive bin cells per axis (cells are at
+// least 2 h wide), so the bound is a bound on the sum of the blobs' largest force components
+// over any 3 x 3 x 3 block of the tile's cells, times the kernel's largest weight (2/3)^3.  The
+// block then adds the copy to f (zeroed beforehand) with vector atomics, skipping all-zero
+// chunks; nodes shared with neighbouring tiles receive every tile's part.  TXc = 0 takes the
+// tile from the arguments (small grids).
 template <int TXc, int TYc, int TZc>
 __global__ void __launch_bounds__(256)
 k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_start, GridGeo g,
@@ -847,9 +850,12 @@ k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_star
         if (r == 31) carry0 = x;
         if (r == 63) rp[64] = x;               // the second warp's total (carry added below)
     }
+    const int ncell = ncx * rows;
+    float* cf = reinterpret_cast<float*>(acc + 3 * SN);          // [ncz][ncy][ncx] force sums
     {
         int4* a4 = reinterpret_cast<int4*>(acc);
         for (int i = threadIdx.x; i < 3 * SN / 4; i += blockDim.x) a4[i] = make_int4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < ncell; i += blockDim.x) cf[i] = 0.0f;
     }
     __syncthreads();
     if (threadIdx.x >= 32 && threadIdx.x < 65) rp[threadIdx.x] += carry0;
@@ -864,18 +870,39 @@ k_spread32(const float4* __restrict__ rec, const int32_t* __restrict__ cell_star
             if (r + step < rows && rp[r + step] <= t) r += step;
         return (int64_t)rb[r] + (t - rp[r]);
     };
-    // the tile's fixed-point scale: 2^(30 - e) with 2^e >= n (2/3)^3 max|F| / h^3
+    // the tile's fixed-point scale: 2^(30 - e) with 2^e above the node bound: per cell the sum
+    // of its blobs' largest force components; a 3 x 3 x 3 block of cells sums at most nine times
+    // the largest sum over three cells along x; times (2/3)^3 / h^3 (and 2^-16 for the float
+    // sums' rounding)
     const float inv_h3 = G.inv_h * G.inv_h * G.inv_h;
-    float fm = 0.f;
+    const int cx0 = T0[0] / G.bs, cy0 = T0[1] / G.bs, cz0 = T0[2] / G.bs;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const float4 fv = rec[2 * slot_of(t) + 1];
-        fm = fmaxf(fm, fmaxf(fabsf(fv.x), fmaxf(fabsf(fv.y), fabsf(fv.z))));
+        const int64_t slot = slot_of(t);
+        const int pk = __float_as_int(rec[2 * slot].w);
+        const float4 fv = rec[2 * slot + 1];
+        const int c = ((cell_unpack(pk, 2) - cz0) * ncy + (cell_unpack(pk, 1) - cy0)) * ncx +
+                      (cell_unpack(pk, 0) - cx0);
+        atomicAdd(cf + c, fmaxf(fabsf(fv.x), fmaxf(fabsf(fv.y), fabsf(fv.z))));
     }
+    __syncthreads();
+    // sums over three neighbouring cells along x by shuffles (one warp per row of cells, lane =
+    // cell, ncx <= 32); a 3 x 3 x 3 block sums nine of them
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    float fm = 0.f;
+    for (int r = warp; r < rows; r += nwarps) {
+        const float v = lane < ncx ? cf[r * ncx + lane] : 0.0f;
+        float left = __shfl_up_sync(0xffffffffu, v, 1);
+        float right = __shfl_down_sync(0xffffffffu, v, 1);
+        if (lane == 0) left = 0.0f;
+        if (lane == 31) right = 0.0f;
+        fm = fmaxf(fm, left + v + right);
+    }
+    fm *= 9.0f;
     for (int o = 16; o > 0; o >>= 1) fm = fmaxf(fm, __shfl_xor_sync(0xffffffffu, fm, o));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = fm;
     __syncthreads();
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) fm = fmaxf(fm, wmax[w]);
-    const float bound = (float)total * (8.0f / 27.0f) * fm * inv_h3;
+    const float bound = fm * (1.0f + 1.0f / 65536.0f) * (8.0f / 27.0f) * inv_h3;
     int e = 0;
     frexpf(bound, &e);                                           // bound < 2^e
     const float scale = bound > 0.f ? ldexpf(1.0f, 30 - e) : 1.0f;
@@ -1159,24 +1186,26 @@ cudaError_t launch_pairs32(cudaStream_t st, int Bx, int64_t max_box_blobs,
     return launch_dep(k_forces32, grid, dim3(256), 0, st, a, g, bg);
 }
 
-size_t spread32_smem(const int tile[3])
+// The shared copy (3 components, 16-byte chunks along x) and one force sum per bin cell.
+size_t spread32_smem(const int tile[3], int bs)
 {
-    return (size_t)3 * (tile[0] + 8) * (tile[1] + 3) * (tile[2] + 3) * sizeof(float);
+    return (size_t)3 * (tile[0] + 8) * (tile[1] + 3) * (tile[2] + 3) * sizeof(float) +
+           (size_t)(tile[0] / bs) * (tile[1] / bs) * (tile[2] / bs) * sizeof(float);
 }
 
 bool spread32_tile_ok(const int tile[3], const GridGeo& g, const BinGeo& bg)
 {
-    bool ok = spread32_smem(tile) <= 200 * 1024;
+    bool ok = spread32_smem(tile, bg.bs) <= 200 * 1024;
     for (int d = 0; d < 3; ++d)
         ok = ok && tile[d] >= 4 && tile[d] <= g.n[d] && g.n[d] % tile[d] == 0 && tile[d] % bg.bs == 0;
-    return ok && (tile[1] / bg.bs) * (tile[2] / bg.bs) <= 64;
+    return ok && (tile[1] / bg.bs) * (tile[2] / bg.bs) <= 64 && tile[0] / bg.bs <= 32;
 }
 
 template <int TX, int TY, int TZ>
 cudaError_t launch_spread32_t(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
                               const GridGeo& g, const BinGeo& bg, const int tile[3], float* f)
 {
-    const size_t smem = spread32_smem(tile);
+    const size_t smem = spread32_smem(tile, bg.bs);
     static std::atomic<unsigned> attr{0};
     if (first_on_device(attr))
         cudaFuncSetAttribute(k_spread32<TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,

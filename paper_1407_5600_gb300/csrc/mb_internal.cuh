@@ -324,7 +324,8 @@ cudaError_t launch_pairs32(cudaStream_t st, int Bx, int64_t max_box_blobs,
                            float4* F, float4* rec, const GridGeo& g, const BinGeo& bg);
 // f = S F from the binned records (zeroes f first unless the caller knows it is zero).  The tile (nodes per block) must satisfy
 // spread32_tile_ok: at least 4 and whole bin cells per side, dividing the grid, at most 64 rows
-// of cells, shared copy within 200 KiB; other tiles return cudaErrorInvalidValue.
+// of cells and 32 cells along x, shared copy within 200 KiB; other tiles return
+// cudaErrorInvalidValue.
 bool spread32_tile_ok(const int tile[3], const GridGeo& g, const BinGeo& bg);
 cudaError_t launch_spread32(cudaStream_t st, int Bx, const float4* rec, const int32_t* cell_start,
                             const GridGeo& g, const BinGeo& bg, const int tile[3], float* f,

@@ -242,6 +242,26 @@ def test_fp32_springs_with_and_without_a_common_bond_pattern():
         assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[0])
 
 
+def test_fp32_step_with_clustered_blobs():
+    """FP32 grid: 40 icosahedra overlapping inside a 3h cube (520 blobs in a few bin cells, no
+    repulsion) with random external forces.  The spreading's fixed-point scale must stay a
+    bound on every node of a tile that holds them all; the step matches the oracle."""
+    rng = np.random.default_rng(23)
+    n = 16
+    L = np.array([float(n)] * 3)
+    centres = 6.5 + rng.uniform(0.0, 3.0, size=(40, 3))
+    s = wl.build_particles(centres, 1.0, rng, L)
+    ext = rng.normal(scale=1e-2, size=s.pos.shape)
+    d = mb.GridDesc(n, n, n, precision=0, dt=0.05, mean_mode=0)
+    nsteps = 2
+    q, v, u, U, W = _run_gpu(d, [s], nsteps, ext_list=[ext])
+    g = _oracle_grid(d)
+    q_ref, v_ref = oracle.step(g, nsteps, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring,
+                               ext=ext)
+    assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[0])
+    assert rel_l2(v[0], v_ref) < TOL[0]
+
+
 @pytest.mark.parametrize("prec", [1, 0])
 def test_batched_boxes_match_independent_runs(prec):
     B = 4
