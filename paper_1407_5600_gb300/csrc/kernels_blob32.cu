@@ -103,6 +103,21 @@ __device__ __forceinline__ Geo32 geo32(const GridGeo& g, const BinGeo& bg)
     return r;
 }
 
+// Items split evenly over the warps of a grid that the GPU holds at once (persistent_grid):
+// warp w takes the contiguous items [w p, (w + 1) p), p = ceil(n / warps), its lanes 32 apart.
+// Every SM then holds the same share of the work to the end, where a grid of one item per
+// thread ends in a partial second wave that leaves SMs idle; neighbouring items (blobs in cell
+// order) stay on one SM, so their shared nodes stay in its L1.
+template <typename Fn>
+__device__ __forceinline__ void for_warp_ranges(int64_t n, Fn&& fn)
+{
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t per = (n + nwarps - 1) / nwarps;
+    const int64_t lo = w * per, hi = lo + per < n ? lo + per : n;
+    for (int64_t t = lo + (threadIdx.x & 31); t < hi; t += 32) fn(t);
+}
+
 // ------------------------------------------------------------------------------------------
 // Conversions between FP64 positions and the split form.
 
@@ -372,9 +387,8 @@ k_interp32_fused(int64_t nb, FusedArgs f, GridGeo g, BinGeo bg)
 {
     dep_wait();
     dep_release();
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= nb) return;
-    fused_blob(t, f, geo32(g, bg));
+    const Geo32 G = geo32(g, bg);
+    for_warp_ranges(nb, [&](int64_t t) { fused_blob(t, f, G); });
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1051,6 +1065,27 @@ __global__ void k_forces_to_fp64(int64_t nb, const float4* __restrict__ F, doubl
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Blocks of `threads` for a for_warp_ranges kernel over n items: as many as the GPU holds at
+// once (SMs x resident blocks, found once per device), fewer when n is small.
+template <typename K>
+unsigned persistent_grid(K kernel, int threads, int64_t n)
+{
+    static int cached[32][2] = {};                    // per device: {SMs, blocks per SM}
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int* c = cached[dev & 31];
+    if (c[0] == 0) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
+        c[1] = per > 0 ? per : 1;
+        c[0] = sms > 0 ? sms : 1;
+    }
+    const int64_t full = (int64_t)c[0] * c[1];
+    const int64_t need = blocks_for(n, threads);
+    return (unsigned)(need < full ? (need > 0 ? need : 1) : full);
+}
+
 }  // namespace
 
 // ==========================================================================================
@@ -1109,7 +1144,8 @@ cudaError_t launch_interp32_fused(cudaStream_t st, int64_t nb, const float4* A, 
     static std::atomic<unsigned> attr{0};
     if (first_on_device(attr))       // no shared memory: all of the SM's L1 for the gathers
         cudaFuncSetAttribute(k_interp32_fused, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    return launch_dep(k_interp32_fused, dim3(blocks_for(nb, 256)), dim3(256), 0, st, nb, f, g, bg);
+    return launch_dep(k_interp32_fused, dim3(persistent_grid(k_interp32_fused, 256, nb)),
+                      dim3(256), 0, st, nb, f, g, bg);
 }
 
 cudaError_t launch_bin32(cudaStream_t st, int64_t nb, const float4* A, const int32_t* box_of,

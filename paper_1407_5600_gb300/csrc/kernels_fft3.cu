@@ -509,8 +509,10 @@ template <typename R, typename K, typename L>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 256 : 512, sizeof(R) == 4 ? 3 : 1)
 k_plane_inv(FluidArgs<R> a, GridGeo g)
 {
+    // no early release: the next kernel (the interpolation's persistent grid, which splits the
+    // blobs evenly over its warps) then starts all its blocks together, not first on the SMs
+    // this pass leaves early
     dep_wait();
-    dep_release();
     using T = typename C2<K>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2], nxh = nx / 2 + 1;
