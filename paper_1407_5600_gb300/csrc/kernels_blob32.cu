@@ -10,6 +10,8 @@
 //
 // Layout per blob: float4 A = {hi.x, hi.y, hi.z, cell bits}, float4 B = {lo.x, lo.y, lo.z, 0},
 // with the cell packed as cx | cy << 10 | cz << 20.
+#include <mutex>
+
 #include "mb_internal.cuh"
 #include "peskin.cuh"
 
@@ -1066,22 +1068,38 @@ __global__ void k_forces_to_fp64(int64_t nb, const float4* __restrict__ F, doubl
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // Blocks of `threads` for a for_warp_ranges kernel over n items: as many as the GPU holds at
-// once (SMs x resident blocks, found once per device), fewer when n is small.
+// once (SMs x resident blocks of this kernel, found once per kernel and device), fewer when n
+// is small.
 template <typename K>
 unsigned persistent_grid(K kernel, int threads, int64_t n)
 {
-    static int cached[32][2] = {};                    // per device: {SMs, blocks per SM}
+    struct Entry {
+        const void* k;
+        int dev, threads, slots;
+    };
+    static Entry cache[64] = {};
+    static std::mutex mu;
     int dev = 0;
     cudaGetDevice(&dev);
-    int* c = cached[dev & 31];
-    if (c[0] == 0) {
-        int sms = 0, per = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
-        c[1] = per > 0 ? per : 1;
-        c[0] = sms > 0 ? sms : 1;
+    int slots = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        int i = 0;
+        for (; i < 64 && cache[i].k; ++i)
+            if (cache[i].k == (const void*)kernel && cache[i].dev == dev &&
+                cache[i].threads == threads) {
+                slots = cache[i].slots;
+                break;
+            }
+        if (slots == 0) {
+            int sms = 0, per = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
+            slots = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+            if (i < 64) cache[i] = Entry{(const void*)kernel, dev, threads, slots};
+        }
     }
-    const int64_t full = (int64_t)c[0] * c[1];
+    const int64_t full = slots;
     const int64_t need = blocks_for(n, threads);
     return (unsigned)(need < full ? (need > 0 ? need : 1) : full);
 }
