@@ -399,6 +399,66 @@ __device__ __forceinline__ void pair_term(const double qb[3], const double* __re
     }
 }
 
+// FP64 springs of a bond pattern shared by all particles (launch_springs64).  A block holds
+// whole particles (one thread per blob, blob order).  Each thread evaluates the bonds its
+// evaluation list names (spring_term<true> on a zero sum: the force on its own blob) into its
+// shared-memory slots; after a barrier it sums ext and, in its adjacency order, its own slots
+// and the negated slots of the bonds its partners evaluated.  Negation is exact and the
+// evaluation of a bond from the other end gives the negated bits, so every sum equals the
+// per-blob adjacency sum of k_forces bit for bit.
+__global__ void __launch_bounds__(256)
+k_springs64(int nb, int m, int S, const double* __restrict__ q, const double* __restrict__ ext,
+            const int4* __restrict__ tmpl, const int32_t* __restrict__ tstart,
+            const int32_t* __restrict__ box_of, const double* __restrict__ box_par, GridGeo g,
+            double* __restrict__ Fout)
+{
+    extern __shared__ double slot_d[];                   // [blockDim][S][3]
+    const int tid = threadIdx.x;
+    const int b = blockIdx.x * blockDim.x + tid;
+    const bool live = b < nb;
+    const int l = tid % m;
+    if (live) {
+        const double qb[3] = {q[3 * b], q[3 * b + 1], q[3 * b + 2]};
+        const double halfL[3] = {0.5 * g.L[0], 0.5 * g.L[1], 0.5 * g.L[2]};
+        const double k_spring = box_par[3 * (box_of ? box_of[b] : 0)];
+        const int e0 = __ldg(tstart + 2 * l), e1 = __ldg(tstart + 2 * l + 1);
+        for (int e = e0; e < e1; ++e) {
+            const int4 ad = __ldg(tmpl + e);
+            const int j = b + (int)(short)(ad.x & 0xffff);
+            const int slot = (ad.x >> 16) - 1;
+            const double r0 = __hiloint2double(ad.z, ad.y);
+            double f[3] = {0.0, 0.0, 0.0};
+            spring_term<true>(qb, q + 3 * j, r0, k_spring, g.L, halfL, f);
+            for (int d = 0; d < 3; ++d) slot_d[(tid * S + slot) * 3 + d] = f[d];
+        }
+    }
+    __syncthreads();
+    if (!live) return;
+    double F[3] = {0.0, 0.0, 0.0};
+    if (ext)
+        for (int d = 0; d < 3; ++d) F[d] = ext[3 * b + d];
+    const int c0 = __ldg(tstart + 2 * l + 1), c1 = __ldg(tstart + 2 * l + 2);
+    for (int e = c0; e < c1; ++e) {
+        const int4 ad = __ldg(tmpl + e);
+        const double* v = slot_d + ((tid + ad.x) * S + ad.y) * 3;
+        for (int d = 0; d < 3; ++d) F[d] = __dadd_rn(F[d], ad.z > 0 ? v[d] : -v[d]);
+    }
+    for (int d = 0; d < 3; ++d) Fout[3 * b + d] = F[d];
+}
+
+cudaError_t launch_springs64(cudaStream_t st, int64_t nb, int m, int slots, const double* q,
+                             const double* ext, const int4* tmpl, const int32_t* tstart,
+                             const int32_t* box_of, const double* box_par, const GridGeo& g,
+                             double* Fout)
+{
+    if (nb <= 0) return cudaSuccess;
+    const int threads = (256 / m) * m;                   // whole particles per block
+    const size_t smem = sizeof(double) * 3 * (size_t)threads * (slots > 0 ? slots : 1);
+    k_springs64<<<(unsigned)((nb + threads - 1) / threads), threads, smem, st>>>(
+        (int)nb, m, slots, q, ext, tmpl, tstart, box_of, box_par, g, Fout);
+    return cudaGetLastError();
+}
+
 template <bool PRECISE>
 __global__ void __launch_bounds__(256)
 k_forces(ForceArgs a, GridGeo g, BinGeo bg)
@@ -413,16 +473,21 @@ k_forces(ForceArgs a, GridGeo g, BinGeo bg)
         const int b = a.sorted[slot];
         const double qb[3] = {a.q[3 * b], a.q[3 * b + 1], a.q[3 * b + 2]};
         const double halfL[3] = {0.5 * g.L[0], 0.5 * g.L[1], 0.5 * g.L[2]};
-        if (a.ext) {
-            F[0] = a.ext[3 * b];
-            F[1] = a.ext[3 * b + 1];
-            F[2] = a.ext[3 * b + 2];
-        }
-        const double k_spring = a.box_par[3 * box];
         const double k_rep = a.box_par[3 * box + 1];
         const double r_cut = a.box_par[3 * box + 2];
-        for (int e = a.adj_start[b]; e < a.adj_start[b + 1]; ++e)
-            spring_term<PRECISE>(qb, a.q + 3 * a.adj_j[e], a.adj_rest[e], k_spring, g.L, halfL, F);
+        if (a.Fpre) {
+            for (int d = 0; d < 3; ++d) F[d] = a.Fpre[3 * b + d];
+        } else {
+            if (a.ext) {
+                F[0] = a.ext[3 * b];
+                F[1] = a.ext[3 * b + 1];
+                F[2] = a.ext[3 * b + 2];
+            }
+            const double k_spring = a.box_par[3 * box];
+            for (int e = a.adj_start[b]; e < a.adj_start[b + 1]; ++e)
+                spring_term<PRECISE>(qb, a.q + 3 * a.adj_j[e], a.adj_rest[e], k_spring, g.L,
+                                     halfL, F);
+        }
         if (k_rep != 0.0 && r_cut > 0.0) {
             double Fp[3] = {0.0, 0.0, 0.0};
             const float4 lb = a.loc[slot];

@@ -169,6 +169,7 @@ struct mb_ctx {
     // the bond pattern common to all particles (tmpl_m blobs each), when there is one
     DBuf tmpl32, tstart32;
     int tmpl_m = 0, tmpl_slots = 0;
+    DBuf Fpre64;        // FP64 grids: external + spring forces of the pattern kernel [nb][3]
     // split midpoints: hA/hB[hcur] hold the predictor of the next step when pred_ready (the
     // previous step's fused corrector wrote them); hlast is the buffer of the last step's
     // midpoints (where its forces were evaluated)
@@ -506,6 +507,104 @@ mb_status rebuild(mb_ctx* ctx)
     ctx->box_par32_h.assign(par.begin(), par.end());
     MB_CUDA(cudaMemcpyAsync(static_cast<double*>(ctx->box_par.p) + 3 * B, ctx->box_par32_h.data(),
                             sizeof(float) * 3 * B, cudaMemcpyHostToDevice, st));
+    // One bond pattern shared by every particle: m blobs each, blob l of particle p numbered
+    // p m + l, the same partners (as offsets inside the particle) and the same rest lengths,
+    // compared exactly.  The pattern is then stored once and every bond evaluated once, by the
+    // end that owner[] names, into slot[] of that end: the light end of a bond to a blob of
+    // more than SPRING_LOCAL_MAX bonds, otherwise the end with fewer evaluations so far (the
+    // lower index on a tie), so that no blob evaluates many more than the mean.  owner[] and
+    // slot[] are per adjacency entry of particle 0 (both entries of a bond alike).
+    ctx->tmpl_m = 0;
+    ctx->tmpl_slots = 0;
+    std::vector<int32_t> owner, slot;
+    int64_t pm = 0;
+    if (np > 0 && nb % np == 0 && nb / np <= 64) {
+        const int64_t m = nb / np;
+        auto heavy = [&](int64_t i) { return adj_start[i + 1] - adj_start[i] > SPRING_LOCAL_MAX; };
+        bool same = true;
+        for (int64_t i = 0; i < nb && same; ++i) same = pid[i] == (int32_t)(i / m);
+        for (int64_t i = 0; i < nb && same; ++i) {
+            const int64_t l = i % m, base = i - l;
+            const int32_t cnt = adj_start[i + 1] - adj_start[i];
+            same = cnt == adj_start[l + 1] - adj_start[l];
+            for (int32_t k = 0; k < cnt && same; ++k) {
+                const int64_t e = adj_start[i] + k, e0 = adj_start[l] + k;
+                const int64_t off = adj_j[e] - base;
+                same = off >= 0 && off < m && off == adj_j[e0] &&
+                       std::memcmp(&adj_rest[e], &adj_rest[e0], sizeof(double)) == 0;
+            }
+        }
+        if (same) {
+            owner.assign(adj_start[m], -1);
+            slot.assign(adj_start[m], -1);
+            std::vector<int> nslot(m, 0);
+            for (int64_t l = 0; l < m; ++l) {
+                for (int32_t e = adj_start[l]; e < adj_start[l + 1]; ++e) {
+                    const int64_t j = adj_j[e];
+                    if (j < l) continue;                  // met from its lower end
+                    // the matching entry at j: the same occurrence of l among j's partners
+                    int occ = 0;
+                    for (int32_t f = adj_start[l]; f < e; ++f) occ += adj_j[f] == j;
+                    int32_t er = -1;
+                    for (int32_t f = adj_start[j]; f < adj_start[j + 1] && er < 0; ++f)
+                        if (adj_j[f] == l && occ-- == 0) er = f;
+                    const bool hl = heavy(l), hj = heavy(j);
+                    const int64_t x = hl && !hj ? j
+                                      : (hj && !hl ? l : (nslot[l] <= nslot[j] ? l : j));
+                    const int sl = nslot[x]++;
+                    owner[e] = (int32_t)x;
+                    slot[e] = sl;
+                    if (er >= 0) {
+                        owner[er] = (int32_t)x;
+                        slot[er] = sl;
+                    }
+                }
+            }
+            pm = m;
+            ctx->tmpl_m = (int)m;
+            ctx->tmpl_slots = *std::max_element(nslot.begin(), nslot.end());
+        }
+    }
+    // the pattern's tables: FP32 grids (k_springs32_shared) per local blob its evaluations
+    // {offset | (slot + 1) << 16, r0, r0^2 hi, lo} and the slots it collects {offset, slot};
+    // FP64 grids (k_springs64) its evaluations {offset | (slot + 1) << 16, r0 low, r0 high} and
+    // its whole adjacency in order {offset of the evaluating blob, slot, sign}
+    if (pm > 0) {
+        std::vector<int32_t> t_start(2 * pm + 1, 0), t;
+        for (int64_t l = 0; l < pm; ++l) {
+            for (int32_t e = adj_start[l]; e < adj_start[l + 1]; ++e) {
+                if (owner[e] != l) continue;
+                const int64_t j = adj_j[e];
+                const double r0 = adj_rest[e];
+                int32_t w[4];
+                w[0] = (int32_t)(((uint32_t)(j - l) & 0xffffu) | ((uint32_t)(slot[e] + 1) << 16));
+                if (ctx->rsz == 4) {
+                    const double r0sq = r0 * r0;
+                    const float h = (float)r0sq, lo = (float)(r0sq - (double)h), rf = (float)r0;
+                    std::memcpy(&w[1], &rf, 4);
+                    std::memcpy(&w[2], &h, 4);
+                    std::memcpy(&w[3], &lo, 4);
+                } else {
+                    std::memcpy(&w[1], &r0, 8);            // low word, then high word
+                    w[3] = 0;
+                }
+                t.insert(t.end(), w, w + 4);
+            }
+            t_start[2 * l + 1] = (int32_t)(t.size() / 4);
+            for (int32_t e = adj_start[l]; e < adj_start[l + 1]; ++e) {
+                if (ctx->rsz == 4 && owner[e] == l) continue;
+                const int32_t w[4] = {(int32_t)(owner[e] - l), slot[e], owner[e] == l ? 1 : -1, 0};
+                t.insert(t.end(), w, w + 4);
+            }
+            t_start[2 * l + 2] = (int32_t)(t.size() / 4);
+        }
+        MB_TRY(ensure(ctx->tmpl32, sizeof(int32_t) * std::max<size_t>(t.size(), 4), E,
+                      "bond pattern"));
+        MB_TRY(ensure(ctx->tstart32, sizeof(int32_t) * (2 * pm + 1), E, "bond pattern"));
+        MB_TRY(up(ctx->tmpl32, t.data(), sizeof(int32_t) * t.size()));
+        MB_TRY(up(ctx->tstart32, t_start.data(), sizeof(int32_t) * (2 * pm + 1)));
+        if (ctx->rsz == 8) MB_TRY(ensure(ctx->Fpre64, sizeof(double) * 3 * nb, E, "spring forces"));
+    }
     if (ctx->rsz == 4) {
         MB_TRY(ensure(ctx->sA, sizeof(float4) * nb, E, "split q"));
         MB_TRY(ensure(ctx->sB, sizeof(float4) * nb, E, "split q"));
@@ -543,69 +642,6 @@ mb_status rebuild(mb_ctx* ctx)
                 a32.insert(a32.end(), w, w + 4);
             }
             s32[i + 1] = (int32_t)(a32.size() / 4);
-        }
-        // one bond pattern shared by every particle: m blobs each, blob l of particle p
-        // numbered p m + l, the same partners (as offsets inside the particle) and the same
-        // rest lengths, compared exactly; the pattern is then stored once (Springs32::tmpl)
-        std::vector<int32_t> t_start, t32;
-        ctx->tmpl_m = 0;
-        if (np > 0 && nb % np == 0 && nb / np <= 64) {
-            const int64_t m = nb / np;
-            bool same = true;
-            for (int64_t i = 0; i < nb && same; ++i) same = pid[i] == (int32_t)(i / m);
-            for (int64_t i = 0; i < nb && same; ++i) {
-                const int64_t l = i % m, base = i - l;
-                const int32_t cnt = adj_start[i + 1] - adj_start[i];
-                same = cnt == adj_start[l + 1] - adj_start[l];
-                for (int32_t k = 0; k < cnt && same; ++k) {
-                    const int64_t e = adj_start[i] + k, e0 = adj_start[l] + k;
-                    const int64_t off = adj_j[e] - base;
-                    same = off >= 0 && off < m && off == adj_j[e0] &&
-                           std::memcmp(&adj_rest[e], &adj_rest[e0], sizeof(double)) == 0;
-                }
-            }
-            if (same) {
-                // every bond is evaluated once, by one end, which leaves the opposite force in
-                // one of its slots for the other end to collect: by the light end of a bond to a
-                // heavy blob, otherwise by the end with fewer evaluations so far (the lower
-                // index on a tie), so that no blob evaluates many more than the mean
-                std::vector<std::vector<std::array<int32_t, 4>>> ev(m), co(m);
-                std::vector<int> nslot(m, 0);
-                for (int64_t l = 0; l < m; ++l) {
-                    for (int32_t e = adj_start[l]; e < adj_start[l + 1]; ++e) {
-                        const int64_t j = adj_j[e];
-                        if (j < l) continue;                  // met from its lower end
-                        const bool hl = heavy(l), hj = heavy(j);
-                        const int64_t x = hl && !hj ? j
-                                          : (hj && !hl ? l : (nslot[l] <= nslot[j] ? l : j));
-                        const int64_t y = x == l ? j : l;
-                        const int slot = nslot[x]++;
-                        co[y].push_back({(int32_t)(x - y), slot, 0, 0});
-                        const double r0 = adj_rest[e], r0sq = r0 * r0;
-                        const float h = (float)r0sq, lo = (float)(r0sq - (double)h), rf = (float)r0;
-                        std::array<int32_t, 4> w;
-                        w[0] = (int32_t)(((uint32_t)(y - x) & 0xffffu) | ((uint32_t)(slot + 1) << 16));
-                        std::memcpy(&w[1], &rf, 4);
-                        std::memcpy(&w[2], &h, 4);
-                        std::memcpy(&w[3], &lo, 4);
-                        ev[x].push_back(w);
-                    }
-                }
-                t_start.assign(2 * m + 1, 0);
-                for (int64_t l = 0; l < m; ++l) {
-                    for (const auto& w : ev[l]) t32.insert(t32.end(), w.begin(), w.end());
-                    t_start[2 * l + 1] = (int32_t)(t32.size() / 4);
-                    for (const auto& w : co[l]) t32.insert(t32.end(), w.begin(), w.end());
-                    t_start[2 * l + 2] = (int32_t)(t32.size() / 4);
-                }
-                ctx->tmpl_m = (int)m;
-                ctx->tmpl_slots = *std::max_element(nslot.begin(), nslot.end());
-                MB_TRY(ensure(ctx->tmpl32, sizeof(int32_t) * std::max<size_t>(t32.size(), 4), E,
-                              "bond pattern"));
-                MB_TRY(ensure(ctx->tstart32, sizeof(int32_t) * (2 * m + 1), E, "bond pattern"));
-                MB_TRY(up(ctx->tmpl32, t32.data(), sizeof(int32_t) * t32.size()));
-                MB_TRY(up(ctx->tstart32, t_start.data(), sizeof(int32_t) * (2 * m + 1)));
-            }
         }
         MB_TRY(ensure(ctx->adj32, sizeof(int32_t) * std::max<size_t>(a32.size(), 4), E, "adj32"));
         MB_TRY(ensure(ctx->adj32_start, sizeof(int32_t) * (nb + 1), E, "adj32_start"));
@@ -749,6 +785,25 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
                                  ctx->d.dt, nullptr, qh));
         ctx->launches += 1;
     }
+    // FP64 grid, one bond pattern for all particles: the springs once per bond, summed with
+    // the external forces in the per-blob order (the same bits); without stage timing on the
+    // side stream, beside the binning
+    const bool pattern = blobs && ctx->rsz == 8 && ctx->tmpl_m > 0 && !springs_per_blob();
+    auto springs64 = [&](cudaStream_t s2) {
+        return launch_springs64(s2, ctx->nb, ctx->tmpl_m, ctx->tmpl_slots, qh, ext,
+                                static_cast<const int4*>(ctx->tmpl32.p),
+                                static_cast<const int32_t*>(ctx->tstart32.p), box_of,
+                                static_cast<const double*>(ctx->box_par.p), g,
+                                static_cast<double*>(ctx->Fpre64.p));
+    };
+    const bool side64 = pattern && !ctx->timing;
+    if (side64) {
+        MB_CUDA(cudaEventRecord(ctx->fork[0], st));
+        MB_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork[0], 0));
+        MB_CUDA(springs64(ctx->side));
+        MB_CUDA(cudaEventRecord(ctx->fork[1], ctx->side));
+        ctx->launches += 1;
+    }
     mark(ST_BIN);
     if (blobs) {
         MB_CUDA(launch_bin(st, ctx->nb, qh, box_of, B, ctx->bg,
@@ -764,7 +819,14 @@ mb_status do_step(mb_ctx* ctx, const double* ext, const double* body)
     }
     mark(ST_FORCES);
     if (blobs) {
+        if (side64) {
+            MB_CUDA(cudaStreamWaitEvent(st, ctx->fork[1], 0));
+        } else if (pattern) {
+            MB_CUDA(springs64(st));
+            ctx->launches += 1;
+        }
         ForceArgs fa{};
+        fa.Fpre = pattern ? static_cast<const double*>(ctx->Fpre64.p) : nullptr;
         fa.box_off = static_cast<const int64_t*>(ctx->box_off.p);
         fa.sorted = static_cast<const int32_t*>(ctx->sorted.p);
         fa.q = qh;
@@ -1578,7 +1640,7 @@ void release(mb_ctx* ctx)
                    &ctx->s_blob_cell, &ctx->s_blob_rank, &ctx->s_sorted, &ctx->s_scan,
                    &ctx->s_u, &ctx->s_g0, &ctx->s_g1, &ctx->s_g2, &ctx->s_out, &ctx->sA,
                    &ctx->sB, &ctx->hA[0], &ctx->hA[1], &ctx->hB[0], &ctx->hB[1], &ctx->F32, &ctx->rec32, &ctx->ext32,
-                   &ctx->ext_sum, &ctx->ext_ticket, &ctx->adj32, &ctx->adj32_start, &ctx->tmpl32, &ctx->tstart32, &ctx->Fs32, &ctx->u32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
+                   &ctx->ext_sum, &ctx->ext_ticket, &ctx->adj32, &ctx->adj32_start, &ctx->tmpl32, &ctx->tstart32, &ctx->Fpre64, &ctx->Fs32, &ctx->u32, &ctx->a_qn, &ctx->a_u, &ctx->a_qh,
                    &ctx->a_gq, &ctx->a_guc, &ctx->a_gqh, &ctx->a_gF, &ctx->a_gu, &ctx->a_gk, &ctx->a_gU,
                    &ctx->a_vn, &ctx->a_vp, &ctx->a_w, &ctx->a_gw, &ctx->a_gvp, &ctx->a_gvn,
                    &ctx->a_gf, &ctx->a_tmp, &ctx->a_zero, &ctx->W, &ctx->step_index,

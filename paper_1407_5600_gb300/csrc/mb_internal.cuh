@@ -99,10 +99,25 @@ struct ForceArgs {
     double* rec;
     double* partial;           // [B][nchunk][3]
     int nchunk;
+    // [nb][3] external plus spring forces already summed (launch_springs64); null: the kernel
+    // sums them from ext and the adjacency lists
+    const double* Fpre;
 };
 // precise: FP64 in the plain operation order without contraction (FP64 grid mode).
 cudaError_t launch_forces(cudaStream_t st, int B, int64_t max_box_blobs, const ForceArgs& a,
                           const GridGeo& g, const BinGeo& bg, bool precise);
+
+// FP64 spring forces when every particle shares one bond pattern (m blobs, blob l of particle
+// p is blob p m + l): each bond evaluated once, in the precise FP64 order, by the end the
+// pattern names, and each blob's sum Fout = ext + the bonds in its adjacency order, so the
+// result has the bits of the per-blob evaluation of launch_forces (the two ends' evaluations
+// are exact negatives).  tmpl: per local blob an evaluation list {offset | (slot + 1) << 16,
+// r0 low word, r0 high word, 0} and a sum list in adjacency order {offset of the evaluating
+// blob, slot, sign, 0}; tstart[2l], tstart[2l + 1], tstart[2l + 2] bound them.
+cudaError_t launch_springs64(cudaStream_t st, int64_t nb, int m, int slots, const double* q,
+                             const double* ext, const int4* tmpl, const int32_t* tstart,
+                             const int32_t* box_of, const double* box_par, const GridGeo& g,
+                             double* Fout);
 
 // Sum partial forces per box (fixed order) and update the FP64 mean velocity:
 // vbar += dt * sumF / (rho L^3) when mean_mode == 0, vbar = 0 otherwise; optionally copies

@@ -242,6 +242,40 @@ def test_fp32_springs_with_and_without_a_common_bond_pattern():
         assert_positions(q, q_ref, s.pos, g.L, nsteps, TOL[0])
 
 
+def test_fp64_springs_pattern_matches_per_blob_sums_bitwise():
+    """FP64 grid: with a bond pattern shared by all particles the springs are evaluated once per
+    bond and summed in each blob's adjacency order, which gives the bits of the per-blob
+    evaluation (the shuffled copy of the suspension has no pattern and takes that path).
+    No repulsion, so the forces are the external forces plus the springs alone."""
+    spec, s = _dense_small(seed=8)
+    d = mb.GridDesc(spec.nx, spec.ny, spec.nz, h=spec.h, rho=spec.rho, eta=spec.eta,
+                    dt=spec.dt, precision=1, mean_mode=spec.mean_mode)
+    rng = np.random.default_rng(29)
+    s.pos = np.mod(s.pos + rng.normal(scale=0.08, size=s.pos.shape), s.L)
+    ext = rng.normal(scale=1e-3, size=s.pos.shape)
+    perm = rng.permutation(s.n_blobs)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(s.n_blobs)
+    shuffled = dataclasses.replace(s, pos=s.pos[perm].copy(), pid=s.pid[perm].copy(),
+                                   bonds=inv[s.bonds].astype(s.bonds.dtype))
+    out = []
+    for susp, e, back in ((s, ext, np.arange(s.n_blobs)), (shuffled, ext[perm], inv)):
+        with mb.Multiblob(d) as sim:
+            sim.set_particles(0, susp.pos, susp.pid, susp.bonds, susp.rest, susp.k_spring)
+            sim.step(1, ext_blob_force=e)
+            F, qh = (to_np(x)[back] for x in sim.last_forces())
+            sim.step(2, ext_blob_force=e)
+            q = to_np(sim.blob_positions())[back]
+        out.append((F, qh, q))
+    assert np.array_equal(out[0][1], out[1][1])           # same midpoints
+    assert np.array_equal(out[0][0], out[1][0])           # same forces, bit for bit
+    g = _oracle_grid(d)
+    F_ref = ext + oracle.bond_forces(g, out[0][1], s.bonds, s.rest, s.k_spring)
+    assert np.max(np.abs(out[0][0] - F_ref)) < 1e-12 * np.max(np.abs(F_ref))
+    q_ref, _ = oracle.step(g, 3, s.pos, g.zeros(), s.pid, s.bonds, s.rest, s.k_spring, ext=ext)
+    assert_positions(out[0][2], q_ref, s.pos, g.L, 3, TOL[1])
+
+
 def test_fp32_step_with_clustered_blobs():
     """FP32 grid: 40 icosahedra overlapping inside a 3h cube (520 blobs in a few bin cells, no
     repulsion) with random external forces.  The spreading's fixed-point scale must stay a
