@@ -105,19 +105,27 @@ __device__ __forceinline__ Geo32 geo32(const GridGeo& g, const BinGeo& bg)
     return r;
 }
 
-// Items split evenly over the warps of a grid that the GPU holds at once (persistent_grid):
-// warp w takes the contiguous items [w p, (w + 1) p), p = ceil(n / warps), its lanes 32 apart.
-// Every SM then holds the same share of the work to the end, where a grid of one item per
-// thread ends in a partial second wave that leaves SMs idle; neighbouring items (blobs in cell
-// order) stay on one SM, so their shared nodes stay in its L1.
+// Items split evenly over the warps of a grid that the GPU holds at once (persistent_grid), in
+// rounds: R = ceil(n / (32 W)) rounds for W warps, c = ceil(n / (R W)) <= 32 items per warp and
+// round, round k giving warp w the items [(k W + w) c, (k W + w + 1) c) (lanes c..31 idle).
+// Every warp then has the same work to the end, where a grid of one item per thread ends in a
+// partial last wave that leaves SMs idle; and each round covers one contiguous window of W c
+// items, so that, with the items in cell order, the GPU works through the grid region by region
+// (its L2 holds the nodes of a window when the grids do not fit) and neighbouring items share
+// an SM's L1.
 template <typename Fn>
-__device__ __forceinline__ void for_warp_ranges(int64_t n, Fn&& fn)
+__device__ __forceinline__ void for_warp_rounds(int64_t n, Fn&& fn)
 {
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t per = (n + nwarps - 1) / nwarps;
-    const int64_t lo = w * per, hi = lo + per < n ? lo + per : n;
-    for (int64_t t = lo + (threadIdx.x & 31); t < hi; t += 32) fn(t);
+    const int lane = threadIdx.x & 31;
+    const int64_t R = (n + 32 * W - 1) / (32 * W);
+    if (R == 0) return;
+    const int64_t c = (n + R * W - 1) / (R * W);
+    for (int64_t k = 0; k < R; ++k) {
+        const int64_t t = (k * W + w) * c + lane;
+        if (lane < c && t < n) fn(t);
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -390,7 +398,7 @@ k_interp32_fused(int64_t nb, FusedArgs f, GridGeo g, BinGeo bg)
     dep_wait();
     dep_release();
     const Geo32 G = geo32(g, bg);
-    for_warp_ranges(nb, [&](int64_t t) { fused_blob(t, f, G); });
+    for_warp_rounds(nb, [&](int64_t t) { fused_blob(t, f, G); });
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1067,7 +1075,7 @@ __global__ void k_forces_to_fp64(int64_t nb, const float4* __restrict__ F, doubl
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Blocks of `threads` for a for_warp_ranges kernel over n items: as many as the GPU holds at
+// Blocks of `threads` for a for_warp_rounds kernel over n items: as many as the GPU holds at
 // once (SMs x resident blocks of this kernel, found once per kernel and device), fewer when n
 // is small.
 template <typename K>
