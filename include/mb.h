@@ -272,11 +272,12 @@ mb_status mb_velocity_adjoint(mb_ctx* ctx, const double* pos, const void* grid_v
 mb_status mb_particle_velocity_adjoint(mb_ctx* ctx, const double* pos, const void* grid_v,
                                        const double* grad_U, double* grad_pos, void* grad_v);
 
-/* Spreading tile (nodes per block along x, y, z) in use and the time one spreading launch
- * took with it when it was chosen (0 if not timed).  In FP32-grid mode the first step after
- * mb_set_particles times a set of candidate tile shapes on the actual blob distribution and
- * keeps the fastest (synchronising the stream once; set MB_NO_AUTOTUNE=1 to keep the default);
- * choices are cached per geometry and blob count for the life of the process. */
+/* Spreading tile (nodes per block along x, y, z) in use and the fastest time of one spreading
+ * launch with it when it was chosen (0 if not timed).  In FP32-grid mode the first step after
+ * mb_set_particles times a set of candidate tile shapes on the actual blob distribution, in
+ * several rounds, and keeps the one with the fastest launch (synchronising the stream after
+ * each timed launch; set MB_NO_AUTOTUNE=1 to keep the default); choices are cached per
+ * geometry and blob count for the life of the process. */
 mb_status mb_get_tuning(const mb_ctx* ctx, int* spread_tile, float* spread_ms);
 
 /* Number of blobs and particles of all boxes together. */

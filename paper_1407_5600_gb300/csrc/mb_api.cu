@@ -1386,13 +1386,15 @@ mb_status autotune_spread(mb_ctx* ctx)
     cudaEvent_t e0, e1;
     MB_CUDA(cudaEventCreate(&e0));
     MB_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_t[3] = {ctx->tile[0], ctx->tile[1], ctx->tile[2]};
-    for (const auto& c : cand) {
-        const int t[3] = {c[0], c[1], c[2]};
-        if (!spread32_tile_ok(t, ctx->g, ctx->bg)) continue;
-        float ms = 0.f;
-        for (int rep = 0; rep < 3; ++rep) {
+    // rounds over the candidates (the first warms up), each candidate's fastest launch kept:
+    // the candidates differ by a few percent, about the spread of single launches
+    constexpr int NCAND = sizeof(cand) / sizeof(cand[0]), ROUNDS = 7;
+    float fastest[NCAND];
+    for (int i = 0; i < NCAND; ++i) fastest[i] = 1e30f;
+    for (int round = 0; round < ROUNDS; ++round) {
+        for (int i = 0; i < NCAND; ++i) {
+            const int t[3] = {cand[i][0], cand[i][1], cand[i][2]};
+            if (!spread32_tile_ok(t, ctx->g, ctx->bg)) continue;
             MB_CUDA(cudaEventRecord(e0, ctx->st));
             MB_CUDA(launch_spread32(ctx->st, ctx->B, static_cast<const float4*>(ctx->rec32.p),
                                     static_cast<const int32_t*>(ctx->cell_start.p), ctx->g,
@@ -1401,17 +1403,20 @@ mb_status autotune_spread(mb_ctx* ctx)
             MB_CUDA(cudaEventSynchronize(e1));
             float one = 0.f;
             MB_CUDA(cudaEventElapsedTime(&one, e0, e1));
-            if (rep > 0) ms += one;                   // first launch warms up
-        }
-        if (ms < best) {
-            best = ms;
-            for (int d = 0; d < 3; ++d) best_t[d] = t[d];
+            if (round > 0) fastest[i] = std::min(fastest[i], one);
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    float best = 1e30f;
+    int best_t[3] = {ctx->tile[0], ctx->tile[1], ctx->tile[2]};
+    for (int i = 0; i < NCAND; ++i)
+        if (fastest[i] < best) {
+            best = fastest[i];
+            for (int d = 0; d < 3; ++d) best_t[d] = cand[i][d];
+        }
     for (int d = 0; d < 3; ++d) ctx->tile[d] = best_t[d];
-    ctx->tile_ms = best / 2;
+    ctx->tile_ms = best;
     // the timing runs left a spread grid in f: clear it for the next step
     MB_CUDA(cudaMemsetAsync(ctx->f.p, 0, sizeof(float) * 3 * (size_t)ctx->B * ctx->g.N, ctx->st));
     ctx->f_zero = true;
